@@ -1,0 +1,150 @@
+"""Seeded synthetic inputs for the multi-particle Smoluchowski right-hand side.
+
+This module only draws numbers and lays them out; it holds none of the
+method's arithmetic, so both the GPU library's tests and the CPU oracle's tests
+can take their inputs from it. Seeds use ``numpy.random.default_rng`` (PCG64)
+with the draws in the order written below.
+
+Layouts follow the library convention: size k is stored at index k-1; CP
+factors per order d are [d][R_d][N] (mode, rank, size) and orders d = 2..D are
+concatenated; TT cores per order d are, for lambda = 1..d, [R_{l-1}][R_l][N].
+
+Workloads (the paper's model from Sec. 1; shapes of its Sec. 3 experiment and
+of the derived configurations):
+  * ``constant_monodisperse`` - D=3, N=64, C^(2)=C^(3)=1 (CP rank 1, all-ones
+    factors), n = e_1, Heun dt=0.01, 100 steps.
+  * ``brownian_cp`` - D=3, N=4096, C^(d) = (sum_m i_m^{1/3})(sum_m i_m^{-1/3})
+    as an exact CP of rank d^2, n_k = exp(-k)/sum exp(-k), dt=1e-3.
+  * ``random_power_cp`` - D=4, N=65536, R=16 per order, U^(m)_r(i) =
+    u_{m,r} i^{a_{m,r}} with u ~ U[0.5,1.5], a ~ U[-0.3,0.3], n_k = exp(-k/10)
+    normalised to M0 = 1, dt=1e-4 (the throughput workload).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 1905
+
+
+@dataclass
+class System:
+    """One Smoluchowski system: orders 2..D, N size classes, a kernel per order."""
+    D: int
+    N: int
+    fmt: str                      # "cp" or "tt"
+    ranks: list                   # CP: [R_2..R_D]; TT: per order d its d+1 ranks, flattened
+    factors: np.ndarray           # float64, layout above
+    n0: np.ndarray                # float64 [N]
+    dt: float = 1e-3
+    steps: int = 1
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+
+def sizes(N: int) -> np.ndarray:
+    """Sizes 1..N as float64 (exact integers)."""
+    return np.arange(1, N + 1, dtype=np.float64)
+
+
+def cp_layout(D: int, N: int, ranks) -> list:
+    """Offsets (in doubles) of each order's block [d][R_d][N]; last entry = total."""
+    offs = [0]
+    for d in range(2, D + 1):
+        offs.append(offs[-1] + d * int(ranks[d - 2]) * N)
+    return offs
+
+
+def cp_from_vectors(D: int, N: int, per_order: dict) -> tuple[list, np.ndarray]:
+    """per_order[d] is an array [d][R_d][N]; returns (ranks, flat factors)."""
+    ranks = [int(per_order[d].shape[1]) for d in range(2, D + 1)]
+    flat = np.concatenate([np.asarray(per_order[d], dtype=np.float64).reshape(-1)
+                           for d in range(2, D + 1)])
+    return ranks, flat
+
+
+def normalised(v: np.ndarray) -> np.ndarray:
+    return v / v.sum()
+
+
+def constant_monodisperse(D: int = 3, N: int = 64) -> System:
+    per = {d: np.ones((d, 1, N)) for d in range(2, D + 1)}
+    ranks, f = cp_from_vectors(D, N, per)
+    n0 = np.zeros(N)
+    n0[0] = 1.0
+    return System(D, N, "cp", ranks, f, n0, dt=0.01, steps=100, name="constant_monodisperse")
+
+
+def brownian_cp(D: int = 3, N: int = 4096) -> System:
+    """(sum_m i_m^{1/3})(sum_m i_m^{-1/3}): term (a, b) has i^{1/3} in mode a,
+    i^{-1/3} in mode b (their product, 1, when a = b) and ones elsewhere."""
+    i = sizes(N)
+    up, dn = np.cbrt(i), 1.0 / np.cbrt(i)
+    per = {}
+    for d in range(2, D + 1):
+        U = np.ones((d, d * d, N))
+        for a in range(d):
+            for b in range(d):
+                r = a * d + b
+                if a != b:
+                    U[a, r] = up
+                    U[b, r] = dn
+        per[d] = U
+    ranks, f = cp_from_vectors(D, N, per)
+    e = np.exp(-i)
+    return System(D, N, "cp", ranks, f, normalised(e), dt=1e-3, steps=1000, name="brownian_cp")
+
+
+def random_power_cp(D: int = 4, N: int = 65536, R: int = 16, seed: int = BASE_SEED,
+                    u_range=(0.5, 1.5), a_range=(-0.3, 0.3), decay: float = 10.0) -> System:
+    """For d = 2..D in order: u = U[u_range] (d, R), then a = U[a_range] (d, R);
+    U^(m)_{d,r}(i) = u[m, r] * i^{a[m, r]} evaluated in FP64 from integer i."""
+    rng = np.random.default_rng(seed)
+    i = sizes(N)
+    logi = np.log(i)
+    per = {}
+    for d in range(2, D + 1):
+        u = rng.uniform(u_range[0], u_range[1], (d, R))
+        a = rng.uniform(a_range[0], a_range[1], (d, R))
+        per[d] = u[:, :, None] * np.exp(a[:, :, None] * logi[None, None, :])
+    ranks, f = cp_from_vectors(D, N, per)
+    n0 = normalised(np.exp(-i / decay))
+    return System(D, N, "cp", ranks, f, n0, dt=1e-4, steps=100, name="random_power_cp",
+                  meta={"seed": seed, "R": R})
+
+
+def random_cp(D: int, N: int, ranks, seed: int, lo: float = 0.5, hi: float = 1.5) -> System:
+    """Unstructured positive CP factors, for small parity cases."""
+    rng = np.random.default_rng(seed)
+    per = {d: rng.uniform(lo, hi, (d, int(ranks[d - 2]), N)) for d in range(2, D + 1)}
+    rk, f = cp_from_vectors(D, N, per)
+    n0 = rng.uniform(0.0, 1.0, N)
+    n0 = normalised(n0)
+    return System(D, N, "cp", rk, f, n0, name=f"random_cp_D{D}_N{N}", meta={"seed": seed})
+
+
+def cp_to_tt_diagonal(sys: System) -> System:
+    """The same kernel in TT form by the diagonal embedding: H^(1) = row of
+    U^(1), H^(l)_{r,i,r'} = delta_{rr'} U^(l)_r(i), H^(d) = column of U^(d)."""
+    assert sys.fmt == "cp"
+    D, N = sys.D, sys.N
+    offs = cp_layout(D, N, sys.ranks)
+    ranks_tt, blocks = [], []
+    for d in range(2, D + 1):
+        R = sys.ranks[d - 2]
+        U = sys.factors[offs[d - 2]:offs[d - 1]].reshape(d, R, N)
+        rk = [1] + [R] * (d - 1) + [1]
+        ranks_tt += rk
+        for l in range(1, d + 1):
+            H = np.zeros((rk[l - 1], rk[l], N))
+            if l == 1:
+                H[0, :, :] = U[0]
+            elif l == d:
+                H[:, 0, :] = U[d - 1]
+            else:
+                for r in range(R):
+                    H[r, r, :] = U[l - 1, r]
+            blocks.append(H.reshape(-1))
+    return System(D, N, "tt", ranks_tt, np.concatenate(blocks), sys.n0.copy(), sys.dt, sys.steps,
+                  name=sys.name + "_tt", meta=dict(sys.meta))

@@ -1,0 +1,317 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle (``oracle/``) against something other than itself:
+brute force against the low-rank route, closed forms derived from the
+definitions of Sec. 1, invariants, textbook special cases, the explicit TT
+cores printed in Sec. 2 and the rank bound of Theorem 1. No test here needs a
+GPU or the CUDA library.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_09071_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rel(x, ref, scale=None):
+    s = np.max(np.abs(ref)) if scale is None else scale
+    return float(np.max(np.abs(np.asarray(x) - np.asarray(ref))) / s)
+
+
+# ---------------------------------------------------------------- P1 brute vs low rank
+@pytest.mark.parametrize("D,N,ranks", [(2, 9, [3]), (3, 7, [2, 3]), (4, 5, [2, 2, 3])])
+@pytest.mark.parametrize("sym", [0, 1])
+def test_brute_equals_direct_cp(D, N, ranks, sym):
+    s = wl.random_cp(D, N, ranks, seed=11 + D)
+    pb, qb, ob = oracle.rhs(s.n0, D, s.ranks, s.factors, mode=oracle.BRUTE, sym=sym, outflow=True)
+    pd, qd, od = oracle.rhs(s.n0, D, s.ranks, s.factors, mode=oracle.DIRECT, sym=sym, outflow=True)
+    scale = np.abs(pb).max() + np.abs(qb).max()
+    assert _rel(pd, pb, scale) < 1e-14
+    assert _rel(qd, qb, scale) < 1e-14
+    assert abs(od - ob) <= 1e-14 * abs(ob)
+
+
+@pytest.mark.parametrize("mode", [oracle.BRUTE, oracle.DIRECT])
+def test_tt_diagonal_embedding_equals_cp(mode):
+    s = wl.random_cp(4, 6, [3, 2, 2], seed=5)
+    t = wl.cp_to_tt_diagonal(s)
+    p1, q1, o1 = oracle.rhs(s.n0, 4, s.ranks, s.factors, mode=mode, outflow=True)
+    p2, q2, o2 = oracle.rhs(t.n0, 4, t.ranks, t.factors, fmt=oracle.TT, mode=mode, outflow=True)
+    scale = np.abs(p1).max() + np.abs(q1).max()
+    assert _rel(p2, p1, scale) < 1e-14 and _rel(q2, q1, scale) < 1e-14
+    assert abs(o2 - o1) <= 1e-13 * abs(o1)
+
+
+def test_symmetrised_q_differs_from_literal_for_asymmetric_kernel():
+    # Guards against the sym flag being ignored: a random CP kernel is not symmetric.
+    s = wl.random_cp(3, 6, [2, 2], seed=3)
+    _, q1 = oracle.rhs(s.n0, 3, s.ranks, s.factors, sym=1)
+    _, q0 = oracle.rhs(s.n0, 3, s.ranks, s.factors, sym=0)
+    assert _rel(q1, q0) > 1e-3
+
+
+# ---------------------------------------------------------------- P2 monodisperse start
+@pytest.mark.parametrize("mode", [oracle.BRUTE, oracle.DIRECT])
+def test_constant_kernel_monodisperse_rhs(mode):
+    D, N = 4, 8
+    s = wl.constant_monodisperse(D, N)
+    p, q = oracle.rhs(s.n0, D, s.ranks, s.factors, mode=mode)
+    rhs = p + q
+    want = np.zeros(N)
+    want[0] = -sum(1.0 / math.factorial(d - 1) for d in range(2, D + 1))
+    for d in range(2, D + 1):
+        want[d - 1] += 1.0 / math.factorial(d)
+    assert np.max(np.abs(rhs - want)) < 1e-15
+
+
+# ---------------------------------------------------------------- P3 geometric closed forms
+def _geometric(N, A=0.3, qr=0.8):
+    k = np.arange(1, N + 1, dtype=np.float64)
+    return A * qr ** (k - 1), A, qr
+
+
+def _binom(n, k):
+    return math.comb(int(n), int(k))
+
+
+@pytest.mark.parametrize("mode", [oracle.BRUTE, oracle.DIRECT])
+def test_geometric_constant_kernel(mode):
+    D, N = 4, (12 if mode == oracle.BRUTE else 40)
+    n, A, qr = _geometric(N)
+    s = wl.constant_monodisperse(D, N)
+    p, q = oracle.rhs(n, D, s.ranks, s.factors, mode=mode)
+    M0 = n.sum()
+    pw, qw = np.zeros(N), np.zeros(N)
+    for d in range(2, D + 1):
+        for k in range(d, N + 1):
+            # compositions of k into d positive parts: binom(k-1, d-1)
+            pw[k - 1] += A ** d * qr ** (k - d) * _binom(k - 1, d - 1) / math.factorial(d)
+        qw += -n * M0 ** (d - 1) / math.factorial(d - 1)
+    assert _rel(p, pw) < 1e-14
+    assert _rel(q, qw) < 1e-14
+
+
+@pytest.mark.parametrize("mode", [oracle.BRUTE, oracle.DIRECT])
+def test_geometric_product_kernel(mode):
+    # Rank-one kernel C = prod_m i_m: sum over compositions of prod i_m = binom(k+d-1, 2d-1).
+    D, N = 4, (10 if mode == oracle.BRUTE else 40)
+    n, A, qr = _geometric(N)
+    i = wl.sizes(N)
+    per = {d: np.broadcast_to(i, (d, 1, N)).copy() for d in range(2, D + 1)}
+    ranks, f = wl.cp_from_vectors(D, N, per)
+    p, q = oracle.rhs(n, D, ranks, f, mode=mode)
+    M1 = (i * n).sum()
+    pw, qw = np.zeros(N), np.zeros(N)
+    for d in range(2, D + 1):
+        for k in range(d, N + 1):
+            pw[k - 1] += A ** d * qr ** (k - d) * _binom(k + d - 1, 2 * d - 1) / math.factorial(d)
+        qw += -n * i * M1 ** (d - 1) / math.factorial(d - 1)
+    assert _rel(p, pw) < 1e-14
+    assert _rel(q, qw) < 1e-14
+
+
+# ---------------------------------------------------------------- P4 total concentration
+def test_m0_identity_constant_kernel_no_tail():
+    # n supported on sizes <= N/D: no tuple leaves the system, so
+    # sum_k rhs_k = -sum_d (d-1)/d! M0^d exactly.
+    D, N = 4, 24
+    rng = np.random.default_rng(7)
+    n = np.zeros(N)
+    n[: N // D] = rng.uniform(0.1, 1.0, N // D)
+    s = wl.constant_monodisperse(D, N)
+    p, q = oracle.rhs(n, D, s.ranks, s.factors)
+    M0 = n.sum()
+    want = -sum((d - 1) / math.factorial(d) * M0 ** d for d in range(2, D + 1))
+    assert abs((p + q).sum() - want) < 1e-14 * abs(want)
+
+
+def _scalar_heun(f, M, dt, steps):
+    for _ in range(steps):
+        k1 = f(M)
+        k2 = f(M + dt * k1)
+        M = M + 0.5 * dt * (k1 + k2)
+    return M
+
+
+def test_m0_discrete_heun_matches_scalar_heun():
+    s = wl.constant_monodisperse()  # D=3, N=64, n=e_1, dt=0.01, 100 steps
+    n, diag = oracle.integrate(s.n0, s.D, s.ranks, s.factors, s.dt, s.steps)
+    f = lambda M: -M * M / 2.0 - M ** 3 / 3.0
+    Ms = _scalar_heun(f, 1.0, s.dt, s.steps)
+    assert abs(diag[-1, 0] - Ms) < 1e-14
+    assert abs(n.sum() - Ms) < 1e-14
+
+
+def _m0_exact(t, a=0.5, b=1.0 / 3.0):
+    # dM/dt = -M^2 (a + b M): F(M) = -1/(aM) + (b/a^2) ln((a+bM)/M), F(M(t)) - F(1) = -t.
+    F = lambda M: -1.0 / (a * M) + b / a ** 2 * math.log((a + b * M) / M)
+    target = F(1.0) - t
+    lo, hi = 1e-6, 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if F(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_m0_exact_solution_second_order():
+    exact = _m0_exact(1.0)
+    assert abs(exact - 0.5724637494) < 1e-9
+    errs = []
+    for steps in (50, 100, 200):
+        s = wl.constant_monodisperse()
+        _, diag = oracle.integrate(s.n0, s.D, s.ranks, s.factors, 1.0 / steps, steps)
+        errs.append(abs(diag[-1, 0] - exact))
+    assert errs[1] < 1e-5
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 3.5 < e0 / e1 < 4.5  # second order
+
+
+# ---------------------------------------------------------------- P5 mass invariant
+@pytest.mark.parametrize("D,N,ranks", [(3, 7, [2, 2]), (4, 5, [2, 2, 2])])
+def test_m1_identity_equals_outflow(D, N, ranks):
+    s = wl.random_cp(D, N, ranks, seed=21)
+    p, q, o = oracle.rhs(s.n0, D, s.ranks, s.factors, mode=oracle.BRUTE, outflow=True)
+    k = wl.sizes(N)
+    assert abs((k * (p + q)).sum() + o) < 1e-13 * abs(o)
+
+
+def test_m1_plus_cumulative_outflow_is_conserved():
+    s = wl.random_cp(3, 16, [2, 3], seed=4)
+    _, diag = oracle.integrate(s.n0, 3, s.ranks, s.factors, 0.05, 20)
+    total = diag[:, 1] + diag[:, 2]
+    assert np.max(np.abs(total - total[0])) < 1e-14 * total[0]
+    assert diag[-1, 2] > 0
+
+
+# ---------------------------------------------------------------- P6 binary textbook case
+def test_binary_constant_kernel_closed_form():
+    # D=2, C=1, n(0)=e_1: n_k(t) = tau^{k-1}/(1+tau)^{k+1}, tau = t/2.
+    N, T = 200, 0.6
+    s = wl.constant_monodisperse(2, N)
+    k = wl.sizes(N)
+    tau = T / 2
+    exact = tau ** (k - 1) / (1 + tau) ** (k + 1)
+    errs = []
+    for steps in (30, 60):
+        n, _ = oracle.integrate(s.n0, 2, s.ranks, s.factors, T / steps, steps, diag=False)
+        errs.append(np.max(np.abs(n - exact)))
+    assert errs[1] < 2e-5
+    assert 3.5 < errs[0] / errs[1] < 4.5
+    # The closed form satisfies the truncated right-hand side up to its tail.
+    p, q = oracle.rhs(exact, 2, s.ranks, s.factors)
+    dndt = (tau ** (k - 2) * (k - 1 - 2 * tau)) / (2 * (1 + tau) ** (k + 2))
+    assert np.max(np.abs(p + q - dndt)) < 1e-15
+
+
+# ---------------------------------------------------------------- P7 kernel identities
+def test_brownian_cp_is_eq17_combination():
+    # (sum i^{1/3})(sum i^{-1/3}) = C^(d)[1/3,-1/3,0..]/(d-2)! + C^(d)[0..0]/(d-1)!
+    s = wl.brownian_cp(3, 6)
+    rng = np.random.default_rng(1)
+    for d in (2, 3):
+        mu1 = [1 / 3, -1 / 3] + [0.0] * (d - 2)
+        mu0 = [0.0] * d
+        for _ in range(20):
+            idx = rng.integers(1, 7, d)
+            got = oracle.kernel_entry(oracle.CP, 3, 6, s.ranks, s.factors, idx)
+            want = (oracle.brownian_entry(mu1, idx) / math.factorial(d - 2)
+                    + oracle.brownian_entry(mu0, idx) / math.factorial(d - 1))
+            assert abs(got - want) < 1e-13 * abs(want)
+
+
+def _tt_contract(ranks, cores, N, idx):
+    off, v = 0, np.ones(1)
+    for l in range(1, len(ranks)):
+        H = cores[off: off + ranks[l - 1] * ranks[l] * N].reshape(ranks[l - 1], ranks[l], N)
+        v = v @ H[:, :, idx[l - 1] - 1]
+        off += ranks[l - 1] * ranks[l] * N
+    return float(v[0])
+
+
+@pytest.mark.parametrize("D", [2, 3, 4, 5])
+def test_theorem1_cores_reproduce_eq17(D):
+    N = 5
+    rng = np.random.default_rng(D)
+    mu = rng.uniform(-0.5, 0.5, D)
+    ranks, cores = oracle.brownian_tt(mu, N)
+    assert list(ranks) == [math.comb(D, l) for l in range(D + 1)]
+    for _ in range(30):
+        idx = rng.integers(1, N + 1, D)
+        want = oracle.brownian_entry(mu, idx)
+        assert abs(_tt_contract(ranks, cores, N, idx) - want) < 1e-13 * abs(want)
+
+
+@pytest.mark.parametrize("D", [3, 4])
+def test_tt_ranks_bounded_by_theorem1(D):
+    # Ranks of the unfoldings of the full tensor never exceed binom(D, lambda).
+    N = 7
+    mu = np.random.default_rng(9).uniform(-0.6, 0.6, D)
+    full = np.zeros((N,) * D)
+    for idx in np.ndindex(*full.shape):
+        full[idx] = oracle.brownian_entry(mu, np.array(idx) + 1)
+    for l in range(1, D):
+        mat = full.reshape(N ** l, -1)
+        sv = np.linalg.svd(mat, compute_uv=False)
+        rank = int((sv > 1e-11 * sv[0]).sum())
+        assert rank <= math.comb(D, l)
+
+
+def _read_golden_patterns():
+    pats = {}
+    with open(os.path.join(GOLDEN, "brownian_tt_d2_d3_cores.txt")) as fh:
+        lines = [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+    i = 0
+    while i < len(lines):
+        _, D, lam, rows, cols = lines[i]
+        D, lam, rows, cols = int(D), int(lam), int(rows), int(cols)
+        pats[(D, lam)] = np.array([[int(x) for x in lines[i + 1 + r]] for r in range(rows)])
+        assert pats[(D, lam)].shape == (rows, cols)
+        i += 1 + rows
+    return pats
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_printed_cores_reproduce_eq17(D):
+    pats = _read_golden_patterns()
+    N = 6
+    rng = np.random.default_rng(30 + D)
+    mu = rng.uniform(-0.5, 0.5, D)
+    ranks = [1] + [pats[(D, l)].shape[1] for l in range(1, D + 1)]
+    i = wl.sizes(N)
+    blocks = []
+    for l in range(1, D + 1):
+        pat = pats[(D, l)]
+        H = np.zeros(pat.shape + (N,))
+        for a in range(pat.shape[0]):
+            for b in range(pat.shape[1]):
+                if pat[a, b]:
+                    H[a, b] = i ** mu[pat[a, b] - 1]
+        blocks.append(H.reshape(-1))
+    cores = np.concatenate(blocks)
+    for idx in np.ndindex(*(N,) * D):
+        idx = np.array(idx) + 1
+        want = oracle.brownian_entry(mu, idx)
+        assert abs(_tt_contract(ranks, cores, N, idx) - want) < 1e-13 * abs(want)
+
+
+def test_theorem1_tt_rhs_matches_brute_force():
+    D, N = 3, 6
+    mu = [0.4, -0.2, 0.1]
+    ranks3, cores3 = oracle.brownian_tt(mu, N)
+    ranks2, cores2 = oracle.brownian_tt(mu[:2], N)
+    ranks = list(ranks2) + list(ranks3)
+    f = np.concatenate([cores2, cores3])
+    n = np.random.default_rng(2).uniform(0, 1, N)
+    pb, qb, ob = oracle.rhs(n, D, ranks, f, fmt=oracle.TT, mode=oracle.BRUTE, outflow=True)
+    pd, qd, od = oracle.rhs(n, D, ranks, f, fmt=oracle.TT, mode=oracle.DIRECT, outflow=True)
+    scale = np.abs(pb).max() + np.abs(qb).max()
+    assert _rel(pd, pb, scale) < 1e-14 and _rel(qd, qb, scale) < 1e-14
+    assert abs(od - ob) < 1e-13 * abs(ob)
