@@ -1,0 +1,151 @@
+/*
+ * sag.h - C ABI of the GB300 library for the multi-particle Smoluchowski
+ * right-hand side with low-rank kernels.
+ *
+ * What it computes (arXiv:1905.09071, Sec. 1): for concentrations n_k of sizes
+ * k = 1..N,
+ *     dn/dt = sum_{d=2..D} ( P^(d)[n] + Q^(d)[n] ),
+ *     p_k^(d) =  1/d!     * sum_{i in [1,N]^d, |i| = k}  C^(d)_i  n_{i_1} ... n_{i_d},
+ *     q_k^(d) = -n_k/(d-1)! * sum_{i in [1,N]^{d-1}}      C^(d)_{i,k} n_{i_1} ... n_{i_{d-1}},
+ * with every index truncated to 1..N. Each kernel C^(d) is given in low-rank
+ * form: CP, C_i = sum_r prod_m U^(m)_r(i_m) (Sec. 1), or TT, Eq. ch3.eq4.
+ * The gain P^(d) is evaluated as d-fold truncated convolutions through FFTs,
+ * the loss Q^(d) through inner products <U^(m)_r, n> (Sec. 1, complexity
+ * O(N D R log N)). Time stepping is the explicit second-order Runge-Kutta
+ * method with two right-hand-side evaluations per step (Sec. 3).
+ *
+ * Conventions of every call:
+ *   - Size k of a system is stored at index k-1 of a contiguous FP64 vector.
+ *   - Vectors passed to sag_rhs / sag_rk2_step / sag_integrate may live in
+ *     device memory or in host memory; host buffers are copied to and from the
+ *     device inside the call, on the given stream.
+ *   - All calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream). A plan must not be used by two streams at once.
+ *   - Argument errors are reported synchronously through the return value and
+ *     sag_last_error(); they never launch work. Errors raised on the device
+ *     (a non-finite right-hand side) are latched in the plan and reported by
+ *     sag_sync_status().
+ *   - The caller owns every buffer it passes. sag_plan copies the factors, so
+ *     they may be freed when it returns; the plan owns its device workspace.
+ */
+#ifndef SAG_H
+#define SAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sag_plan_s* sag_plan_t;
+
+typedef enum {
+  SAG_OK = 0,
+  SAG_EINVAL = 1,          /* bad argument (null pointer, size, rank, layout) */
+  SAG_ENOMEM = 2,          /* device or host allocation failed */
+  SAG_ECUDA = 3,           /* a CUDA runtime call failed (message has the CUDA error) */
+  SAG_EUNSUPPORTED = 4,    /* valid request outside what this build implements */
+  SAG_ETIMEOUT = 5,        /* a bounded device-side wait expired */
+  SAG_ENONFINITE = 6       /* the right-hand side produced Inf or NaN */
+} sag_status;
+
+typedef enum { SAG_CP = 0, SAG_TT = 1 } sag_format;
+
+/* SAG_FP64: every FFT in FP64. SAG_FP32_SPLIT: FFTs in double-word FP32
+ * (hi + lo pairs, about 48 bits); the loss inner products, the Runge-Kutta
+ * accumulation and the diagnostics stay FP64 in both. */
+typedef enum { SAG_FP64 = 0, SAG_FP32_SPLIT = 1 } sag_precision;
+
+/* Second-order explicit Runge-Kutta variant (Sec. 3 names the order only):
+ * Heun  n+ = n + dt/2 (F(n) + F(n + dt F(n)));
+ * midpoint n+ = n + dt F(n + dt/2 F(n)). */
+typedef enum { SAG_HEUN = 0, SAG_MIDPOINT = 1 } sag_rk;
+
+/* One system. Orders d = 2..D (2 <= D <= 8), sizes 1..N (N >= 1).
+ *   fmt = SAG_CP: rank[d-2] = R_d for d = 2..D; factors holds, for each d in
+ *     turn, the array [d][R_d][N] (mode m, rank r, size), i.e. U^(m)_r(k) at
+ *     offset_d + (m R_d + r) N + k - 1.
+ *   fmt = SAG_TT: for each d in turn, d+1 ranks R_0..R_d with R_0 = R_d = 1
+ *     (Eq. ch3.eq4); factors holds, for each d and each core lambda = 1..d,
+ *     the array [R_{lambda-1}][R_lambda][N] (the vectors h^(lambda)_{r,r'} of
+ *     Sec. 3 stored along the size axis).
+ * factors_on_device = 1 if `factors` is a device pointer, 0 for host memory. */
+typedef struct {
+  int32_t N;
+  int32_t D;
+  int32_t fmt;
+  const int32_t* rank;
+  const double* factors;
+  int32_t factors_on_device;
+} sag_system;
+
+typedef struct {
+  int32_t prec;          /* sag_precision, default SAG_FP32_SPLIT */
+  int32_t rk;            /* sag_rk, default SAG_HEUN */
+  int32_t symmetrize_q;  /* 1 (default): loss term of the mode-symmetrised kernel;
+                            0: the kernel's last mode holds k, exactly as printed.
+                            The two coincide for symmetric kernels (Sec. 1 assumes
+                            symmetric coefficients). */
+  int32_t reserved;
+} sag_options;
+
+/* Fills *opt with the defaults. */
+void sag_default_options(sag_options* opt);
+
+/* Builds a plan for B independent systems sys[0..B-1]. Validates the systems,
+ * chooses FFT lengths L_d >= d N (products of 2, 3, 5), builds twiddle tables,
+ * copies the factors (FP64, plus the double-word copy for SAG_FP32_SPLIT) and
+ * allocates the workspace. opt may be NULL (defaults). On success *out holds
+ * the plan. B = 1 in this build; B > 1 returns SAG_EUNSUPPORTED. */
+sag_status sag_plan(const sag_system* sys, int32_t B, const sag_options* opt, sag_plan_t* out);
+
+/* Offsets of each system's block in packed state vectors: offsets[b] is the
+ * index of system b's size 1, offsets[B] the total length. `offsets` is a host
+ * array of B+1 entries. */
+sag_status sag_plan_layout(sag_plan_t plan, int64_t* offsets);
+
+/* Device bytes the plan holds (factor copies, tables, workspace). */
+sag_status sag_plan_bytes(sag_plan_t plan, size_t* bytes);
+
+/* dndt = sum_d P^(d)[n] + Q^(d)[n] (Sec. 1). n and dndt hold the packed state
+ * (length offsets[B]); they may alias. */
+sag_status sag_rhs(sag_plan_t plan, const double* n, double* dndt, void* stream);
+
+/* The gain and loss parts separately: p = sum_d P^(d)[n], q = sum_d Q^(d)[n]
+ * (either may be NULL), and outflow[b] (host or device, may be NULL) = the
+ * first-moment flux out of the truncated system,
+ *     sum_d 1/d! sum_{i in [1,N]^d, |i| > N} |i| C^(d)_i prod_m n_{i_m}. */
+sag_status sag_rhs_parts(sag_plan_t plan, const double* n, double* p, double* q,
+                         double* outflow, void* stream);
+
+/* One explicit RK2 step of size dt on n, in place (Sec. 3: two right-hand-side
+ * evaluations per step). */
+sag_status sag_rk2_step(sag_plan_t plan, double* n, double dt, void* stream);
+
+/* `steps` RK2 steps of size dt on n, in place. The step is captured once as a
+ * CUDA graph per (n, dt, diag) and replayed. diag (may be NULL; host or device)
+ * receives [steps+1][B][3] doubles: M0 = sum_k n_k, M1 = sum_k k n_k and the
+ * cumulative first-moment outflow (the time integral, by the same RK2 rule, of
+ * the outflow of sag_rhs_parts); row 0 is the initial state. With a symmetric
+ * (or symmetrised) kernel M1 + outflow stays constant. */
+sag_status sag_integrate(sag_plan_t plan, double* n, double dt, int64_t steps, double* diag,
+                         void* stream);
+
+/* Waits for `stream`, then returns and clears the plan's latched device-side
+ * status (SAG_OK, SAG_ENONFINITE or SAG_ETIMEOUT). */
+sag_status sag_sync_status(sag_plan_t plan, void* stream);
+
+/* Releases the plan (after the work queued on it has finished). NULL is a no-op. */
+void sag_plan_destroy(sag_plan_t plan);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* sag_last_error(void);
+
+/* Library version string. */
+const char* sag_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,21 @@
+// Instantiation of the FFT kernels for the FP64 path.
+#include "fft_kernels.cuh"
+#include "launch.h"
+
+namespace sag {
+
+cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
+  k_fwd_col<cd><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin);
+  k_rows<cd><<<L.row_blocks, kThreads, L.row_smem, st>>>(P);
+  k_inv_col<cd><<<L.inv_blocks, kThreads, L.inv_smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_fft_kernels_f64(const LaunchCfg& L) {
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.col_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.inv_smem);
+  return e;
+}
+
+}  // namespace sag

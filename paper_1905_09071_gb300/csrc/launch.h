@@ -1,0 +1,41 @@
+// Host-side launch interface between the ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace sag {
+
+// Grid and shared-memory sizes of one plan, computed once at plan time.
+struct LaunchCfg {
+  int prep_blocks;
+  int col_blocks, row_blocks, inv_blocks, epi_blocks;
+  size_t col_smem, row_smem, inv_smem, epi_smem;
+};
+
+// What the epilogue writes (see EpiMode).
+struct EpiArgs {
+  const double* nin;    // state the right-hand side is evaluated at
+  double* nbase;        // RK2 base state (updated in place by the second stage)
+  double* out0;         // EPI_RHS: dn/dt; first stages: the intermediate state
+  double* pout;         // EPI_RHS: gain part (nullable)
+  double* qout;         // EPI_RHS: loss part (nullable)
+  double* k1buf;        // Heun: F at the first stage
+  double* diag;         // second stages: [steps+1][3] diagnostics (nullable)
+  double* outflow_out;  // EPI_RHS: outflow (nullable, device)
+  double* part;         // [epi_blocks][4] block partials
+  double dt;
+  int mode;
+};
+
+cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
+                         const EpiArgs& A, cudaStream_t st);
+cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, cudaStream_t st);
+cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+cudaError_t setup_common_kernels(const LaunchCfg& L);
+cudaError_t setup_fft_kernels_f64(const LaunchCfg& L);
+cudaError_t setup_fft_kernels_dw(const LaunchCfg& L);
+
+}  // namespace sag

@@ -1,0 +1,208 @@
+"""Thin ctypes binding of the C ABI in ``include/sag.h`` (libsag.so).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels. Buffers may be torch CUDA tensors (device pointers, the
+current torch stream is used unless one is given) or numpy arrays (host
+pointers; the library copies them to and from the device inside the call).
+If the library cannot be loaded the binding raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SAG_OK, SAG_EINVAL, SAG_ENOMEM, SAG_ECUDA, SAG_EUNSUPPORTED, SAG_ETIMEOUT, SAG_ENONFINITE = range(7)
+SAG_CP, SAG_TT = 0, 1
+SAG_FP64, SAG_FP32_SPLIT = 0, 1
+SAG_HEUN, SAG_MIDPOINT = 0, 1
+
+# Every function include/sag.h declares.
+EXPORTS = [
+    "sag_default_options", "sag_plan", "sag_plan_layout", "sag_plan_bytes", "sag_rhs",
+    "sag_rhs_parts", "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_plan_destroy",
+    "sag_last_error", "sag_version",
+]
+
+_STATUS_NAMES = {0: "SAG_OK", 1: "SAG_EINVAL", 2: "SAG_ENOMEM", 3: "SAG_ECUDA",
+                 4: "SAG_EUNSUPPORTED", 5: "SAG_ETIMEOUT", 6: "SAG_ENONFINITE"}
+
+
+class SagError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _System(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("D", ctypes.c_int32), ("fmt", ctypes.c_int32),
+                ("rank", ctypes.POINTER(ctypes.c_int32)), ("factors", ctypes.c_void_p),
+                ("factors_on_device", ctypes.c_int32)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("rk", ctypes.c_int32),
+                ("symmetrize_q", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Opens libsag.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise OSError(f"libsag.so not found at {path}")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.sag_default_options.argtypes = [ctypes.POINTER(_Options)]
+        lib.sag_default_options.restype = None
+        lib.sag_plan.argtypes = [ctypes.POINTER(_System), i32, ctypes.POINTER(_Options),
+                                 ctypes.POINTER(vp)]
+        lib.sag_plan_layout.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.sag_plan_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.sag_rhs.argtypes = [vp, vp, vp, vp]
+        lib.sag_rhs_parts.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.sag_rk2_step.argtypes = [vp, vp, f64, vp]
+        lib.sag_integrate.argtypes = [vp, vp, f64, i64, vp, vp]
+        lib.sag_sync_status.argtypes = [vp, vp]
+        lib.sag_plan_destroy.argtypes = [vp]
+        lib.sag_plan_destroy.restype = None
+        lib.sag_last_error.restype = ctypes.c_char_p
+        lib.sag_version.restype = ctypes.c_char_p
+        for name in ("sag_plan", "sag_plan_layout", "sag_plan_bytes", "sag_rhs", "sag_rhs_parts",
+                     "sag_rk2_step", "sag_integrate", "sag_sync_status"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != SAG_OK:
+        raise SagError(status, load().sag_last_error().decode())
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (FP64, contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffers must be contiguous float64")
+        return x.ctypes.data
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("torch buffers must be contiguous float64")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream, *tensors):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    import torch
+    if any(isinstance(t, torch.Tensor) and t.is_cuda for t in tensors):
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+def default_options() -> dict:
+    o = _Options()
+    load().sag_default_options(ctypes.byref(o))
+    return {"prec": o.prec, "rk": o.rk, "symmetrize_q": o.symmetrize_q}
+
+
+class Plan:
+    """A planned system (sag_plan). ``factors`` is a flat float64 array in the
+    layout of include/sag.h (numpy: host; torch CUDA tensor: device)."""
+
+    def __init__(self, N: int, D: int, ranks, factors, *, fmt: int = SAG_CP,
+                 prec: int = SAG_FP32_SPLIT, rk: int = SAG_HEUN, symmetrize_q: int = 1):
+        lib = load()
+        self._ranks = np.ascontiguousarray(np.asarray(ranks, dtype=np.int32))
+        self.N, self.D, self.fmt, self.prec = int(N), int(D), int(fmt), int(prec)
+        on_dev = 0
+        try:
+            import torch
+            on_dev = int(isinstance(factors, torch.Tensor) and factors.is_cuda)
+        except ImportError:
+            pass
+        if not on_dev:
+            factors = np.ascontiguousarray(np.asarray(factors, dtype=np.float64))
+        self._factors_ref = factors
+        sysd = _System(self.N, self.D, self.fmt,
+                       self._ranks.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                       _ptr(factors), on_dev)
+        opt = _Options(int(prec), int(rk), int(symmetrize_q), 0)
+        h = ctypes.c_void_p()
+        _check(lib.sag_plan(ctypes.byref(sysd), 1, ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+
+    @property
+    def handle(self):
+        return self._h
+
+    def layout(self):
+        off = (ctypes.c_int64 * 2)()
+        _check(self._lib.sag_plan_layout(self._h, off))
+        return [off[0], off[1]]
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        _check(self._lib.sag_plan_bytes(self._h, ctypes.byref(b)))
+        return int(b.value)
+
+    def rhs(self, n, dndt, stream=None):
+        _check(self._lib.sag_rhs(self._h, _ptr(n), _ptr(dndt), _stream(stream, n, dndt)))
+        return dndt
+
+    def rhs_parts(self, n, p=None, q=None, outflow=None, stream=None):
+        _check(self._lib.sag_rhs_parts(self._h, _ptr(n), _ptr(p), _ptr(q), _ptr(outflow),
+                                       _stream(stream, n, p, q, outflow)))
+        return p, q, outflow
+
+    def rk2_step(self, n, dt: float, stream=None):
+        _check(self._lib.sag_rk2_step(self._h, _ptr(n), float(dt), _stream(stream, n)))
+        return n
+
+    def integrate(self, n, dt: float, steps: int, diag=None, stream=None):
+        _check(self._lib.sag_integrate(self._h, _ptr(n), float(dt), int(steps), _ptr(diag),
+                                       _stream(stream, n, diag)))
+        return n
+
+    def sync_status(self, stream=None) -> int:
+        """Returns the latched device status (SAG_OK, SAG_ENONFINITE, ...), clearing it."""
+        st = self._lib.sag_sync_status(self._h, _stream(stream))
+        return int(st)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.sag_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
