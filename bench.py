@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Throughput of the multi-particle Smoluchowski RK2 step on GB300.
+
+Workload (the throughput configuration): D = 4 (orders 2, 3, 4), N = 65536
+sizes, CP rank 16 per order with factors U^(m)_r(i) = u_{m,r} i^{a_{m,r}}
+(u ~ U[0.5, 1.5], a ~ U[-0.3, 0.3], seed 1905), n_k = exp(-k/10) normalised
+to M0 = 1, Heun RK2 with dt = 1e-4. A step is one RK2 step = two right-hand-
+side evaluations; the headline path is the double-word FP32 ("FP32-split")
+FFT path, the FP64 path is measured beside it.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle
+instead (the only other place this script runs oracle code), on bounded
+samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "RHS evals/sec & RK2 steps/sec (N=2^16,D=4,R=16) FP32-split vs FP64 at stated error"
+UNIT = "RK2 steps/s"
+WORKLOAD = "random_power_cp: D=4 (d=2,3,4), N=65536, CP rank 16 per order, Heun dt=1e-4"
+FP32_PEAK_PER_SM_CLK = 128      # FP32 lanes per SM per clock (FADD/FMUL/FFMA issue)
+FP64_PEAK_PER_SM_CLK = 2        # FP64 operations per SM per clock on GB300
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--prec", default="both", choices=["both", "fp32_split", "fp64"],
+                    help="paths to run (profiling runs use one)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed region only: no parity check, kernel profile, e2e or CPU baseline "
+                         "(for ncu captures); prints no JSON line")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_slice(s, r):
+    """The workload's CP kernel restricted to rank term r of every order."""
+    from paper_1905_09071_gb300 import workloads as wl
+    offs = wl.cp_layout(s.D, s.N, s.ranks)
+    per = {}
+    for d in range(2, s.D + 1):
+        R = s.ranks[d - 2]
+        per[d] = s.factors[offs[d - 2]:offs[d - 1]].reshape(d, R, s.N)[:, r:r + 1, :]
+    return wl.cp_from_vectors(s.D, s.N, per)
+
+
+def pair_slice(s, d, r):
+    """A D = 2, rank-one system from the first two mode vectors of term (d, r):
+    its gain term is one truncated length-N convolution, the unit of work of
+    the oracle's direct mode (a full right-hand side is sum_d (d-1) R_d of them)."""
+    from paper_1905_09071_gb300 import workloads as wl
+    offs = wl.cp_layout(s.D, s.N, s.ranks)
+    R = s.ranks[d - 2]
+    U = s.factors[offs[d - 2]:offs[d - 1]].reshape(d, R, s.N)
+    return wl.cp_from_vectors(2, s.N, {2: U[:2, r:r + 1, :].copy()})
+
+
+def oracle_sample(s, seconds: float, max_samples: int = 10 ** 9, warmup: int = 0):
+    """Times the oracle (direct CP mode, all host cores) on one-convolution
+    samples of the workload, cycling over the terms (d, r). Returns
+    (seconds per full right-hand side, samples, cores)."""
+    import oracle
+    terms = [(d, r) for d in range(2, s.D + 1) for r in range(s.ranks[d - 2])]
+    convs_per_rhs = sum((d - 1) * s.ranks[d - 2] for d in range(2, s.D + 1))
+    times = []
+    i = 0
+    t_all = time.perf_counter()
+    while True:
+        d, r = terms[i % len(terms)]
+        ranks, f = pair_slice(s, d, r)
+        t0 = time.perf_counter()
+        oracle.rhs(s.n0, 2, ranks, f, mode=oracle.DIRECT)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+        i += 1
+        if len(times) >= max_samples or (time.perf_counter() - t_all >= seconds and times):
+            break
+    per_conv = sum(times) / len(times)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return per_conv * convs_per_rhs, len(times), cores
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1905_09071_gb300 import workloads as wl
+    s = wl.random_power_cp()
+    sec_per_rhs, samples, cores = oracle_sample(s, seconds=0.0, max_samples=args.steps,
+                                                warmup=args.warmup)
+    value = 1.0 / (2.0 * sec_per_rhs)
+    sample = (f"{samples} timed steps; each step = the oracle's direct-mode right-hand side of a "
+              f"D=2 rank-one subsystem made of two factor vectors of one term (d, r) of the "
+              f"workload: one truncated convolution of length 65536; a full right-hand side is "
+              f"96 of them (sum_d (d-1) R_d), an RK2 step 2 right-hand sides")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "N": s.N, "D": s.D, "R": 16,
+                                           "oracle_mode": "direct CP (FP64, Neumaier sums, OpenMP)"},
+           "rhs_evals_per_s": 1.0 / sec_per_rhs,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def time_integrate(pl, n, dt, steps, world):
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    pl.integrate(n, dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return e0.elapsed_time(e1) / 1e3
+
+
+def time_rhs(pl, n, out, reps):
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        pl.rhs(n, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def parity_error(pl, s, K=2048):
+    """Normwise error of one right-hand side at n0 against the oracle: gain
+    outputs k <= K (oracle on the size prefix, exact for those k) and every
+    loss output (oracle inner-product route)."""
+    import torch
+    import oracle
+    from paper_1905_09071_gb300 import workloads as wl
+    offs = wl.cp_layout(s.D, s.N, s.ranks)
+    per = {d: s.factors[offs[d - 2]:offs[d - 1]].reshape(d, s.ranks[d - 2], s.N)[:, :, :K]
+           for d in range(2, s.D + 1)}
+    rk, f = wl.cp_from_vectors(s.D, K, per)
+    p_ref, _ = oracle.rhs(s.n0[:K], s.D, rk, f, mode=oracle.DIRECT)
+    q_ref = oracle.loss(s.n0, s.D, s.ranks, s.factors)
+    n = torch.tensor(s.n0, device="cuda")
+    p, q = torch.empty_like(n), torch.empty_like(n)
+    pl.rhs_parts(n, p, q)
+    torch.cuda.synchronize()
+    p, q = p.cpu().numpy(), q.cpu().numpy()
+    scale = np.abs(p).max() + np.abs(q_ref).max()
+    return float(max(np.abs(p[:K] - p_ref).max(), np.abs(q - q_ref).max()) / scale)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1905_09071_gb300 import sag, workloads as wl
+    torch.cuda.set_device(local)
+    s = wl.random_power_cp()
+    K, W = args.steps, args.warmup
+    res = {}
+    sampler = ClockSampler(local)
+    clocks = None
+    precs = {"both": (sag.SAG_FP32_SPLIT, sag.SAG_FP64), "fp32_split": (sag.SAG_FP32_SPLIT,),
+             "fp64": (sag.SAG_FP64,)}[args.prec]
+    if args.quick:
+        for prec in precs:
+            pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec)
+            n = torch.tensor(s.n0, device="cuda")
+            pl.integrate(n, s.dt, W)
+            t = time_integrate(pl, n, s.dt, K, world)
+            assert pl.sync_status() == sag.SAG_OK
+            print(f"prec {prec}: {K / t:.1f} RK2 steps/s", file=sys.stderr)
+            pl.close()
+        return
+    if args.prec != "both":
+        raise SystemExit("--prec other than both needs --quick")
+    for prec in precs:
+        pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec)
+        n = torch.tensor(s.n0, device="cuda")
+        pl.integrate(n, s.dt, max(W, 3))
+        torch.cuda.synchronize()
+        if prec == sag.SAG_FP32_SPLIT:
+            sampler.start()
+        t = time_integrate(pl, n, s.dt, K, world)
+        if prec == sag.SAG_FP32_SPLIT:
+            clocks = sampler.stop()
+        t = max_over_ranks(t, world)
+        assert pl.sync_status() == sag.SAG_OK
+        out = torch.empty_like(n)
+        nr = torch.tensor(s.n0, device="cuda")
+        pl.rhs(nr, out)
+        t_rhs = time_rhs(pl, nr, out, max(K, 10))
+        # per-kernel CUDA-event times over K non-graph RK2 steps
+        pl.profile(True)
+        nprof = torch.tensor(s.n0, device="cuda")
+        for _ in range(K):
+            pl.rk2_step(nprof, s.dt)
+        prof = pl.profile_read()
+        pl.profile(False)
+        work = {name: pl.kernel_work(name) for name in prof}
+        err = parity_error(pl, s) if rank == 0 else None
+        res[prec] = dict(t=t, t_rhs=t_rhs, prof=prof, work=work, err=err, desc=pl.describe())
+        pl.close()
+
+    # end-to-end: the public call with host buffers (pinned), copies inside
+    pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT)
+    host_n = torch.tensor(s.n0).pin_memory().numpy()
+    for _ in range(max(W, 3)):
+        pl.rk2_step(host_n, s.dt)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        pl.rk2_step(host_n, s.dt)  # H2D of n, two right-hand sides, D2H of n (synchronous)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    pl.close()
+
+    if rank != 0:
+        return
+    dw, f64 = res[sag.SAG_FP32_SPLIT], res[sag.SAG_FP64]
+    value = K * world / dw["t"]
+    # dominant kernel of the headline path and its roofline
+    name, (ms, cnt) = max(dw["prof"].items(), key=lambda kv: kv[1][0])
+    w = dw["work"][name]
+    dur = ms / cnt / 1e3
+    if w["ops_fp64"]:
+        peak = NUM_SMS * FP64_PEAK_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    else:
+        peak = NUM_SMS * FP32_PEAK_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = w["ops"] / dur / 1e12
+    total_ms = sum(v[0] for v in dw["prof"].values())
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / total_ms,
+                   "ops_per_launch": dw["work"][k]["ops"],
+                   "bytes_per_launch": dw["work"][k]["bytes"]} for k, v in dw["prof"].items()}
+    kernels_per_step = sum(v[1] for v in dw["prof"].values()) / K
+    n_bytes = 8 * s.N
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        sec_per_rhs, samples, cores = oracle_sample(s, seconds=args.cpu_seconds)
+        cpu = {"value": 1.0 / (2 * sec_per_rhs), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{samples} one-convolution samples (D=2 rank-one subsystems of the "
+                         f"workload's term vectors, oracle direct mode) scaled by the 96 "
+                         f"convolutions of a full right-hand side and 2 right-hand sides per step"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": dw["t"] / K * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32x2 (double-word FP32 FFTs; FP64 inner products, RK2, diagnostics)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": s.N, "D": s.D, "R": 16, "precision": "FP32_SPLIT",
+                   "timed": "sag_integrate: K Heun steps as CUDA-graph replays, inputs resident in HBM",
+                   "l2": "working set (factor copies 151 MB + FFT workspace 243 MB) larger than the 129 MB L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "fft_geometry": dw["desc"]["orders"]},
+        "rhs_evals_per_s": max(K, 10) / dw["t_rhs"],
+        "error_vs_oracle": {"fp32_split": dw["err"], "fp64": f64["err"],
+                            "metric": "max|x - oracle| / (max|P| + max|Q|), one RHS at n0"},
+        "fp64": {"value": K * world / f64["t"], "unit": UNIT, "ms_per_step": f64["t"] / K * 1e3,
+                 "rhs_evals_per_s": max(K, 10) / f64["t_rhs"]},
+        "speedup_vs_fp64": f64["t"] / dw["t"],
+        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                     "unit": "TFP64op/s" if w["ops_fp64"] else "TFP32op/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "peak_source": "derived: 152 SMs x %d ops/clk/SM x 2070 MHz" %
+                                    (FP64_PEAK_PER_SM_CLK if w["ops_fp64"] else FP32_PEAK_PER_SM_CLK)},
+        "kernels": kernels,
+        "clocks": clocks,
+        "gpu_launches": int(round(kernels_per_step * K)) + 1,
+        "e2e": {"value": K * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n_bytes,
+                "d2h_bytes_per_step": n_bytes},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # CPU work only: rank 0 runs it, other ranks exit without work.
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    world, rank, local = dist_setup(args)
+    run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -136,6 +136,32 @@ sag_status sag_integrate(sag_plan_t plan, double* n, double dt, int64_t steps, d
  * status (SAG_OK, SAG_ENONFINITE or SAG_ETIMEOUT). */
 sag_status sag_sync_status(sag_plan_t plan, void* stream);
 
+/* Kernel timing, for profiling and roofline reporting. While enabled, every
+ * kernel that sag_rhs / sag_rhs_parts / sag_rk2_step launch (not the graph
+ * replays of sag_integrate) is bracketed by CUDA events recorded on the
+ * launch stream. sag_profile_read waits for that work, adds each kernel's
+ * total time (ms) and launch count to ms[id] and launches[id] for
+ * id < min(n, SAG_NUM_KERNELS), and forgets the records. */
+#define SAG_NUM_KERNELS 8
+sag_status sag_profile_enable(sag_plan_t plan, int32_t on);
+sag_status sag_profile_read(sag_plan_t plan, double* ms, int64_t* launches, int32_t n);
+/* Name of kernel id (0 <= id < SAG_NUM_KERNELS), or NULL. */
+const char* sag_kernel_name(int32_t id);
+
+/* Algorithmic work of one launch of kernel id for this plan: *ops = arithmetic
+ * instructions of the method (one FP32 add, multiply or FMA = 1 op for the
+ * double-word path, one FP64 op for FP64 arithmetic; index arithmetic, loads
+ * and stores excluded), *ops_fp64 = 1 if those are FP64 instructions, and
+ * *bytes = the HBM bytes the step must move at minimum (its inputs and
+ * outputs, not the workspace between kernels). Counts follow the radix
+ * schedule and the double-word operation costs stated in the source. */
+sag_status sag_kernel_work(sag_plan_t plan, int32_t id, double* ops, int32_t* ops_fp64,
+                           double* bytes);
+
+/* JSON description of the plan's FFT geometry (per order: L, M1, M2, radix
+ * schedules, block shapes), written to buf (NUL-terminated, truncated to len). */
+sag_status sag_plan_describe(sag_plan_t plan, char* buf, size_t len);
+
 /* Releases the plan (after the work queued on it has finished). NULL is a no-op. */
 void sag_plan_destroy(sag_plan_t plan);
 

@@ -62,6 +62,8 @@ def _load():
         lib.orc_kernel_entry.argtypes = [ctypes.c_int] * 3 + [i32p, f64p, ctypes.c_int, i32p]
         lib.orc_rhs.restype = ctypes.c_int
         lib.orc_rhs.argtypes = [ctypes.c_int] * 4 + [i32p, f64p, f64p, ctypes.c_int, f64p, f64p, f64p]
+        lib.orc_loss.restype = ctypes.c_int
+        lib.orc_loss.argtypes = [ctypes.c_int] * 3 + [i32p, f64p, f64p, ctypes.c_int, f64p]
         lib.orc_integrate.restype = ctypes.c_int
         lib.orc_integrate.argtypes = ([ctypes.c_int] * 4 + [i32p, f64p, f64p, ctypes.c_double,
                                       ctypes.c_long, ctypes.c_int, ctypes.c_int, f64p])
@@ -120,6 +122,22 @@ def rhs(n, D: int, ranks, factors, *, fmt: int = CP, mode: int = DIRECT, sym: in
     if rc != 0:
         raise ValueError(f"orc_rhs failed ({rc})")
     return (p, q, float(o[0])) if outflow else (p, q)
+
+
+def loss(n, D: int, ranks, factors, *, fmt: int = CP, sym: int = 1):
+    """Q = sum_d Q^(d)[n] alone (inner products only; cheap at any N)."""
+    n, np_ = _f64(n)
+    N = n.shape[0]
+    r, rp = _i32(ranks)
+    f, fp = _f64(factors)
+    if f.size != factor_count(fmt, D, N, r):
+        raise ValueError("factor array has the wrong length")
+    q = np.zeros(N)
+    rc = _load().orc_loss(fmt, D, N, rp, fp, np_, sym,
+                          q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError(f"orc_loss failed ({rc})")
+    return q
 
 
 def integrate(n0, D: int, ranks, factors, dt: float, steps: int, *, fmt: int = CP,

@@ -256,16 +256,13 @@ static void scatter_gain(const double* g, int lg, int N, double inv_dfact, nsum*
   }
 }
 
-static void rhs_direct_cp_order(int N, int R, const double* blk, int d, const double* n, int sym,
-                                nsum* p, nsum* q, nsum* out) {
+static void gain_cp_order(int N, int R, const double* blk, int d, const double* n, nsum* p,
+                          nsum* out) {
   const double inv_dfact = 1.0 / factorial(d);
-  const double inv_d1fact = 1.0 / factorial(d - 1);
   const int Lmax = out ? d * N : N;
   double* a = (double*)malloc(sizeof(double) * N);
   double* b = (double*)malloc(sizeof(double) * Lmax);
   double* c = (double*)malloc(sizeof(double) * Lmax);
-  double* s = (double*)malloc(sizeof(double) * d);
-  double* w = (double*)calloc(N, sizeof(double));
   for (int r = 0; r < R; ++r) {
     /* Gain: a^(1) * a^(2) * ... * a^(d), a^(m) = U^(m)_r o n. */
     const double* u1 = cp_vec(blk, R, N, 0, r);
@@ -280,9 +277,18 @@ static void rhs_direct_cp_order(int N, int R, const double* blk, int d, const do
       lb = lc;
     }
     scatter_gain(b, lb, N, inv_dfact, p, out);
+  }
+  free(a); free(b); free(c);
+}
 
-    /* Loss: s_m = <U^(m)_r, n>; the kernel row through k is a sum over the
-     * position k takes (sym) or the last mode only (literal). */
+/* Loss of a CP order: s_m = <U^(m)_r, n>; the kernel row through k is a sum
+ * over the position k takes (sym) or the last mode only (literal). */
+static void loss_cp_order(int N, int R, const double* blk, int d, const double* n, int sym,
+                          nsum* q) {
+  const double inv_d1fact = 1.0 / factorial(d - 1);
+  double* s = (double*)malloc(sizeof(double) * d);
+  double* w = (double*)calloc(N, sizeof(double));
+  for (int r = 0; r < R; ++r) {
     for (int m = 0; m < d; ++m) s[m] = dot_n(cp_vec(blk, R, N, m, r), n, N);
     for (int m = (sym ? 0 : d - 1); m < d; ++m) {
       double coef = 1.0;
@@ -294,13 +300,12 @@ static void rhs_direct_cp_order(int N, int R, const double* blk, int d, const do
     }
   }
   for (int k = 0; k < N; ++k) ns_add(&q[k], -n[k] * inv_d1fact * w[k]);
-  free(a); free(b); free(c); free(s); free(w);
+  free(s); free(w);
 }
 
-static void rhs_direct_tt_order(int N, const int* rk, const double* blk, int d, const double* n,
-                                int sym, nsum* p, nsum* q, nsum* out) {
+static void gain_tt_order(int N, const int* rk, const double* blk, int d, const double* n, nsum* p,
+                          nsum* out) {
   const double inv_dfact = 1.0 / factorial(d);
-  const double inv_d1fact = 1.0 / factorial(d - 1);
   const int Lmax = out ? d * N : N;
   int rmax = 1;
   for (int l = 0; l <= d; ++l) rmax = rk[l] > rmax ? rk[l] : rmax;
@@ -330,9 +335,16 @@ static void rhs_direct_tt_order(int N, const int* rk, const double* blk, int d, 
     lv = lw;
   }
   scatter_gain(V, lv, N, inv_dfact, p, out);
+  free(V); free(W); free(a); free(c);
+}
 
-  /* Loss: M_l = sum_i n_i H^(l)(i) (R_{l-1} x R_l); for k at position pos the
-   * kernel sum is M_1 ... M_{pos-1} H^(pos)(k) M_{pos+1} ... M_d. */
+/* Loss of a TT order: M_l = sum_i n_i H^(l)(i) (R_{l-1} x R_l); for k at
+ * position pos the kernel sum is M_1 ... M_{pos-1} H^(pos)(k) M_{pos+1} ... M_d. */
+static void loss_tt_order(int N, const int* rk, const double* blk, int d, const double* n, int sym,
+                          nsum* q) {
+  const double inv_d1fact = 1.0 / factorial(d - 1);
+  int rmax = 1;
+  for (int l = 0; l <= d; ++l) rmax = rk[l] > rmax ? rk[l] : rmax;
   double* M = (double*)malloc(sizeof(double) * (size_t)d * rmax * rmax);
   for (int l = 1; l <= d; ++l)
     for (int aa = 0; aa < rk[l - 1]; ++aa)
@@ -370,7 +382,7 @@ static void rhs_direct_tt_order(int N, const int* rk, const double* blk, int d, 
       }
   }
   for (int k = 0; k < N; ++k) ns_add(&q[k], -n[k] * inv_d1fact * wsum[k]);
-  free(V); free(W); free(a); free(c); free(M); free(wsum);
+  free(M); free(wsum);
 }
 
 int orc_rhs(int mode, int fmt, int D, int N, const int* ranks, const double* factors,
@@ -393,14 +405,43 @@ int orc_rhs(int mode, int fmt, int D, int N, const int* ranks, const double* fac
     const double* blk = factors + order_offset(fmt, N, ranks, d, &rk);
     if (mode == ORC_BRUTE)
       rhs_brute_order(fmt, N, rk, blk, d, n, sym, ps, qs, outflow ? &os : NULL);
-    else if (fmt == ORC_CP)
-      rhs_direct_cp_order(N, rk[0], blk, d, n, sym, ps, qs, outflow ? &os : NULL);
-    else
-      rhs_direct_tt_order(N, rk, blk, d, n, sym, ps, qs, outflow ? &os : NULL);
+    else if (fmt == ORC_CP) {
+      gain_cp_order(N, rk[0], blk, d, n, ps, outflow ? &os : NULL);
+      loss_cp_order(N, rk[0], blk, d, n, sym, qs);
+    } else {
+      gain_tt_order(N, rk, blk, d, n, ps, outflow ? &os : NULL);
+      loss_tt_order(N, rk, blk, d, n, sym, qs);
+    }
   }
   for (int k = 0; k < N; ++k) { p[k] = ns_val(&ps[k]); q[k] = ns_val(&qs[k]); }
   if (outflow) *outflow = ns_val(&os);
   free(ps); free(qs);
+  return 0;
+}
+
+static int tt_ranks_small(int fmt, int D, const int* ranks) {
+  if (fmt != ORC_TT) return 1;
+  const int* rk = ranks;
+  for (int d = 2; d <= D; ++d) {
+    for (int l = 0; l <= d; ++l)
+      if (rk[l] > 128) return 0;
+    rk += d + 1;
+  }
+  return 1;
+}
+
+int orc_loss(int fmt, int D, int N, const int* ranks, const double* factors, const double* n,
+             int sym, double* q) {
+  if (!ranks_ok(fmt, D, N, ranks) || !factors || !n || !q || !tt_ranks_small(fmt, D, ranks)) return -1;
+  nsum* qs = (nsum*)calloc(N, sizeof(nsum));
+  for (int d = 2; d <= D; ++d) {
+    const int* rk;
+    const double* blk = factors + order_offset(fmt, N, ranks, d, &rk);
+    if (fmt == ORC_CP) loss_cp_order(N, rk[0], blk, d, n, sym, qs);
+    else loss_tt_order(N, rk, blk, d, n, sym, qs);
+  }
+  for (int k = 0; k < N; ++k) q[k] = ns_val(&qs[k]);
+  free(qs);
   return 0;
 }
 

@@ -45,6 +45,11 @@ double orc_kernel_entry(int fmt, int D, int N, const int* ranks, const double* f
 int orc_rhs(int mode, int fmt, int D, int N, const int* ranks, const double* factors,
             const double* n, int sym, double* p, double* q, double* outflow);
 
+/* Loss part only, q = sum_d Q^(d)[n] (length N), in O(N sum_d d R_d) for CP.
+ * Same definition and sym flag as orc_rhs. */
+int orc_loss(int fmt, int D, int N, const int* ranks, const double* factors, const double* n,
+             int sym, double* q);
+
 /* `steps` explicit RK2 steps of size dt on n (in place). diag (nullable)
  * receives [steps+1][3] = (M0, M1, cumulative outflow mass) after each step,
  * row 0 for the initial state. */

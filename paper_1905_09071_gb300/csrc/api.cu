@@ -62,6 +62,29 @@ void unit_root(int64_t k, int64_t P, double& c, double& s) {
 
 }  // namespace
 
+// Records one CUDA event before each kernel launch and one after the last.
+struct EventHook : LaunchHook {
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  bool failed = false;
+  void mark(int id, cudaStream_t st) override {
+    if (marks.size() == pool.size()) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) {
+        failed = true;
+        return;
+      }
+      pool.push_back(ev);
+    }
+    cudaEvent_t ev = pool[marks.size()];
+    if (cudaEventRecord(ev, st) != cudaSuccess) failed = true;
+    marks.emplace_back(id, ev);
+  }
+  ~EventHook() override {
+    for (cudaEvent_t ev : pool) cudaEventDestroy(ev);
+  }
+};
+
 struct sag_plan_s {
   RhsParams P{};
   LaunchCfg L{};
@@ -78,6 +101,8 @@ struct sag_plan_s {
   double* stage_diag = nullptr;
   size_t stage_diag_len = 0;
   cudaStream_t cap_stream = nullptr;
+  bool prof = false;
+  EventHook hook;
   cudaGraphExec_t gexec = nullptr;
   const double* g_n = nullptr;
   double g_dt = 0.0;
@@ -346,21 +371,22 @@ struct Staged {
   double* out;
 };
 
-sag_status eval(sag_plan_t pl, const double* nin, EpiArgs A, cudaStream_t st) {
+sag_status eval(sag_plan_t pl, const double* nin, EpiArgs A, cudaStream_t st, bool allow_hook = true) {
   A.part = pl->epi_part;
-  cudaError_t e = enqueue_eval(pl->P, pl->L, nin, A, st);
+  cudaError_t e = enqueue_eval(pl->P, pl->L, nin, A, st, (pl->prof && allow_hook) ? &pl->hook : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return SAG_OK;
 }
 
-sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaStream_t st) {
+sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaStream_t st,
+                        bool allow_hook) {
   EpiArgs a{};
   a.nin = n;
   a.k1buf = pl->k1buf;
   a.out0 = pl->nstar;
   a.dt = dt;
   a.mode = pl->rk == SAG_HEUN ? EPI_HEUN1 : EPI_MID1;
-  sag_status s = eval(pl, n, a, st);
+  sag_status s = eval(pl, n, a, st, allow_hook);
   if (s != SAG_OK) return s;
   EpiArgs b{};
   b.nin = pl->nstar;
@@ -369,7 +395,7 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
   b.diag = diag;
   b.dt = dt;
   b.mode = pl->rk == SAG_HEUN ? EPI_HEUN2 : EPI_MID2;
-  return eval(pl, pl->nstar, b, st);
+  return eval(pl, pl->nstar, b, st, allow_hook);
 }
 
 }  // namespace
@@ -494,7 +520,7 @@ sag_status sag_rk2_step(sag_plan_t pl, double* n, double dt, void* stream) {
       return cuda_fail(e, "copy n");
     nd = pl->stage_a;
   }
-  sag_status s = enqueue_step(pl, nd, dt, nullptr, st);
+  sag_status s = enqueue_step(pl, nd, dt, nullptr, st, true);
   if (s != SAG_OK) return s;
   if (h) {
     if ((e = cudaMemcpyAsync(n, pl->stage_a, nb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -544,7 +570,7 @@ sag_status sag_integrate(sag_plan_t pl, double* n, double dt, int64_t steps, dou
       cudaGraph_t g = nullptr;
       if ((e = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "begin capture");
-      sag_status s = enqueue_step(pl, nd, dt, dd, pl->cap_stream);
+      sag_status s = enqueue_step(pl, nd, dt, dd, pl->cap_stream, false);
       e = cudaStreamEndCapture(pl->cap_stream, &g);
       if (s != SAG_OK) {
         if (g) cudaGraphDestroy(g);
@@ -585,6 +611,177 @@ sag_status sag_sync_status(sag_plan_t pl, void* stream) {
     if (status & kStatusTimeout) return fail(SAG_ETIMEOUT, "a device-side wait timed out");
     return fail(SAG_ENONFINITE, "the right-hand side produced Inf or NaN");
   }
+  return SAG_OK;
+}
+
+sag_status sag_profile_enable(sag_plan_t pl, int32_t on) {
+  if (!pl) return fail(SAG_EINVAL, "NULL plan");
+  pl->prof = on != 0;
+  return SAG_OK;
+}
+
+sag_status sag_profile_read(sag_plan_t pl, double* ms, int64_t* launches, int32_t n) {
+  if (!pl || (n > 0 && (!ms || !launches))) return fail(SAG_EINVAL, "NULL argument");
+  EventHook& h = pl->hook;
+  if (h.failed) {
+    h.marks.clear();
+    h.failed = false;
+    return fail(SAG_ECUDA, "event record failed while profiling");
+  }
+  if (!h.marks.empty()) {
+    cudaError_t e = cudaEventSynchronize(h.marks.back().second);
+    if (e != cudaSuccess) return cuda_fail(e, "event sync");
+  }
+  for (size_t i = 0; i + 1 < h.marks.size(); ++i) {
+    const int id = h.marks[i].first;
+    if (id < 0 || id >= n) continue;
+    float t = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&t, h.marks[i].second, h.marks[i + 1].second);
+    if (e != cudaSuccess) return cuda_fail(e, "event elapsed time");
+    ms[id] += t;
+    launches[id] += 1;
+  }
+  h.marks.clear();
+  return SAG_OK;
+}
+
+// Operation counts of the double-word arithmetic (FP32 instructions), as
+// written in dw.cuh: dw_add 11, dw_mul 7, one component of a complex product
+// (dot2) 19, so a complex add 22, a complex product 38, a real double-word
+// constant times a complex 14, a power-of-two scale 4. FP64 arithmetic: a
+// complex add 2, a complex product 4 (2 multiplies, 2 FMAs), a real times a
+// complex 2.
+struct OpCost {
+  double cadd, cmul, kmul, scale;
+};
+static constexpr OpCost kCostDW{22, 38, 14, 4};
+static constexpr OpCost kCostF64{2, 4, 2, 2};
+
+static double dft_ops(int R, const OpCost& c) {
+  switch (R) {
+    case 2: return 2 * c.cadd;
+    case 3: return 6 * c.cadd + c.kmul + c.scale;
+    case 4: return 8 * c.cadd;
+    case 5: return 16 * c.cadd + 8 * c.kmul;
+    default: return 26 * c.cadd + 2 * c.kmul;  // radix 8: 8 + 2 + 16 adds, 2 constant products
+  }
+}
+
+// One length-P transform with the given radix schedule.
+static double fft_ops(int P, const radix_plan& rp, const OpCost& c) {
+  double ops = 0.0;
+  int Ns = 1;
+  for (int s = 0; s < rp.n; ++s) {
+    const int R = rp.r[s];
+    ops += (double)(P / R) * (dft_ops(R, c) + (Ns > 1 ? (R - 1) * c.cmul : 0.0));
+    Ns *= R;
+  }
+  return ops;
+}
+
+const char* sag_kernel_name(int32_t id) {
+  static const char* names[KID_COUNT] = {"k_nmax", "k_nsplit", "k_dot", "k_fwd_col",
+                                         "k_rows", "k_inv_col", "k_epilogue", "k_moments"};
+  return (id >= 0 && id < KID_COUNT) ? names[id] : nullptr;
+}
+
+sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_fp64, double* bytes) {
+  if (!pl || !ops || !ops_fp64 || !bytes) return fail(SAG_EINVAL, "NULL argument");
+  if (id < 0 || id >= KID_COUNT) return fail(SAG_EINVAL, "kernel id out of range");
+  const RhsParams& P = pl->P;
+  const bool dwp = P.dwpath != 0;
+  const OpCost& c = dwp ? kCostDW : kCostF64;
+  const double N = P.N, V = P.Vtot;
+  const double load_mul = dwp ? 7.0 : 1.0;  // a = U n: dw_mul or one FP64 multiply
+  double o = 0.0, b = 0.0;
+  int fp64 = dwp ? 0 : 1;
+  switch (id) {
+    case KID_NMAX:
+      o = 2 * N;
+      b = 8 * N;
+      fp64 = 1;
+      break;
+    case KID_NSPLIT:
+      o = 4 * N;
+      b = 16 * N;
+      fp64 = 1;
+      break;
+    case KID_DOT:  // u n, sum, k (u n) + t
+      o = 3 * V * N;
+      b = 8 * V * N + 8 * N;
+      fp64 = 1;
+      break;
+    case KID_FWD_COL:
+      for (int i = 0; i < P.nord; ++i) {
+        const OrderDesc& od = P.ord[i];
+        const double Vd = (double)od.d * od.R;
+        o += Vd * (od.M2 * fft_ops(od.M1, od.rp1, c) + (double)od.M * c.cmul +
+                   2.0 * std::min<double>(od.M, N) * load_mul);
+      }
+      b = (dwp ? 8.0 : 8.0) * V * N + (dwp ? 8.0 : 8.0) * N;
+      break;
+    case KID_ROWS:
+      for (int i = 0; i < P.nord; ++i) {
+        const OrderDesc& od = P.ord[i];
+        const double Vd = (double)od.d * od.R, M = od.M;
+        const double unpack = 4 * c.cadd + c.cmul;
+        const double repack = 4 * c.cadd + c.cmul;
+        o += Vd * od.M1 * fft_ops(od.M2, od.rp2, c)            // forward rows of every vector
+             + Vd * M * unpack                                   // real split
+             + (Vd - od.R) * M * c.cmul                          // product over the modes
+             + (double)od.R * M * (c.cadd + (dwp ? c.scale : 0)) // rank sum
+             + M * repack + od.M1 * fft_ops(od.M2, od.rp2, c)    // inverse rows
+             + M * c.cmul;                                       // four-step twiddle
+      }
+      b = 0.0;  // reads and writes only the FFT workspace
+      break;
+    case KID_INV_COL:
+      for (int i = 0; i < P.nord; ++i) {
+        const OrderDesc& od = P.ord[i];
+        o += od.M2 * fft_ops(od.M1, od.rp1, c);
+      }
+      b = 8.0 * P.nord * N;  // P^(d) written
+      break;
+    case KID_EPILOGUE:  // w = sum_v coef_v U_v(k); rhs = p + n w; stage update
+      o = V * N + (P.nord + 6) * N;
+      b = 8 * V * N + 8 * P.nord * N + 3 * 8 * N;
+      fp64 = 1;
+      break;
+    case KID_MOMENTS:
+      o = 3 * N;
+      b = 8 * N;
+      fp64 = 1;
+      break;
+  }
+  *ops = o;
+  *ops_fp64 = fp64;
+  *bytes = b;
+  return SAG_OK;
+}
+
+sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
+  if (!pl || !buf || len == 0) return fail(SAG_EINVAL, "NULL argument");
+  const RhsParams& P = pl->P;
+  std::string js = "{\"N\": " + std::to_string(P.N) + ", \"D\": " + std::to_string(P.D) +
+                   ", \"precision\": \"" + (P.dwpath ? "fp32_split" : "fp64") + "\", \"orders\": [";
+  for (int i = 0; i < P.nord; ++i) {
+    const OrderDesc& od = P.ord[i];
+    auto rps = [](const radix_plan& rp) {
+      std::string r = "[";
+      for (int s = 0; s < rp.n; ++s) r += (s ? ", " : "") + std::to_string(rp.r[s]);
+      return r + "]";
+    };
+    js += std::string(i ? ", " : "") + "{\"d\": " + std::to_string(od.d) + ", \"R\": " +
+          std::to_string(od.R) + ", \"L\": " + std::to_string(od.L) + ", \"M1\": " +
+          std::to_string(od.M1) + ", \"M2\": " + std::to_string(od.M2) + ", \"radix_M1\": " +
+          rps(od.rp1) + ", \"radix_M2\": " + rps(od.rp2) + ", \"W\": " + std::to_string(od.W) +
+          ", \"G\": " + std::to_string(od.G) + "}";
+  }
+  js += "], \"blocks\": {\"fwd_col\": " + std::to_string(pl->L.col_blocks) + ", \"rows\": " +
+        std::to_string(pl->L.row_blocks) + ", \"inv_col\": " + std::to_string(pl->L.inv_blocks) +
+        ", \"epilogue\": " + std::to_string(pl->L.epi_blocks) + "}, \"device_bytes\": " +
+        std::to_string(pl->bytes) + "}";
+  std::snprintf(buf, len, "%s", js.c_str());
   return SAG_OK;
 }
 

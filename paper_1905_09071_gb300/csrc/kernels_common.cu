@@ -242,15 +242,20 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ n, i
 
 // ---- launch of one evaluation ---------------------------------------------
 cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
-                         const EpiArgs& A, cudaStream_t st) {
+                         const EpiArgs& A, cudaStream_t st, LaunchHook* hook) {
   if (P.dwpath) {
+    if (hook) hook->mark(KID_NMAX, st);
     k_nmax<<<L.prep_blocks, 256, 0, st>>>(nin, P.N, P.sc);
+    if (hook) hook->mark(KID_NSPLIT, st);
     k_nsplit<<<L.prep_blocks, 256, 0, st>>>(nin, P.N, P.sc, P.ndw);
   }
+  if (hook) hook->mark(KID_DOT, st);
   k_dot<<<dim3(P.ndotchunk, P.Vtot), 256, 0, st>>>(P, nin);
-  cudaError_t e = P.dwpath ? enqueue_fft_dw(P, L, nin, st) : enqueue_fft_f64(P, L, nin, st);
+  cudaError_t e = P.dwpath ? enqueue_fft_dw(P, L, nin, st, hook) : enqueue_fft_f64(P, L, nin, st, hook);
   if (e != cudaSuccess) return e;
+  if (hook) hook->mark(KID_EPILOGUE, st);
   k_epilogue<<<L.epi_blocks, 256, L.epi_smem, st>>>(P, A);
+  if (hook) hook->mark(-1, st);
   return cudaGetLastError();
 }
 

@@ -4,9 +4,13 @@
 
 namespace sag {
 
-cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
+cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
+                           LaunchHook* hook) {
+  if (hook) hook->mark(KID_FWD_COL, st);
   k_fwd_col<cdw><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin);
+  if (hook) hook->mark(KID_ROWS, st);
   k_rows<cdw><<<L.row_blocks, kThreads, L.row_smem, st>>>(P);
+  if (hook) hook->mark(KID_INV_COL, st);
   k_inv_col<cdw><<<L.inv_blocks, kThreads, L.inv_smem, st>>>(P);
   return cudaGetLastError();
 }

@@ -29,11 +29,26 @@ struct EpiArgs {
   int mode;
 };
 
+// Kernel ids for profiling (order of sag_kernel_name).
+enum KernelId : int {
+  KID_NMAX = 0, KID_NSPLIT = 1, KID_DOT = 2, KID_FWD_COL = 3, KID_ROWS = 4, KID_INV_COL = 5,
+  KID_EPILOGUE = 6, KID_MOMENTS = 7, KID_COUNT = 8
+};
+
+// Optional hook called before each kernel launch (id) and once after the last
+// one (id = -1), on the launch stream.
+struct LaunchHook {
+  virtual void mark(int id, cudaStream_t st) = 0;
+  virtual ~LaunchHook() = default;
+};
+
 cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
-                         const EpiArgs& A, cudaStream_t st);
+                         const EpiArgs& A, cudaStream_t st, LaunchHook* hook = nullptr);
 cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, cudaStream_t st);
-cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
-cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
+                            LaunchHook* hook);
+cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
+                           LaunchHook* hook);
 cudaError_t setup_common_kernels(const LaunchCfg& L);
 cudaError_t setup_fft_kernels_f64(const LaunchCfg& L);
 cudaError_t setup_fft_kernels_dw(const LaunchCfg& L);

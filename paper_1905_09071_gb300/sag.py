@@ -25,8 +25,10 @@ SAG_HEUN, SAG_MIDPOINT = 0, 1
 EXPORTS = [
     "sag_default_options", "sag_plan", "sag_plan_layout", "sag_plan_bytes", "sag_rhs",
     "sag_rhs_parts", "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_plan_destroy",
-    "sag_last_error", "sag_version",
+    "sag_last_error", "sag_version", "sag_profile_enable", "sag_profile_read", "sag_kernel_name",
+    "sag_kernel_work", "sag_plan_describe",
 ]
+SAG_NUM_KERNELS = 8
 
 _STATUS_NAMES = {0: "SAG_OK", 1: "SAG_EINVAL", 2: "SAG_ENOMEM", 3: "SAG_ECUDA",
                  4: "SAG_EUNSUPPORTED", 5: "SAG_ETIMEOUT", 6: "SAG_ENONFINITE"}
@@ -83,8 +85,16 @@ def load(build_if_missing: bool = True):
         lib.sag_plan_destroy.restype = None
         lib.sag_last_error.restype = ctypes.c_char_p
         lib.sag_version.restype = ctypes.c_char_p
+        lib.sag_profile_enable.argtypes = [vp, i32]
+        lib.sag_profile_read.argtypes = [vp, ctypes.POINTER(f64), ctypes.POINTER(i64), i32]
+        lib.sag_kernel_name.argtypes = [i32]
+        lib.sag_kernel_name.restype = ctypes.c_char_p
+        lib.sag_kernel_work.argtypes = [vp, i32, ctypes.POINTER(f64), ctypes.POINTER(i32),
+                                        ctypes.POINTER(f64)]
+        lib.sag_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         for name in ("sag_plan", "sag_plan_layout", "sag_plan_bytes", "sag_rhs", "sag_rhs_parts",
-                     "sag_rk2_step", "sag_integrate", "sag_sync_status"):
+                     "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_profile_enable",
+                     "sag_profile_read", "sag_kernel_work", "sag_plan_describe"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -189,6 +199,35 @@ class Plan:
         """Returns the latched device status (SAG_OK, SAG_ENONFINITE, ...), clearing it."""
         st = self._lib.sag_sync_status(self._h, _stream(stream))
         return int(st)
+
+    def profile(self, on: bool = True):
+        """Turns per-kernel event timing on or off (non-graph launches only)."""
+        _check(self._lib.sag_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last read; waits for the work."""
+        ms = (ctypes.c_double * SAG_NUM_KERNELS)()
+        cnt = (ctypes.c_int64 * SAG_NUM_KERNELS)()
+        _check(self._lib.sag_profile_read(self._h, ms, cnt, SAG_NUM_KERNELS))
+        return {self._lib.sag_kernel_name(i).decode(): (ms[i], cnt[i])
+                for i in range(SAG_NUM_KERNELS) if cnt[i]}
+
+    def kernel_work(self, name_or_id) -> dict:
+        """Algorithmic ops (FP32 or FP64 instructions) and HBM bytes of one launch."""
+        kid = name_or_id
+        if isinstance(name_or_id, str):
+            names = [self._lib.sag_kernel_name(i).decode() for i in range(SAG_NUM_KERNELS)]
+            kid = names.index(name_or_id)
+        ops, f64, b = ctypes.c_double(), ctypes.c_int32(), ctypes.c_double()
+        _check(self._lib.sag_kernel_work(self._h, int(kid), ctypes.byref(ops), ctypes.byref(f64),
+                                         ctypes.byref(b)))
+        return {"ops": ops.value, "ops_fp64": bool(f64.value), "bytes": b.value}
+
+    def describe(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(8192)
+        _check(self._lib.sag_plan_describe(self._h, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

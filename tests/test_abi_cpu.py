@@ -1,0 +1,88 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every function
+include/sag.h declares, and rejects bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1905_09071_gb300 import sag
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sag.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(sag_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return sag.load()
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(sag.EXPORTS)
+
+
+def test_library_exports_every_declared_function(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_defaults(lib):
+    assert b"sm_103a" in lib.sag_version()
+    assert sag.default_options() == {"prec": sag.SAG_FP32_SPLIT, "rk": sag.SAG_HEUN,
+                                     "symmetrize_q": 1}
+
+
+def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=True, out=True):
+    lib = sag.load()
+    r = np.array(ranks, dtype=np.int32)
+    f = np.ones(1024)
+    s = sag._System(N, D, fmt, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                    f.ctypes.data if factors else None, 0)
+    o = sag._Options(*(opt or (sag.SAG_FP32_SPLIT, sag.SAG_HEUN, 1, 0)))
+    h = ctypes.c_void_p()
+    st = lib.sag_plan(ctypes.byref(s), B, ctypes.byref(o), ctypes.byref(h) if out else None)
+    return st, lib.sag_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(N=0), sag.SAG_EINVAL),
+    (dict(D=1, ranks=()), sag.SAG_EINVAL),
+    (dict(D=9, ranks=(1,) * 7), sag.SAG_EINVAL),
+    (dict(ranks=(2, 0)), sag.SAG_EINVAL),
+    (dict(fmt=7), sag.SAG_EINVAL),
+    (dict(B=0), sag.SAG_EINVAL),
+    (dict(factors=False), sag.SAG_EINVAL),
+    (dict(out=False), sag.SAG_EINVAL),
+    (dict(opt=(9, 0, 1, 0)), sag.SAG_EINVAL),
+    (dict(opt=(0, 4, 1, 0)), sag.SAG_EINVAL),
+    (dict(opt=(0, 0, 2, 0)), sag.SAG_EINVAL),
+    (dict(B=2), sag.SAG_EUNSUPPORTED),
+])
+def test_plan_rejects_bad_arguments(kw, status):
+    st, msg = _plan_status(**kw)
+    assert st == status
+    assert msg
+
+
+def test_null_plan_calls_are_rejected(lib):
+    x = np.zeros(4)
+    assert lib.sag_rhs(None, x.ctypes.data, x.ctypes.data, None) == sag.SAG_EINVAL
+    assert lib.sag_rk2_step(None, x.ctypes.data, 0.1, None) == sag.SAG_EINVAL
+    assert lib.sag_integrate(None, x.ctypes.data, 0.1, 1, None, None) == sag.SAG_EINVAL
+    assert lib.sag_rhs_parts(None, x.ctypes.data, None, None, None, None) == sag.SAG_EINVAL
+    assert lib.sag_sync_status(None, None) == sag.SAG_EINVAL
+    lib.sag_plan_destroy(None)
+
+
+def test_binding_raises_typed_error():
+    with pytest.raises(sag.SagError) as ei:
+        sag.Plan(0, 3, [1, 1], np.ones(10))
+    assert ei.value.status == sag.SAG_EINVAL

@@ -1,0 +1,305 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Error metric (normwise, as the gain and loss parts can cancel):
+    err = max_k |x_k - x_ref_k| / (max |P_ref| + max |Q_ref|).
+Tolerances: FP64 path 1e-12, double-word FP32 path 1e-10. Trajectories are
+compared relative to max |n_ref|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_09071_gb300 import sag, workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {sag.SAG_FP64: 1e-12, sag.SAG_FP32_SPLIT: 1e-10}
+PRECS = [sag.SAG_FP64, sag.SAG_FP32_SPLIT]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(x):
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def gpu_parts(s, n0, prec, sym=1, rk=sag.SAG_HEUN):
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, symmetrize_q=sym, rk=rk) as pl:
+        n = dev(n0)
+        p, q = torch.empty_like(n), torch.empty_like(n)
+        o = torch.zeros(1, dtype=torch.float64, device="cuda")
+        pl.rhs_parts(n, p, q, o)
+        out = torch.empty_like(n)
+        pl.rhs(n, out)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+        return p.cpu().numpy(), q.cpu().numpy(), float(o.item()), out.cpu().numpy()
+
+
+def nerr(x, ref, scale):
+    return float(np.max(np.abs(np.asarray(x) - ref)) / scale)
+
+
+# ------------------------------------------------------------------ RHS parity
+SMALL = [
+    ("D2_N1", lambda: wl.random_cp(2, 1, [2], seed=1)),
+    ("D3_N2", lambda: wl.random_cp(3, 2, [1, 2], seed=2)),
+    ("D4_N3", lambda: wl.random_cp(4, 3, [2, 1, 2], seed=3)),
+    ("D2_N9", lambda: wl.random_cp(2, 9, [3], seed=4)),
+    ("D3_N7", lambda: wl.random_cp(3, 7, [2, 3], seed=5)),
+    ("D4_N5", lambda: wl.random_cp(4, 5, [2, 2, 3], seed=6)),
+    ("D6_N3", lambda: wl.random_cp(6, 3, [1, 2, 1, 1, 2], seed=7)),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("sym", [0, 1])
+@pytest.mark.parametrize("name,make", SMALL)
+def test_rhs_matches_brute_force(name, make, sym, prec):
+    s = make()
+    p_ref, q_ref, o_ref = oracle.rhs(s.n0, s.D, s.ranks, s.factors, mode=oracle.BRUTE, sym=sym,
+                                     outflow=True)
+    scale = np.abs(p_ref).max() + np.abs(q_ref).max()
+    p, q, o, r = gpu_parts(s, s.n0, prec, sym)
+    assert nerr(p, p_ref, scale) < TOL[prec]
+    assert nerr(q, q_ref, scale) < TOL[prec]
+    assert nerr(r, p_ref + q_ref, scale) < TOL[prec]
+    # outflow is a difference of two first-moment fluxes of size ~ sum k |P_k|
+    flux = np.sum(np.arange(1, s.N + 1) * np.abs(p_ref)) + abs(o_ref) + 1e-300
+    assert abs(o - o_ref) <= 1e3 * TOL[prec] * flux
+
+
+MEDIUM = [
+    ("D3_N100_ragged", lambda: wl.random_cp(3, 100, [3, 4], seed=8)),
+    ("D4_N333_ragged", lambda: wl.random_cp(4, 333, [2, 3, 2], seed=9)),
+    ("D2_N1000_R40", lambda: wl.random_cp(2, 1000, [40], seed=10)),
+    ("D4_N1537_ragged", lambda: wl.random_cp(4, 1537, [3, 2, 2], seed=11)),
+    ("brownian_D3_N4096", lambda: wl.brownian_cp(3, 4096)),
+    ("D8_N40", lambda: wl.random_cp(8, 40, [2, 1, 1, 2, 1, 1, 2], seed=17)),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name,make", MEDIUM)
+def test_rhs_matches_direct_oracle(name, make, prec):
+    s = make()
+    p_ref, q_ref = oracle.rhs(s.n0, s.D, s.ranks, s.factors, mode=oracle.DIRECT)
+    scale = np.abs(p_ref).max() + np.abs(q_ref).max()
+    p, q, _, r = gpu_parts(s, s.n0, prec)
+    assert nerr(p, p_ref, scale) < TOL[prec]
+    assert nerr(q, q_ref, scale) < TOL[prec]
+    assert nerr(r, p_ref + q_ref, scale) < TOL[prec]
+
+
+def _prefix(s, K):
+    """The same kernel restricted to sizes 1..K: its gain term equals the full
+    system's gain term at every size k <= K."""
+    offs = wl.cp_layout(s.D, s.N, s.ranks)
+    per = {}
+    for d in range(2, s.D + 1):
+        R = s.ranks[d - 2]
+        per[d] = s.factors[offs[d - 2]:offs[d - 1]].reshape(d, R, s.N)[:, :, :K]
+    ranks, f = wl.cp_from_vectors(s.D, K, per)
+    return ranks, f
+
+
+@pytest.fixture(scope="module")
+def throughput_case():
+    s = wl.random_power_cp()  # D=4, N=65536, R=16: the throughput workload
+    K = 2048
+    ranks_k, f_k = _prefix(s, K)
+    p_pre, _ = oracle.rhs(s.n0[:K], s.D, ranks_k, f_k, mode=oracle.DIRECT)
+    q_ref = oracle.loss(s.n0, s.D, s.ranks, s.factors)
+    return s, K, p_pre, q_ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_sampled_parity(throughput_case, prec):
+    # N = 65536: every gain output k <= 2048 against the oracle on the prefix
+    # system, every loss output against the oracle's inner-product route.
+    s, K, p_pre, q_ref = throughput_case
+    p, q, _, r = gpu_parts(s, s.n0, prec)
+    scale = np.abs(p).max() + np.abs(q_ref).max()
+    assert np.abs(p).max() <= 1.0001 * np.abs(p_pre).max() + 1e-300  # the maximum is in the prefix
+    assert nerr(p[:K], p_pre, scale) < TOL[prec]
+    assert nerr(q, q_ref, scale) < TOL[prec]
+    assert nerr(r[:K], p_pre + q_ref[:K], scale) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("kernel", ["constant", "product"])
+def test_full_length_fft_geometric_closed_form(kernel, prec):
+    # n_k = A r^(k-1) at N = 65536, D = 4 (FFT lengths 2^17, 3 2^16, 2^18):
+    # constant kernel p_k^(d) = A^d r^(k-d) binom(k-1, d-1)/d!,
+    # product kernel C = prod i_m: p_k^(d) = A^d r^(k-d) binom(k+d-1, 2d-1)/d!.
+    N, D, A, rr = 65536, 4, 1e-4, 0.9999
+    k = np.arange(1, N + 1, dtype=np.float64)
+    n0 = A * rr ** (k - 1)
+    vec = np.ones(N) if kernel == "constant" else k.copy()
+    per = {d: np.broadcast_to(vec, (d, 1, N)).copy() for d in range(2, D + 1)}
+    ranks, f = wl.cp_from_vectors(D, N, per)
+    s = wl.System(D, N, "cp", ranks, f, n0)
+    p, q, _, _ = gpu_parts(s, n0, prec)
+    def binom(a, b):  # exact products for the small b used here
+        out = np.ones_like(a)
+        for i in range(b):
+            out = out * (a - i) / (i + 1)
+        return out
+
+    p_ref = np.zeros(N)
+    for d in range(2, D + 1):
+        kk = k[d - 1:]
+        b = binom(kk - 1, d - 1) if kernel == "constant" else binom(kk + d - 1, 2 * d - 1)
+        p_ref[d - 1:] += A ** d * rr ** (kk - d) * b / math.factorial(d)
+    if kernel == "constant":
+        M = n0.sum()
+        q_ref = sum(-n0 * M ** (d - 1) / math.factorial(d - 1) for d in range(2, D + 1))
+    else:
+        M1 = (k * n0).sum()
+        q_ref = sum(-n0 * k * M1 ** (d - 1) / math.factorial(d - 1) for d in range(2, D + 1))
+    scale = np.abs(p_ref).max() + np.abs(q_ref).max()
+    assert nerr(p, p_ref, scale) < max(TOL[prec], 1e-11)
+    assert nerr(q, q_ref, scale) < max(TOL[prec], 1e-11)
+
+
+# ------------------------------------------------------------------ buffers and status
+def test_host_buffers_equal_device_buffers():
+    s = wl.random_cp(3, 500, [3, 3], seed=12)
+    with sag.Plan(s.N, s.D, s.ranks, s.factors) as pl:
+        out_h = np.zeros(s.N)
+        pl.rhs(s.n0.copy(), out_h)
+        n = dev(s.n0)
+        out_d = torch.empty_like(n)
+        pl.rhs(n, out_d)
+        torch.cuda.synchronize()
+        assert np.array_equal(out_h, out_d.cpu().numpy())
+        nh = s.n0.copy()
+        pl.rk2_step(nh, 1e-2)
+        pl.rk2_step(n, 1e-2)
+        torch.cuda.synchronize()
+        assert np.array_equal(nh, n.cpu().numpy())
+
+
+def test_rhs_in_place_alias():
+    s = wl.random_cp(3, 300, [2, 2], seed=13)
+    with sag.Plan(s.N, s.D, s.ranks, s.factors) as pl:
+        n = dev(s.n0)
+        ref = torch.empty_like(n)
+        pl.rhs(n, ref)
+        pl.rhs(n, n)
+        torch.cuda.synchronize()
+        assert torch.equal(n, ref)
+
+
+def test_nonfinite_input_is_latched_and_cleared():
+    s = wl.random_cp(3, 64, [2, 2], seed=14)
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP64) as pl:
+        bad = s.n0.copy()
+        bad[5] = np.nan
+        n = dev(bad)
+        out = torch.empty_like(n)
+        pl.rhs(n, out)
+        assert pl.sync_status() == sag.SAG_ENONFINITE
+        assert pl.sync_status() == sag.SAG_OK
+        pl.rhs(dev(s.n0), out)
+        assert pl.sync_status() == sag.SAG_OK
+
+
+def test_scale_invariance_of_double_word_path():
+    # n and the factors far outside FP32's range: the power-of-two scaling of
+    # the double-word path keeps the relative error unchanged.
+    s = wl.random_cp(3, 200, [2, 3], seed=15)
+    n_small = s.n0 * 1e-60
+    f_big = s.factors * 1e50
+    p_ref, q_ref = oracle.rhs(n_small, s.D, s.ranks, f_big, mode=oracle.DIRECT)
+    s2 = wl.System(s.D, s.N, "cp", s.ranks, f_big, n_small)
+    p, q, _, _ = gpu_parts(s2, n_small, sag.SAG_FP32_SPLIT)
+    scale = np.abs(p_ref).max() + np.abs(q_ref).max()
+    assert np.isfinite(scale) and scale > 0
+    assert nerr(p, p_ref, scale) < 1e-10
+    assert nerr(q, q_ref, scale) < 1e-10
+
+
+# ------------------------------------------------------------------ time integration
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("rk", [sag.SAG_HEUN, sag.SAG_MIDPOINT])
+def test_constant_kernel_trajectory(prec, rk):
+    s = wl.constant_monodisperse()  # D=3, N=64, n=e_1, dt=0.01, 100 steps
+    method = oracle.HEUN if rk == sag.SAG_HEUN else oracle.MIDPOINT
+    n_ref, d_ref = oracle.integrate(s.n0, s.D, s.ranks, s.factors, s.dt, s.steps, method=method)
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, rk=rk) as pl:
+        n = dev(s.n0)
+        diag = torch.zeros((s.steps + 1, 3), dtype=torch.float64, device="cuda")
+        pl.integrate(n, s.dt, s.steps, diag)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+        n, diag = n.cpu().numpy(), diag.cpu().numpy()
+    assert nerr(n, n_ref, np.abs(n_ref).max()) < TOL[prec]
+    assert np.max(np.abs(diag[:, :2] - d_ref[:, :2])) < 1e-13
+    # total concentration follows the scalar RK2 recursion of the closed-form
+    # M0 equation exactly (Heun), and M1 + outflow is conserved
+    if rk == sag.SAG_HEUN:
+        f = lambda M: -M * M / 2 - M ** 3 / 3
+        M = 1.0
+        for _ in range(s.steps):
+            k1 = f(M)
+            M = M + 0.5 * s.dt * (k1 + f(M + s.dt * k1))
+        assert abs(diag[-1, 0] - M) < 1e-14
+    tot = diag[:, 1] + diag[:, 2]
+    assert np.max(np.abs(tot - tot[0])) < 1e-12
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_brownian_trajectory_matches_oracle(prec):
+    s = wl.brownian_cp(3, 4096)
+    steps = 4
+    n_ref, d_ref = oracle.integrate(s.n0, s.D, s.ranks, s.factors, s.dt, steps)
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec) as pl:
+        n = dev(s.n0)
+        diag = torch.zeros((steps + 1, 3), dtype=torch.float64, device="cuda")
+        pl.integrate(n, s.dt, steps, diag)
+        torch.cuda.synchronize()
+        n = n.cpu().numpy()
+        diag = diag.cpu().numpy()
+    assert nerr(n, n_ref, np.abs(n_ref).max()) < TOL[prec]
+    assert np.max(np.abs(diag[:, :2] - d_ref[:, :2]) / np.abs(d_ref[:, :2]).max(axis=0)) < TOL[prec]
+
+
+def test_graph_recaptured_when_dt_or_buffer_changes():
+    s = wl.random_cp(3, 128, [2, 2], seed=16)
+    refs = {dt: oracle.integrate(s.n0, s.D, s.ranks, s.factors, dt, 3, diag=False)[0]
+            for dt in (0.01, 0.02)}
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP64) as pl:
+        for dt in (0.01, 0.02, 0.01):
+            for _ in range(2):
+                n = dev(s.n0)
+                pl.integrate(n, dt, 3)
+                torch.cuda.synchronize()
+                assert nerr(n.cpu().numpy(), refs[dt], np.abs(refs[dt]).max()) < 1e-12
+
+
+def test_fp32_split_tracks_fp64_over_long_trajectory():
+    # Brownian kernel, N = 4096, 1000 steps of dt = 1e-3: the double-word path
+    # stays within 1e-9 of the FP64 path, and both conserve M1 + outflow.
+    s = wl.brownian_cp(3, 4096)
+    res = {}
+    for prec in PRECS:
+        with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec) as pl:
+            n = dev(s.n0)
+            diag = torch.zeros((s.steps + 1, 3), dtype=torch.float64, device="cuda")
+            pl.integrate(n, s.dt, s.steps, diag)
+            torch.cuda.synchronize()
+            res[prec] = (n.cpu().numpy(), diag.cpu().numpy())
+    n64, d64 = res[sag.SAG_FP64]
+    ndw, ddw = res[sag.SAG_FP32_SPLIT]
+    assert nerr(ndw, n64, np.abs(n64).max()) < 1e-9
+    for dg in (d64, ddw):
+        tot = dg[:, 1] + dg[:, 2]
+        assert np.max(np.abs(tot - tot[0])) < 1e-9 * tot[0]
