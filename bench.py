@@ -130,15 +130,23 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def rank_slice(s, r):
-    """The workload's CP kernel restricted to rank term r of every order."""
-    from paper_1905_09071_gb300 import workloads as wl
-    offs = wl.cp_layout(s.D, s.N, s.ranks)
-    per = {}
-    for d in range(2, s.D + 1):
-        R = s.ranks[d - 2]
-        per[d] = s.factors[offs[d - 2]:offs[d - 1]].reshape(d, R, s.N)[:, r:r + 1, :]
-    return wl.cp_from_vectors(s.D, s.N, per)
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, or None
+    when the CUDA sources changed since that capture."""
+    import glob
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1905_09071_gb300", "csrc", "*"))):
+        h.update(os.path.basename(p).encode())
+        h.update(open(p, "rb").read())
+    if h.hexdigest() != rec.get("csrc_sha256"):
+        return None
+    k = rec.get("kernels", {}).get(kernel)
+    return None if k is None else float(k["dram_bytes"])
 
 
 def pair_slice(s, d, r):
@@ -362,7 +370,7 @@ def run_ours(args, world, rank, local):
         "speedup_vs_fp64": f64["t"] / dw["t"],
         "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
                      "unit": "TFP64op/s" if w["ops_fp64"] else "TFP32op/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": recorded_traffic(name),
                      "peak_source": "derived: 152 SMs x %d ops/clk/SM x 2070 MHz" %
                                     (FP64_PEAK_PER_SM_CLK if w["ops_fp64"] else FP32_PEAK_PER_SM_CLK)},
         "kernels": kernels,
