@@ -162,6 +162,26 @@ sag_status sag_kernel_work(sag_plan_t plan, int32_t id, double* ops, int32_t* op
  * schedules, block shapes), written to buf (NUL-terminated, truncated to len). */
 sag_status sag_plan_describe(sag_plan_t plan, char* buf, size_t len);
 
+/* Loss term without allocation: q = sum_d Q^(d)[n] (same definition and
+ * symmetrize_q meaning as sag_rhs_parts) for one CP system, computed directly
+ * from caller-owned device buffers with no plan. The paper has no counterpart;
+ * it exists for callers that cannot allocate device memory (code running under
+ * an allocator it does not own, in a fixed-budget memory pool, or in a process
+ * that reserved its device memory up front): this call performs no cudaMalloc,
+ * cudaFree or other allocation.
+ *   sys: fmt = SAG_CP, factors_on_device = 1, factors a device pointer in the
+ *        layout of sag_system; rank is read on the host.
+ *   n, q: device vectors of length N (may not alias).
+ * Limits: V = sum_d d R_d <= 2048 and V * ceil(N / 8192) <= 32768; larger
+ * systems, host pointers or TT kernels return SAG_EINVAL / SAG_EUNSUPPORTED
+ * with a message. Partial sums live in one static device array of 256 KB that
+ * every device loading the library keeps until exit; all calls share it, so
+ * calls that overlap on the GPU (any streams) race. The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress), so make
+ * it before any stream capture. Asynchronous on `stream`. */
+sag_status sag_loss_noalloc(const sag_system* sys, int32_t symmetrize_q, const double* n, double* q,
+                            void* stream);
+
 /* Releases the plan (after the work queued on it has finished). NULL is a no-op. */
 void sag_plan_destroy(sag_plan_t plan);
 

@@ -62,6 +62,14 @@ void unit_root(int64_t k, int64_t P, double& c, double& s) {
 
 }  // namespace
 
+namespace sag {
+// Lets other translation units of the library report through sag_last_error.
+sag_status set_last_error(sag_status s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+}  // namespace sag
+
 // Records one CUDA event before each kernel launch and one after the last.
 struct EventHook : LaunchHook {
   std::vector<cudaEvent_t> pool;

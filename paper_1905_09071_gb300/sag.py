@@ -26,7 +26,7 @@ EXPORTS = [
     "sag_default_options", "sag_plan", "sag_plan_layout", "sag_plan_bytes", "sag_rhs",
     "sag_rhs_parts", "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_plan_destroy",
     "sag_last_error", "sag_version", "sag_profile_enable", "sag_profile_read", "sag_kernel_name",
-    "sag_kernel_work", "sag_plan_describe",
+    "sag_kernel_work", "sag_plan_describe", "sag_loss_noalloc",
 ]
 SAG_NUM_KERNELS = 8
 
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
         lib.sag_kernel_work.argtypes = [vp, i32, ctypes.POINTER(f64), ctypes.POINTER(i32),
                                         ctypes.POINTER(f64)]
         lib.sag_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+        lib.sag_loss_noalloc.argtypes = [ctypes.POINTER(_System), i32, vp, vp, vp]
+        lib.sag_loss_noalloc.restype = ctypes.c_int
         for name in ("sag_plan", "sag_plan_layout", "sag_plan_bytes", "sag_rhs", "sag_rhs_parts",
                      "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_profile_enable",
                      "sag_profile_read", "sag_kernel_work", "sag_plan_describe"):
@@ -128,6 +130,18 @@ def _stream(stream, *tensors):
     if any(isinstance(t, torch.Tensor) and t.is_cuda for t in tensors):
         return torch.cuda.current_stream().cuda_stream
     return None
+
+
+def loss_noalloc(N: int, D: int, ranks, factors, n, q, symmetrize_q: int = 1, stream=None):
+    """sag_loss_noalloc: q = sum_d Q^(d)[n] for a CP system from device buffers
+    (torch CUDA tensors), without any device allocation by the library."""
+    lib = load()
+    r = np.ascontiguousarray(np.asarray(ranks, dtype=np.int32))
+    sysd = _System(int(N), int(D), SAG_CP, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                   _ptr(factors), 1)
+    _check(lib.sag_loss_noalloc(ctypes.byref(sysd), int(symmetrize_q), _ptr(n), _ptr(q),
+                                _stream(stream, n, q)))
+    return q
 
 
 def default_options() -> dict:
