@@ -211,8 +211,12 @@ sag_status build_plan(const sag_system* sys, const sag_options& opt, sag_plan_s*
     od.rp1 = make_radix_plan(od.M1);
     od.rp2 = make_radix_plan(od.M2);
     if (od.rp1.n < 0 || od.rp2.n < 0) return fail(SAG_EUNSUPPORTED, "FFT length not a supported product");
+    // Compile-time kernels (double-word path) for the common lengths.
+    od.ct1 = (dwp && ct_supported(od.M1) && M2 >= ct_cols(od.M1)) ? 1 : 0;
+    od.ct2 = (dwp && ct_supported(od.M2) && od.M2 <= 512) ? 1 : 0;
     int W = 1;
     while (2 * W <= M2 && (int64_t)2 * W * od.M1 <= 2048) W *= 2;
+    if (od.ct1) W = ct_cols(od.M1);
     od.W = W;
     od.ld1 = od.M1 + 1;
     od.ld2 = od.M2 + 1;
@@ -221,6 +225,9 @@ sag_status build_plan(const sag_system* sys, const sag_options& opt, sag_plan_s*
     int G = std::max(1, 2048 / (2 * M2));
     G = std::min(G, d * od.R);
     G = std::min(G, 64);
+    if (od.ct2) G = ct_group(od.M2);
+    if (dwp && !od.ct2 && 2 * od.M2 > kThreads)
+      return fail(SAG_EUNSUPPORTED, "row length without a compile-time kernel above 128");
     od.G = G;
     od.scr_off = scr;
     scr += (int64_t)d * od.R * od.M;
@@ -232,13 +239,17 @@ sag_status build_plan(const sag_system* sys, const sag_options& opt, sag_plan_s*
     colpre += d * od.R * od.ncolblk;
     rowpre += od.nrowpair;
     invpre += od.ncolblk;
-    col_smem = std::max(col_smem, (size_t)(2 * W * od.ld1 + od.M1) * csize);
-    row_smem = std::max(row_smem, (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize);
+    // Compile-time kernels work in place (one buffer), the generic ones ping-pong.
+    col_smem = std::max(col_smem, (size_t)((od.ct1 ? 1 : 2) * W * od.ld1 + od.M1) * csize);
+    // The compile-time row kernel double-buffers its input through bulk copies
+    // (two stages plus two mbarriers).
+    row_smem = std::max(row_smem, (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize + (od.ct2 ? 16 : 0));
   }
   P.colpre[D - 1] = colpre;
   P.rowpre[D - 1] = rowpre;
   P.invpre[D - 1] = invpre;
   P.Vtot = Vtot;
+  P.spin_limit = 4000000000LL;  // about 2 s at the maximum SM clock
   P.dotchunk = 8192;
   P.ndotchunk = (N + P.dotchunk - 1) / P.dotchunk;
 

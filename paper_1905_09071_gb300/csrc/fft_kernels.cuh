@@ -15,6 +15,10 @@
 // j = M2 j1 + j2 holds sizes 2j and 2j+1; spectrum index k = k1 + M1 k2.
 #pragma once
 
+#include <type_traits>
+
+#include "async_copy.cuh"
+#include "fft_ct.cuh"
 #include "plan.h"
 
 namespace sag {
@@ -62,97 +66,150 @@ __device__ __forceinline__ int find_order(const int* pre, int nord, int b) {
   return oi;
 }
 
+// Mirror of spectrum index k = k1 + M1 pos (row slot `row` of the block's
+// row pair) at M - k, as (row slot, position).
+__device__ __forceinline__ void mirror_of(int k1, int row, int pos, int M1, int M2, int& mrow,
+                                          int& mpos) {
+  if (k1 == 0) {
+    mrow = row;
+    mpos = pos == 0 ? 0 : M2 - pos;
+  } else {
+    mrow = (2 * k1 == M1) ? row : 1 - row;
+    mpos = M2 - 1 - pos;
+  }
+}
+
 // ---------------------------------------------------------------------------
-template <class C>
-__global__ void __launch_bounds__(kThreads) k_fwd_col(const __grid_constant__ RhsParams P,
-                                                      const double* __restrict__ n) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int oi = find_order(P.colpre, P.nord, blockIdx.x);
-  const OrderDesc& od = P.ord[oi];
-  const int local = blockIdx.x - P.colpre[oi];
-  const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
+// Forward column pass of one block: vector vloc of order od, column block cb.
+// P1 > 0: compile-time length, in place; P1 == 0: runtime length, ping-pong.
+template <class C, int P1>
+__device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc& od, int vloc,
+                                             int cb, const double* __restrict__ n, C* buf) {
+  constexpr bool CT = P1 > 0;
+  const int M1 = CT ? P1 : od.M1;
+  const int W = CT ? ct_cols(P1) : od.W;
+  const int ld = CT ? P1 + 1 : od.ld1;
+  const int M2 = od.M2;
   const int v = od.vbase + vloc;
-  const int W = od.W, M1 = od.M1, M2 = od.M2, ld = od.ld1;
-  C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + W * ld;
-  C* tw = buf1 + W * ld;
+  C* buf1 = buf + W * ld;
+  C* tw = CT ? buf + W * ld : buf1 + W * ld;
   const C* tw1 = static_cast<const C*>(od.tw1);
-  for (int i = threadIdx.x; i < M1; i += blockDim.x) tw[i] = tw1[i];
-  for (int e = threadIdx.x; e < W * M1; e += blockDim.x) {
+  for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
+  for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
-    buf0[c * ld + j1] = load_a_pair(P, v, 2 * j, n, C{});
+    buf[c * ld + j1] = load_a_pair(P, v, 2 * j, n, C{});
   }
   __syncthreads();
-  C* res = fft_batch(buf0, buf1, M1, ld, W, od.rp1, tw);
+  C* res;
+  if constexpr (CT) {
+    fft_ct<C, P1, ct_cols(P1), kThreads>(buf, ld, tw);
+    res = buf;
+  } else {
+    res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
+  }
   C* dst = static_cast<C*>(P.scratch) + od.scr_off + (int64_t)vloc * od.M;
   const C* tw4 = static_cast<const C*>(od.tw4);
-  for (int e = threadIdx.x; e < W * M1; e += blockDim.x) {
+  for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, k1 = e / W, j2 = cb * W + c;
     dst[(int64_t)k1 * M2 + j2] = c_mul(res[c * ld + k1], tw4[j2 * k1]);
   }
 }
 
-// ---------------------------------------------------------------------------
-// One block per row pair {k1a, M1 - k1a} of one order: both rows hold every
-// spectrum index k together with its mirror M - k, which the real split needs.
 template <class C>
-__global__ void __launch_bounds__(kThreads) k_rows(const __grid_constant__ RhsParams P) {
+__global__ void __launch_bounds__(kThreads) k_fwd_col(const __grid_constant__ RhsParams P,
+                                                      const double* __restrict__ n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int oi = find_order(P.rowpre, P.nord, blockIdx.x);
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int oi = find_order(P.colpre, P.nord, blockIdx.x);
   const OrderDesc& od = P.ord[oi];
-  const int kp = blockIdx.x - P.rowpre[oi];
-  const int d = od.d, R = od.R, M1 = od.M1, M2 = od.M2, M = od.M, ld = od.ld2, G = od.G;
+  const int local = blockIdx.x - P.colpre[oi];
+  const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
+  if constexpr (!std::is_same<C, cdw>::value) {
+    fwd_col_body<C, 0>(P, od, vloc, cb, n, buf);
+    return;
+  }
+  switch (od.ct1 ? od.M1 : 0) {
+    case 64: fwd_col_body<C, 64>(P, od, vloc, cb, n, buf); break;
+    case 96: fwd_col_body<C, 96>(P, od, vloc, cb, n, buf); break;
+    case 128: fwd_col_body<C, 128>(P, od, vloc, cb, n, buf); break;
+    case 192: fwd_col_body<C, 192>(P, od, vloc, cb, n, buf); break;
+    case 256: fwd_col_body<C, 256>(P, od, vloc, cb, n, buf); break;
+    case 384: fwd_col_body<C, 384>(P, od, vloc, cb, n, buf); break;
+    case 512: fwd_col_body<C, 512>(P, od, vloc, cb, n, buf); break;
+    case 768: fwd_col_body<C, 768>(P, od, vloc, cb, n, buf); break;
+    default: fwd_col_body<C, 0>(P, od, vloc, cb, n, buf); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row pass of one block: the row pair {k1a, M1 - k1a} of order od. Both rows
+// hold every spectrum index k together with its mirror M - k, which the real
+// split needs. P2 > 0: compile-time row length; P2 == 0: runtime.
+template <class C, int P2>
+__device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& od, int kp, C* buf) {
+  constexpr bool CT = P2 > 0;
+  // Positions per thread: the double-word path reaches the runtime variant only
+  // for rows of at most 128 points (the plan checks this), FP64 for up to 512.
+  constexpr int PPT = CT ? (2 * P2 + kThreads - 1) / kThreads
+                         : (std::is_same<C, cdw>::value ? 1 : kRowPosPerThread);
+  const int d = od.d, R = od.R, M1 = od.M1, M = od.M;
+  const int M2 = CT ? P2 : od.M2;
+  const int ld = CT ? P2 + 1 : od.ld2;
+  const int G = CT ? ct_group(P2) : od.G;
   const int k1a = kp, k1b = M1 - kp;
   const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
   const int NP = nrow * M2;
-  C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + G * 2 * ld;
-  C* tw = buf1 + G * 2 * ld;
+  // Slots: transform (g, row) at buf + (2 g + row) ld in the compile-time
+  // layout, at buf + (g nrow + row) ld in the runtime layout.
+  C* buf1 = buf + G * 2 * ld;
+  C* tw = CT ? buf + G * 2 * ld : buf1 + G * 2 * ld;
   const C* tw2 = static_cast<const C*>(od.tw2);
   const C* twL = static_cast<const C*>(od.twL);
   const C* src = static_cast<const C*>(P.scratch) + od.scr_off;
-  for (int i = threadIdx.x; i < M2; i += blockDim.x) tw[i] = tw2[i];
+  for (int i = threadIdx.x; i < M2; i += kThreads) tw[i] = tw2[i];
 
-  C S[kRowPosPerThread], Pr[kRowPosPerThread];
+  C S[PPT], Pr[PPT];
 #pragma unroll
-  for (int i = 0; i < kRowPosPerThread; ++i) {
+  for (int i = 0; i < PPT; ++i) {
     S[i] = c_zero(C{});
     Pr[i] = c_zero(C{});
   }
   C SN = c_zero(C{}), PrN = c_zero(C{});  // Nyquist index k = M (row 0 only)
   const bool nyq = (kp == 0 && threadIdx.x == 0);
+  const int slot_stride = CT ? 2 : nrow;
 
   const int Vd = d * R;
   for (int q0 = 0; q0 < Vd; q0 += G) {
     const int gc = min(G, Vd - q0);
-    for (int e = threadIdx.x; e < gc * NP; e += blockDim.x) {
+    for (int e = threadIdx.x; e < gc * NP; e += kThreads) {
       const int g = e / NP, p = e - g * NP;
       const int row = p / M2, pos = p - row * M2;
       const int q = q0 + g, r = q / d, m = q - r * d;
       const int k1 = row ? k1b : k1a;
-      buf0[(g * nrow + row) * ld + pos] = src[(int64_t)(m * R + r) * M + (int64_t)k1 * M2 + pos];
+      buf[(g * slot_stride + row) * ld + pos] = src[(int64_t)(m * R + r) * M + (int64_t)k1 * M2 + pos];
     }
     __syncthreads();
-    C* res = fft_batch(buf0, buf1, M2, ld, gc * nrow, od.rp2, tw);
+    C* res;
+    if constexpr (CT) {
+      fft_ct<C, P2, 2 * ct_group(P2), kThreads>(buf, ld, tw);  // unused slots hold stale data
+      res = buf;
+    } else {
+      res = fft_batch(buf, buf1, M2, ld, gc * nrow, od.rp2, tw);
+    }
 #pragma unroll
-    for (int i = 0; i < kRowPosPerThread; ++i) {
-      const int p = threadIdx.x + i * blockDim.x;
+    for (int i = 0; i < PPT; ++i) {
+      const int p = threadIdx.x + i * kThreads;
       if (p < NP) {
         const int row = p / M2, pos = p - row * M2;
         const int k1 = row ? k1b : k1a;
         int mrow, mpos;
-        if (k1 == 0) {
-          mrow = row;
-          mpos = pos == 0 ? 0 : M2 - pos;
-        } else {
-          mrow = (2 * k1 == M1) ? row : 1 - row;
-          mpos = M2 - 1 - pos;
-        }
+        mirror_of(k1, row, pos, M1, M2, mrow, mpos);
         const C wL = twL[k1 + M1 * pos];
         for (int g = 0; g < gc; ++g) {
           const int q = q0 + g, r = q / d, m = q - r * d;
-          const C A = unpack2(res[(g * nrow + row) * ld + pos], res[(g * nrow + mrow) * ld + mpos], wL);
+          const C A = unpack2(res[(g * slot_stride + row) * ld + pos],
+                              res[(g * slot_stride + mrow) * ld + mpos], wL);
           Pr[i] = (m == 0) ? A : c_mul(Pr[i], A);
           if (m == d - 1) S[i] = c_add(S[i], rank_weight(Pr[i], od, r));
         }
@@ -161,7 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(const __grid_constant__ RhsPa
     if (nyq) {
       for (int g = 0; g < gc; ++g) {
         const int q = q0 + g, r = q / d, m = q - r * d;
-        const C z0 = res[(g * nrow) * ld];
+        const C z0 = res[(g * slot_stride) * ld];
         const C zc = c_conj(z0);
         const C A = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));  // 2 A[M]
         PrN = (m == 0) ? A : c_mul(PrN, A);
@@ -174,67 +231,264 @@ __global__ void __launch_bounds__(kThreads) k_rows(const __grid_constant__ RhsPa
   // Inverse, row half: Z''[k] = (S[k] + S[k+M]) + i omega_L^-k (S[k] - S[k+M]),
   // S[k+M] = conj S[M-k] (Hermitian), S[M] for k = 0. The inverse transform is
   // run as a forward transform of conj(Z''); the final conjugation happens in
-  // the column kernel.
-  C* sS = buf1;  // NP + 1 entries
+  // the column kernel. S is staged past the first two slots.
+  C* sS = buf + 2 * ld;  // NP + 1 <= 2 ld entries, disjoint from slots 0 and 1
 #pragma unroll
-  for (int i = 0; i < kRowPosPerThread; ++i) {
-    const int p = threadIdx.x + i * blockDim.x;
+  for (int i = 0; i < PPT; ++i) {
+    const int p = threadIdx.x + i * kThreads;
     if (p < NP) sS[p] = S[i];
   }
   if (nyq) sS[NP] = SN;
   __syncthreads();
-  for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
     const int row = p / M2, pos = p - row * M2;
     const int k1 = row ? k1b : k1a;
     const int k = k1 + M1 * pos;
-    int mp;
-    if (k1 == 0) mp = row * M2 + (pos == 0 ? 0 : M2 - pos);
-    else mp = ((2 * k1 == M1) ? row : 1 - row) * M2 + (M2 - 1 - pos);
+    int mrow, mpos;
+    mirror_of(k1, row, pos, M1, M2, mrow, mpos);
     const C Sk = sS[p];
-    const C Sm = (k == 0) ? sS[NP] : c_conj(sS[mp]);
+    const C Sm = (k == 0) ? sS[NP] : c_conj(sS[mrow * M2 + mpos]);
     const C zpp = c_add(c_add(Sk, Sm), c_mul_pi(c_mul(c_conj(twL[k]), c_sub(Sk, Sm))));
-    buf0[row * ld + pos] = c_conj(zpp);
+    buf[row * ld + pos] = c_conj(zpp);
   }
   __syncthreads();
-  C* res = fft_batch(buf0, buf1, M2, ld, nrow, od.rp2, tw);
+  C* res;
+  if constexpr (CT) {
+    fft_ct<C, P2, 2, kThreads>(buf, ld, tw);
+    res = buf;
+  } else {
+    res = fft_batch(buf, buf1, M2, ld, nrow, od.rp2, tw);
+  }
   C* dst = static_cast<C*>(P.scratch2) + od.scr2_off;
   const C* tw4 = static_cast<const C*>(od.tw4);
-  for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
     const int row = p / M2, j2 = p - row * M2;
     const int k1 = row ? k1b : k1a;
     dst[(int64_t)k1 * M2 + j2] = c_mul(res[row * ld + j2], tw4[j2 * k1]);
   }
 }
 
-// ---------------------------------------------------------------------------
-template <class C>
-__global__ void __launch_bounds__(kThreads) k_inv_col(const __grid_constant__ RhsParams P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int oi = find_order(P.invpre, P.nord, blockIdx.x);
-  const OrderDesc& od = P.ord[oi];
-  const int cb = blockIdx.x - P.invpre[oi];
-  const int W = od.W, M1 = od.M1, M2 = od.M2, ld = od.ld1, N = P.N;
-  C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + W * ld;
-  C* tw = buf1 + W * ld;
-  const C* tw1 = static_cast<const C*>(od.tw1);
-  for (int i = threadIdx.x; i < M1; i += blockDim.x) tw[i] = tw1[i];
-  const C* src = static_cast<const C*>(P.scratch2) + od.scr2_off;
-  for (int e = threadIdx.x; e < W * M1; e += blockDim.x) {
-    const int c = e % W, k1 = e / W;
-    buf0[c * ld + k1] = src[(int64_t)k1 * M2 + cb * W + c];
+// Row pass, compile-time row length, with the rows of the next chunk of
+// vectors streamed into a second shared-memory stage by bulk asynchronous
+// copies while the current chunk is transformed. Layout: two mbarriers, then
+// stage 0 and stage 1 (2 G transform slots of ld = P2 + 1 each), then the
+// twiddle table. Returns false (after setting the timeout status) if a copy
+// did not complete within P.spin_limit cycles.
+template <class C, int P2>
+__device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderDesc& od, int kp,
+                                                unsigned char* smem_raw) {
+  constexpr int G = ct_group(P2);
+  constexpr int SLOTS = 2 * G;
+  constexpr int ld = P2 + 1;
+  constexpr int PPT = (2 * P2 + kThreads - 1) / kThreads;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  C* stage[2];
+  stage[0] = reinterpret_cast<C*>(smem_raw + 16);
+  stage[1] = stage[0] + SLOTS * ld;
+  C* tw = stage[1] + SLOTS * ld;
+  const int d = od.d, R = od.R, M1 = od.M1, M = od.M;
+  const int k1a = kp, k1b = M1 - kp;
+  const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
+  const int NP = nrow * P2;
+  const C* tw2 = static_cast<const C*>(od.tw2);
+  const C* twL = static_cast<const C*>(od.twL);
+  const C* src = static_cast<const C*>(P.scratch) + od.scr_off;
+  const int Vd = d * R;
+  const int nchunk = (Vd + G - 1) / G;
+
+  // One thread issues the copies of chunk c into stage c & 1.
+  auto issue = [&](int c) {
+    const int q0 = c * G, gc = min(G, Vd - q0);
+    uint64_t* bar = &bars[c & 1];
+    mbar_arrive_expect_tx(bar, (uint32_t)(gc * nrow * P2 * sizeof(C)));
+    for (int g = 0; g < gc; ++g) {
+      const int q = q0 + g, r = q / d, m = q - r * d;
+      for (int row = 0; row < nrow; ++row) {
+        const int k1 = row ? k1b : k1a;
+        bulk_copy_g2s(stage[c & 1] + (2 * g + row) * ld,
+                      src + (int64_t)(m * R + r) * M + (int64_t)k1 * P2,
+                      (uint32_t)(P2 * sizeof(C)), bar);
+      }
+    }
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init_fence();
+  }
+  for (int i = threadIdx.x; i < P2; i += kThreads) tw[i] = tw2[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    issue(0);
+    if (nchunk > 1) issue(1);
+  }
+
+  C S[PPT], Pr[PPT];
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    S[i] = c_zero(C{});
+    Pr[i] = c_zero(C{});
+  }
+  C SN = c_zero(C{}), PrN = c_zero(C{});
+  const bool nyq = (kp == 0 && threadIdx.x == 0);
+
+  for (int c = 0; c < nchunk; ++c) {
+    const int q0 = c * G, gc = min(G, Vd - q0);
+    C* buf = stage[c & 1];
+    const bool ok = mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1), P.spin_limit);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(&P.sc->status, kStatusTimeout);
+      return;
+    }
+    fft_ct<C, P2, SLOTS, kThreads>(buf, ld, tw);  // unused slots hold stale data
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int p = threadIdx.x + i * kThreads;
+      if (p < NP) {
+        const int row = p / P2, pos = p - row * P2;
+        const int k1 = row ? k1b : k1a;
+        int mrow, mpos;
+        mirror_of(k1, row, pos, M1, P2, mrow, mpos);
+        const C wL = twL[k1 + M1 * pos];
+        for (int g = 0; g < gc; ++g) {
+          const int q = q0 + g, r = q / d, m = q - r * d;
+          const C A = unpack2(buf[(2 * g + row) * ld + pos], buf[(2 * g + mrow) * ld + mpos], wL);
+          Pr[i] = (m == 0) ? A : c_mul(Pr[i], A);
+          if (m == d - 1) S[i] = c_add(S[i], rank_weight(Pr[i], od, r));
+        }
+      }
+    }
+    if (nyq) {
+      for (int g = 0; g < gc; ++g) {
+        const int q = q0 + g, r = q / d, m = q - r * d;
+        const C z0 = buf[(2 * g) * ld];
+        const C zc = c_conj(z0);
+        const C A = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));  // 2 A[M]
+        PrN = (m == 0) ? A : c_mul(PrN, A);
+        if (m == d - 1) SN = c_add(SN, rank_weight(PrN, od, r));
+      }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0 && c + 2 < nchunk) issue(c + 2);
+  }
+
+  // Inverse, row half (as in rows_body), in stage 0; every copy has landed.
+  C* buf = stage[0];
+  C* sS = buf + 2 * ld;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = threadIdx.x + i * kThreads;
+    if (p < NP) sS[p] = S[i];
+  }
+  if (nyq) sS[NP] = SN;
+  __syncthreads();
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / P2, pos = p - row * P2;
+    const int k1 = row ? k1b : k1a;
+    const int k = k1 + M1 * pos;
+    int mrow, mpos;
+    mirror_of(k1, row, pos, M1, P2, mrow, mpos);
+    const C Sk = sS[p];
+    const C Sm = (k == 0) ? sS[NP] : c_conj(sS[mrow * P2 + mpos]);
+    const C zpp = c_add(c_add(Sk, Sm), c_mul_pi(c_mul(c_conj(twL[k]), c_sub(Sk, Sm))));
+    buf[row * ld + pos] = c_conj(zpp);
   }
   __syncthreads();
-  C* res = fft_batch(buf0, buf1, M1, ld, W, od.rp1, tw);
+  fft_ct<C, P2, 2, kThreads>(buf, ld, tw);
+  C* dst = static_cast<C*>(P.scratch2) + od.scr2_off;
+  const C* tw4 = static_cast<const C*>(od.tw4);
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / P2, j2 = p - row * P2;
+    const int k1 = row ? k1b : k1a;
+    dst[(int64_t)k1 * P2 + j2] = c_mul(buf[row * ld + j2], tw4[j2 * k1]);
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ RhsParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  // Highest orders (most vectors per row pair) take the lowest block indices so
+  // that they are scheduled first.
+  const int b = gridDim.x - 1 - blockIdx.x;
+  const int oi = find_order(P.rowpre, P.nord, b);
+  const OrderDesc& od = P.ord[oi];
+  const int kp = b - P.rowpre[oi];
+  if constexpr (!std::is_same<C, cdw>::value) {
+    rows_body<C, 0>(P, od, kp, buf);
+    return;
+  }
+  switch (od.ct2 ? od.M2 : 0) {
+    case 64: rows_body_async<C, 64>(P, od, kp, smem_raw); break;
+    case 128: rows_body_async<C, 128>(P, od, kp, smem_raw); break;
+    case 256: rows_body_async<C, 256>(P, od, kp, smem_raw); break;
+    case 512: rows_body_async<C, 512>(P, od, kp, smem_raw); break;
+    default: rows_body<C, 0>(P, od, kp, buf); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse column pass: column block cb of order od; keeps sizes 1..N.
+template <class C, int P1>
+__device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc& od, int oi, int cb,
+                                             C* buf) {
+  constexpr bool CT = P1 > 0;
+  const int M1 = CT ? P1 : od.M1;
+  const int W = CT ? ct_cols(P1) : od.W;
+  const int ld = CT ? P1 + 1 : od.ld1;
+  const int M2 = od.M2, N = P.N;
+  C* buf1 = buf + W * ld;
+  C* tw = CT ? buf + W * ld : buf1 + W * ld;
+  const C* tw1 = static_cast<const C*>(od.tw1);
+  for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
+  const C* src = static_cast<const C*>(P.scratch2) + od.scr2_off;
+  for (int e = threadIdx.x; e < W * M1; e += kThreads) {
+    const int c = e % W, k1 = e / W;
+    buf[c * ld + k1] = src[(int64_t)k1 * M2 + cb * W + c];
+  }
+  __syncthreads();
+  C* res;
+  if constexpr (CT) {
+    fft_ct<C, P1, ct_cols(P1), kThreads>(buf, ld, tw);
+    res = buf;
+  } else {
+    res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
+  }
   const double scale = ldexp(od.pscale, P.dwpath ? od.d * P.sc->e_n : 0);
   double* out = P.pd + (int64_t)oi * N;
-  for (int e = threadIdx.x; e < W * M1; e += blockDim.x) {
+  for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
     const C w = res[c * ld + j1];
     const int k = 2 * j;  // sizes k (real part) and k + 1 (minus the imaginary part)
     if (k >= 1 && k <= N) out[k - 1] = cre(w) * scale;
     if (k + 1 <= N) out[k] = -cim(w) * scale;
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(kThreads) k_inv_col(const __grid_constant__ RhsParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int oi = find_order(P.invpre, P.nord, blockIdx.x);
+  const OrderDesc& od = P.ord[oi];
+  const int cb = blockIdx.x - P.invpre[oi];
+  if constexpr (!std::is_same<C, cdw>::value) {
+    inv_col_body<C, 0>(P, od, oi, cb, buf);
+    return;
+  }
+  switch (od.ct1 ? od.M1 : 0) {
+    case 64: inv_col_body<C, 64>(P, od, oi, cb, buf); break;
+    case 96: inv_col_body<C, 96>(P, od, oi, cb, buf); break;
+    case 128: inv_col_body<C, 128>(P, od, oi, cb, buf); break;
+    case 192: inv_col_body<C, 192>(P, od, oi, cb, buf); break;
+    case 256: inv_col_body<C, 256>(P, od, oi, cb, buf); break;
+    case 384: inv_col_body<C, 384>(P, od, oi, cb, buf); break;
+    case 512: inv_col_body<C, 512>(P, od, oi, cb, buf); break;
+    case 768: inv_col_body<C, 768>(P, od, oi, cb, buf); break;
+    default: inv_col_body<C, 0>(P, od, oi, cb, buf); break;
   }
 }
 

@@ -1,24 +1,31 @@
-// Instantiation of the FFT kernels for the double-word FP32 path.
-#include "fft_kernels.cuh"
+// FFT stage of the double-word FP32 path: the three kernels live in their own
+// translation units (kernels_dw_{fwd,rows,inv}.cu).
 #include "launch.h"
 
 namespace sag {
 
+cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+cudaError_t launch_k_inv_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L);
+cudaError_t setup_k_rows_dw(const LaunchCfg& L);
+cudaError_t setup_k_inv_col_dw(const LaunchCfg& L);
+
 cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
                            LaunchHook* hook) {
   if (hook) hook->mark(KID_FWD_COL, st);
-  k_fwd_col<cdw><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin);
+  cudaError_t e = launch_k_fwd_col_dw(P, L, nin, st);
+  if (e != cudaSuccess) return e;
   if (hook) hook->mark(KID_ROWS, st);
-  k_rows<cdw><<<L.row_blocks, kThreads, L.row_smem, st>>>(P);
+  if ((e = launch_k_rows_dw(P, L, nin, st)) != cudaSuccess) return e;
   if (hook) hook->mark(KID_INV_COL, st);
-  k_inv_col<cdw><<<L.inv_blocks, kThreads, L.inv_smem, st>>>(P);
-  return cudaGetLastError();
+  return launch_k_inv_col_dw(P, L, nin, st);
 }
 
 cudaError_t setup_fft_kernels_dw(const LaunchCfg& L) {
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_col<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.col_smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.inv_smem);
+  cudaError_t e = setup_k_fwd_col_dw(L);
+  if (e == cudaSuccess) e = setup_k_rows_dw(L);
+  if (e == cudaSuccess) e = setup_k_inv_col_dw(L);
   return e;
 }
 

@@ -1,0 +1,18 @@
+// k_fwd_col for the double-word FP32 path (own translation unit: the
+// compile-time length variants make it the slowest file to compile).
+#include "fft_kernels.cuh"
+#include "launch.h"
+
+namespace sag {
+
+cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
+  (void)nin;
+  k_fwd_col<cdw><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L) {
+  return cudaFuncSetAttribute(k_fwd_col<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.col_smem);
+}
+
+}  // namespace sag

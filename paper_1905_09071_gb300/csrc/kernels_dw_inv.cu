@@ -1,0 +1,18 @@
+// k_inv_col for the double-word FP32 path (own translation unit: the
+// compile-time length variants make it the slowest file to compile).
+#include "fft_kernels.cuh"
+#include "launch.h"
+
+namespace sag {
+
+cudaError_t launch_k_inv_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
+  (void)nin;
+  k_inv_col<cdw><<<L.inv_blocks, kThreads, L.inv_smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_k_inv_col_dw(const LaunchCfg& L) {
+  return cudaFuncSetAttribute(k_inv_col<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.inv_smem);
+}
+
+}  // namespace sag

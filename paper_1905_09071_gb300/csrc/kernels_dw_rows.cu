@@ -1,0 +1,18 @@
+// k_rows for the double-word FP32 path (own translation unit: the
+// compile-time length variants make it the slowest file to compile).
+#include "fft_kernels.cuh"
+#include "launch.h"
+
+namespace sag {
+
+cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
+  (void)nin;
+  k_rows<cdw><<<L.row_blocks, kThreads, L.row_smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_k_rows_dw(const LaunchCfg& L) {
+  return cudaFuncSetAttribute(k_rows<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
+}
+
+}  // namespace sag

@@ -5,7 +5,7 @@
 
 #include <cstdint>
 
-#include "fft.cuh"
+#include "fft_ct.cuh"
 
 namespace sag {
 
@@ -30,6 +30,7 @@ struct OrderDesc {
   int ncolblk;         // M2 / W
   int nrowpair;        // floor(M1 / 2) + 1 row pairs {k1, M1 - k1}
   int G;               // vectors per chunk in the row kernel
+  int ct1, ct2;        // 1: the column (M1) / row (M2) transforms use the compile-time kernels
   radix_plan rp1, rp2; // radix schedules of M1 and M2
   int64_t scr_off;     // scratch offset (elements) of this order's first vector
   int64_t scr2_off;    // offset of this order's spectral-sum buffer in scratch2
@@ -64,6 +65,7 @@ enum EpiMode : int {
 
 struct RhsParams {
   int N, D, nord, Vtot, sym, dwpath;
+  long long spin_limit;          // clock cycles a bounded device-side wait may take
   int ndotchunk;                 // chunks of the inner-product kernel per vector
   int dotchunk;                  // sizes per chunk
   OrderDesc ord[kMaxD];          // ord[i] describes order d = i + 2
