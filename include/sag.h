@@ -93,11 +93,14 @@ typedef struct {
 /* Fills *opt with the defaults. */
 void sag_default_options(sag_options* opt);
 
-/* Builds a plan for B independent systems sys[0..B-1]. Validates the systems,
+/* Builds a plan for B independent systems sys[0..B-1] (1 <= B <= 65535; each
+ * with its own N, D and ranks; all CP or all TT). Validates the systems,
  * chooses FFT lengths L_d >= d N (products of 2, 3, 5), builds twiddle tables,
- * copies the factors (FP64, plus the double-word copy for SAG_FP32_SPLIT) and
- * allocates the workspace. opt may be NULL (defaults). On success *out holds
- * the plan. B = 1 in this build; B > 1 returns SAG_EUNSUPPORTED. */
+ * copies the factors (FP64, plus the double-word copy for SAG_FP32_SPLIT; TT
+ * core vectors that are identically zero are skipped) and allocates the
+ * workspace. Every kernel of an evaluation then covers all B systems in one
+ * launch. Limits: N <= 2^22, d N <= 2^24, CP ranks <= 4096, TT ranks <= 16.
+ * opt may be NULL (defaults). On success *out holds the plan. */
 sag_status sag_plan(const sag_system* sys, int32_t B, const sag_options* opt, sag_plan_t* out);
 
 /* Offsets of each system's block in packed state vectors: offsets[b] is the
@@ -113,8 +116,8 @@ sag_status sag_plan_bytes(sag_plan_t plan, size_t* bytes);
 sag_status sag_rhs(sag_plan_t plan, const double* n, double* dndt, void* stream);
 
 /* The gain and loss parts separately: p = sum_d P^(d)[n], q = sum_d Q^(d)[n]
- * (either may be NULL), and outflow[b] (host or device, may be NULL) = the
- * first-moment flux out of the truncated system,
+ * (either may be NULL), and outflow[b], b < B (host or device, may be NULL) =
+ * the first-moment flux out of truncated system b,
  *     sum_d 1/d! sum_{i in [1,N]^d, |i| > N} |i| C^(d)_i prod_m n_{i_m}. */
 sag_status sag_rhs_parts(sag_plan_t plan, const double* n, double* p, double* q,
                          double* outflow, void* stream);
@@ -142,7 +145,7 @@ sag_status sag_sync_status(sag_plan_t plan, void* stream);
  * launch stream. sag_profile_read waits for that work, adds each kernel's
  * total time (ms) and launch count to ms[id] and launches[id] for
  * id < min(n, SAG_NUM_KERNELS), and forgets the records. */
-#define SAG_NUM_KERNELS 8
+#define SAG_NUM_KERNELS 12
 sag_status sag_profile_enable(sag_plan_t plan, int32_t on);
 sag_status sag_profile_read(sag_plan_t plan, double* ms, int64_t* launches, int32_t n);
 /* Name of kernel id (0 <= id < SAG_NUM_KERNELS), or NULL. */

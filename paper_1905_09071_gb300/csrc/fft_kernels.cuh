@@ -24,22 +24,26 @@
 namespace sag {
 
 // ---- loading a = U o n, two sizes per complex point -------------------------
-__device__ __forceinline__ cd load_a_pair(const RhsParams& P, int v, int k, const double* n, cd) {
+__device__ __forceinline__ cd load_a_pair(const RhsParams& P, const OrderDesc& od, int v, int k,
+                                          const double* n, cd) {
   double re = 0.0, im = 0.0;
-  const double* u = P.U64 + (int64_t)v * P.N;
-  if (k >= 1 && k <= P.N) re = u[k - 1] * n[k - 1];
-  if (k + 1 <= P.N) im = u[k] * n[k];
+  const double* u = P.U64 + P.voff[v];
+  const double* nn = n + od.noff;
+  if (k >= 1 && k <= od.N) re = u[k - 1] * nn[k - 1];
+  if (k + 1 <= od.N) im = u[k] * nn[k];
   return cd{re, im};
 }
-__device__ __forceinline__ cdw load_a_pair(const RhsParams& P, int v, int k, const double*, cdw) {
+__device__ __forceinline__ cdw load_a_pair(const RhsParams& P, const OrderDesc& od, int v, int k,
+                                           const double*, cdw) {
   dw re{0.f, 0.f}, im{0.f, 0.f};
-  const float2* u = P.Udw + (int64_t)v * P.N;
-  if (k >= 1 && k <= P.N) {
-    float2 a = u[k - 1], b = P.ndw[k - 1];
+  const float2* u = P.Udw + P.voff[v];
+  const float2* nn = P.ndw + od.noff;
+  if (k >= 1 && k <= od.N) {
+    float2 a = u[k - 1], b = nn[k - 1];
     re = dw_mul(dw{a.x, a.y}, dw{b.x, b.y});
   }
-  if (k + 1 <= P.N) {
-    float2 a = u[k], b = P.ndw[k];
+  if (k + 1 <= od.N) {
+    float2 a = u[k], b = nn[k];
     im = dw_mul(dw{a.x, a.y}, dw{b.x, b.y});
   }
   return make_cdw(re, im);
@@ -58,12 +62,6 @@ template <class C>
 __device__ __forceinline__ C unpack2(C zk, C zm, C wL) {
   C zc = c_conj(zm);
   return c_sub(c_add(zk, zc), c_mul_pi(c_mul(wL, c_sub(zk, zc))));
-}
-
-__device__ __forceinline__ int find_order(const int* pre, int nord, int b) {
-  int oi = 0;
-  while (oi + 1 < nord && b >= pre[oi + 1]) ++oi;
-  return oi;
 }
 
 // Mirror of spectrum index k = k1 + M1 pos (row slot `row` of the block's
@@ -98,7 +96,7 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
-    buf[c * ld + j1] = load_a_pair(P, v, 2 * j, n, C{});
+    buf[c * ld + j1] = load_a_pair(P, od, v, 2 * j, n, C{});
   }
   __syncthreads();
   C* res;
@@ -121,9 +119,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd_col(const __grid_constant__ Rh
                                                       const double* __restrict__ n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int oi = find_order(P.colpre, P.nord, blockIdx.x);
-  const OrderDesc& od = P.ord[oi];
-  const int local = blockIdx.x - P.colpre[oi];
+  const int it = find_segment(P.colpre, P.nitems, blockIdx.x);
+  const OrderDesc& od = P.ord[it];
+  const int local = blockIdx.x - P.colpre[it];
   const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
   if constexpr (!std::is_same<C, cdw>::value) {
     fwd_col_body<C, 0>(P, od, vloc, cb, n, buf);
@@ -338,7 +336,7 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
     C* buf = stage[c & 1];
     const bool ok = mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1), P.spin_limit);
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicOr(&P.sc->status, kStatusTimeout);
+      if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
       return;
     }
     fft_ct<C, P2, SLOTS, kThreads>(buf, ld, tw);  // unused slots hold stale data
@@ -410,12 +408,11 @@ template <class C>
 __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ RhsParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  // Highest orders (most vectors per row pair) take the lowest block indices so
-  // that they are scheduled first.
-  const int b = gridDim.x - 1 - blockIdx.x;
-  const int oi = find_order(P.rowpre, P.nord, b);
-  const OrderDesc& od = P.ord[oi];
-  const int kp = b - P.rowpre[oi];
+  // Items with the most vectors per row pair come first (rowperm), so that
+  // they are scheduled first.
+  const int j = find_segment(P.rowpre, P.nitems, blockIdx.x);
+  const OrderDesc& od = P.ord[P.rowperm[j]];
+  const int kp = blockIdx.x - P.rowpre[j];
   if constexpr (!std::is_same<C, cdw>::value) {
     rows_body<C, 0>(P, od, kp, buf);
     return;
@@ -438,7 +435,7 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   const int M1 = CT ? P1 : od.M1;
   const int W = CT ? ct_cols(P1) : od.W;
   const int ld = CT ? P1 + 1 : od.ld1;
-  const int M2 = od.M2, N = P.N;
+  const int M2 = od.M2, N = od.N;
   C* buf1 = buf + W * ld;
   C* tw = CT ? buf + W * ld : buf1 + W * ld;
   const C* tw1 = static_cast<const C*>(od.tw1);
@@ -456,8 +453,8 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   } else {
     res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
   }
-  const double scale = ldexp(od.pscale, P.dwpath ? od.d * P.sc->e_n : 0);
-  double* out = P.pd + (int64_t)oi * N;
+  const double scale = ldexp(od.pscale, P.dwpath ? od.d * P.sc[od.sys].e_n : 0);
+  double* out = P.pd + od.pd_off;
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
@@ -472,7 +469,7 @@ template <class C>
 __global__ void __launch_bounds__(kThreads) k_inv_col(const __grid_constant__ RhsParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int oi = find_order(P.invpre, P.nord, blockIdx.x);
+  const int oi = find_segment(P.invpre, P.nitems, blockIdx.x);
   const OrderDesc& od = P.ord[oi];
   const int cb = blockIdx.x - P.invpre[oi];
   if constexpr (!std::is_same<C, cdw>::value) {
@@ -489,6 +486,172 @@ __global__ void __launch_bounds__(kThreads) k_inv_col(const __grid_constant__ Rh
     case 512: inv_col_body<C, 512>(P, od, oi, cb, buf); break;
     case 768: inv_col_body<C, 768>(P, od, oi, cb, buf); break;
     default: inv_col_body<C, 0>(P, od, oi, cb, buf); break;
+  }
+}
+
+}  // namespace sag
+
+// ===========================================================================
+// TT kernels (Eq. ch3.eq4). The forward column pass is shared with CP; the
+// spectra of the nonzero core vectors are then combined per frequency by the
+// matrix chain S_d[k] = e_0 A^(1)[k] A^(2)[k] ... A^(d)[k] e_0, where
+// A^(l)_{a,b}[k] is the spectrum of h^(l)_{a,b} o n (Sec. 3 stores the cores as
+// these vectors along the size axis).
+namespace sag {
+
+// Row pass of the TT path: row FFTs of every vector of the order at the row
+// pair {k1a, M1 - k1a}, split into real spectra 2 A[k] written back in place
+// (same rows of the workspace); the Nyquist value goes to spec_nyq.
+template <class C>
+__global__ void __launch_bounds__(kThreads) k_rows_tt_fwd(const __grid_constant__ RhsParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int j = find_segment(P.rowpre, P.nitems, blockIdx.x);
+  const int oi = P.rowperm[j];
+  const OrderDesc& od = P.ord[oi];
+  const int kp = blockIdx.x - P.rowpre[j];
+  const int M1 = od.M1, M2 = od.M2, M = od.M, ld = od.ld2, G = od.G;
+  const int k1a = kp, k1b = M1 - kp;
+  const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
+  const int NP = nrow * M2;
+  C* buf1 = buf + G * 2 * ld;
+  C* tw = buf1 + G * 2 * ld;
+  const C* tw2 = static_cast<const C*>(od.tw2);
+  const C* twL = static_cast<const C*>(od.twL);
+  C* spec = static_cast<C*>(P.scratch) + od.scr_off;
+  C* nyq = static_cast<C*>(P.spec_nyq) + od.vbase;
+  for (int i = threadIdx.x; i < M2; i += kThreads) tw[i] = tw2[i];
+  for (int q0 = 0; q0 < od.nvec; q0 += G) {
+    const int gc = min(G, od.nvec - q0);
+    for (int e = threadIdx.x; e < gc * NP; e += kThreads) {
+      const int g = e / NP, p = e - g * NP;
+      const int row = p / M2, pos = p - row * M2;
+      const int k1 = row ? k1b : k1a;
+      buf[(g * nrow + row) * ld + pos] = spec[(int64_t)(q0 + g) * M + (int64_t)k1 * M2 + pos];
+    }
+    __syncthreads();
+    C* res = fft_batch(buf, buf1, M2, ld, gc * nrow, od.rp2, tw);
+    for (int e = threadIdx.x; e < gc * NP; e += kThreads) {
+      const int g = e / NP, p = e - g * NP;
+      const int row = p / M2, pos = p - row * M2;
+      const int k1 = row ? k1b : k1a;
+      int mrow, mpos;
+      mirror_of(k1, row, pos, M1, M2, mrow, mpos);
+      const C A = unpack2(res[(g * nrow + row) * ld + pos], res[(g * nrow + mrow) * ld + mpos],
+                          twL[k1 + M1 * pos]);
+      spec[(int64_t)(q0 + g) * M + (int64_t)k1 * M2 + pos] = A;
+      if (k1 == 0 && pos == 0) {
+        const C z0 = res[(g * nrow + row) * ld];
+        const C zc = c_conj(z0);
+        nyq[q0 + g] = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));  // 2 A[M]
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ cd tt_weight(cd x, const RhsParams&, int) { return x; }
+__device__ __forceinline__ cdw tt_weight(cdw x, const RhsParams& P, int v) {
+  return c_scale2(x, P.vweight[v]);
+}
+
+// Per-frequency matrix chain of one order; thread e < M handles the spectrum
+// slot e (same [k1][k2] layout as the vectors' spectra), e = M the Nyquist.
+template <class C, int RMAX>
+__global__ void __launch_bounds__(256) k_tt_chain(const __grid_constant__ RhsParams P) {
+  const int oi = find_segment(P.chainpre, P.nitems, blockIdx.x);
+  const OrderDesc& od = P.ord[oi];
+  const int e = (blockIdx.x - P.chainpre[oi]) * blockDim.x + threadIdx.x;
+  const int M = od.M;
+  if (e > M) return;
+  const C* spec = static_cast<const C*>(P.scratch) + od.scr_off;
+  const C* nyq = static_cast<const C*>(P.spec_nyq);
+  const int* vid = P.vid + od.vid_off;
+  auto load = [&](int v) -> C {
+    const C z = (e < M) ? spec[(int64_t)(v - od.vbase) * M + e] : nyq[v];
+    return tt_weight(z, P, v);
+  };
+  C x[RMAX], xn[RMAX];
+  const int r1 = od.ttr[1];
+#pragma unroll
+  for (int b = 0; b < RMAX; ++b) {
+    x[b] = c_zero(C{});
+    if (b < r1) {
+      const int v = vid[b];
+      if (v >= 0) x[b] = load(v);
+    }
+  }
+  int off = r1;
+  for (int l = 2; l <= od.d; ++l) {
+    const int ra = od.ttr[l - 1], rb = od.ttr[l];
+#pragma unroll
+    for (int b = 0; b < RMAX; ++b) {
+      xn[b] = c_zero(C{});
+      if (b < rb) {
+#pragma unroll
+        for (int a = 0; a < RMAX; ++a) {
+          if (a < ra) {
+            const int v = vid[off + a * rb + b];
+            if (v >= 0) xn[b] = c_add(xn[b], c_mul(x[a], load(v)));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < RMAX; ++b) x[b] = xn[b];
+    off += ra * rb;
+  }
+  if (e < M) static_cast<C*>(P.scratch2)[od.scr2_off + e] = x[0];
+  else static_cast<C*>(P.s_nyq)[oi] = x[0];
+}
+
+// Inverse row half of the TT path: repack the spectral sum of rows
+// {k1a, M1 - k1a} (with its Nyquist value), inverse row FFTs, four-step
+// twiddle, written back in place for the inverse column kernel.
+template <class C>
+__global__ void __launch_bounds__(kThreads) k_rows_tt_inv(const __grid_constant__ RhsParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int j = find_segment(P.rowpre, P.nitems, blockIdx.x);
+  const int oi = P.rowperm[j];
+  const OrderDesc& od = P.ord[oi];
+  const int kp = blockIdx.x - P.rowpre[j];
+  const int M1 = od.M1, M2 = od.M2, ld = od.ld2;
+  const int k1a = kp, k1b = M1 - kp;
+  const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
+  const int NP = nrow * M2;
+  C* sS = buf;               // NP staged spectral sums
+  C* bufa = buf + 2 * ld;    // two transform slots
+  C* bufb = bufa + 2 * ld;
+  C* tw = bufb + 2 * ld;
+  const C* tw2 = static_cast<const C*>(od.tw2);
+  const C* twL = static_cast<const C*>(od.twL);
+  C* S = static_cast<C*>(P.scratch2) + od.scr2_off;
+  const C SM = static_cast<const C*>(P.s_nyq)[oi];
+  for (int i = threadIdx.x; i < M2; i += kThreads) tw[i] = tw2[i];
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / M2, pos = p - row * M2;
+    sS[p] = S[(int64_t)(row ? k1b : k1a) * M2 + pos];
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / M2, pos = p - row * M2;
+    const int k1 = row ? k1b : k1a;
+    const int k = k1 + M1 * pos;
+    int mrow, mpos;
+    mirror_of(k1, row, pos, M1, M2, mrow, mpos);
+    const C Sk = sS[p];
+    const C Sm = (k == 0) ? SM : c_conj(sS[mrow * M2 + mpos]);
+    const C zpp = c_add(c_add(Sk, Sm), c_mul_pi(c_mul(c_conj(twL[k]), c_sub(Sk, Sm))));
+    bufa[row * ld + pos] = c_conj(zpp);
+  }
+  __syncthreads();
+  C* res = fft_batch(bufa, bufb, M2, ld, nrow, od.rp2, tw);
+  const C* tw4 = static_cast<const C*>(od.tw4);
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / M2, j2 = p - row * M2;
+    const int k1 = row ? k1b : k1a;
+    S[(int64_t)k1 * M2 + j2] = c_mul(res[row * ld + j2], tw4[j2 * k1]);
   }
 }
 

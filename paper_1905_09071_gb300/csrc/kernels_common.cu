@@ -1,6 +1,7 @@
 // Kernels of the right-hand side that are not FFTs: the double-word scaling of
-// n, the loss-term inner products, and the epilogue that assembles
-// dn/dt = P + Q and applies the Runge-Kutta stage update.
+// n, the loss-term inner products and weights, and the epilogue that
+// assembles dn/dt = P + Q and applies the Runge-Kutta stage update. Every
+// kernel covers all systems of the plan in one launch.
 #include "launch.h"
 
 namespace sag {
@@ -26,175 +27,256 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* 32 * NV
   __syncthreads();
 }
 
-// ---- n for the double-word path: n * 2^-e_n with max |n| 2^-e_n in [0.5, 1) --
-__global__ void k_nmax(const double* __restrict__ n, int N, DevScalars* sc) {
-  double m = 0.0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x)
-    m = fmax(m, fabs(n[k]));
-  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.0)
-    atomicMax(&sc->nmax_bits, (unsigned long long)__double_as_longlong(m));
-}
-
-__global__ void k_nsplit(const double* __restrict__ n, int N, DevScalars* sc, float2* ndw) {
-  const double mx = __longlong_as_double((long long)sc->nmax_bits);
-  const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) + 1 : 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
-    const dw v = dw_from_double(scalbn(n[k], -e));
-    ndw[k] = make_float2(v.hi, v.lo);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc->e_n = e;
-}
-
-// ---- loss-term inner products (Sec. 1: the (d-1)-fold sums of q^(d) split
-// into products of s_{d,m,r} = <U^(m)_r, n> for a CP kernel), FP64, plus the
-// first moments t = <k U^(m)_r, n> used for the outflow diagnostic. --------
-__global__ void __launch_bounds__(256) k_dot(const __grid_constant__ RhsParams P,
-                                             const double* __restrict__ n) {
-  __shared__ double sh[64];
-  const int v = blockIdx.y, c = blockIdx.x;
-  const int k0 = c * P.dotchunk, k1 = min(P.N, k0 + P.dotchunk);
-  const double* u = P.U64 + (int64_t)v * P.N;
-  double acc[2] = {0.0, 0.0};
-  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    const double un = u[k] * n[k];
-    acc[0] += un;
-    acc[1] = fma((double)(k + 1), un, acc[1]);
-  }
-  block_sum<2>(acc, sh);
-  if (threadIdx.x == 0) {
-    P.dot_s[v * P.ndotchunk + c] = acc[0];
-    P.dot_t[v * P.ndotchunk + c] = acc[1];
-  }
-}
-
-// Order index of a global vector.
-__device__ __forceinline__ int order_of_vector(const RhsParams& P, int v) {
-  int oi = 0;
-  while (oi + 1 < P.nord && v >= P.ord[oi + 1].vbase) ++oi;
-  return oi;
-}
-
 __device__ __forceinline__ double inv_factorial(int d) {
   double f = 1.0;
   for (int i = 2; i <= d; ++i) f *= i;
   return 1.0 / f;
 }
 
-// ---- epilogue --------------------------------------------------------------
-// Every block first reduces the inner products s_v and turns them into the
-// loss weights: q_k = n_k sum_v coef_v U_v(k) with, for v = (d, m, r),
-//   coef_v = -1/(d-1)! * (1/d) prod_{m' != m} s_{d,m',r}   (symmetrised kernel)
-//   coef_v = -1/(d-1)! * [m = d-1] prod_{m' < d-1} s_{d,m',r}   (literal, last mode)
-// The last block to finish reduces the block partials and evaluates the
-// outflow sum_d 1/d! sum_{i in [1,N]^d} |i| C_i prod n  -  sum_{k<=N} k P_k,
-// whose first part is sum_r sum_m t_{d,m,r} prod_{m' != m} s_{d,m',r} / d!.
-__global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsParams P, EpiArgs A) {
-  extern __shared__ double esh[];  // [Vtot] s, [Vtot] coef
-  __shared__ double red[32 * 4];
-  __shared__ int is_last;
-  double* s = esh;
-  double* coef = esh + P.Vtot;
-  const int N = P.N, V = P.Vtot, nc = P.ndotchunk;
-  for (int v = threadIdx.x; v < V; v += blockDim.x) {
-    double a = 0.0;
-    for (int c = 0; c < nc; ++c) a += P.dot_s[v * nc + c];
-    s[v] = a;
+// ---- n for the double-word path: per system, n 2^-e_n with max |n| 2^-e_n in
+// [0.5, 1) (an exact power-of-two scale). Grid: (blocks per system, B).
+__global__ void k_nmax(const __grid_constant__ RhsParams P, const double* __restrict__ n) {
+  const SysDesc& s = P.sys[blockIdx.y];
+  const double* x = n + s.noff;
+  double m = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.N; k += gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[k]));
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(&P.sc[blockIdx.y].nmax_bits, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_nsplit(const __grid_constant__ RhsParams P, const double* __restrict__ n) {
+  const SysDesc& s = P.sys[blockIdx.y];
+  SysScalars* sc = &P.sc[blockIdx.y];
+  const double mx = __longlong_as_double((long long)sc->nmax_bits);
+  const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) + 1 : 0;
+  const double* x = n + s.noff;
+  float2* out = P.ndw + s.noff;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.N; k += gridDim.x * blockDim.x) {
+    const dw v = dw_from_double(scalbn(x[k], -e));
+    out[k] = make_float2(v.hi, v.lo);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->e_n = e;
+}
+
+// ---- loss-term inner products (Sec. 1: for a low-rank kernel the (d-1)-fold
+// sums of q^(d) split into products of s_v = <U_v, n>), FP64, plus the first
+// moments t_v = <k U_v, n> used by the outflow diagnostic. Per thread the sizes
+// k_i = base + 256 i are visited in decreasing i with x_i = U(k_i) n(k_i):
+// acc1 = sum x_i and acc2 = sum (i + 1) x_i (a running sum of running sums),
+// so t = base acc1 + 256 (acc2 - acc1) costs one FMA and one add per size.
+// Grid: (vectors, most chunks of any vector).
+__global__ void __launch_bounds__(256) k_dot(const __grid_constant__ RhsParams P,
+                                             const double* __restrict__ n) {
+  __shared__ double sh[64];
+  const int v = blockIdx.x, c = blockIdx.y;
+  const SysDesc& s = P.sys[P.vsys[v]];
+  if (c >= s.ndotchunk) return;
+  const int k0 = c * P.dotchunk, k1 = min(s.N, k0 + P.dotchunk);
+  const double* u = P.U64 + P.voff[v];
+  const double* x = n + s.noff;
+  const int first = k0 + threadIdx.x;
+  const int cnt = first < k1 ? (k1 - first + 255) / 256 : 0;
+  double acc1 = 0.0, acc2 = 0.0;
+  for (int i = cnt - 1; i >= 0; --i) {
+    const int k = first + i * 256;
+    acc1 = fma(u[k], x[k], acc1);
+    acc2 += acc1;
+  }
+  double acc[2] = {acc1, (double)(first + 1) * acc1 + 256.0 * (acc2 - acc1)};
+  block_sum<2>(acc, sh);
+  if (threadIdx.x == 0) {
+    P.dot_s[(int64_t)v * P.maxdotchunk + c] = acc[0];
+    P.dot_t[(int64_t)v * P.maxdotchunk + c] = acc[1];
+  }
+}
+
+// ---- loss weights and the complete first-moment flux, one block per system --
+// q_k = n_k sum_v coef_v U_v(k). For a CP vector v = (d, m, r):
+//   coef_v = -1/(d-1)! (1/d) prod_{m' != m} s_{d,m',r}   (symmetrised kernel)
+//   coef_v = -1/(d-1)! [m = d-1] prod_{m' < d-1} s_{d,m',r}   (last mode)
+// For a TT vector v = h^(l)_{a,b} of order d, with M_l[a][b] = s of h^(l)_{a,b}:
+//   coef_v = -1/(d-1)! w_l (e_0 M_1 ... M_{l-1})[a] (M_{l+1} ... M_d e_0)[b],
+//   w_l = 1/d (symmetrised) or [l = d] (last mode).
+// gflux = sum_d 1/d! sum_{i in [1,N]^d} |i| C_i prod n: the same products with
+// one s replaced by the first moment t.
+__global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams P) {
+  extern __shared__ double csh[];  // [vectors of the system] s, then t
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  const SysDesc& sy = P.sys[b];
+  const int nv = sy.vend - sy.vbeg, nc = sy.ndotchunk;
+  double* s = csh;
+  double* t = csh + nv;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const int64_t base = (int64_t)(sy.vbeg + i) * P.maxdotchunk;
+    double a = 0.0, c2 = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      a += P.dot_s[base + c];
+      c2 += P.dot_t[base + c];
+    }
+    s[i] = a;
+    t[i] = c2;
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < V; v += blockDim.x) {
-    const int oi = order_of_vector(P, v);
-    const OrderDesc& od = P.ord[oi];
-    const int d = od.d, R = od.R, loc = v - od.vbase, m = loc / R, r = loc - m * R;
-    double prod = 1.0;
-    for (int mm = 0; mm < d; ++mm)
-      if (mm != m) prod *= s[od.vbase + mm * R + r];
-    double c;
-    if (P.sym) c = prod / d;
-    else c = (m == d - 1) ? prod : 0.0;
-    coef[v] = -inv_factorial(d - 1) * c;
+  double g[1] = {0.0};
+  if (sy.fmt == 0) {
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      const int v = sy.vbeg + i;
+      int it = sy.ibeg;
+      while (it + 1 < sy.iend && v >= P.ord[it + 1].vbase) ++it;
+      const OrderDesc& od = P.ord[it];
+      const int d = od.d, R = od.R, loc = v - od.vbase, m = loc / R, r = loc - m * R;
+      const int lb = od.vbase - sy.vbeg;
+      double prod = 1.0;
+      for (int mm = 0; mm < d; ++mm)
+        if (mm != m) prod *= s[lb + mm * R + r];
+      const double c = P.sym ? prod / d : (m == d - 1 ? prod : 0.0);
+      P.coef[v] = -inv_factorial(d - 1) * c;
+      g[0] += t[i] * prod * inv_factorial(d);
+    }
+  } else if (threadIdx.x < sy.iend - sy.ibeg) {
+    // One thread per order: left and right products of the inner-product matrices.
+    const OrderDesc& od = P.ord[sy.ibeg + threadIdx.x];
+    const int d = od.d;
+    const int* vid = P.vid + od.vid_off;
+    double left[kMaxD + 1][kMaxTTRank], right[kMaxD + 1][kMaxTTRank];
+    int offs[kMaxD + 1];
+    // left[l] = e_0 M_1 ... M_l (length R_l); right[l] = M_{l+1} ... M_d e_0 (length R_l)
+    left[0][0] = 1.0;
+    int off = 0;
+    for (int l = 1; l <= d; ++l) {
+      offs[l] = off;
+      const int ra = od.ttr[l - 1], rb = od.ttr[l];
+      for (int bb = 0; bb < rb; ++bb) {
+        double acc = 0.0;
+        for (int a = 0; a < ra; ++a) {
+          const int w = vid[off + a * rb + bb];
+          if (w >= 0) acc += left[l - 1][a] * s[w - sy.vbeg];
+        }
+        left[l][bb] = acc;
+      }
+      off += ra * rb;
+    }
+    right[d][0] = 1.0;
+    for (int l = d; l >= 1; --l) {
+      const int ra = od.ttr[l - 1], rb = od.ttr[l];
+      for (int a = 0; a < ra; ++a) {
+        double acc = 0.0;
+        for (int bb = 0; bb < rb; ++bb) {
+          const int w = vid[offs[l] + a * rb + bb];
+          if (w >= 0) acc += s[w - sy.vbeg] * right[l][bb];
+        }
+        right[l - 1][a] = acc;
+      }
+    }
+    for (int l = 1; l <= d; ++l) {
+      const int ra = od.ttr[l - 1], rb = od.ttr[l];
+      const double wl = P.sym ? 1.0 / d : (l == d ? 1.0 : 0.0);
+      for (int a = 0; a < ra; ++a)
+        for (int bb = 0; bb < rb; ++bb) {
+          const int w = vid[offs[l] + a * rb + bb];
+          if (w < 0) continue;
+          const double lr = left[l - 1][a] * right[l][bb];
+          P.coef[w] = -inv_factorial(d - 1) * wl * lr;
+          g[0] += t[w - sy.vbeg] * lr * inv_factorial(d);
+        }
+    }
   }
+  block_sum<1>(g, red);
+  if (threadIdx.x == 0) P.sc[b].gflux = g[0];
+}
+
+// ---- epilogue --------------------------------------------------------------
+// rhs_k = sum_d P^(d)_k + n_k sum_v coef_v U_v(k), then the Runge-Kutta stage.
+// The last block of each system to finish reduces that system's block
+// partials in a fixed order and evaluates its outflow gflux - sum_{k<=N} k P_k.
+__global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsParams P, EpiArgs A) {
+  extern __shared__ double esh[];  // [vectors of the system] coef
+  __shared__ double red[32 * 4];
+  __shared__ int is_last;
+  const int b = find_segment(P.epipre, P.B, blockIdx.x);
+  const SysDesc& sy = P.sys[b];
+  const int blk = blockIdx.x - P.epipre[b];
+  const int nv = sy.vend - sy.vbeg, N = sy.N;
+  double* coef = esh;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) coef[i] = P.coef[sy.vbeg + i];
   __syncthreads();
 
   double part[3] = {0.0, 0.0, 0.0};  // sum k p_k, M0 and M1 of the new state
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blk * blockDim.x + threadIdx.x;
   if (k < N) {
+    const int64_t g = sy.noff + k;
     double p = 0.0;
-    for (int oi = 0; oi < P.nord; ++oi) p += P.pd[(int64_t)oi * N + k];
-    double w = 0.0;
-    for (int v = 0; v < V; ++v) w = fma(coef[v], P.U64[(int64_t)v * N + k], w);
-    const double nk = A.nin[k];
-    const double q = nk * w;
+    for (int it = sy.ibeg; it < sy.iend; ++it) p += P.pd[P.ord[it].pd_off + k];
+    double w0 = 0.0, w1 = 0.0;
+    int i = 0;
+    for (; i + 1 < nv; i += 2) {
+      w0 = fma(coef[i], P.U64[P.voff[sy.vbeg + i] + k], w0);
+      w1 = fma(coef[i + 1], P.U64[P.voff[sy.vbeg + i + 1] + k], w1);
+    }
+    if (i < nv) w0 = fma(coef[i], P.U64[P.voff[sy.vbeg + i] + k], w0);
+    const double nk = A.nin[g];
+    const double q = nk * (w0 + w1);
     const double rhs = p + q;
-    if (!isfinite(rhs)) atomicOr(&P.sc->status, kStatusNonFinite);
+    if (!isfinite(rhs)) atomicOr(P.status, kStatusNonFinite);
     const double size = (double)(k + 1);
     part[0] = size * p;
     double nn = 0.0;
     switch (A.mode) {
       case EPI_RHS:
-        if (A.out0) A.out0[k] = rhs;
-        if (A.pout) A.pout[k] = p;
-        if (A.qout) A.qout[k] = q;
+        if (A.out0) A.out0[g] = rhs;
+        if (A.pout) A.pout[g] = p;
+        if (A.qout) A.qout[g] = q;
         break;
       case EPI_HEUN1:
-        A.k1buf[k] = rhs;
-        A.out0[k] = nk + A.dt * rhs;
+        A.k1buf[g] = rhs;
+        A.out0[g] = nk + A.dt * rhs;
         break;
       case EPI_MID1:
-        A.out0[k] = nk + 0.5 * A.dt * rhs;
+        A.out0[g] = nk + 0.5 * A.dt * rhs;
         break;
       case EPI_HEUN2:
-        nn = A.nbase[k] + 0.5 * A.dt * (A.k1buf[k] + rhs);
-        A.nbase[k] = nn;
+        nn = A.nbase[g] + 0.5 * A.dt * (A.k1buf[g] + rhs);
+        A.nbase[g] = nn;
         break;
       case EPI_MID2:
-        nn = A.nbase[k] + A.dt * rhs;
-        A.nbase[k] = nn;
+        nn = A.nbase[g] + A.dt * rhs;
+        A.nbase[g] = nn;
         break;
     }
     part[1] = nn;
     part[2] = size * nn;
   }
   block_sum<3>(part, red);
+  SysScalars* sc = &P.sc[b];
   if (threadIdx.x == 0) {
     A.part[blockIdx.x * 4 + 0] = part[0];
     A.part[blockIdx.x * 4 + 1] = part[1];
     A.part[blockIdx.x * 4 + 2] = part[2];
     __threadfence();
-    const unsigned ticket = atomicAdd(&P.sc->counter, 1u);
-    is_last = (ticket == gridDim.x - 1);
+    const unsigned ticket = atomicAdd(&sc->counter, 1u);
+    is_last = (ticket == (unsigned)sy.epi_blocks - 1);
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
 
-  // Last block: fixed-order reduction of the block partials and of the
-  // outflow's complete-sum term.
-  double tot[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    tot[0] += __ldcg(&A.part[b * 4 + 0]);
-    tot[1] += __ldcg(&A.part[b * 4 + 1]);
-    tot[2] += __ldcg(&A.part[b * 4 + 2]);
+  double tot[3] = {0.0, 0.0, 0.0};
+  for (int j = threadIdx.x; j < sy.epi_blocks; j += blockDim.x) {
+    const int r = P.epipre[b] + j;
+    tot[0] += __ldcg(&A.part[r * 4 + 0]);
+    tot[1] += __ldcg(&A.part[r * 4 + 1]);
+    tot[2] += __ldcg(&A.part[r * 4 + 2]);
   }
-  for (int v = threadIdx.x; v < V; v += blockDim.x) {
-    const int oi = order_of_vector(P, v);
-    const OrderDesc& od = P.ord[oi];
-    const int d = od.d, R = od.R, loc = v - od.vbase, m = loc / R, r = loc - m * R;
-    double t = 0.0;
-    for (int c = 0; c < nc; ++c) t += P.dot_t[v * nc + c];
-    double prod = 1.0;
-    for (int mm = 0; mm < d; ++mm)
-      if (mm != m) prod *= s[od.vbase + mm * R + r];
-    tot[3] += t * prod * inv_factorial(d);
-  }
-  block_sum<4>(tot, red);
+  block_sum<3>(tot, red);
   if (threadIdx.x == 0) {
-    DevScalars* sc = P.sc;
-    const double outflow = tot[3] - tot[0];
+    const double outflow = sc->gflux - tot[0];
     sc->outflow = outflow;
     switch (A.mode) {
       case EPI_RHS:
-        if (A.outflow_out) *A.outflow_out = outflow;
+        if (A.outflow_out) A.outflow_out[b] = outflow;
         break;
       case EPI_HEUN1:
         sc->o_stage1 = outflow;
@@ -206,9 +288,10 @@ __global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsPar
         sc->cum += (A.mode == EPI_HEUN2) ? 0.5 * A.dt * (sc->o_stage1 + outflow) : A.dt * outflow;
         const int row = ++sc->step;
         if (A.diag) {
-          A.diag[row * 3 + 0] = tot[1];
-          A.diag[row * 3 + 1] = tot[2];
-          A.diag[row * 3 + 2] = sc->cum;
+          double* dr = A.diag + ((int64_t)row * P.B + b) * 3;
+          dr[0] = tot[1];
+          dr[1] = tot[2];
+          dr[2] = sc->cum;
         }
         break;
       }
@@ -219,23 +302,26 @@ __global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsPar
 }
 
 // Row 0 of the diagnostics (M0, M1 of n, zero outflow) and the integrator's
-// counters. One block.
-__global__ void __launch_bounds__(256) k_moments(const double* __restrict__ n, int N, DevScalars* sc,
-                                                 double* diag) {
+// counters. One block per system.
+__global__ void __launch_bounds__(1024) k_moments(const __grid_constant__ RhsParams P,
+                                                  const double* __restrict__ n, double* diag) {
   __shared__ double red[64];
+  const int b = blockIdx.x;
+  const SysDesc& sy = P.sys[b];
+  const double* x = n + sy.noff;
   double acc[2] = {0.0, 0.0};
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    acc[0] += n[k];
-    acc[1] = fma((double)(k + 1), n[k], acc[1]);
+  for (int k = threadIdx.x; k < sy.N; k += blockDim.x) {
+    acc[0] += x[k];
+    acc[1] = fma((double)(k + 1), x[k], acc[1]);
   }
   block_sum<2>(acc, red);
   if (threadIdx.x == 0) {
-    sc->step = 0;
-    sc->cum = 0.0;
+    P.sc[b].step = 0;
+    P.sc[b].cum = 0.0;
     if (diag) {
-      diag[0] = acc[0];
-      diag[1] = acc[1];
-      diag[2] = 0.0;
+      diag[b * 3 + 0] = acc[0];
+      diag[b * 3 + 1] = acc[1];
+      diag[b * 3 + 2] = 0.0;
     }
   }
 }
@@ -245,12 +331,14 @@ cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* n
                          const EpiArgs& A, cudaStream_t st, LaunchHook* hook) {
   if (P.dwpath) {
     if (hook) hook->mark(KID_NMAX, st);
-    k_nmax<<<L.prep_blocks, 256, 0, st>>>(nin, P.N, P.sc);
+    k_nmax<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, nin);
     if (hook) hook->mark(KID_NSPLIT, st);
-    k_nsplit<<<L.prep_blocks, 256, 0, st>>>(nin, P.N, P.sc, P.ndw);
+    k_nsplit<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, nin);
   }
   if (hook) hook->mark(KID_DOT, st);
-  k_dot<<<dim3(P.ndotchunk, P.Vtot), 256, 0, st>>>(P, nin);
+  k_dot<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, st>>>(P, nin);
+  if (hook) hook->mark(KID_COEF, st);
+  k_coef<<<P.B, 256, L.coef_smem, st>>>(P);
   cudaError_t e = P.dwpath ? enqueue_fft_dw(P, L, nin, st, hook) : enqueue_fft_f64(P, L, nin, st, hook);
   if (e != cudaSuccess) return e;
   if (hook) hook->mark(KID_EPILOGUE, st);
@@ -260,12 +348,15 @@ cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* n
 }
 
 cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, cudaStream_t st) {
-  k_moments<<<1, 256, 0, st>>>(n, P.N, P.sc, diag);
+  k_moments<<<P.B, 1024, 0, st>>>(P, n, diag);
   return cudaGetLastError();
 }
 
 cudaError_t setup_common_kernels(const LaunchCfg& L) {
-  return cudaFuncSetAttribute(k_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.epi_smem);
+  cudaError_t e = cudaFuncSetAttribute(k_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.epi_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_coef, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.coef_smem);
+  return e;
 }
 
 }  // namespace sag

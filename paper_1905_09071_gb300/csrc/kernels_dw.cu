@@ -1,5 +1,5 @@
-// FFT stage of the double-word FP32 path: the three kernels live in their own
-// translation units (kernels_dw_{fwd,rows,inv}.cu).
+// FFT stage of the double-word FP32 path: the kernels live in their own
+// translation units (kernels_dw_{fwd,rows,inv,tt}.cu).
 #include "launch.h"
 
 namespace sag {
@@ -7,17 +7,23 @@ namespace sag {
 cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
 cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
 cudaError_t launch_k_inv_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+cudaError_t launch_tt_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, LaunchHook* hook);
 cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L);
 cudaError_t setup_k_rows_dw(const LaunchCfg& L);
 cudaError_t setup_k_inv_col_dw(const LaunchCfg& L);
+cudaError_t setup_tt_dw(const LaunchCfg& L);
 
 cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
                            LaunchHook* hook) {
   if (hook) hook->mark(KID_FWD_COL, st);
   cudaError_t e = launch_k_fwd_col_dw(P, L, nin, st);
   if (e != cudaSuccess) return e;
-  if (hook) hook->mark(KID_ROWS, st);
-  if ((e = launch_k_rows_dw(P, L, nin, st)) != cudaSuccess) return e;
+  if (L.has_tt) {
+    if ((e = launch_tt_dw(P, L, st, hook)) != cudaSuccess) return e;
+  } else {
+    if (hook) hook->mark(KID_ROWS, st);
+    if ((e = launch_k_rows_dw(P, L, nin, st)) != cudaSuccess) return e;
+  }
   if (hook) hook->mark(KID_INV_COL, st);
   return launch_k_inv_col_dw(P, L, nin, st);
 }
@@ -26,6 +32,7 @@ cudaError_t setup_fft_kernels_dw(const LaunchCfg& L) {
   cudaError_t e = setup_k_fwd_col_dw(L);
   if (e == cudaSuccess) e = setup_k_rows_dw(L);
   if (e == cudaSuccess) e = setup_k_inv_col_dw(L);
+  if (e == cudaSuccess) e = setup_tt_dw(L);
   return e;
 }
 

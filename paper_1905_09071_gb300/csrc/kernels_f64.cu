@@ -1,15 +1,19 @@
-// Instantiation of the FFT kernels for the FP64 path.
-#include "fft_kernels.cuh"
-#include "launch.h"
+// FFT stage of the FP64 path (runtime-length kernels only).
+#include "tt_launch.cuh"
 
 namespace sag {
 
 cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                           LaunchHook* hook) {
+                            LaunchHook* hook) {
   if (hook) hook->mark(KID_FWD_COL, st);
   k_fwd_col<cd><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin);
-  if (hook) hook->mark(KID_ROWS, st);
-  k_rows<cd><<<L.row_blocks, kThreads, L.row_smem, st>>>(P);
+  if (L.has_tt) {
+    cudaError_t e = launch_tt_stage<cd>(P, L, st, hook);
+    if (e != cudaSuccess) return e;
+  } else {
+    if (hook) hook->mark(KID_ROWS, st);
+    k_rows<cd><<<L.row_blocks, kThreads, L.row_smem, st>>>(P);
+  }
   if (hook) hook->mark(KID_INV_COL, st);
   k_inv_col<cd><<<L.inv_blocks, kThreads, L.inv_smem, st>>>(P);
   return cudaGetLastError();
@@ -19,6 +23,7 @@ cudaError_t setup_fft_kernels_f64(const LaunchCfg& L) {
   cudaError_t e = cudaFuncSetAttribute(k_fwd_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.col_smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.inv_smem);
+  if (e == cudaSuccess) e = setup_tt_stage<cd>(L);
   return e;
 }
 

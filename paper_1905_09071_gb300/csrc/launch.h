@@ -11,7 +11,9 @@ namespace sag {
 struct LaunchCfg {
   int prep_blocks;
   int col_blocks, row_blocks, inv_blocks, epi_blocks;
-  size_t col_smem, row_smem, inv_smem, epi_smem;
+  int chain_blocks;
+  int has_tt;           // the plan's systems use TT kernels (one format per plan)
+  size_t col_smem, row_smem, inv_smem, epi_smem, coef_smem, rowtt_smem;
 };
 
 // What the epilogue writes (see EpiMode).
@@ -32,7 +34,8 @@ struct EpiArgs {
 // Kernel ids for profiling (order of sag_kernel_name).
 enum KernelId : int {
   KID_NMAX = 0, KID_NSPLIT = 1, KID_DOT = 2, KID_FWD_COL = 3, KID_ROWS = 4, KID_INV_COL = 5,
-  KID_EPILOGUE = 6, KID_MOMENTS = 7, KID_COUNT = 8
+  KID_EPILOGUE = 6, KID_MOMENTS = 7, KID_COEF = 8, KID_ROWS_TT = 9, KID_TT_CHAIN = 10,
+  KID_ROWS_TT_INV = 11, KID_COUNT = 12
 };
 
 // Optional hook called before each kernel launch (id) and once after the last

@@ -1,5 +1,7 @@
 // Device-side description of a plan: what the kernels of one right-hand-side
-// evaluation read. Built on the host by the ABI layer, passed by value as a
+// evaluation read. A plan holds B independent systems; each order d of each
+// system is one "item" with its own FFT geometry. Item and system tables live
+// in device memory; the small RhsParams header is passed by value as a
 // __grid_constant__ kernel parameter.
 #pragma once
 
@@ -10,47 +12,67 @@
 namespace sag {
 
 constexpr int kMaxD = 8;
-constexpr int kThreads = 256;      // block size of the FFT kernels
+constexpr int kThreads = 256;        // block size of the FFT kernels
 constexpr int kRowPosPerThread = 4;  // row kernel: positions owned per thread (2 rows x M2 <= 1024)
+constexpr int kMaxTTRank = 16;       // largest TT rank R_lambda the chain kernel holds in registers
 
-// One order d of the system: its FFT geometry and where its data lives.
+// One order d of one system: its FFT geometry and where its data lives.
 //
 // Complex half-length trick: the real length-L sequence a (index = size,
 // a[0] = 0, a[k] = 0 for k > N) is packed as z_j = a[2j] + i a[2j+1],
 // j < M = L/2, and z is transformed by a four-step FFT with M = M1 * M2:
-// input j = M2 j1 + j2, output k = k1 + M1 k2,
-//   Z[k] = sum_{j1} omega_M1^{j1 k1} omega_M^{j2 k1} sum ... (columns j2 first,
-//   length M1, then rows k1, length M2).
+// input j = M2 j1 + j2, output k = k1 + M1 k2 (columns j2 first, length M1,
+// then rows k1, length M2).
 struct OrderDesc {
-  int d, R;            // order and CP rank
+  int sys;             // system index b
+  int d, R;            // order and CP rank (TT: unused)
+  int nvec;            // factor vectors of this order (CP: d R; TT: nonzero core vectors)
+  int N;               // sizes of the system
+  int64_t noff;        // offset of the system's size 1 in packed state vectors
   int L, M, M1, M2;    // real FFT length, complex length, four-step factors
-  int vbase;           // first global vector index (vectors v = vbase + m R + r)
+  int vbase;           // first global vector index (CP: v = vbase + m R + r)
   int W;               // columns per block in the column kernels
   int ld1, ld2;        // shared-memory leading dimensions (M1 + 1, M2 + 1)
   int ncolblk;         // M2 / W
   int nrowpair;        // floor(M1 / 2) + 1 row pairs {k1, M1 - k1}
   int G;               // vectors per chunk in the row kernel
   int ct1, ct2;        // 1: the column (M1) / row (M2) transforms use the compile-time kernels
+  int fmt;             // 0 CP, 1 TT
+  int ttr[kMaxD + 1];  // TT ranks R_0..R_d (R_0 = R_d = 1)
+  int vid_off;         // TT: offset of this order's (lambda, a, b) -> vector table
   radix_plan rp1, rp2; // radix schedules of M1 and M2
   int64_t scr_off;     // scratch offset (elements) of this order's first vector
   int64_t scr2_off;    // offset of this order's spectral-sum buffer in scratch2
+  int64_t pd_off;      // offset of P^(d) (N doubles) in the gain buffer
   const void* tw1;     // M1 entries omega_M1^k
   const void* tw2;     // M2 entries omega_M2^k
   const void* tw4;     // M entries omega_M^e (four-step twiddle, e = j2 k1 < M)
   const void* twL;     // M entries omega_L^k, k < M (real-FFT split)
-  const float* rscale; // [R] power-of-two weight of rank term r (double-word path)
-  double pscale;       // 2^(E_d - d) / (L d!): final scale of P^(d) before the n scale
+  const float* rscale; // CP, double-word path: [R] power-of-two weight of rank term r
+  double pscale;       // final FP64 scale of P^(d) (1/(L d!), factors of two), before the n scale
 };
 
-struct DevScalars {
+// One system of the batch.
+struct SysDesc {
+  int N, D, fmt;
+  int64_t noff;        // packed offset of size 1
+  int vbeg, vend;      // its global vectors
+  int ibeg, iend;      // its items (orders)
+  int ndotchunk;       // inner-product chunks per vector
+  int epi_beg, epi_blocks;  // its epilogue blocks
+};
+
+// Per-system device scalars (one 64-byte line each).
+struct SysScalars {
   unsigned long long nmax_bits;  // bits of max |n| (non-negative doubles order like integers)
   int e_n;                       // power-of-two scale of n in the double-word path
   int step;                      // diagnostic row counter of sag_integrate
   double o_stage1;               // outflow at the first stage of an RK2 step
   double cum;                    // cumulative outflow
   double outflow;                // last evaluated outflow
+  double gflux;                  // sum_d 1/d! sum_{i in [1,N]^d} |i| C_i prod n (complete first-moment flux)
   unsigned int counter;          // last-block detection of the epilogue
-  unsigned int status;           // latched device status bits
+  unsigned int pad[3];
 };
 
 enum : unsigned { kStatusNonFinite = 1u, kStatusTimeout = 2u };
@@ -64,24 +86,49 @@ enum EpiMode : int {
 };
 
 struct RhsParams {
-  int N, D, nord, Vtot, sym, dwpath;
+  int B, nitems, Vtot, sym, dwpath;
+  int64_t Ntot;                  // packed state length
+  int tt_rmax;                   // largest TT rank of the plan (chain kernel variant)
   long long spin_limit;          // clock cycles a bounded device-side wait may take
-  int ndotchunk;                 // chunks of the inner-product kernel per vector
-  int dotchunk;                  // sizes per chunk
-  OrderDesc ord[kMaxD];          // ord[i] describes order d = i + 2
-  int colpre[kMaxD + 1];         // prefix sums of column blocks (forward column kernel)
-  int rowpre[kMaxD + 1];         // prefix sums of row pairs (row kernel)
-  int invpre[kMaxD + 1];         // prefix sums of column blocks (inverse column kernel)
-  const double* U64;             // [Vtot][N] FP64 factors
-  const float2* Udw;             // [Vtot][N] double-word factors, scaled by 2^-e_v
-  float2* ndw;                   // [N] double-word n scaled by 2^-e_n
-  void* scratch;                 // forward column output, all vectors
-  void* scratch2;                // per order: spectral sum after the inverse row step
-  double* pd;                    // [nord][N] P^(d) per order
-  double* dot_s;                 // [Vtot][ndotchunk] partial <U, n>
-  double* dot_t;                 // [Vtot][ndotchunk] partial <k U, n>
-  double* epi_part;              // [gridDim][4] epilogue block partials
-  DevScalars* sc;
+  int dotchunk;                  // sizes per inner-product chunk
+  int maxdotchunk;               // most chunks of any vector
+  const OrderDesc* ord;          // [nitems]
+  const SysDesc* sys;            // [B]
+  const int* colpre;             // [nitems + 1] forward/inverse column kernel blocks
+  const int* rowpre;             // [nitems + 1] row kernel blocks, in rowperm order
+  const int* invpre;             // [nitems + 1] inverse column kernel blocks
+  const int* chainpre;           // [nitems + 1] TT chain kernel blocks
+  const int* epipre;             // [B + 1] epilogue blocks
+  const int* vsys;               // [Vtot] system of each vector
+  const int* rowperm;            // [nitems] items in row-kernel order, heaviest first (rowpre follows it)
+  const double* U64;             // [Vtot][N_b] FP64 factors (vector v at voff[v])
+  const int64_t* voff;           // [Vtot] offset of vector v in the factor arrays
+  const float2* Udw;             // double-word factors, scaled by 2^-e_v (same offsets)
+  float2* ndw;                   // [Ntot] double-word n scaled by 2^-e_n of its system
+  void* scratch;                 // forward column output, all vectors (TT: then their spectra)
+  void* scratch2;                // per item: spectral sum after the inverse row step
+  void* spec_nyq;                // TT: [Vtot] Nyquist value of each vector's spectrum
+  void* s_nyq;                   // TT: [nitems] Nyquist value of each order's spectral sum
+  const int* vid;                // TT: (lambda, a, b) -> vector index or -1, per item
+  const float* vweight;          // TT, double-word path: [Vtot] power-of-two weight 2^(e_v - E_lambda)
+  double* pd;                    // gain per item: P^(d) of system b at pd_off
+  double* dot_s;                 // [Vtot][maxdotchunk] partial <U, n>
+  double* dot_t;                 // [Vtot][maxdotchunk] partial <k U, n>
+  double* coef;                  // [Vtot] loss weights: q_k = n_k sum_v coef_v U_v(k)
+  double* epi_part;              // [epilogue blocks][4] block partials
+  SysScalars* sc;                // [B]
+  unsigned int* status;          // latched device status bits of the plan
 };
+
+// Binary search: the largest i in [0, n) with pre[i] <= x (pre[0] = 0, nondecreasing).
+__host__ __device__ __forceinline__ int find_segment(const int* pre, int n, int x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 }  // namespace sag

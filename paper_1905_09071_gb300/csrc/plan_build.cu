@@ -1,0 +1,459 @@
+// Plan construction: validation of the systems, factor vectors (CP modes or
+// the nonzero TT core vectors), FFT geometry per (system, order) item,
+// twiddle tables, double-word copies with exact power-of-two scaling, block
+// tables of every kernel, and the workspace.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "plan_host.h"
+
+namespace sag {
+namespace {
+
+double factorial(int d) {
+  double f = 1.0;
+  for (int i = 2; i <= d; ++i) f *= i;
+  return f;
+}
+
+// Smallest L = 2^a f (f in {1, 3, 5, 15}, a >= 1) with L >= need.
+int64_t choose_fft_length(int64_t need) {
+  int64_t best = -1;
+  const int64_t fs[4] = {1, 3, 5, 15};
+  for (int64_t f : fs) {
+    int64_t L = 2 * f;
+    while (L < need) L *= 2;
+    if (best < 0 || L < best) best = L;
+  }
+  return best;
+}
+
+// omega_P^k = exp(-2 pi i k / P) in FP64.
+void unit_root(int64_t k, int64_t P, double& c, double& s) {
+  const double a = 2.0 * M_PI * (double)(k % P) / (double)P;
+  c = std::cos(a);
+  s = -std::sin(a);
+}
+
+template <class C>
+C to_c(double re, double im);
+template <>
+cd to_c<cd>(double re, double im) { return cd{re, im}; }
+template <>
+cdw to_c<cdw>(double re, double im) {
+  dw r = dw_from_double(re), i = dw_from_double(im);
+  return cdw{r.hi, r.lo, i.hi, i.lo};
+}
+
+// Twiddle tables, shared by every item with the same (table length, root order).
+template <class C>
+struct TwiddleCache {
+  std::map<std::pair<int64_t, int64_t>, const void*> tables;
+  cudaError_t get(sag_plan_s* pl, int64_t P, int64_t count, const void** out) {
+    auto key = std::make_pair(P, count);
+    auto it = tables.find(key);
+    if (it != tables.end()) {
+      *out = it->second;
+      return cudaSuccess;
+    }
+    std::vector<C> h(count);
+    for (int64_t k = 0; k < count; ++k) {
+      double c, s;
+      unit_root(k, P, c, s);
+      h[k] = to_c<C>(c, s);
+    }
+    C* d = nullptr;
+    cudaError_t e = pl->upload(&d, h);
+    if (e != cudaSuccess) return e;
+    tables[key] = d;
+    *out = d;
+    return cudaSuccess;
+  }
+};
+
+template <class C>
+cudaError_t item_tables(sag_plan_s* pl, TwiddleCache<C>& tc, OrderDesc& od) {
+  cudaError_t e = tc.get(pl, od.M1, od.M1, &od.tw1);
+  if (e == cudaSuccess) e = tc.get(pl, od.M2, od.M2, &od.tw2);
+  if (e == cudaSuccess) e = tc.get(pl, od.M, od.M, &od.tw4);
+  if (e == cudaSuccess) e = tc.get(pl, od.L, od.M, &od.twL);
+  return e;
+}
+
+int64_t factor_count(const sag_system& s) {
+  int64_t nf = 0;
+  const int32_t* rk = s.rank;
+  for (int d = 2; d <= s.D; ++d) {
+    if (s.fmt == SAG_CP) {
+      nf += (int64_t)d * rk[0] * s.N;
+      rk += 1;
+    } else {
+      for (int l = 1; l <= d; ++l) nf += (int64_t)rk[l - 1] * rk[l] * s.N;
+      rk += d + 1;
+    }
+  }
+  return nf;
+}
+
+}  // namespace
+
+sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options& opt) {
+  if (!sys) return fail(SAG_EINVAL, "sys is NULL");
+  if (B < 1) return fail(SAG_EINVAL, "B must be >= 1");
+  if (B > 65535) return fail(SAG_EINVAL, "B must be <= 65535");
+  if (opt.prec != SAG_FP64 && opt.prec != SAG_FP32_SPLIT) return fail(SAG_EINVAL, "unknown precision");
+  if (opt.rk != SAG_HEUN && opt.rk != SAG_MIDPOINT) return fail(SAG_EINVAL, "unknown RK2 variant");
+  if (opt.symmetrize_q != 0 && opt.symmetrize_q != 1) return fail(SAG_EINVAL, "symmetrize_q must be 0 or 1");
+  for (int b = 0; b < B; ++b) {
+    const sag_system& s = sys[b];
+    const std::string at = B > 1 ? " (system " + std::to_string(b) + ")" : "";
+    if (s.N < 1) return fail(SAG_EINVAL, "N must be >= 1" + at);
+    if (s.N > (1 << 22)) return fail(SAG_EUNSUPPORTED, "N above 2^22" + at);
+    if (s.D < 2 || s.D > kMaxD) return fail(SAG_EINVAL, "D must be in [2, 8]" + at);
+    if (!s.rank) return fail(SAG_EINVAL, "rank is NULL" + at);
+    if (!s.factors) return fail(SAG_EINVAL, "factors is NULL" + at);
+    if (s.fmt != SAG_CP && s.fmt != SAG_TT) return fail(SAG_EINVAL, "unknown format" + at);
+    if (s.fmt != sys[0].fmt) return fail(SAG_EUNSUPPORTED, "all systems of a plan must share one format" + at);
+    const int32_t* rk = s.rank;
+    for (int d = 2; d <= s.D; ++d) {
+      if (s.fmt == SAG_CP) {
+        if (rk[0] < 1 || rk[0] > 4096) return fail(SAG_EINVAL, "CP rank out of [1, 4096]" + at);
+        rk += 1;
+      } else {
+        if (rk[0] != 1 || rk[d] != 1) return fail(SAG_EINVAL, "TT ranks must start and end with 1" + at);
+        for (int l = 1; l < d; ++l)
+          if (rk[l] < 1 || rk[l] > kMaxTTRank) return fail(SAG_EINVAL, "TT rank out of [1, 16]" + at);
+        rk += d + 1;
+      }
+    }
+    if (factor_count(s) > ((int64_t)1 << 34)) return fail(SAG_EINVAL, "factor array too large" + at);
+  }
+  return SAG_OK;
+}
+
+sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, sag_plan_s* pl) {
+  const bool dwp = opt.prec == SAG_FP32_SPLIT;
+  const bool tt = sys[0].fmt == SAG_TT;
+  const size_t csize = dwp ? sizeof(cdw) : sizeof(cd);
+  pl->B = B;
+  pl->prec = opt.prec;
+  pl->rk = opt.rk;
+  pl->sym = opt.symmetrize_q;
+  pl->fmt = sys[0].fmt;
+  RhsParams& P = pl->P;
+  P.B = B;
+  P.sym = opt.symmetrize_q;
+  P.dwpath = dwp ? 1 : 0;
+  P.spin_limit = 4000000000LL;  // about 2 s at the maximum SM clock
+  P.dotchunk = 8192;
+
+  // ---- vectors: host copy of every nonzero factor vector, packed ----------
+  std::vector<double> hf;          // concatenated vectors
+  std::vector<int64_t> voff;       // offset of each vector in hf
+  std::vector<int> vsys;           // system of each vector
+  std::vector<int> vid;            // TT tables
+  std::vector<SysDesc>& S = pl->systems;
+  std::vector<OrderDesc>& I = pl->items;
+  S.resize(B);
+  pl->offsets.assign(B + 1, 0);
+  int64_t noff = 0;
+  cudaError_t e;
+  for (int b = 0; b < B; ++b) {
+    const sag_system& s = sys[b];
+    const int N = s.N;
+    const int64_t nf = factor_count(s);
+    std::vector<double> src((size_t)nf);
+    e = cudaMemcpy(src.data(), s.factors, (size_t)nf * sizeof(double),
+                   s.factors_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "copy factors");
+    for (double x : src)
+      if (!std::isfinite(x)) return fail(SAG_EINVAL, "factors contain Inf or NaN");
+    SysDesc& sd = S[b];
+    sd.N = N;
+    sd.D = s.D;
+    sd.fmt = s.fmt;
+    sd.noff = noff;
+    sd.vbeg = (int)vsys.size();
+    sd.ibeg = (int)I.size();
+    sd.ndotchunk = (N + P.dotchunk - 1) / P.dotchunk;
+    const int32_t* rk = s.rank;
+    int64_t soff = 0;  // offset in the caller's factor array
+    for (int d = 2; d <= s.D; ++d) {
+      OrderDesc od{};
+      od.sys = b;
+      od.d = d;
+      od.N = N;
+      od.noff = noff;
+      od.fmt = s.fmt;
+      od.vbase = (int)vsys.size();
+      auto push_vector = [&](const double* x) {
+        voff.push_back((int64_t)hf.size());
+        vsys.push_back(b);
+        hf.insert(hf.end(), x, x + N);
+        return (int)vsys.size() - 1;
+      };
+      if (s.fmt == SAG_CP) {
+        od.R = rk[0];
+        od.nvec = d * od.R;
+        for (int v = 0; v < od.nvec; ++v) push_vector(src.data() + soff + (int64_t)v * N);
+        soff += (int64_t)od.nvec * N;
+        rk += 1;
+      } else {
+        od.R = 0;
+        for (int l = 0; l <= d; ++l) od.ttr[l] = rk[l];
+        od.vid_off = (int)vid.size();
+        int cnt = 0;
+        for (int l = 1; l <= d; ++l)
+          for (int a = 0; a < rk[l - 1]; ++a)
+            for (int c = 0; c < rk[l]; ++c) {
+              const double* x = src.data() + soff;
+              soff += N;
+              bool nz = false;
+              for (int k = 0; k < N && !nz; ++k) nz = x[k] != 0.0;
+              vid.push_back(nz ? push_vector(x) : -1);
+              cnt += nz ? 1 : 0;
+            }
+        od.nvec = cnt;
+        rk += d + 1;
+        for (int l = 0; l <= d; ++l) P.tt_rmax = std::max(P.tt_rmax, od.ttr[l]);
+      }
+      I.push_back(od);
+    }
+    sd.vend = (int)vsys.size();
+    sd.iend = (int)I.size();
+    noff += N;
+    pl->offsets[b + 1] = noff;
+  }
+  pl->Ntot = noff;
+  P.Ntot = noff;
+  P.Vtot = (int)vsys.size();
+  P.nitems = (int)I.size();
+  const int Vtot = P.Vtot;
+  if (Vtot == 0) return fail(SAG_EINVAL, "every kernel is identically zero");
+
+  // ---- FFT geometry of each item ------------------------------------------
+  int64_t scr = 0, scr2 = 0, pdo = 0;
+  size_t col_smem = 0, row_smem = 0, rowtt_smem = 0;
+  std::vector<int> colpre(1, 0), invpre(1, 0), chainpre(1, 0);
+  for (OrderDesc& od : I) {
+    const int d = od.d;
+    const int64_t L = choose_fft_length(std::max<int64_t>((int64_t)d * od.N, 16));
+    if (L > (int64_t)1 << 24) return fail(SAG_EUNSUPPORTED, "FFT length above 2^24 (d N too large)");
+    od.L = (int)L;
+    od.M = (int)(L / 2);
+    int M2 = 1;
+    while ((int64_t)(2 * M2) * (2 * M2) <= od.M && 2 * M2 <= 512 && od.M % (2 * M2) == 0) M2 *= 2;
+    od.M2 = M2;
+    od.M1 = od.M / M2;
+    if (od.M1 > 4096) return fail(SAG_EUNSUPPORTED, "FFT column length above 4096");
+    od.rp1 = make_radix_plan(od.M1);
+    od.rp2 = make_radix_plan(od.M2);
+    if (od.rp1.n < 0 || od.rp2.n < 0) return fail(SAG_EUNSUPPORTED, "FFT length not a supported product");
+    // Compile-time kernels (double-word path) for the common lengths; the
+    // compile-time row kernel serves CP only.
+    od.ct1 = (dwp && ct_supported(od.M1) && M2 >= ct_cols(od.M1)) ? 1 : 0;
+    od.ct2 = (dwp && !tt && ct_supported(od.M2) && od.M2 <= 512) ? 1 : 0;
+    int W = 1;
+    while (2 * W <= M2 && (int64_t)2 * W * od.M1 <= 2048) W *= 2;
+    if (od.ct1) W = ct_cols(od.M1);
+    od.W = W;
+    od.ld1 = od.M1 + 1;
+    od.ld2 = od.M2 + 1;
+    od.ncolblk = M2 / W;
+    od.nrowpair = od.M1 / 2 + 1;
+    int G = std::max(1, 2048 / (2 * M2));
+    G = std::min(G, std::max(1, od.nvec));
+    G = std::min(G, 64);
+    if (od.ct2) G = ct_group(od.M2);
+    if (dwp && !tt && !od.ct2 && 2 * od.M2 > kThreads)
+      return fail(SAG_EUNSUPPORTED, "row length without a compile-time kernel above 128");
+    od.G = G;
+    od.scr_off = scr;
+    scr += (int64_t)od.nvec * od.M;
+    od.scr2_off = scr2;
+    scr2 += od.M;
+    od.pd_off = pdo;
+    pdo += od.N;
+    colpre.push_back(colpre.back() + od.nvec * od.ncolblk);
+    invpre.push_back(invpre.back() + od.ncolblk);
+    chainpre.push_back(chainpre.back() + (tt ? (od.M + 1 + 255) / 256 : 0));
+    // Compile-time kernels work in place (one buffer), the generic ones ping-pong.
+    col_smem = std::max(col_smem, (size_t)((od.ct1 ? 1 : 2) * W * od.ld1 + od.M1) * csize);
+    // The compile-time row kernel double-buffers its input through bulk copies
+    // (two stages plus two mbarriers).
+    row_smem = std::max(row_smem, (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize + (od.ct2 ? 16 : 0));
+    rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * G * 2 * od.ld2, 6 * od.ld2) * csize +
+                                          (size_t)od.M2 * csize);
+  }
+  // Row blocks: items with the most vectors first.
+  std::vector<int> rowperm(I.size());
+  for (size_t i = 0; i < I.size(); ++i) rowperm[i] = (int)i;
+  std::stable_sort(rowperm.begin(), rowperm.end(),
+                   [&](int a, int b) { return I[a].nvec > I[b].nvec; });
+  std::vector<int> rowpre(1, 0);
+  for (int i : rowperm) rowpre.push_back(rowpre.back() + I[i].nrowpair);
+  // Epilogue blocks per system; largest vector count per system.
+  std::vector<int> epipre(1, 0);
+  int maxnv = 1, maxchunk = 1;
+  for (SysDesc& sd : S) {
+    sd.epi_beg = epipre.back();
+    sd.epi_blocks = (sd.N + 255) / 256;
+    epipre.push_back(epipre.back() + sd.epi_blocks);
+    maxnv = std::max(maxnv, sd.vend - sd.vbeg);
+    maxchunk = std::max(maxchunk, sd.ndotchunk);
+  }
+  P.maxdotchunk = maxchunk;
+
+  LaunchCfg& L = pl->L;
+  int maxN = 1;
+  for (const SysDesc& sd : S) maxN = std::max(maxN, sd.N);
+  L.prep_blocks = std::max(1, std::min(64, (maxN + 255) / 256));
+  L.col_blocks = colpre.back();
+  L.row_blocks = rowpre.back();
+  L.inv_blocks = invpre.back();
+  L.chain_blocks = chainpre.back();
+  L.epi_blocks = epipre.back();
+  L.has_tt = tt ? 1 : 0;
+  L.col_smem = col_smem;
+  L.row_smem = row_smem;
+  L.inv_smem = col_smem;
+  L.rowtt_smem = rowtt_smem;
+  L.epi_smem = (size_t)maxnv * sizeof(double);
+  L.coef_smem = (size_t)2 * maxnv * sizeof(double);
+  if (col_smem > 227 * 1024 || row_smem > 227 * 1024 || rowtt_smem > 227 * 1024 ||
+      L.coef_smem > 200 * 1024)
+    return fail(SAG_EUNSUPPORTED, "shared-memory footprint above the per-block limit (too many vectors)");
+
+  // ---- factor copies --------------------------------------------------------
+  double* U64 = nullptr;
+  if ((e = pl->upload(&U64, hf)) != cudaSuccess) return fail(SAG_ENOMEM, "cudaMalloc factors");
+  P.U64 = U64;
+  // Double-word copy: each vector scaled by 2^-e_v so that max |U| lies in
+  // [0.5, 1). CP: rank term r of an order carries 2^(sigma_r - E) with
+  // sigma_r = sum_m e_{v(m,r)}, E = max_r sigma_r. TT: vector v of core l
+  // carries 2^(e_v - E_l), E_l = max over the core. The remaining 2^E (CP) or
+  // 2^(sum_l E_l) (TT) moves into the FP64 scale of P^(d).
+  std::vector<int> ev(Vtot, 0);
+  if (dwp) {
+    std::vector<float2> hdw(hf.size());
+    for (int v = 0; v < Vtot; ++v) {
+      const int N = S[vsys[v]].N;
+      const double* x = hf.data() + voff[v];
+      double mx = 0.0;
+      for (int k = 0; k < N; ++k) mx = std::max(mx, std::fabs(x[k]));
+      int ex = 0;
+      if (mx > 0.0) std::frexp(mx, &ex);
+      ev[v] = ex;
+      for (int k = 0; k < N; ++k) {
+        dw y = dw_from_double(std::ldexp(x[k], -ex));
+        hdw[voff[v] + k] = make_float2(y.hi, y.lo);
+      }
+    }
+    float2* Udw = nullptr;
+    if ((e = pl->upload(&Udw, hdw)) != cudaSuccess) return fail(SAG_ENOMEM, "cudaMalloc dw factors");
+    P.Udw = Udw;
+    float2* ndw = nullptr;
+    if ((e = pl->alloc(&ndw, (size_t)pl->Ntot)) != cudaSuccess) return fail(SAG_ENOMEM, "cudaMalloc n");
+    P.ndw = ndw;
+  }
+  std::vector<float> vweight(Vtot, 1.0f);
+  TwiddleCache<cdw> tcw;
+  TwiddleCache<cd> tcd;
+  for (OrderDesc& od : I) {
+    const int d = od.d;
+    int Esum = 0;
+    if (dwp && od.fmt == SAG_CP) {
+      std::vector<int> sig(od.R, 0);
+      for (int r = 0; r < od.R; ++r)
+        for (int m = 0; m < d; ++m) sig[r] += ev[od.vbase + m * od.R + r];
+      Esum = *std::max_element(sig.begin(), sig.end());
+      std::vector<float> rs(od.R);
+      for (int r = 0; r < od.R; ++r) rs[r] = std::ldexp(1.0f, sig[r] - Esum);
+      float* drs = nullptr;
+      if ((e = pl->upload(&drs, rs)) != cudaSuccess) return fail(SAG_ENOMEM, "cudaMalloc rank scales");
+      od.rscale = drs;
+    } else if (dwp) {
+      int off = od.vid_off;
+      for (int l = 1; l <= d; ++l) {
+        const int cnt = od.ttr[l - 1] * od.ttr[l];
+        int El = INT32_MIN;
+        for (int j = 0; j < cnt; ++j)
+          if (vid[off + j] >= 0) El = std::max(El, ev[vid[off + j]]);
+        if (El == INT32_MIN) El = 0;
+        for (int j = 0; j < cnt; ++j)
+          if (vid[off + j] >= 0) vweight[vid[off + j]] = std::ldexp(1.0f, ev[vid[off + j]] - El);
+        Esum += El;
+        off += cnt;
+      }
+    }
+    e = dwp ? item_tables<cdw>(pl, tcw, od) : item_tables<cd>(pl, tcd, od);
+    if (e != cudaSuccess) return cuda_fail(e, "twiddle tables");
+    // A factor 2 per mode comes from the real split (2 A[k]), 1/L from the
+    // unnormalised inverse, 1/d! from the definition of p^(d).
+    od.pscale = std::ldexp(1.0, Esum - d) / ((double)od.L * factorial(d));
+  }
+
+  // ---- workspace and tables ---------------------------------------------------
+  void* scratch = nullptr;
+  void* scratch2 = nullptr;
+  if ((e = pl->alloc((unsigned char**)&scratch, (size_t)std::max<int64_t>(scr, 1) * csize)) != cudaSuccess ||
+      (e = pl->alloc((unsigned char**)&scratch2, (size_t)scr2 * csize)) != cudaSuccess)
+    return fail(SAG_ENOMEM, "cudaMalloc FFT workspace");
+  P.scratch = scratch;
+  P.scratch2 = scratch2;
+  OrderDesc* d_ord = nullptr;
+  SysDesc* d_sys = nullptr;
+  int *d_colpre = nullptr, *d_rowpre = nullptr, *d_invpre = nullptr, *d_chainpre = nullptr,
+      *d_epipre = nullptr, *d_vsys = nullptr, *d_rowperm = nullptr, *d_vid = nullptr;
+  int64_t* d_voff = nullptr;
+  float* d_vw = nullptr;
+  if (pl->upload(&d_ord, I) != cudaSuccess || pl->upload(&d_sys, S) != cudaSuccess ||
+      pl->upload(&d_colpre, colpre) != cudaSuccess || pl->upload(&d_rowpre, rowpre) != cudaSuccess ||
+      pl->upload(&d_invpre, invpre) != cudaSuccess || pl->upload(&d_chainpre, chainpre) != cudaSuccess ||
+      pl->upload(&d_epipre, epipre) != cudaSuccess || pl->upload(&d_vsys, vsys) != cudaSuccess ||
+      pl->upload(&d_rowperm, rowperm) != cudaSuccess || pl->upload(&d_vid, vid) != cudaSuccess ||
+      pl->upload(&d_voff, voff) != cudaSuccess || pl->upload(&d_vw, vweight) != cudaSuccess)
+    return fail(SAG_ENOMEM, "cudaMalloc tables");
+  P.ord = d_ord;
+  P.sys = d_sys;
+  P.colpre = d_colpre;
+  P.rowpre = d_rowpre;
+  P.invpre = d_invpre;
+  P.chainpre = d_chainpre;
+  P.epipre = d_epipre;
+  P.vsys = d_vsys;
+  P.rowperm = d_rowperm;
+  P.vid = d_vid;
+  P.voff = d_voff;
+  P.vweight = d_vw;
+  const size_t Nt = (size_t)pl->Ntot;
+  if (pl->alloc((unsigned char**)&P.spec_nyq, (size_t)Vtot * csize) != cudaSuccess ||
+      pl->alloc((unsigned char**)&P.s_nyq, (size_t)P.nitems * csize) != cudaSuccess ||
+      pl->alloc(&P.pd, (size_t)pdo) != cudaSuccess ||
+      pl->alloc(&P.dot_s, (size_t)Vtot * P.maxdotchunk) != cudaSuccess ||
+      pl->alloc(&P.dot_t, (size_t)Vtot * P.maxdotchunk) != cudaSuccess ||
+      pl->alloc(&P.coef, (size_t)Vtot) != cudaSuccess ||
+      pl->alloc(&pl->epi_part, (size_t)L.epi_blocks * 4) != cudaSuccess ||
+      pl->alloc(&P.sc, (size_t)B) != cudaSuccess || pl->alloc(&P.status, 1) != cudaSuccess ||
+      pl->alloc(&pl->nstar, Nt) != cudaSuccess || pl->alloc(&pl->k1buf, Nt) != cudaSuccess ||
+      pl->alloc(&pl->stage_a, Nt) != cudaSuccess || pl->alloc(&pl->stage_b, Nt) != cudaSuccess ||
+      pl->alloc(&pl->stage_c, Nt) != cudaSuccess || pl->alloc(&pl->dev_outflow, (size_t)B) != cudaSuccess)
+    return fail(SAG_ENOMEM, "cudaMalloc workspace");
+  P.epi_part = pl->epi_part;
+  if ((e = cudaMemset(P.sc, 0, sizeof(SysScalars) * B)) != cudaSuccess ||
+      (e = cudaMemset(P.status, 0, sizeof(unsigned))) != cudaSuccess)
+    return cuda_fail(e, "memset");
+
+  e = setup_common_kernels(L);
+  if (e == cudaSuccess) e = dwp ? setup_fft_kernels_dw(L) : setup_fft_kernels_f64(L);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+  if ((e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "stream");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "plan setup");
+  return SAG_OK;
+}
+
+}  // namespace sag

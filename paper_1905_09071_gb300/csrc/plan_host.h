@@ -1,0 +1,84 @@
+// Host-side plan object shared by the plan builder (plan_build.cu) and the C
+// ABI (api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "launch.h"
+#include "sag.h"
+
+namespace sag {
+
+sag_status fail(sag_status s, const std::string& msg);
+sag_status cuda_fail(cudaError_t e, const char* where);
+
+// Records one CUDA event before each kernel launch and one after the last.
+struct EventHook : LaunchHook {
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  bool failed = false;
+  void mark(int id, cudaStream_t st) override;
+  ~EventHook() override;
+};
+
+}  // namespace sag
+
+struct sag_plan_s {
+  sag::RhsParams P{};
+  sag::LaunchCfg L{};
+  int B = 0, prec = 0, rk = 0, sym = 1, fmt = 0;
+  int64_t Ntot = 0;
+  std::vector<int64_t> offsets;           // [B + 1] packed offsets
+  std::vector<sag::OrderDesc> items;      // host copy of the item table
+  std::vector<sag::SysDesc> systems;      // host copy of the system table
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  double* nstar = nullptr;
+  double* k1buf = nullptr;
+  double* epi_part = nullptr;
+  double* stage_a = nullptr;   // host-buffer staging (inputs)
+  double* stage_b = nullptr;   // host-buffer staging (outputs)
+  double* stage_c = nullptr;
+  double* dev_outflow = nullptr;
+  double* stage_diag = nullptr;
+  size_t stage_diag_len = 0;
+  cudaStream_t cap_stream = nullptr;
+  bool prof = false;
+  sag::EventHook hook;
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_n = nullptr;
+  double g_dt = 0.0;
+  double* g_diag = nullptr;
+
+  template <class T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    if (e != cudaSuccess) return e;
+    allocs.push_back(q);
+    bytes += count * sizeof(T);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+  }
+  template <class T>
+  cudaError_t upload(T** p, const std::vector<T>& h) {
+    cudaError_t e = alloc(p, h.size() ? h.size() : 1);
+    if (e != cudaSuccess || h.empty()) return e;
+    return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  }
+  ~sag_plan_s() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (void* q : allocs) cudaFree(q);
+    if (stage_diag) cudaFree(stage_diag);
+  }
+};
+
+namespace sag {
+sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options& opt);
+sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, sag_plan_s* pl);
+}  // namespace sag

@@ -28,7 +28,7 @@ EXPORTS = [
     "sag_last_error", "sag_version", "sag_profile_enable", "sag_profile_read", "sag_kernel_name",
     "sag_kernel_work", "sag_plan_describe", "sag_loss_noalloc",
 ]
-SAG_NUM_KERNELS = 8
+SAG_NUM_KERNELS = 12
 
 _STATUS_NAMES = {0: "SAG_OK", 1: "SAG_EINVAL", 2: "SAG_ENOMEM", 3: "SAG_ECUDA",
                  4: "SAG_EUNSUPPORTED", 5: "SAG_ETIMEOUT", 6: "SAG_ENONFINITE"}
@@ -151,40 +151,56 @@ def default_options() -> dict:
 
 
 class Plan:
-    """A planned system (sag_plan). ``factors`` is a flat float64 array in the
-    layout of include/sag.h (numpy: host; torch CUDA tensor: device)."""
+    """A plan (sag_plan) for one system, or for several with ``Plan.batch``.
+    ``factors`` is a flat float64 array in the layout of include/sag.h (numpy:
+    host memory; torch CUDA tensor: device memory). State vectors of a batched
+    plan are packed: system b occupies ``layout()[b]:layout()[b+1]``."""
 
     def __init__(self, N: int, D: int, ranks, factors, *, fmt: int = SAG_CP,
-                 prec: int = SAG_FP32_SPLIT, rk: int = SAG_HEUN, symmetrize_q: int = 1):
+                 prec: int = SAG_FP32_SPLIT, rk: int = SAG_HEUN, symmetrize_q: int = 1,
+                 _systems=None):
         lib = load()
-        self._ranks = np.ascontiguousarray(np.asarray(ranks, dtype=np.int32))
-        self.N, self.D, self.fmt, self.prec = int(N), int(D), int(fmt), int(prec)
-        on_dev = 0
-        try:
-            import torch
-            on_dev = int(isinstance(factors, torch.Tensor) and factors.is_cuda)
-        except ImportError:
-            pass
-        if not on_dev:
-            factors = np.ascontiguousarray(np.asarray(factors, dtype=np.float64))
-        self._factors_ref = factors
-        sysd = _System(self.N, self.D, self.fmt,
-                       self._ranks.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                       _ptr(factors), on_dev)
+        systems = _systems if _systems is not None else [(N, D, ranks, factors, fmt)]
+        self.B = len(systems)
+        self.N, self.D, self.fmt, self.prec = int(systems[0][0]), int(systems[0][1]), \
+            int(systems[0][4]), int(prec)
+        arr = (_System * self.B)()
+        self._keep = []
+        for b, (Nb, Db, rb, fb, fmtb) in enumerate(systems):
+            r = np.ascontiguousarray(np.asarray(rb, dtype=np.int32))
+            on_dev = 0
+            try:
+                import torch
+                on_dev = int(isinstance(fb, torch.Tensor) and fb.is_cuda)
+            except ImportError:
+                pass
+            if not on_dev:
+                fb = np.ascontiguousarray(np.asarray(fb, dtype=np.float64))
+            self._keep += [r, fb]
+            arr[b] = _System(int(Nb), int(Db), int(fmtb),
+                             r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(fb), on_dev)
         opt = _Options(int(prec), int(rk), int(symmetrize_q), 0)
         h = ctypes.c_void_p()
-        _check(lib.sag_plan(ctypes.byref(sysd), 1, ctypes.byref(opt), ctypes.byref(h)))
+        _check(lib.sag_plan(arr, self.B, ctypes.byref(opt), ctypes.byref(h)))
         self._h = h
         self._lib = lib
+        self._keep = None
+
+    @classmethod
+    def batch(cls, systems, *, prec: int = SAG_FP32_SPLIT, rk: int = SAG_HEUN,
+              symmetrize_q: int = 1):
+        """systems: list of (N, D, ranks, factors, fmt); one plan, one launch per kernel."""
+        return cls(0, 0, None, None, prec=prec, rk=rk, symmetrize_q=symmetrize_q,
+                   _systems=list(systems))
 
     @property
     def handle(self):
         return self._h
 
     def layout(self):
-        off = (ctypes.c_int64 * 2)()
+        off = (ctypes.c_int64 * (self.B + 1))()
         _check(self._lib.sag_plan_layout(self._h, off))
-        return [off[0], off[1]]
+        return [int(off[i]) for i in range(self.B + 1)]
 
     def device_bytes(self) -> int:
         b = ctypes.c_size_t()

@@ -148,3 +148,80 @@ def cp_to_tt_diagonal(sys: System) -> System:
             blocks.append(H.reshape(-1))
     return System(D, N, "tt", ranks_tt, np.concatenate(blocks), sys.n0.copy(), sys.dt, sys.steps,
                   name=sys.name + "_tt", meta=dict(sys.meta))
+
+
+def brownian_tt_cores(mu, N: int):
+    """TT cores of the generalized Brownian kernel (Eq. ch3.eq17) in the form the
+    proof of Theorem 1 builds them: ranks binom(D, l); core l maps a rank index
+    (an l-1 element subset of {1..D}) and a size i to the l-element subsets that
+    add one element j, with entry i^{mu_j}. Subsets are numbered by their bit
+    masks in increasing order. Returns (ranks[D+1], flat cores)."""
+    D = len(mu)
+    i = sizes(N)
+    subsets = [[m for m in range(1 << D) if bin(m).count("1") == l] for l in range(D + 1)]
+    ranks = [len(s) for s in subsets]
+    blocks = []
+    for l in range(1, D + 1):
+        H = np.zeros((ranks[l - 1], ranks[l], N))
+        for a, sa in enumerate(subsets[l - 1]):
+            for b, sb in enumerate(subsets[l]):
+                diff = sb & ~sa
+                if (sa & ~sb) == 0 and bin(diff).count("1") == 1:
+                    j = diff.bit_length() - 1
+                    H[a, b] = i ** mu[j]
+        blocks.append(H.reshape(-1))
+    return ranks, np.concatenate(blocks)
+
+
+def brownian_tt(D: int, N: int, mu, n0=None, decay: float = 10.0) -> System:
+    """Orders d = 2..D, order d's kernel the Eq. ch3.eq17 kernel with the first
+    d exponents mu[:d], each in its Theorem-1 TT form."""
+    ranks_all, blocks = [], []
+    for d in range(2, D + 1):
+        r, c = brownian_tt_cores(list(mu[:d]), N)
+        ranks_all += r
+        blocks.append(c)
+    if n0 is None:
+        n0 = normalised(np.exp(-sizes(N) / decay))
+    return System(D, N, "tt", ranks_all, np.concatenate(blocks), n0, name=f"brownian_tt_D{D}_N{N}",
+                  meta={"mu": list(mu)})
+
+
+def random_tt(D: int, N: int, ranks_per_order: dict, seed: int, lo: float = 0.2,
+              hi: float = 1.0) -> System:
+    """Dense positive TT cores: ranks_per_order[d] = [1, R_1, ..., R_{d-1}, 1]."""
+    rng = np.random.default_rng(seed)
+    ranks_all, blocks = [], []
+    for d in range(2, D + 1):
+        rk = list(ranks_per_order[d])
+        ranks_all += rk
+        for l in range(1, d + 1):
+            blocks.append(rng.uniform(lo, hi, rk[l - 1] * rk[l] * N))
+    n0 = normalised(rng.uniform(0.0, 1.0, N))
+    return System(D, N, "tt", ranks_all, np.concatenate(blocks), n0, name=f"random_tt_D{D}_N{N}",
+                  meta={"seed": seed})
+
+
+def batched_power_cp(B: int = 256, seed: int = BASE_SEED + 1, n_range=(1024, 32768),
+                     rank_range=(4, 32), u_range=(0.5, 1.5), a_range=(-0.5, 0.5),
+                     decay: float = 10.0) -> list:
+    """B independent systems: for each in turn N = round(exp(U[ln n_lo, ln n_hi])),
+    D uniform in {3, 4}, then for d = 2..D: R uniform in rank_range, u ~ U[u_range]
+    (d, R), a ~ U[a_range] (d, R); U^(m)_r(i) = u i^a; n_k = exp(-k/10)
+    normalised to M0 = 1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(B):
+        N = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        D = int(rng.integers(3, 5))
+        logi = np.log(sizes(N))
+        per = {}
+        for d in range(2, D + 1):
+            R = int(rng.integers(rank_range[0], rank_range[1] + 1))
+            u = rng.uniform(u_range[0], u_range[1], (d, R))
+            a = rng.uniform(a_range[0], a_range[1], (d, R))
+            per[d] = u[:, :, None] * np.exp(a[:, :, None] * logi[None, None, :])
+        ranks, f = cp_from_vectors(D, N, per)
+        out.append(System(D, N, "cp", ranks, f, normalised(np.exp(-sizes(N) / decay)), dt=1e-4,
+                          name=f"batched_{b}", meta={"seed": seed, "index": b}))
+    return out

@@ -64,12 +64,27 @@ def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=
     (dict(opt=(9, 0, 1, 0)), sag.SAG_EINVAL),
     (dict(opt=(0, 4, 1, 0)), sag.SAG_EINVAL),
     (dict(opt=(0, 0, 2, 0)), sag.SAG_EINVAL),
-    (dict(B=2), sag.SAG_EUNSUPPORTED),
 ])
 def test_plan_rejects_bad_arguments(kw, status):
     st, msg = _plan_status(**kw)
     assert st == status
     assert msg
+
+
+def test_batched_plan_rejects_mixed_formats_and_bad_tt_ranks(lib):
+    f = np.ones(4096)
+    cp_r = np.array([1, 1], dtype=np.int32)
+    tt_r = np.array([1, 2, 1, 1, 2, 2, 1], dtype=np.int32)  # d = 2: (1,2,1); d = 3: (1,2,2,1)
+    bad_tt = np.array([1, 17, 1, 1, 2, 2, 1], dtype=np.int32)
+    P = ctypes.POINTER(ctypes.c_int32)
+    h = ctypes.c_void_p()
+    o = sag._Options(sag.SAG_FP32_SPLIT, sag.SAG_HEUN, 1, 0)
+    arr = (sag._System * 2)(sag._System(8, 3, sag.SAG_CP, cp_r.ctypes.data_as(P), f.ctypes.data, 0),
+                            sag._System(8, 3, sag.SAG_TT, tt_r.ctypes.data_as(P), f.ctypes.data, 0))
+    assert lib.sag_plan(arr, 2, ctypes.byref(o), ctypes.byref(h)) == sag.SAG_EUNSUPPORTED
+    assert b"one format" in lib.sag_last_error()
+    one = (sag._System * 1)(sag._System(8, 3, sag.SAG_TT, bad_tt.ctypes.data_as(P), f.ctypes.data, 0))
+    assert lib.sag_plan(one, 1, ctypes.byref(o), ctypes.byref(h)) == sag.SAG_EINVAL
 
 
 def test_null_plan_calls_are_rejected(lib):

@@ -315,3 +315,18 @@ def test_theorem1_tt_rhs_matches_brute_force():
     scale = np.abs(pb).max() + np.abs(qb).max()
     assert _rel(pd, pb, scale) < 1e-14 and _rel(qd, qb, scale) < 1e-14
     assert abs(od - ob) < 1e-13 * abs(ob)
+
+
+@pytest.mark.parametrize("D", [2, 3, 4])
+def test_workload_theorem1_cores_reproduce_eq17(D):
+    # The input generator's TT cores (used as GPU inputs) against the oracle's
+    # permutation-sum definition of Eq. ch3.eq17.
+    N = 5
+    mu = np.random.default_rng(40 + D).uniform(-0.5, 0.5, D)
+    ranks, cores = wl.brownian_tt_cores(list(mu), N)
+    assert ranks == [math.comb(D, l) for l in range(D + 1)]
+    rng = np.random.default_rng(D)
+    for _ in range(30):
+        idx = rng.integers(1, N + 1, D)
+        want = oracle.brownian_entry(mu, idx)
+        assert abs(_tt_contract(ranks, cores, N, idx) - want) < 1e-13 * abs(want)
