@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="timed region only: no parity check, kernel profile, e2e or CPU baseline "
                          "(for ncu captures); prints no JSON line")
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "batched"],
+                    help="batched: 256 independent systems in one plan vs a loop of plans")
+    ap.add_argument("--systems", type=int, default=256)
     return ap.parse_args()
 
 
@@ -383,6 +386,63 @@ def run_ours(args, world, rank, local):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args, world, rank, local):
+    """B = 256 independent systems (N log-uniform in [1024, 32768], D in {3, 4},
+    CP ranks in [4, 32], exponents in [-0.5, 0.5], seed 1906), FP32-split:
+    one batched plan (each kernel launched once per RK2 stage for all systems,
+    stages replayed as a CUDA graph) against a loop over one plan per system
+    (the same kernels, one system per launch, each plan's steps replayed as its
+    own graph)."""
+    import torch
+    from paper_1905_09071_gb300 import sag, workloads as wl
+    torch.cuda.set_device(local)
+    systems = wl.batched_power_cp(B=args.systems)
+    K, W = args.steps, max(args.warmup, 1)
+    dt = systems[0].dt
+    desc = [(s.N, s.D, s.ranks, s.factors, sag.SAG_CP) for s in systems]
+    n0 = np.concatenate([s.n0 for s in systems])
+    pl = sag.Plan.batch(desc, prec=sag.SAG_FP32_SPLIT)
+    n = torch.tensor(n0, device="cuda")
+    pl.integrate(n, dt, W)
+    t_batch = max_over_ranks(time_integrate(pl, n, dt, K, world), world)
+    assert pl.sync_status() == sag.SAG_OK
+    nb = n.cpu().numpy()
+    pl.close()
+    plans = [sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT) for s in systems]
+    ns = [torch.tensor(s.n0, device="cuda") for s in systems]
+    for p_, x in zip(plans, ns):
+        p_.integrate(x, dt, W)
+    import torch as _t
+    stream = _t.cuda.current_stream()
+    e0, e1 = _t.cuda.Event(enable_timing=True), _t.cuda.Event(enable_timing=True)
+    barrier(world)
+    _t.cuda.synchronize()
+    e0.record(stream)
+    for p_, x in zip(plans, ns):
+        p_.integrate(x, dt, K)
+    e1.record(stream)
+    _t.cuda.synchronize()
+    t_loop = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+    nl = np.concatenate([x.cpu().numpy() for x in ns])
+    for p_ in plans:
+        p_.close()
+    if rank != 0:
+        return
+    out = {"metric": "batched RK2 steps/s (B=%d systems, all advanced one step)" % len(systems),
+           "value": K * world / t_batch, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+           "ms_per_step": t_batch / K * 1e3, "higher_is_better": True, "scaling": "weak",
+           "dtype": "f32x2", "data": "synthetic",
+           "config": {"workload": "batched_power_cp: B=%d, N in [1024, 32768] log-uniform, D in {3,4}, "
+                                  "CP ranks in [4, 32], a in [-0.5, 0.5], Heun dt=1e-4" % len(systems),
+                      "total_sizes": int(n0.size), "vectors": int(sum(sum(d * r for d, r in
+                                                                       zip(range(2, s.D + 1), s.ranks))
+                                                                   for s in systems))},
+           "loop_over_systems": {"value": K * world / t_loop, "ms_per_step": t_loop / K * 1e3},
+           "speedup_vs_loop": t_loop / t_batch,
+           "max_abs_diff_batched_vs_loop": float(np.max(np.abs(nb - nl)))}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -390,7 +450,10 @@ def main():
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
         return
     world, rank, local = dist_setup(args)
-    run_ours(args, world, rank, local)
+    if args.workload == "batched":
+        run_batched(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

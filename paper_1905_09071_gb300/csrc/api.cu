@@ -62,7 +62,8 @@ bool is_device_ptr(const void* p) {
 
 sag_status eval(sag_plan_t pl, const double* nin, EpiArgs A, cudaStream_t st, bool allow_hook = true) {
   A.part = pl->epi_part;
-  cudaError_t e = enqueue_eval(pl->P, pl->L, nin, A, st, (pl->prof && allow_hook) ? &pl->hook : nullptr);
+  cudaError_t e = enqueue_eval(pl->P, pl->L, nin, A, st, (pl->prof && allow_hook) ? &pl->hook : nullptr,
+                               &pl->side);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return SAG_OK;
 }

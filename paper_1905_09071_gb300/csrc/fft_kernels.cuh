@@ -24,29 +24,34 @@
 namespace sag {
 
 // ---- loading a = U o n, two sizes per complex point -------------------------
-__device__ __forceinline__ cd load_a_pair(const RhsParams& P, const OrderDesc& od, int v, int k,
-                                          const double* n, cd) {
+// u, nn: the vector and the system's n, both indexed by size - 1; N sizes.
+__device__ __forceinline__ cd load_a_pair(const double* __restrict__ u, const double* __restrict__ nn,
+                                          int N, int k, cd) {
   double re = 0.0, im = 0.0;
-  const double* u = P.U64 + P.voff[v];
-  const double* nn = n + od.noff;
-  if (k >= 1 && k <= od.N) re = u[k - 1] * nn[k - 1];
-  if (k + 1 <= od.N) im = u[k] * nn[k];
+  if (k >= 1 && k <= N) re = u[k - 1] * nn[k - 1];
+  if (k + 1 <= N) im = u[k] * nn[k];
   return cd{re, im};
 }
-__device__ __forceinline__ cdw load_a_pair(const RhsParams& P, const OrderDesc& od, int v, int k,
-                                           const double*, cdw) {
+__device__ __forceinline__ cdw load_a_pair(const float2* __restrict__ u, const float2* __restrict__ nn,
+                                           int N, int k, cdw) {
   dw re{0.f, 0.f}, im{0.f, 0.f};
-  const float2* u = P.Udw + P.voff[v];
-  const float2* nn = P.ndw + od.noff;
-  if (k >= 1 && k <= od.N) {
+  if (k >= 1 && k <= N) {
     float2 a = u[k - 1], b = nn[k - 1];
     re = dw_mul(dw{a.x, a.y}, dw{b.x, b.y});
   }
-  if (k + 1 <= od.N) {
+  if (k + 1 <= N) {
     float2 a = u[k], b = nn[k];
     im = dw_mul(dw{a.x, a.y}, dw{b.x, b.y});
   }
   return make_cdw(re, im);
+}
+__device__ __forceinline__ const double* vec_ptr(const RhsParams& P, int v, cd) { return P.U64 + P.voff[v]; }
+__device__ __forceinline__ const float2* vec_ptr(const RhsParams& P, int v, cdw) { return P.Udw + P.voff[v]; }
+__device__ __forceinline__ const double* n_ptr(const RhsParams&, const double* n, int64_t off, cd) {
+  return n + off;
+}
+__device__ __forceinline__ const float2* n_ptr(const RhsParams& P, const double*, int64_t off, cdw) {
+  return P.ndw + off;
 }
 
 // Power-of-two weight of a rank term (double-word path keeps every factor
@@ -93,10 +98,13 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   C* tw = CT ? buf + W * ld : buf1 + W * ld;
   const C* tw1 = static_cast<const C*>(od.tw1);
   for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
+  const auto u = vec_ptr(P, v, C{});
+  const auto nn = n_ptr(P, n, od.noff, C{});
+  const int N = od.N;
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
-    buf[c * ld + j1] = load_a_pair(P, od, v, 2 * j, n, C{});
+    buf[c * ld + j1] = load_a_pair(u, nn, N, 2 * j, C{});
   }
   __syncthreads();
   C* res;
@@ -115,7 +123,7 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
 }
 
 template <class C>
-__global__ void __launch_bounds__(kThreads) k_fwd_col(const __grid_constant__ RhsParams P,
+__global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__ RhsParams P,
                                                       const double* __restrict__ n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -466,7 +474,7 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
 }
 
 template <class C>
-__global__ void __launch_bounds__(kThreads) k_inv_col(const __grid_constant__ RhsParams P) {
+__global__ void __launch_bounds__(kThreads, 4) k_inv_col(const __grid_constant__ RhsParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int oi = find_segment(P.invpre, P.nitems, blockIdx.x);

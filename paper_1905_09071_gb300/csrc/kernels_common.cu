@@ -36,7 +36,7 @@ __device__ __forceinline__ double inv_factorial(int d) {
 // ---- n for the double-word path: per system, n 2^-e_n with max |n| 2^-e_n in
 // [0.5, 1) (an exact power-of-two scale). Grid: (blocks per system, B).
 __global__ void k_nmax(const __grid_constant__ RhsParams P, const double* __restrict__ n) {
-  const SysDesc& s = P.sys[blockIdx.y];
+  const SysDesc s = P.sys[blockIdx.y];
   const double* x = n + s.noff;
   double m = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.N; k += gridDim.x * blockDim.x)
@@ -47,7 +47,7 @@ __global__ void k_nmax(const __grid_constant__ RhsParams P, const double* __rest
 }
 
 __global__ void k_nsplit(const __grid_constant__ RhsParams P, const double* __restrict__ n) {
-  const SysDesc& s = P.sys[blockIdx.y];
+  const SysDesc s = P.sys[blockIdx.y];
   SysScalars* sc = &P.sc[blockIdx.y];
   const double mx = __longlong_as_double((long long)sc->nmax_bits);
   const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) + 1 : 0;
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ RhsParams P
                                              const double* __restrict__ n) {
   __shared__ double sh[64];
   const int v = blockIdx.x, c = blockIdx.y;
-  const SysDesc& s = P.sys[P.vsys[v]];
+  const SysDesc s = P.sys[P.vsys[v]];
   if (c >= s.ndotchunk) return;
   const int k0 = c * P.dotchunk, k1 = min(s.N, k0 + P.dotchunk);
   const double* u = P.U64 + P.voff[v];
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
   extern __shared__ double csh[];  // [vectors of the system] s, then t
   __shared__ double red[32];
   const int b = blockIdx.x;
-  const SysDesc& sy = P.sys[b];
+  const SysDesc sy = P.sys[b];
   const int nv = sy.vend - sy.vbeg, nc = sy.ndotchunk;
   double* s = csh;
   double* t = csh + nv;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
       const int v = sy.vbeg + i;
       int it = sy.ibeg;
       while (it + 1 < sy.iend && v >= P.ord[it + 1].vbase) ++it;
-      const OrderDesc& od = P.ord[it];
+      const OrderDesc od = P.ord[it];
       const int d = od.d, R = od.R, loc = v - od.vbase, m = loc / R, r = loc - m * R;
       const int lb = od.vbase - sy.vbeg;
       double prod = 1.0;
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
     }
   } else if (threadIdx.x < sy.iend - sy.ibeg) {
     // One thread per order: left and right products of the inner-product matrices.
-    const OrderDesc& od = P.ord[sy.ibeg + threadIdx.x];
+    const OrderDesc od = P.ord[sy.ibeg + threadIdx.x];
     const int d = od.d;
     const int* vid = P.vid + od.vid_off;
     double left[kMaxD + 1][kMaxTTRank], right[kMaxD + 1][kMaxTTRank];
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsPar
   __shared__ double red[32 * 4];
   __shared__ int is_last;
   const int b = find_segment(P.epipre, P.B, blockIdx.x);
-  const SysDesc& sy = P.sys[b];
+  const SysDesc sy = P.sys[b];
   const int blk = blockIdx.x - P.epipre[b];
   const int nv = sy.vend - sy.vbeg, N = sy.N;
   double* coef = esh;
@@ -210,13 +210,15 @@ __global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsPar
     const int64_t g = sy.noff + k;
     double p = 0.0;
     for (int it = sy.ibeg; it < sy.iend; ++it) p += P.pd[P.ord[it].pd_off + k];
+    // A system's vectors are stored back to back, N sizes each.
+    const double* Ub = P.U64 + P.voff[sy.vbeg] + k;
     double w0 = 0.0, w1 = 0.0;
     int i = 0;
     for (; i + 1 < nv; i += 2) {
-      w0 = fma(coef[i], P.U64[P.voff[sy.vbeg + i] + k], w0);
-      w1 = fma(coef[i + 1], P.U64[P.voff[sy.vbeg + i + 1] + k], w1);
+      w0 = fma(coef[i], Ub[(int64_t)i * N], w0);
+      w1 = fma(coef[i + 1], Ub[(int64_t)(i + 1) * N], w1);
     }
-    if (i < nv) w0 = fma(coef[i], P.U64[P.voff[sy.vbeg + i] + k], w0);
+    if (i < nv) w0 = fma(coef[i], Ub[(int64_t)i * N], w0);
     const double nk = A.nin[g];
     const double q = nk * (w0 + w1);
     const double rhs = p + q;
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(1024) k_moments(const __grid_constant__ RhsPar
                                                   const double* __restrict__ n, double* diag) {
   __shared__ double red[64];
   const int b = blockIdx.x;
-  const SysDesc& sy = P.sys[b];
+  const SysDesc sy = P.sys[b];
   const double* x = n + sy.noff;
   double acc[2] = {0.0, 0.0};
   for (int k = threadIdx.x; k < sy.N; k += blockDim.x) {
@@ -328,19 +330,30 @@ __global__ void __launch_bounds__(1024) k_moments(const __grid_constant__ RhsPar
 
 // ---- launch of one evaluation ---------------------------------------------
 cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
-                         const EpiArgs& A, cudaStream_t st, LaunchHook* hook) {
+                         const EpiArgs& A, cudaStream_t st, LaunchHook* hook, const SideStream* side) {
   if (P.dwpath) {
     if (hook) hook->mark(KID_NMAX, st);
     k_nmax<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, nin);
     if (hook) hook->mark(KID_NSPLIT, st);
     k_nsplit<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, nin);
   }
+  // The inner products and loss weights (FP64 pipe) overlap the FFT kernels
+  // (FP32 pipe) on the side stream; per-kernel timing runs everything in order.
+  const bool fork = side != nullptr && hook == nullptr;
+  cudaStream_t ds = fork ? side->stream : st;
+  cudaError_t e;
+  if (fork) {
+    if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ds, side->fork, 0)) != cudaSuccess) return e;
+  }
   if (hook) hook->mark(KID_DOT, st);
-  k_dot<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, st>>>(P, nin);
+  k_dot<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, ds>>>(P, nin);
   if (hook) hook->mark(KID_COEF, st);
-  k_coef<<<P.B, 256, L.coef_smem, st>>>(P);
-  cudaError_t e = P.dwpath ? enqueue_fft_dw(P, L, nin, st, hook) : enqueue_fft_f64(P, L, nin, st, hook);
+  k_coef<<<P.B, 256, L.coef_smem, ds>>>(P);
+  if (fork && (e = cudaEventRecord(side->join, ds)) != cudaSuccess) return e;
+  e = P.dwpath ? enqueue_fft_dw(P, L, nin, st, hook) : enqueue_fft_f64(P, L, nin, st, hook);
   if (e != cudaSuccess) return e;
+  if (fork && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return e;
   if (hook) hook->mark(KID_EPILOGUE, st);
   k_epilogue<<<L.epi_blocks, 256, L.epi_smem, st>>>(P, A);
   if (hook) hook->mark(-1, st);

@@ -45,8 +45,16 @@ struct LaunchHook {
   virtual ~LaunchHook() = default;
 };
 
+// A second stream with fork/join events: the FP64 inner products run on it,
+// beside the FFT kernels (also inside a captured graph, as a parallel branch).
+struct SideStream {
+  cudaStream_t stream;
+  cudaEvent_t fork, join;
+};
+
 cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
-                         const EpiArgs& A, cudaStream_t st, LaunchHook* hook = nullptr);
+                         const EpiArgs& A, cudaStream_t st, LaunchHook* hook = nullptr,
+                         const SideStream* side = nullptr);
 cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, cudaStream_t st);
 cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
                             LaunchHook* hook);

@@ -450,7 +450,10 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   e = setup_common_kernels(L);
   if (e == cudaSuccess) e = dwp ? setup_fft_kernels_dw(L) : setup_fft_kernels_f64(L);
   if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
-  if ((e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+  if ((e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&pl->side.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&pl->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&pl->side.join, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(e, "stream");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "plan setup");
   return SAG_OK;

@@ -47,6 +47,7 @@ struct sag_plan_s {
   double* stage_diag = nullptr;
   size_t stage_diag_len = 0;
   cudaStream_t cap_stream = nullptr;
+  sag::SideStream side{nullptr, nullptr, nullptr};
   bool prof = false;
   sag::EventHook hook;
   cudaGraphExec_t gexec = nullptr;
@@ -73,6 +74,9 @@ struct sag_plan_s {
   ~sag_plan_s() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (side.stream) cudaStreamDestroy(side.stream);
+    if (side.fork) cudaEventDestroy(side.fork);
+    if (side.join) cudaEventDestroy(side.join);
     for (void* q : allocs) cudaFree(q);
     if (stage_diag) cudaFree(stage_diag);
   }
