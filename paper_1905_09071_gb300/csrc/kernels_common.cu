@@ -366,9 +366,9 @@ cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, c
 }
 
 cudaError_t setup_common_kernels(const LaunchCfg& L) {
-  cudaError_t e = cudaFuncSetAttribute(k_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.epi_smem);
+  cudaError_t e = cudaFuncSetAttribute(k_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_coef, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.coef_smem);
+    e = cudaFuncSetAttribute(k_coef, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
   return e;
 }
 

@@ -20,9 +20,9 @@ cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double
 }
 
 cudaError_t setup_fft_kernels_f64(const LaunchCfg& L) {
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.col_smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.inv_smem);
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
   if (e == cudaSuccess) e = setup_tt_stage<cd>(L);
   return e;
 }

@@ -55,6 +55,16 @@ struct SideStream {
 cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
                          const EpiArgs& A, cudaStream_t st, LaunchHook* hook = nullptr,
                          const SideStream* side = nullptr);
+// Largest dynamic shared memory a block may use on the current device. Every
+// kernel's attribute is set to it: the attribute is per function for the
+// whole process, so a per-plan value would shrink the limit of other plans.
+inline int smem_limit() {
+  int dev = 0, v = 48 * 1024;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
 cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, cudaStream_t st);
 cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
                             LaunchHook* hook);

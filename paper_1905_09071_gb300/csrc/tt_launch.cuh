@@ -23,9 +23,9 @@ cudaError_t launch_tt_stage(const RhsParams& P, const LaunchCfg& L, cudaStream_t
 template <class C>
 cudaError_t setup_tt_stage(const LaunchCfg& L) {
   cudaError_t e = cudaFuncSetAttribute(k_rows_tt_fwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)L.rowtt_smem);
+                                       smem_limit());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_rows_tt_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.rowtt_smem);
+    e = cudaFuncSetAttribute(k_rows_tt_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
   return e;
 }
 

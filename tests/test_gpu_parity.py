@@ -303,3 +303,18 @@ def test_fp32_split_tracks_fp64_over_long_trajectory():
     for dg in (d64, ddw):
         tot = dg[:, 1] + dg[:, 2]
         assert np.max(np.abs(tot - tot[0])) < 1e-9 * tot[0]
+
+
+def test_plans_with_different_footprints_coexist():
+    # A later plan with smaller shared-memory blocks must not break an earlier one.
+    big = wl.random_cp(4, 20000, [2, 2, 2], seed=18)
+    small = wl.random_cp(2, 16, [1], seed=19)
+    for prec in PRECS:
+        with sag.Plan(big.N, big.D, big.ranks, big.factors, prec=prec) as p1, \
+                sag.Plan(small.N, small.D, small.ranks, small.factors, prec=prec) as p2:
+            for pl, s in ((p2, small), (p1, big), (p2, small)):
+                n = dev(s.n0)
+                out = torch.empty_like(n)
+                pl.rhs(n, out)
+                torch.cuda.synchronize()
+                assert pl.sync_status() == sag.SAG_OK
