@@ -563,3 +563,149 @@ int orc_brownian_tt(int D, int N, const double* mu, int* ranks_out, double* core
   }
   return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Discrete adjoint (vector-Jacobian products), CP kernels. Written from the
+ * definitions of p_k^(d) and q_k^(d) (Sec. 1) by the product rule:
+ *   d p_k / d a^(m)_r[i] = 1/d! (conv_{m' != m} a^(m')_r)[k - i],
+ * so the cotangent of a^(m)_r is the correlation of g with the other modes'
+ * convolution, and a^(m)_r = U^(m)_r o n passes it to n and to U; the loss
+ * term q_k = n_k sum_v coef_v U_v(k) is differentiated through n_k, through
+ * U_v(k) and through the inner products s inside coef.
+ * ------------------------------------------------------------------------- */
+static void vjp_cp_order(int N, int R, const double* blk, int d, const double* n, const double* g,
+                         int sym, double* gn, double* gblk) {
+  const double inv_dfact = 1.0 / factorial(d);
+  const double inv_d1fact = 1.0 / factorial(d - 1);
+  double* a = (double*)malloc(sizeof(double) * (size_t)d * N);
+  double* c = (double*)malloc(sizeof(double) * N);
+  double* t = (double*)malloc(sizeof(double) * N);
+  double* s = (double*)malloc(sizeof(double) * d);
+  double* z = (double*)malloc(sizeof(double) * d);
+  double* gn_n = (double*)malloc(sizeof(double) * N);
+  for (int k = 0; k < N; ++k) gn_n[k] = g[k] * n[k];
+  for (int r = 0; r < R; ++r) {
+    for (int m = 0; m < d; ++m) {
+      const double* u = cp_vec(blk, R, N, m, r);
+      for (int k = 0; k < N; ++k) a[(size_t)m * N + k] = u[k] * n[k];
+    }
+    /* Gain. */
+    for (int m = 0; m < d; ++m) {
+      /* c = convolution of every other mode, sizes 1..N */
+      int first = 1;
+      for (int mm = 0; mm < d; ++mm) {
+        if (mm == m) continue;
+        if (first) {
+          memcpy(c, a + (size_t)mm * N, sizeof(double) * N);
+          first = 0;
+        } else {
+          conv_sizes(c, N, a + (size_t)mm * N, N, t, N);
+          memcpy(c, t, sizeof(double) * N);
+        }
+      }
+      /* ga[i] = 1/d! sum_{j >= 1, i + j <= N} g[i + j] c[j] (sizes, 1-based) */
+      const double* u = cp_vec(blk, R, N, m, r);
+      double* gu = gblk + ((size_t)m * R + r) * N;
+#pragma omp parallel for schedule(dynamic, 64)
+      for (int i = 1; i <= N; ++i) {
+        nsum acc = {0.0, 0.0};
+        for (int j = 1; i + j <= N; ++j) ns_add(&acc, g[i + j - 1] * c[j - 1]);
+        const double ga = inv_dfact * ns_val(&acc);
+        gn[i - 1] += u[i - 1] * ga;
+        gu[i - 1] += n[i - 1] * ga;
+      }
+    }
+    /* Loss. coef_m = -1/(d-1)! w_m prod_{m' != m} s_{m'}, w_m = 1/d (sym) or [m = d-1]. */
+    for (int m = 0; m < d; ++m) {
+      s[m] = dot_n(cp_vec(blk, R, N, m, r), n, N);
+      z[m] = dot_n(cp_vec(blk, R, N, m, r), gn_n, N);
+    }
+    for (int m = 0; m < d; ++m) {
+      const double wm = sym ? 1.0 / d : (m == d - 1 ? 1.0 : 0.0);
+      double coef = -inv_d1fact * wm;
+      for (int mm = 0; mm < d; ++mm)
+        if (mm != m) coef *= s[mm];
+      /* sigma = dL/ds_m: coef_{m2} depends on s_m for every m2 != m */
+      double sigma = 0.0;
+      for (int m2 = 0; m2 < d; ++m2) {
+        if (m2 == m) continue;
+        const double w2 = sym ? 1.0 / d : (m2 == d - 1 ? 1.0 : 0.0);
+        double p = -inv_d1fact * w2 * z[m2];
+        for (int mm = 0; mm < d; ++mm)
+          if (mm != m2 && mm != m) p *= s[mm];
+        sigma += p;
+      }
+      const double* u = cp_vec(blk, R, N, m, r);
+      double* gu = gblk + ((size_t)m * R + r) * N;
+      for (int k = 0; k < N; ++k) {
+        gn[k] += g[k] * coef * u[k] + sigma * u[k];
+        gu[k] += coef * g[k] * n[k] + sigma * n[k];
+      }
+    }
+  }
+  free(a); free(c); free(t); free(s); free(z); free(gn_n);
+}
+
+int orc_rhs_vjp(int D, int N, const int* ranks, const double* factors, const double* n,
+                const double* g, int sym, double* gn, double* gU) {
+  if (!ranks_ok(ORC_CP, D, N, ranks) || !factors || !n || !g || !gn || !gU) return -1;
+  const long nf = orc_factor_count(ORC_CP, D, N, ranks);
+  for (int k = 0; k < N; ++k) gn[k] = 0.0;
+  for (long i = 0; i < nf; ++i) gU[i] = 0.0;
+  for (int d = 2; d <= D; ++d) {
+    const int* rk;
+    const long off = order_offset(ORC_CP, N, ranks, d, &rk);
+    vjp_cp_order(N, rk[0], factors + off, d, n, g, sym, gn, gU + off);
+  }
+  return 0;
+}
+
+/* Reverse pass through `steps` RK2 steps from n0 (states kept in memory).
+ * g_in: cotangent of the final state. Outputs g_n0 (cotangent of n0) and g_U
+ * (cotangent of the factors, accumulated over all steps). */
+int orc_integrate_vjp(int D, int N, const int* ranks, const double* factors, const double* n0,
+                      double dt, long steps, int sym, int method, const double* g_in, double* g_n0,
+                      double* g_U) {
+  if (!ranks_ok(ORC_CP, D, N, ranks) || !factors || !n0 || !g_in || !g_n0 || !g_U || steps < 0)
+    return -1;
+  if (method != ORC_HEUN && method != ORC_MIDPOINT) return -1;
+  const long nf = orc_factor_count(ORC_CP, D, N, ranks);
+  double* states = (double*)malloc(sizeof(double) * (size_t)(steps + 1) * N);
+  double* p = (double*)malloc(sizeof(double) * N);
+  double* q = (double*)malloc(sizeof(double) * N);
+  double* ns = (double*)malloc(sizeof(double) * N);
+  double* gbar = (double*)malloc(sizeof(double) * N);
+  double* gk = (double*)malloc(sizeof(double) * N);
+  double* gA = (double*)malloc(sizeof(double) * N);
+  double* gB = (double*)malloc(sizeof(double) * N);
+  double* gUa = (double*)malloc(sizeof(double) * nf);
+  memcpy(states, n0, sizeof(double) * N);
+  for (long s = 0; s < steps; ++s) {
+    memcpy(states + (size_t)(s + 1) * N, states + (size_t)s * N, sizeof(double) * N);
+    orc_integrate(ORC_DIRECT, ORC_CP, D, N, ranks, factors, states + (size_t)(s + 1) * N, dt, 1, sym,
+                  method, NULL);
+  }
+  memcpy(gbar, g_in, sizeof(double) * N);
+  for (long i = 0; i < nf; ++i) g_U[i] = 0.0;
+  for (long s = steps - 1; s >= 0; --s) {
+    const double* n = states + (size_t)s * N;
+    orc_rhs(ORC_DIRECT, ORC_CP, D, N, ranks, factors, n, sym, p, q, NULL);
+    const double h1 = method == ORC_HEUN ? dt : 0.5 * dt;
+    for (int k = 0; k < N; ++k) ns[k] = n[k] + h1 * (p[k] + q[k]);
+    /* second stage: k2 = F(n*) enters with weight dt/2 (Heun) or dt (midpoint) */
+    const double w2 = method == ORC_HEUN ? 0.5 * dt : dt;
+    for (int k = 0; k < N; ++k) gk[k] = w2 * gbar[k];
+    orc_rhs_vjp(D, N, ranks, factors, ns, gk, sym, gA, gUa);
+    for (long i = 0; i < nf; ++i) g_U[i] += gUa[i];
+    /* first stage: k1 = F(n) enters n' with weight dt/2 (Heun, 0 for midpoint)
+     * and n* with weight h1 */
+    const double w1 = method == ORC_HEUN ? 0.5 * dt : 0.0;
+    for (int k = 0; k < N; ++k) gk[k] = w1 * gbar[k] + h1 * gA[k];
+    orc_rhs_vjp(D, N, ranks, factors, n, gk, sym, gB, gUa);
+    for (long i = 0; i < nf; ++i) g_U[i] += gUa[i];
+    for (int k = 0; k < N; ++k) gbar[k] = gbar[k] + gA[k] + gB[k];
+  }
+  memcpy(g_n0, gbar, sizeof(double) * N);
+  free(states); free(p); free(q); free(ns); free(gbar); free(gk); free(gA); free(gB); free(gUa);
+  return 0;
+}

@@ -56,6 +56,18 @@ int orc_loss(int fmt, int D, int N, const int* ranks, const double* factors, con
 int orc_integrate(int mode, int fmt, int D, int N, const int* ranks, const double* factors,
                   double* n, double dt, long steps, int sym, int method, double* diag);
 
+/* Vector-Jacobian product of the right-hand side, CP kernels: for a cotangent
+ * g (length N), gn = (dF/dn)^T g and gU = (dF/dU)^T g (factor layout). */
+int orc_rhs_vjp(int D, int N, const int* ranks, const double* factors, const double* n,
+                const double* g, int sym, double* gn, double* gU);
+
+/* Discrete adjoint of `steps` RK2 steps from n0, CP kernels: given the
+ * cotangent g_in of the final state, returns the cotangent of n0 and the
+ * factors' cotangent accumulated over the steps. */
+int orc_integrate_vjp(int D, int N, const int* ranks, const double* factors, const double* n0,
+                      double dt, long steps, int sym, int method, const double* g_in, double* g_n0,
+                      double* g_U);
+
 /* Generalized Brownian kernel entry, Eq. ch3.eq17: sum over permutations sigma
  * of prod_m i_{sigma(m)}^{mu_m}. */
 double orc_brownian_entry(int D, const double* mu, const int* idx);

@@ -330,3 +330,47 @@ def test_workload_theorem1_cores_reproduce_eq17(D):
         idx = rng.integers(1, N + 1, D)
         want = oracle.brownian_entry(mu, idx)
         assert abs(_tt_contract(ranks, cores, N, idx) - want) < 1e-13 * abs(want)
+
+
+# ---------------------------------------------------------------- P9 adjoint
+def _F(n, D, ranks, f, sym):
+    p, q = oracle.rhs(n, D, ranks, f, sym=sym)
+    return p + q
+
+
+@pytest.mark.parametrize("sym", [1, 0])
+@pytest.mark.parametrize("D,N,ranks", [(2, 11, [3]), (3, 9, [2, 3]), (4, 7, [2, 1, 2])])
+def test_rhs_vjp_matches_central_differences(D, N, ranks, sym):
+    s = wl.random_cp(D, N, ranks, seed=60 + D)
+    rng = np.random.default_rng(61)
+    g = rng.normal(size=N)
+    un = rng.normal(size=N)
+    uf = rng.normal(size=s.factors.size)
+    gn, gU = oracle.rhs_vjp(s.n0, g, D, s.ranks, s.factors, sym=sym)
+    h = 1e-6
+    dn = (_F(s.n0 + h * un, D, s.ranks, s.factors, sym) - _F(s.n0 - h * un, D, s.ranks, s.factors, sym)) / (2 * h)
+    df = (_F(s.n0, D, s.ranks, s.factors + h * uf, sym) - _F(s.n0, D, s.ranks, s.factors - h * uf, sym)) / (2 * h)
+    assert abs(g @ dn - gn @ un) < 1e-8 * (abs(g) @ abs(dn) + 1e-30)
+    assert abs(g @ df - gU @ uf) < 1e-8 * (abs(g) @ abs(df) + 1e-30)
+
+
+@pytest.mark.parametrize("method", [oracle.HEUN, oracle.MIDPOINT])
+def test_integrate_vjp_matches_central_differences(method):
+    D, N = 3, 12
+    s = wl.random_cp(D, N, [2, 2], seed=70)
+    rng = np.random.default_rng(71)
+    g = rng.normal(size=N)
+    un = rng.normal(size=N)
+    uf = rng.normal(size=s.factors.size)
+    dt, steps = 0.05, 6
+    gn0, gU = oracle.integrate_vjp(s.n0, D, s.ranks, s.factors, dt, steps, g, method=method)
+
+    def L(n0, f):
+        n, _ = oracle.integrate(n0, D, s.ranks, f, dt, steps, method=method, diag=False)
+        return g @ n
+
+    h = 1e-6
+    d_n = (L(s.n0 + h * un, s.factors) - L(s.n0 - h * un, s.factors)) / (2 * h)
+    d_f = (L(s.n0, s.factors + h * uf) - L(s.n0, s.factors - h * uf)) / (2 * h)
+    assert abs(d_n - gn0 @ un) < 1e-7 * abs(d_n)
+    assert abs(d_f - gU @ uf) < 1e-7 * abs(d_f)
