@@ -135,6 +135,36 @@ sag_status sag_rk2_step(sag_plan_t plan, double* n, double dt, void* stream);
 sag_status sag_integrate(sag_plan_t plan, double* n, double dt, int64_t steps, double* diag,
                          void* stream);
 
+/* Adjoint (CP plans). The factors' cotangent uses the plan's vector layout:
+ * the systems' CP factor arrays ([d][R_d][N] per order) concatenated in system
+ * order, sag_plan_factor_count values in all.
+ *
+ * sag_rhs_vjp: vector-Jacobian product of the right-hand side at n for the
+ * cotangent g (packed state layout): gn = (dF/dn)^T g, gU = (dF/dU)^T g
+ * (either output may be NULL; both are overwritten). The gain term's
+ * derivative is a correlation of g with the other modes' convolution,
+ * evaluated with the same FFT lengths as the forward pass; the loss term's
+ * through n, U and the inner products s = <U, n> (product rule). */
+sag_status sag_rhs_vjp(sag_plan_t plan, const double* n, const double* g, double* gn, double* gU,
+                       void* stream);
+
+/* Discrete adjoint of `steps` RK2 steps of size dt from n0 (n0 is not
+ * modified): given the cotangent g_final of the final state, writes the
+ * cotangent of n0 to g_n0 and the factors' cotangent, summed over the steps,
+ * to g_U (either may be NULL). The forward states are recomputed from
+ * checkpoints every `ckpt` steps (ckpt <= 0: about sqrt(steps)); device memory
+ * for (steps/ckpt + ckpt + 5) state vectors is allocated on first use. */
+sag_status sag_integrate_vjp(sag_plan_t plan, const double* n0, double dt, int64_t steps, int64_t ckpt,
+                             const double* g_final, double* g_n0, double* g_U, void* stream);
+
+/* Replaces the factors of a CP plan (same systems and ranks; vector layout as
+ * above, host or device pointer) without allocating, so captured graphs stay
+ * valid. Synchronises the device first. */
+sag_status sag_plan_update_factors(sag_plan_t plan, const double* factors, int32_t on_device);
+
+/* Number of factor values in the plan's vector layout. */
+sag_status sag_plan_factor_count(sag_plan_t plan, int64_t* count);
+
 /* Waits for `stream`, then returns and clears the plan's latched device-side
  * status (SAG_OK, SAG_ENONFINITE or SAG_ETIMEOUT). */
 sag_status sag_sync_status(sag_plan_t plan, void* stream);

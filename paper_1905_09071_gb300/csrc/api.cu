@@ -325,6 +325,192 @@ sag_status sag_integrate(sag_plan_t pl, double* n, double dt, int64_t steps, dou
   return SAG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Checks that the plan can run the vector-Jacobian product.
+sag_status vjp_supported(sag_plan_t pl) {
+  if (pl->fmt != SAG_CP) return fail(SAG_EUNSUPPORTED, "the adjoint is implemented for CP kernels");
+  if ((int)pl->L.vrow_smem > smem_limit() || (int)pl->L.vcol_smem > smem_limit())
+    return fail(SAG_EUNSUPPORTED, "adjoint row blocks exceed shared memory (order or row length too large)");
+  return SAG_OK;
+}
+
+// Device view of a caller buffer of `count` doubles: the buffer itself if it
+// is device memory, else a plan staging buffer (copied in when `in`).
+sag_status stage(sag_plan_t pl, double* user, size_t count, bool in, double** dev, double** pool,
+                 size_t* pool_len, cudaStream_t st) {
+  if (!user || is_device_ptr(user)) {
+    *dev = user;
+    return SAG_OK;
+  }
+  if (*pool_len < count) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "sync");
+    if (*pool) cudaFree(*pool);
+    *pool = nullptr;
+    *pool_len = 0;
+    if (cudaMalloc(pool, count * sizeof(double)) != cudaSuccess) return fail(SAG_ENOMEM, "cudaMalloc staging");
+    *pool_len = count;
+  }
+  *dev = *pool;
+  if (in) {
+    cudaError_t e = cudaMemcpyAsync(*pool, user, count * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy in");
+  }
+  return SAG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sag_status sag_rhs_vjp(sag_plan_t pl, const double* n, const double* g, double* gn, double* gU,
+                       void* stream) {
+  if (!pl || !n || !g) return fail(SAG_EINVAL, "NULL argument");
+  sag_status s = vjp_supported(pl);
+  if (s != SAG_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t Nt = (size_t)pl->Ntot;
+  double *nd, *gd, *gnd, *gud;
+  // n -> stage_a, g -> stage_b, gn -> stage_c (state-sized); gU -> stage_g (factor-sized)
+  size_t la = Nt, lb = Nt, lc = Nt;
+  if ((s = stage(pl, const_cast<double*>(n), Nt, true, &nd, &pl->stage_a, &la, st)) != SAG_OK ||
+      (s = stage(pl, const_cast<double*>(g), Nt, true, &gd, &pl->stage_b, &lb, st)) != SAG_OK ||
+      (s = stage(pl, gn, Nt, false, &gnd, &pl->stage_c, &lc, st)) != SAG_OK ||
+      (s = stage(pl, gU, (size_t)pl->nfactor, false, &gud, &pl->stage_g, &pl->stage_g_len, st)) != SAG_OK)
+    return s;
+  cudaError_t e = enqueue_vjp(pl->P, pl->L, nd, gd, gnd, gud, 0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  bool sync = false;
+  if (gn && gnd != gn) {
+    if ((e = cudaMemcpyAsync(gn, gnd, Nt * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "copy gn");
+    sync = true;
+  }
+  if (gU && gud != gU) {
+    if ((e = cudaMemcpyAsync(gU, gud, (size_t)pl->nfactor * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "copy gU");
+    sync = true;
+  }
+  if (sync && (e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
+  return SAG_OK;
+}
+
+sag_status sag_integrate_vjp(sag_plan_t pl, const double* n0, double dt, int64_t steps, int64_t ckpt,
+                             const double* g_final, double* g_n0, double* g_U, void* stream) {
+  if (!pl || !n0 || !g_final) return fail(SAG_EINVAL, "NULL argument");
+  if (steps < 0) return fail(SAG_EINVAL, "steps must be >= 0");
+  if (!std::isfinite(dt)) return fail(SAG_EINVAL, "dt is not finite");
+  sag_status s = vjp_supported(pl);
+  if (s != SAG_OK) return s;
+  if (ckpt <= 0) {
+    ckpt = 1;
+    while (ckpt * ckpt < steps) ++ckpt;
+  }
+  if (ckpt > steps && steps > 0) ckpt = steps;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t Nt = (size_t)pl->Ntot;
+  const int64_t nck = steps > 0 ? (steps + ckpt - 1) / ckpt : 1;
+  // pool: checkpoints [nck], segment states [ckpt], x, gbar, gk, gA, gB
+  const size_t need = ((size_t)nck + (size_t)ckpt + 5) * Nt;
+  cudaError_t e;
+  if (pl->vjp_pool_len < need) {
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
+    if (pl->vjp_pool) cudaFree(pl->vjp_pool);
+    pl->vjp_pool = nullptr;
+    pl->vjp_pool_len = 0;
+    if (cudaMalloc(&pl->vjp_pool, need * sizeof(double)) != cudaSuccess)
+      return fail(SAG_ENOMEM, "cudaMalloc adjoint checkpoints");
+    pl->vjp_pool_len = need;
+  }
+  double* ck = pl->vjp_pool;
+  double* seg = ck + (size_t)nck * Nt;
+  double* x = seg + (size_t)ckpt * Nt;
+  double* gbar = x + Nt;
+  double* gk = gbar + Nt;
+  double* gA = gk + Nt;
+  double* gB = gA + Nt;
+  const size_t nb = Nt * sizeof(double);
+  const cudaMemcpyKind in_kind = is_device_ptr(n0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  double* gud;
+  if ((s = stage(pl, g_U, (size_t)pl->nfactor, false, &gud, &pl->stage_g, &pl->stage_g_len, st)) != SAG_OK)
+    return s;
+  // Forward sweep, keeping the state at the start of every segment.
+  if ((e = cudaMemcpyAsync(x, n0, nb, in_kind, st)) != cudaSuccess) return cuda_fail(e, "copy n0");
+  for (int64_t t = 0; t < steps; ++t) {
+    if (t % ckpt == 0 && (e = cudaMemcpyAsync(ck + (size_t)(t / ckpt) * Nt, x, nb, cudaMemcpyDeviceToDevice,
+                                              st)) != cudaSuccess)
+      return cuda_fail(e, "checkpoint");
+    if ((s = enqueue_step(pl, x, dt, nullptr, st, false)) != SAG_OK) return s;
+  }
+  // Reverse sweep: recompute each segment's states, then step backwards.
+  const cudaMemcpyKind g_kind = is_device_ptr(g_final) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if ((e = cudaMemcpyAsync(gbar, g_final, nb, g_kind, st)) != cudaSuccess) return cuda_fail(e, "copy g");
+  if (gud && (e = cudaMemsetAsync(gud, 0, (size_t)pl->nfactor * sizeof(double), st)) != cudaSuccess)
+    return cuda_fail(e, "zero gU");
+  const bool heun = pl->rk == SAG_HEUN;
+  const double h1 = heun ? dt : 0.5 * dt;   // n* = n + h1 k1
+  const double w1 = heun ? 0.5 * dt : 0.0;  // weight of k1 in the update
+  const double w2 = heun ? 0.5 * dt : dt;   // weight of k2 in the update
+  for (int64_t c = nck - 1; c >= 0 && steps > 0; --c) {
+    const int64_t t0 = c * ckpt, t1 = std::min<int64_t>(t0 + ckpt, steps);
+    if ((e = cudaMemcpyAsync(seg, ck + (size_t)c * Nt, nb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return cuda_fail(e, "restore");
+    for (int64_t t = t0; t + 1 < t1; ++t) {
+      double* cur = seg + (size_t)(t - t0) * Nt;
+      double* nxt = cur + Nt;
+      if ((e = cudaMemcpyAsync(nxt, cur, nb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "recompute");
+      if ((s = enqueue_step(pl, nxt, dt, nullptr, st, false)) != SAG_OK) return s;
+    }
+    for (int64_t t = t1 - 1; t >= t0; --t) {
+      double* n = seg + (size_t)(t - t0) * Nt;
+      EpiArgs a{};
+      a.nin = n;
+      a.k1buf = pl->k1buf;
+      a.out0 = pl->nstar;
+      a.dt = dt;
+      a.mode = heun ? EPI_HEUN1 : EPI_MID1;
+      if ((s = eval(pl, n, a, st, false)) != SAG_OK) return s;  // n* of this step
+      if ((e = enqueue_axpby(gk, w2, gbar, 0.0, nullptr, (int64_t)Nt, st)) != cudaSuccess ||
+          (e = enqueue_vjp(pl->P, pl->L, pl->nstar, gk, gA, gud, 1, st)) != cudaSuccess ||
+          (e = enqueue_axpby(gk, w1, gbar, h1, gA, (int64_t)Nt, st)) != cudaSuccess ||
+          (e = enqueue_vjp(pl->P, pl->L, n, gk, gB, gud, 1, st)) != cudaSuccess ||
+          (e = enqueue_axpby(gbar, 1.0, gbar, 1.0, gA, (int64_t)Nt, st)) != cudaSuccess ||
+          (e = enqueue_axpby(gbar, 1.0, gbar, 1.0, gB, (int64_t)Nt, st)) != cudaSuccess)
+        return cuda_fail(e, "adjoint step");
+    }
+  }
+  if (g_n0) {
+    const cudaMemcpyKind out_kind = is_device_ptr(g_n0) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if ((e = cudaMemcpyAsync(g_n0, gbar, nb, out_kind, st)) != cudaSuccess) return cuda_fail(e, "copy g_n0");
+  }
+  if (g_U && gud != g_U &&
+      (e = cudaMemcpyAsync(g_U, gud, (size_t)pl->nfactor * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess)
+    return cuda_fail(e, "copy g_U");
+  if ((g_n0 && !is_device_ptr(g_n0)) || (g_U && gud != g_U)) {
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
+  }
+  return SAG_OK;
+}
+
+sag_status sag_plan_update_factors(sag_plan_t pl, const double* factors, int32_t on_device) {
+  if (!pl || !factors) return fail(SAG_EINVAL, "NULL argument");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  return update_factors(pl, factors, on_device);
+}
+
+sag_status sag_plan_factor_count(sag_plan_t pl, int64_t* count) {
+  if (!pl || !count) return fail(SAG_EINVAL, "NULL argument");
+  *count = pl->nfactor;
+  return SAG_OK;
+}
+
 sag_status sag_sync_status(sag_plan_t pl, void* stream) {
   if (!pl) return fail(SAG_EINVAL, "NULL plan");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -360,6 +360,12 @@ cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* n
   return cudaGetLastError();
 }
 
+cudaError_t enqueue_nsplit(const RhsParams& P, const LaunchCfg& L, const double* n, cudaStream_t st) {
+  k_nmax<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, n);
+  k_nsplit<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, n);
+  return cudaGetLastError();
+}
+
 cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, cudaStream_t st) {
   k_moments<<<P.B, 1024, 0, st>>>(P, n, diag);
   return cudaGetLastError();

@@ -19,6 +19,11 @@ cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double
   return cudaGetLastError();
 }
 
+cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
+  k_fwd_col<cd><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin);
+  return cudaGetLastError();
+}
+
 cudaError_t setup_fft_kernels_f64(const LaunchCfg& L) {
   cudaError_t e = cudaFuncSetAttribute(k_fwd_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());

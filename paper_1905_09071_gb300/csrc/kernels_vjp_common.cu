@@ -1,0 +1,222 @@
+// Vector-Jacobian product of the CP right-hand side: the non-FFT kernels
+// (cotangent scaling, inner products, loss-term derivatives, assembly) and
+// the launch sequence. The loss term q_k = n_k sum_v coef_v U_v(k), with
+// coef_v built from the inner products s = <U, n>, is differentiated by the
+// product rule: through n_k, through U_v(k), and through every s in coef:
+//   sigma_v = dL/ds_v = sum_{v' of the same rank term, v' != v}
+//             z_{v'} d coef_{v'} / d s_v,   z_v = <U_v, g o n>.
+#include "launch.h"
+
+namespace sag {
+
+cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                              cudaStream_t st);
+cudaError_t launch_vjp_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                               cudaStream_t st);
+
+namespace {
+
+template <int NV>
+__device__ __forceinline__ void block_sum_v(double (&v)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[warp * NV + i] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      v[i] = lane < nw ? sh[lane * NV + i] : 0.0;
+      for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double inv_fact(int d) {
+  double f = 1.0;
+  for (int i = 2; i <= d; ++i) f *= i;
+  return 1.0 / f;
+}
+
+// g for the double-word path: g 2^-e_g with max |g| 2^-e_g in [0.5, 1), per system.
+__global__ void k_gmax(const __grid_constant__ RhsParams P, const double* __restrict__ g) {
+  const SysDesc s = P.sys[blockIdx.y];
+  const double* x = g + s.noff;
+  double m = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.N; k += gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[k]));
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(&P.sc[blockIdx.y].gmax_bits, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_gsplit(const __grid_constant__ RhsParams P, const double* __restrict__ g) {
+  const SysDesc s = P.sys[blockIdx.y];
+  SysScalars* sc = &P.sc[blockIdx.y];
+  const double mx = __longlong_as_double((long long)sc->gmax_bits);
+  const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) + 1 : 0;
+  const double* x = g + s.noff;
+  float2* out = P.gdw + s.noff;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.N; k += gridDim.x * blockDim.x) {
+    const dw v = dw_from_double(scalbn(x[k], -e));
+    out[k] = make_float2(v.hi, v.lo);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->e_g = e;
+}
+
+// s_v = <U_v, n> and z_v = <U_v, g o n> partial sums (FP64).
+__global__ void __launch_bounds__(256) k_dot2(const __grid_constant__ RhsParams P,
+                                              const double* __restrict__ n,
+                                              const double* __restrict__ g) {
+  __shared__ double sh[64];
+  const int v = blockIdx.x, c = blockIdx.y;
+  const SysDesc s = P.sys[P.vsys[v]];
+  if (c >= s.ndotchunk) return;
+  const int k0 = c * P.dotchunk, k1 = min(s.N, k0 + P.dotchunk);
+  const double* u = P.U64 + P.voff[v];
+  const double* x = n + s.noff;
+  const double* y = g + s.noff;
+  double acc[2] = {0.0, 0.0};
+  for (int k = k0 + threadIdx.x; k < k1; k += 256) {
+    const double un = u[k] * x[k];
+    acc[0] += un;
+    acc[1] = fma(un, y[k], acc[1]);
+  }
+  block_sum_v<2>(acc, sh);
+  if (threadIdx.x == 0) {
+    P.dot_s[(int64_t)v * P.maxdotchunk + c] = acc[0];
+    P.dot_z[(int64_t)v * P.maxdotchunk + c] = acc[1];
+  }
+}
+
+// coef_v (as in the forward pass) and sigma_v, one block per system.
+__global__ void __launch_bounds__(256) k_coef_vjp(const __grid_constant__ RhsParams P) {
+  extern __shared__ double csh[];  // s, z of the system's vectors
+  const int b = blockIdx.x;
+  const SysDesc sy = P.sys[b];
+  const int nv = sy.vend - sy.vbeg, nc = sy.ndotchunk;
+  double* s = csh;
+  double* z = csh + nv;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const int64_t base = (int64_t)(sy.vbeg + i) * P.maxdotchunk;
+    double a = 0.0, c2 = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      a += P.dot_s[base + c];
+      c2 += P.dot_z[base + c];
+    }
+    s[i] = a;
+    z[i] = c2;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const int v = sy.vbeg + i;
+    int it = sy.ibeg;
+    while (it + 1 < sy.iend && v >= P.ord[it + 1].vbase) ++it;
+    const OrderDesc& od = P.ord[it];
+    const int d = od.d, R = od.R, loc = v - od.vbase, m = loc / R, r = loc - m * R;
+    const int lb = od.vbase - sy.vbeg;
+    const double f1 = inv_fact(d - 1);
+    double prod = 1.0;
+    for (int mm = 0; mm < d; ++mm)
+      if (mm != m) prod *= s[lb + mm * R + r];
+    const double wm = P.sym ? 1.0 / d : (m == d - 1 ? 1.0 : 0.0);
+    P.coef[v] = -f1 * wm * prod;
+    double sg = 0.0;
+    for (int m2 = 0; m2 < d; ++m2) {
+      if (m2 == m) continue;
+      const double w2 = P.sym ? 1.0 / d : (m2 == d - 1 ? 1.0 : 0.0);
+      double p2 = -f1 * w2 * z[lb + m2 * R + r];
+      for (int mm = 0; mm < d; ++mm)
+        if (mm != m2 && mm != m) p2 *= s[lb + mm * R + r];
+      sg += p2;
+    }
+    P.sigma[v] = sg;
+  }
+  if (threadIdx.x == 0) {
+    P.sc[b].nmax_bits = 0ull;
+    P.sc[b].gmax_bits = 0ull;
+  }
+}
+
+// gn_k = g_k w_k + sum_v U_v(k) (ga_v(k) + sigma_v),
+// gU_v(k) (=|+=) n_k (ga_v(k) + sigma_v) + coef_v g_k n_k.
+__global__ void __launch_bounds__(256) k_vjp_final(const __grid_constant__ RhsParams P,
+                                                   const double* __restrict__ n,
+                                                   const double* __restrict__ g, double* gn,
+                                                   double* gU, int accumulate) {
+  extern __shared__ double fsh[];  // coef, sigma of the system's vectors
+  const int b = find_segment(P.epipre, P.B, blockIdx.x);
+  const SysDesc sy = P.sys[b];
+  const int nv = sy.vend - sy.vbeg, N = sy.N;
+  double* coef = fsh;
+  double* sig = fsh + nv;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    coef[i] = P.coef[sy.vbeg + i];
+    sig[i] = P.sigma[sy.vbeg + i];
+  }
+  __syncthreads();
+  const int k = (blockIdx.x - P.epipre[b]) * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int64_t gk = sy.noff + k;
+  const double nk = n[gk], gg = g[gk];
+  const int64_t base = P.voff[sy.vbeg] + k;  // a system's vectors are stored back to back
+  double w = 0.0, acc = 0.0;
+  for (int i = 0; i < nv; ++i) {
+    const int64_t o = base + (int64_t)i * N;
+    const double u = P.U64[o];
+    const double ga = P.gabuf[o] + sig[i];
+    w = fma(coef[i], u, w);
+    acc = fma(u, ga, acc);
+    if (gU) {
+      const double val = fma(nk, ga, coef[i] * gg * nk);
+      gU[o] = accumulate ? gU[o] + val : val;
+    }
+  }
+  if (gn) gn[gk] = fma(gg, w, acc);
+}
+
+__global__ void k_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (y ? fma(a, x[i], b * y[i]) : a * x[i]);
+}
+
+}  // namespace
+
+cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                        double* gn, double* gU, int accumulate, cudaStream_t st) {
+  cudaError_t e;
+  if (P.dwpath) {
+    // n and g to double-word with their own power-of-two scales; the max
+    // counters start at zero and k_coef_vjp resets them for the next call.
+    enqueue_nsplit(P, L, n, st);
+    k_gmax<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, g);
+    k_gsplit<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, g);
+  }
+  e = P.dwpath ? launch_vjp_fft_dw(P, L, n, g, st) : launch_vjp_fft_f64(P, L, n, g, st);
+  if (e != cudaSuccess) return e;
+  k_dot2<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, st>>>(P, n, g);
+  k_coef_vjp<<<P.B, 256, L.coef_smem, st>>>(P);
+  k_vjp_final<<<L.epi_blocks, 256, L.coef_smem, st>>>(P, n, g, gn, gU, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n,
+                          cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  k_axpby<<<blocks, 256, 0, st>>>(out, a, x, b, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_vjp_common(const LaunchCfg& L) {
+  (void)L;
+  cudaError_t e = cudaFuncSetAttribute(k_coef_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vjp_final, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  return e;
+}
+
+}  // namespace sag

@@ -1,0 +1,27 @@
+// FFT kernels of the vector-Jacobian product, double-word FP32 path.
+#include "launch.h"
+#include "vjp_kernels.cuh"
+
+namespace sag {
+
+cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+
+cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                              cudaStream_t st) {
+  cudaError_t e = launch_k_fwd_col_dw(P, L, n, st);
+  if (e != cudaSuccess) return e;
+  k_gcol<cdw><<<L.inv_blocks, kThreads, L.vcol_smem, st>>>(P, g);
+  k_rows_vjp<cdw><<<L.row_blocks, kThreads, L.vrow_smem, st>>>(P);
+  k_inv_col_vjp<cdw><<<L.col_blocks, kThreads, L.vcol_smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_vjp_fft_dw(const LaunchCfg& L) {
+  (void)L;
+  cudaError_t e = cudaFuncSetAttribute(k_gcol<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows_vjp<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col_vjp<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  return e;
+}
+
+}  // namespace sag

@@ -1,0 +1,27 @@
+// FFT kernels of the vector-Jacobian product, FP64 path.
+#include "launch.h"
+#include "vjp_kernels.cuh"
+
+namespace sag {
+
+cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+
+cudaError_t launch_vjp_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                              cudaStream_t st) {
+  cudaError_t e = launch_fwd_col_f64(P, L, n, st);
+  if (e != cudaSuccess) return e;
+  k_gcol<cd><<<L.inv_blocks, kThreads, L.vcol_smem, st>>>(P, g);
+  k_rows_vjp<cd><<<L.row_blocks, kThreads, L.vrow_smem, st>>>(P);
+  k_inv_col_vjp<cd><<<L.col_blocks, kThreads, L.vcol_smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_vjp_fft_f64(const LaunchCfg& L) {
+  (void)L;
+  cudaError_t e = cudaFuncSetAttribute(k_gcol<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows_vjp<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col_vjp<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  return e;
+}
+
+}  // namespace sag

@@ -14,6 +14,7 @@ struct LaunchCfg {
   int chain_blocks;
   int has_tt;           // the plan's systems use TT kernels (one format per plan)
   size_t col_smem, row_smem, inv_smem, epi_smem, coef_smem, rowtt_smem;
+  size_t vcol_smem, vrow_smem;  // vector-Jacobian product kernels (0: not available)
 };
 
 // What the epilogue writes (see EpiMode).
@@ -71,6 +72,17 @@ cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double
 cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
                            LaunchHook* hook);
 cudaError_t setup_common_kernels(const LaunchCfg& L);
+// n -> double-word with its per-system power-of-two scale (resets nothing).
+cudaError_t enqueue_nsplit(const RhsParams& P, const LaunchCfg& L, const double* n, cudaStream_t st);
+// Vector-Jacobian product of the CP right-hand side at n for cotangent g:
+// gn = (dF/dn)^T g, gU (vector layout) = (dF/dU)^T g, added to gU if accumulate.
+cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                        double* gn, double* gU, int accumulate, cudaStream_t st);
+cudaError_t enqueue_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n,
+                          cudaStream_t st);
+cudaError_t setup_vjp_common(const LaunchCfg& L);
+cudaError_t setup_vjp_fft_dw(const LaunchCfg& L);
+cudaError_t setup_vjp_fft_f64(const LaunchCfg& L);
 cudaError_t setup_fft_kernels_f64(const LaunchCfg& L);
 cudaError_t setup_fft_kernels_dw(const LaunchCfg& L);
 

@@ -50,6 +50,7 @@ struct OrderDesc {
   const void* twL;     // M entries omega_L^k, k < M (real-FFT split)
   const float* rscale; // CP, double-word path: [R] power-of-two weight of rank term r
   double pscale;       // final FP64 scale of P^(d) (1/(L d!), factors of two), before the n scale
+  double gscale;       // 2^-d / (L d!): final scale of a vector's cotangent before its exponents
 };
 
 // One system of the batch.
@@ -65,14 +66,15 @@ struct SysDesc {
 // Per-system device scalars (one 64-byte line each).
 struct SysScalars {
   unsigned long long nmax_bits;  // bits of max |n| (non-negative doubles order like integers)
+  unsigned long long gmax_bits;  // bits of max |g| of a vector-Jacobian product's cotangent
   int e_n;                       // power-of-two scale of n in the double-word path
+  int e_g;                       // power-of-two scale of the cotangent g
   int step;                      // diagnostic row counter of sag_integrate
+  unsigned int counter;          // last-block detection of the epilogue
   double o_stage1;               // outflow at the first stage of an RK2 step
   double cum;                    // cumulative outflow
   double outflow;                // last evaluated outflow
   double gflux;                  // sum_d 1/d! sum_{i in [1,N]^d} |i| C_i prod n (complete first-moment flux)
-  unsigned int counter;          // last-block detection of the epilogue
-  unsigned int pad[3];
 };
 
 enum : unsigned { kStatusNonFinite = 1u, kStatusTimeout = 2u };
@@ -116,6 +118,12 @@ struct RhsParams {
   double* dot_t;                 // [Vtot][maxdotchunk] partial <k U, n>
   double* coef;                  // [Vtot] loss weights: q_k = n_k sum_v coef_v U_v(k)
   double* epi_part;              // [epilogue blocks][4] block partials
+  // vector-Jacobian product workspace (CP)
+  float2* gdw;                   // [Ntot] double-word cotangent scaled by 2^-e_g of its system
+  double* gabuf;                 // cotangent of each a = U o n (vector layout, voff)
+  double* dot_z;                 // [Vtot][maxdotchunk] partial <U, g o n>
+  double* sigma;                 // [Vtot] dL/ds_v through the loss weights
+  const int* vexcl;              // [Vtot] sum of the other modes' exponents e_v of the rank term
   SysScalars* sc;                // [B]
   unsigned int* status;          // latched device status bits of the plan
 };

@@ -228,6 +228,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     pl->offsets[b + 1] = noff;
   }
   pl->Ntot = noff;
+  pl->nfactor = (int64_t)hf.size();
   P.Ntot = noff;
   P.Vtot = (int)vsys.size();
   P.nitems = (int)I.size();
@@ -287,6 +288,11 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     row_smem = std::max(row_smem, (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize + (od.ct2 ? 16 : 0));
     rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * G * 2 * od.ld2, 6 * od.ld2) * csize +
                                           (size_t)od.M2 * csize);
+    // Vector-Jacobian product kernels (CP): ping-pong column blocks; row
+    // blocks hold the d vectors of a rank term, g's spectrum and d spectra.
+    pl->L.vcol_smem = std::max(pl->L.vcol_smem, (size_t)(2 * W * od.ld1 + od.M1) * csize);
+    pl->L.vrow_smem = std::max(pl->L.vrow_smem, (size_t)(4 * d * od.ld2 + (d + 1) * (2 * od.M2 + 1) +
+                                                         od.M2) * csize);
   }
   // Row blocks: items with the most vectors first.
   std::vector<int> rowperm(I.size());
@@ -394,7 +400,19 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     // A factor 2 per mode comes from the real split (2 A[k]), 1/L from the
     // unnormalised inverse, 1/d! from the definition of p^(d).
     od.pscale = std::ldexp(1.0, Esum - d) / ((double)od.L * factorial(d));
+    od.gscale = std::ldexp(1.0, -d) / ((double)od.L * factorial(d));
   }
+  // Vector-Jacobian product: exponent sum of the other modes of each CP vector.
+  std::vector<int> vexcl(Vtot, 0);
+  if (!tt)
+    for (const OrderDesc& od : I)
+      for (int m = 0; m < od.d; ++m)
+        for (int r = 0; r < od.R; ++r) {
+          int sum = 0;
+          for (int mm = 0; mm < od.d; ++mm)
+            if (mm != m) sum += ev[od.vbase + mm * od.R + r];
+          vexcl[od.vbase + m * od.R + r] = sum;
+        }
 
   // ---- workspace and tables ---------------------------------------------------
   void* scratch = nullptr;
@@ -443,12 +461,23 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       pl->alloc(&pl->stage_c, Nt) != cudaSuccess || pl->alloc(&pl->dev_outflow, (size_t)B) != cudaSuccess)
     return fail(SAG_ENOMEM, "cudaMalloc workspace");
   P.epi_part = pl->epi_part;
+  if (!tt) {
+    int* d_vexcl = nullptr;
+    if (pl->upload(&d_vexcl, vexcl) != cudaSuccess || pl->alloc(&P.gabuf, hf.size()) != cudaSuccess ||
+        pl->alloc(&P.dot_z, (size_t)Vtot * P.maxdotchunk) != cudaSuccess ||
+        pl->alloc(&P.sigma, (size_t)Vtot) != cudaSuccess ||
+        (dwp && pl->alloc(&P.gdw, Nt) != cudaSuccess))
+      return fail(SAG_ENOMEM, "cudaMalloc adjoint workspace");
+    P.vexcl = d_vexcl;
+  }
   if ((e = cudaMemset(P.sc, 0, sizeof(SysScalars) * B)) != cudaSuccess ||
       (e = cudaMemset(P.status, 0, sizeof(unsigned))) != cudaSuccess)
     return cuda_fail(e, "memset");
 
   e = setup_common_kernels(L);
   if (e == cudaSuccess) e = dwp ? setup_fft_kernels_dw(L) : setup_fft_kernels_f64(L);
+  if (e == cudaSuccess) e = setup_vjp_common(L);
+  if (e == cudaSuccess) e = dwp ? setup_vjp_fft_dw(L) : setup_vjp_fft_f64(L);
   if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
   if ((e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&pl->side.stream, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -456,6 +485,81 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       (e = cudaEventCreateWithFlags(&pl->side.join, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(e, "stream");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "plan setup");
+  return SAG_OK;
+}
+
+}  // namespace sag
+
+namespace sag {
+
+// New values for the factors of a CP plan (same systems, ranks and layout):
+// the FP64 and double-word copies, the power-of-two scales and the tables
+// that depend on them are rewritten in place; nothing is allocated, so
+// captured graphs stay valid.
+sag_status update_factors(sag_plan_s* pl, const double* factors, int on_device) {
+  if (pl->fmt != SAG_CP) return fail(SAG_EUNSUPPORTED, "factor updates need a CP plan");
+  RhsParams& P = pl->P;
+  const bool dwp = P.dwpath != 0;
+  const int Vtot = P.Vtot;
+  const size_t nf = (size_t)pl->nfactor;
+  std::vector<double> hf(nf);
+  cudaError_t e = cudaMemcpy(hf.data(), factors, nf * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "copy factors");
+  for (double x : hf)
+    if (!std::isfinite(x)) return fail(SAG_EINVAL, "factors contain Inf or NaN");
+  if ((e = cudaMemcpy((void*)P.U64, hf.data(), nf * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "upload factors");
+  std::vector<int> ev(Vtot, 0);
+  std::vector<int64_t> voff(Vtot);
+  if ((e = cudaMemcpy(voff.data(), P.voff, sizeof(int64_t) * Vtot, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "read layout");
+  if (dwp) {
+    std::vector<float2> hdw(nf);
+    for (const SysDesc& sd : pl->systems)
+      for (int v = sd.vbeg; v < sd.vend; ++v) {
+        const double* x = hf.data() + voff[v];
+        double mx = 0.0;
+        for (int k = 0; k < sd.N; ++k) mx = std::max(mx, std::fabs(x[k]));
+        int ex = 0;
+        if (mx > 0.0) std::frexp(mx, &ex);
+        ev[v] = ex;
+        for (int k = 0; k < sd.N; ++k) {
+          dw y = dw_from_double(std::ldexp(x[k], -ex));
+          hdw[voff[v] + k] = make_float2(y.hi, y.lo);
+        }
+      }
+    if ((e = cudaMemcpy((void*)P.Udw, hdw.data(), nf * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "upload dw factors");
+  }
+  std::vector<int> vexcl(Vtot, 0);
+  for (OrderDesc& od : pl->items) {
+    const int d = od.d;
+    int Esum = 0;
+    if (dwp) {
+      std::vector<int> sig(od.R, 0);
+      for (int r = 0; r < od.R; ++r)
+        for (int m = 0; m < d; ++m) sig[r] += ev[od.vbase + m * od.R + r];
+      Esum = *std::max_element(sig.begin(), sig.end());
+      std::vector<float> rs(od.R);
+      for (int r = 0; r < od.R; ++r) rs[r] = std::ldexp(1.0f, sig[r] - Esum);
+      if ((e = cudaMemcpy((void*)od.rscale, rs.data(), sizeof(float) * od.R, cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return cuda_fail(e, "upload rank scales");
+    }
+    od.pscale = std::ldexp(1.0, Esum - d) / ((double)od.L * factorial(d));
+    for (int m = 0; m < d; ++m)
+      for (int r = 0; r < od.R; ++r) {
+        int sum = 0;
+        for (int mm = 0; mm < d; ++mm)
+          if (mm != m) sum += ev[od.vbase + mm * od.R + r];
+        vexcl[od.vbase + m * od.R + r] = sum;
+      }
+  }
+  if ((e = cudaMemcpy((void*)P.ord, pl->items.data(), sizeof(OrderDesc) * pl->items.size(),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy((void*)P.vexcl, vexcl.data(), sizeof(int) * Vtot, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "upload tables");
   return SAG_OK;
 }
 

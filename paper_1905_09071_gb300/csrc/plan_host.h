@@ -32,6 +32,12 @@ struct sag_plan_s {
   sag::LaunchCfg L{};
   int B = 0, prec = 0, rk = 0, sym = 1, fmt = 0;
   int64_t Ntot = 0;
+  int64_t nfactor = 0;                    // factor values over all vectors (vector layout)
+  // integrate_vjp buffers, allocated on first use
+  double* vjp_pool = nullptr;
+  size_t vjp_pool_len = 0;
+  double* stage_g = nullptr;              // host-buffer staging of factor-sized arrays
+  size_t stage_g_len = 0;
   std::vector<int64_t> offsets;           // [B + 1] packed offsets
   std::vector<sag::OrderDesc> items;      // host copy of the item table
   std::vector<sag::SysDesc> systems;      // host copy of the system table
@@ -79,10 +85,13 @@ struct sag_plan_s {
     if (side.join) cudaEventDestroy(side.join);
     for (void* q : allocs) cudaFree(q);
     if (stage_diag) cudaFree(stage_diag);
+    if (vjp_pool) cudaFree(vjp_pool);
+    if (stage_g) cudaFree(stage_g);
   }
 };
 
 namespace sag {
 sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options& opt);
 sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, sag_plan_s* pl);
+sag_status update_factors(sag_plan_s* pl, const double* factors, int on_device);
 }  // namespace sag

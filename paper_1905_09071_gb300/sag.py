@@ -26,7 +26,8 @@ EXPORTS = [
     "sag_default_options", "sag_plan", "sag_plan_layout", "sag_plan_bytes", "sag_rhs",
     "sag_rhs_parts", "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_plan_destroy",
     "sag_last_error", "sag_version", "sag_profile_enable", "sag_profile_read", "sag_kernel_name",
-    "sag_kernel_work", "sag_plan_describe", "sag_loss_noalloc",
+    "sag_kernel_work", "sag_plan_describe", "sag_loss_noalloc", "sag_rhs_vjp", "sag_integrate_vjp",
+    "sag_plan_update_factors", "sag_plan_factor_count",
 ]
 SAG_NUM_KERNELS = 12
 
@@ -93,10 +94,15 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(f64)]
         lib.sag_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         lib.sag_loss_noalloc.argtypes = [ctypes.POINTER(_System), i32, vp, vp, vp]
+        lib.sag_rhs_vjp.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.sag_integrate_vjp.argtypes = [vp, vp, f64, i64, i64, vp, vp, vp, vp]
+        lib.sag_plan_update_factors.argtypes = [vp, vp, i32]
+        lib.sag_plan_factor_count.argtypes = [vp, ctypes.POINTER(i64)]
         lib.sag_loss_noalloc.restype = ctypes.c_int
         for name in ("sag_plan", "sag_plan_layout", "sag_plan_bytes", "sag_rhs", "sag_rhs_parts",
                      "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_profile_enable",
-                     "sag_profile_read", "sag_kernel_work", "sag_plan_describe"):
+                     "sag_profile_read", "sag_kernel_work", "sag_plan_describe", "sag_rhs_vjp",
+                     "sag_integrate_vjp", "sag_plan_update_factors", "sag_plan_factor_count"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -241,6 +247,37 @@ class Plan:
         _check(self._lib.sag_profile_read(self._h, ms, cnt, SAG_NUM_KERNELS))
         return {self._lib.sag_kernel_name(i).decode(): (ms[i], cnt[i])
                 for i in range(SAG_NUM_KERNELS) if cnt[i]}
+
+    def factor_count(self) -> int:
+        c = ctypes.c_int64()
+        _check(self._lib.sag_plan_factor_count(self._h, ctypes.byref(c)))
+        return int(c.value)
+
+    def rhs_vjp(self, n, g, gn=None, gU=None, stream=None):
+        """gn = (dF/dn)^T g, gU = (dF/dU)^T g (vector layout)."""
+        _check(self._lib.sag_rhs_vjp(self._h, _ptr(n), _ptr(g), _ptr(gn), _ptr(gU),
+                                     _stream(stream, n, g, gn, gU)))
+        return gn, gU
+
+    def integrate_vjp(self, n0, dt: float, steps: int, g_final, g_n0=None, g_U=None, ckpt: int = 0,
+                      stream=None):
+        """Discrete adjoint of `steps` RK2 steps from n0 (checkpointed)."""
+        _check(self._lib.sag_integrate_vjp(self._h, _ptr(n0), float(dt), int(steps), int(ckpt),
+                                           _ptr(g_final), _ptr(g_n0), _ptr(g_U),
+                                           _stream(stream, n0, g_final, g_n0, g_U)))
+        return g_n0, g_U
+
+    def update_factors(self, factors):
+        """New factor values (same ranks), host numpy or device torch FP64."""
+        on_dev = 0
+        try:
+            import torch
+            on_dev = int(isinstance(factors, torch.Tensor) and factors.is_cuda)
+        except ImportError:
+            pass
+        if not on_dev:
+            factors = np.ascontiguousarray(np.asarray(factors, dtype=np.float64))
+        _check(self._lib.sag_plan_update_factors(self._h, _ptr(factors), on_dev))
 
     def kernel_work(self, name_or_id) -> dict:
         """Algorithmic ops (FP32 or FP64 instructions) and HBM bytes of one launch."""

@@ -225,3 +225,38 @@ def batched_power_cp(B: int = 256, seed: int = BASE_SEED + 1, n_range=(1024, 327
         out.append(System(D, N, "cp", ranks, f, normalised(np.exp(-sizes(N) / decay)), dt=1e-4,
                           name=f"batched_{b}", meta={"seed": seed, "index": b}))
     return out
+
+
+def adjoint_fit_problem(N: int = 8192, R: int = 9, seed: int = BASE_SEED + 2, extra_scale: float = 1e-3,
+                        rel_perturb: float = 0.05) -> dict:
+    """Kernel fitting: D = 3 with CP rank R for both orders. The first terms of
+    each order are the Brownian CP of ``brownian_cp`` (4 for d = 2, 9 for
+    d = 3); the remaining terms of order 2 are u i^a with u = extra_scale^{1/d}
+    per mode and a ~ U[-0.3, 0.3] (drawn in order). The initial factors are
+    rounded to FP32 (trainable FP32 parameters). The target kernel scales each
+    factor vector by (1 + rel_perturb N(0, 1)) (drawn in vector order after the
+    exponents). Start n_k proportional to exp(-k), Heun dt = 1e-3, 200 steps,
+    checkpoints every 20."""
+    rng = np.random.default_rng(seed)
+    D = 3
+    base = brownian_cp(D, N)
+    offs = cp_layout(D, N, base.ranks)
+    i = sizes(N)
+    per = {}
+    for d in range(2, D + 1):
+        Rb = base.ranks[d - 2]
+        Ub = base.factors[offs[d - 2]:offs[d - 1]].reshape(d, Rb, N)
+        U = np.empty((d, R, N))
+        U[:, :Rb] = Ub[:, :min(Rb, R)]
+        for r in range(Rb, R):
+            a = rng.uniform(-0.3, 0.3, d)
+            for m in range(d):
+                U[m, r] = extra_scale ** (1.0 / d) * i ** a[m]
+        per[d] = U
+    ranks, f = cp_from_vectors(D, N, per)
+    f0 = f.astype(np.float32).astype(np.float64)
+    nvec = f.size // N
+    scale = 1.0 + rel_perturb * rng.normal(size=nvec)
+    target = (f0.reshape(nvec, N) * scale[:, None]).reshape(-1)
+    return {"D": D, "N": N, "ranks": ranks, "factors0": f0, "target_factors": target,
+            "n0": base.n0.copy(), "dt": 1e-3, "steps": 200, "ckpt": 20}

@@ -1,0 +1,150 @@
+"""The adjoint: vector-Jacobian products of the right-hand side and the
+checkpointed discrete adjoint of RK2, against the CPU oracle's adjoint and
+central finite differences; the PyTorch autograd wrapper on the kernel-fitting
+workload (D=3, N=8192, CP rank 9, 200 Heun steps, checkpoints every 20)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_09071_gb300 import sag, workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECS = [sag.SAG_FP64, sag.SAG_FP32_SPLIT]
+# relative max-norm tolerances of cotangents
+TOL = {sag.SAG_FP64: 1e-11, sag.SAG_FP32_SPLIT: 1e-9}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(x):
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def rel(x, ref):
+    return float(np.max(np.abs(np.asarray(x) - ref)) / np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("sym", [1, 0])
+@pytest.mark.parametrize("D,N,ranks", [(2, 7, [3]), (3, 100, [2, 3]), (4, 333, [2, 1, 2]),
+                                       (3, 1537, [3, 2])])
+def test_rhs_vjp_matches_oracle(D, N, ranks, sym, prec):
+    s = wl.random_cp(D, N, ranks, seed=80 + N)
+    g = np.random.default_rng(81).normal(size=N)
+    gn_ref, gU_ref = oracle.rhs_vjp(s.n0, g, D, s.ranks, s.factors, sym=sym)
+    with sag.Plan(N, D, s.ranks, s.factors, prec=prec, symmetrize_q=sym) as pl:
+        assert pl.factor_count() == s.factors.size
+        gn = torch.empty(N, dtype=torch.float64, device="cuda")
+        gU = torch.empty(s.factors.size, dtype=torch.float64, device="cuda")
+        pl.rhs_vjp(dev(s.n0), dev(g), gn, gU)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+    assert rel(gn.cpu().numpy(), gn_ref) < TOL[prec]
+    assert rel(gU.cpu().numpy(), gU_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("rk", [sag.SAG_HEUN, sag.SAG_MIDPOINT])
+def test_integrate_vjp_matches_oracle_adjoint(prec, rk):
+    s = wl.random_cp(3, 256, [3, 4], seed=90)
+    steps, dt, ckpt = 13, 0.05, 4  # segments of 4, 4, 4, 1 steps
+    g = np.random.default_rng(91).normal(size=s.N)
+    method = oracle.HEUN if rk == sag.SAG_HEUN else oracle.MIDPOINT
+    gn_ref, gU_ref = oracle.integrate_vjp(s.n0, s.D, s.ranks, s.factors, dt, steps, g, method=method)
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, rk=rk) as pl:
+        n0 = dev(s.n0)
+        gn = torch.empty_like(n0)
+        gU = torch.empty(s.factors.size, dtype=torch.float64, device="cuda")
+        pl.integrate_vjp(n0, dt, steps, dev(g), gn, gU, ckpt=ckpt)
+        torch.cuda.synchronize()
+        assert torch.equal(n0, dev(s.n0))  # the initial state is not modified
+    assert rel(gn.cpu().numpy(), gn_ref) < 10 * TOL[prec]
+    assert rel(gU.cpu().numpy(), gU_ref) < 10 * TOL[prec]
+
+
+def test_vjp_dot_product_identity():
+    # <v, J u> = <J^T v, u> with J u from central differences of the FP64 path.
+    s = wl.random_cp(4, 700, [2, 3, 2], seed=92)
+    rng = np.random.default_rng(93)
+    u = rng.normal(size=s.N)
+    v = rng.normal(size=s.N)
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP64) as pl:
+        def F(x):
+            out = torch.empty(s.N, dtype=torch.float64, device="cuda")
+            pl.rhs(dev(x), out)
+            torch.cuda.synchronize()
+            return out.cpu().numpy()
+        h = 1e-6
+        Ju = (F(s.n0 + h * u) - F(s.n0 - h * u)) / (2 * h)
+        gn = torch.empty(s.N, dtype=torch.float64, device="cuda")
+        pl.rhs_vjp(dev(s.n0), dev(v), gn, None)
+        torch.cuda.synchronize()
+    lhs, r = v @ Ju, gn.cpu().numpy() @ u
+    assert abs(lhs - r) < 1e-7 * (np.abs(v) @ np.abs(Ju))
+
+
+@pytest.fixture(scope="module")
+def fit_problem():
+    return wl.adjoint_fit_problem()
+
+
+def _final_state(plan, factors64, n0, dt, steps):
+    plan.update_factors(factors64)
+    n = dev(n0)
+    plan.integrate(n, dt, steps)
+    torch.cuda.synchronize()
+    return n.cpu().numpy()
+
+
+def test_autograd_gradient_matches_central_differences(fit_problem):
+    from paper_1905_09071_gb300 import autograd as sag_autograd
+    p = fit_problem
+    D, N, ranks, dt, steps, ckpt = p["D"], p["N"], p["ranks"], p["dt"], p["steps"], p["ckpt"]
+    with sag.Plan(N, D, ranks, p["target_factors"], prec=sag.SAG_FP64) as ref_plan:
+        n_target = _final_state(ref_plan, p["target_factors"], p["n0"], dt, steps)
+        with sag.Plan(N, D, ranks, p["factors0"], prec=sag.SAG_FP32_SPLIT) as plan:
+            factors = torch.tensor(p["factors0"], dtype=torch.float32, device="cuda", requires_grad=True)
+            n0 = dev(p["n0"])
+            nT = sag_autograd.integrate(factors, n0, plan, dt, steps, ckpt)
+            loss = ((nT - dev(n_target)) ** 2).sum()
+            loss.backward()
+            grad = factors.grad.double().cpu().numpy()
+        assert np.isfinite(grad).all() and np.abs(grad).max() > 0
+        # central differences of the FP64 forward along 16 random unit directions
+        rng = np.random.default_rng(94)
+        f0 = p["factors0"]
+
+        def L(f):
+            n = _final_state(ref_plan, f, p["n0"], dt, steps)
+            return float(((n - n_target) ** 2).sum())
+
+        h = 1e-6
+        for _ in range(16):
+            u = rng.normal(size=f0.size)
+            u /= np.linalg.norm(u)
+            fd = (L(f0 + h * u) - L(f0 - h * u)) / (2 * h)
+            an = float(grad @ u)
+            assert abs(fd - an) <= 1e-5 * (abs(fd) + 1e-3 * np.linalg.norm(grad)), (fd, an)
+
+
+def test_gpu_adjoint_matches_oracle_adjoint_on_fit_problem_prefix():
+    # The fitting workload's kernel on its first 384 sizes, 20 steps: the
+    # library's FP64 adjoint against the oracle's.
+    p = wl.adjoint_fit_problem(N=384)
+    D, N, ranks, dt = p["D"], p["N"], p["ranks"], p["dt"]
+    steps = 20
+    g = np.random.default_rng(95).normal(size=N)
+    gn_ref, gU_ref = oracle.integrate_vjp(p["n0"], D, ranks, p["factors0"], dt, steps, g)
+    with sag.Plan(N, D, ranks, p["factors0"], prec=sag.SAG_FP64) as pl:
+        gn = torch.empty(N, dtype=torch.float64, device="cuda")
+        gU = torch.empty(p["factors0"].size, dtype=torch.float64, device="cuda")
+        pl.integrate_vjp(dev(p["n0"]), dt, steps, dev(g), gn, gU, ckpt=5)
+        torch.cuda.synchronize()
+    assert rel(gn.cpu().numpy(), gn_ref) < 1e-10
+    assert rel(gU.cpu().numpy(), gU_ref) < 1e-10
