@@ -372,9 +372,9 @@ cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, c
 }
 
 cudaError_t setup_common_kernels(const LaunchCfg& L) {
-  cudaError_t e = cudaFuncSetAttribute(k_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  cudaError_t e = allow_max_smem(k_epilogue);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_coef, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+    e = allow_max_smem(k_coef);
   return e;
 }
 

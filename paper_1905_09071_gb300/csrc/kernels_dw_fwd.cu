@@ -12,7 +12,7 @@ cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const do
 }
 
 cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L) {
-  return cudaFuncSetAttribute(k_fwd_col<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  return allow_max_smem(k_fwd_col<cdw>);
 }
 
 }  // namespace sag

@@ -12,7 +12,7 @@ cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, const doubl
 }
 
 cudaError_t setup_k_rows_dw(const LaunchCfg& L) {
-  return cudaFuncSetAttribute(k_rows<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  return allow_max_smem(k_rows<cdw>);
 }
 
 }  // namespace sag

@@ -25,9 +25,9 @@ cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const dou
 }
 
 cudaError_t setup_fft_kernels_f64(const LaunchCfg& L) {
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  cudaError_t e = allow_max_smem(k_fwd_col<cd>);
+  if (e == cudaSuccess) e = allow_max_smem(k_rows<cd>);
+  if (e == cudaSuccess) e = allow_max_smem(k_inv_col<cd>);
   if (e == cudaSuccess) e = setup_tt_stage<cd>(L);
   return e;
 }

@@ -213,9 +213,9 @@ cudaError_t enqueue_axpby(double* out, double a, const double* x, double b, cons
 
 cudaError_t setup_vjp_common(const LaunchCfg& L) {
   (void)L;
-  cudaError_t e = cudaFuncSetAttribute(k_coef_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  cudaError_t e = allow_max_smem(k_coef_vjp);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_vjp_final, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+    e = allow_max_smem(k_vjp_final);
   return e;
 }
 

@@ -18,9 +18,9 @@ cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const doub
 
 cudaError_t setup_vjp_fft_dw(const LaunchCfg& L) {
   (void)L;
-  cudaError_t e = cudaFuncSetAttribute(k_gcol<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows_vjp<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col_vjp<cdw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  cudaError_t e = allow_max_smem(k_gcol<cdw>);
+  if (e == cudaSuccess) e = allow_max_smem(k_rows_vjp<cdw>);
+  if (e == cudaSuccess) e = allow_max_smem(k_inv_col_vjp<cdw>);
   return e;
 }
 

@@ -18,9 +18,9 @@ cudaError_t launch_vjp_fft_f64(const RhsParams& P, const LaunchCfg& L, const dou
 
 cudaError_t setup_vjp_fft_f64(const LaunchCfg& L) {
   (void)L;
-  cudaError_t e = cudaFuncSetAttribute(k_gcol<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows_vjp<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_col_vjp<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+  cudaError_t e = allow_max_smem(k_gcol<cd>);
+  if (e == cudaSuccess) e = allow_max_smem(k_rows_vjp<cd>);
+  if (e == cudaSuccess) e = allow_max_smem(k_inv_col_vjp<cd>);
   return e;
 }
 

@@ -56,14 +56,24 @@ struct SideStream {
 cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
                          const EpiArgs& A, cudaStream_t st, LaunchHook* hook = nullptr,
                          const SideStream* side = nullptr);
-// Largest dynamic shared memory a block may use on the current device. Every
-// kernel's attribute is set to it: the attribute is per function for the
-// whole process, so a per-plan value would shrink the limit of other plans.
+// Largest dynamic shared memory a block may use on the current device.
 inline int smem_limit() {
   int dev = 0, v = 48 * 1024;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   return v;
+}
+
+// Lets `func` use all the dynamic shared memory its static shared memory
+// leaves free. The attribute is per function for the whole process, so a
+// per-plan value would shrink the limit of plans built earlier.
+template <class F>
+inline cudaError_t allow_max_smem(F* func) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, func);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_limit() - (int)a.sharedSizeBytes);
 }
 
 cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, cudaStream_t st);

@@ -22,10 +22,9 @@ cudaError_t launch_tt_stage(const RhsParams& P, const LaunchCfg& L, cudaStream_t
 
 template <class C>
 cudaError_t setup_tt_stage(const LaunchCfg& L) {
-  cudaError_t e = cudaFuncSetAttribute(k_rows_tt_fwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem_limit());
+  cudaError_t e = allow_max_smem(k_rows_tt_fwd<C>);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_rows_tt_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+    e = allow_max_smem(k_rows_tt_inv<C>);
   return e;
 }
 
