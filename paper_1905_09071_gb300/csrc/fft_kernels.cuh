@@ -91,7 +91,7 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   constexpr bool CT = P1 > 0;
   const int M1 = CT ? P1 : od.M1;
   const int W = CT ? ct_cols(P1) : od.W;
-  const int ld = CT ? P1 + 1 : od.ld1;
+  const int ld = CT ? ct_ld(P1, ct_cols(P1)) : od.ld1;
   const int M2 = od.M2;
   const int v = od.vbase + vloc;
   C* buf1 = buf + W * ld;
@@ -104,7 +104,7 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
-    buf[c * ld + j1] = load_a_pair(u, nn, N, 2 * j, C{});
+    buf[c * ld + (CT ? pad8(j1) : j1)] = load_a_pair(u, nn, N, 2 * j, C{});
   }
   __syncthreads();
   C* res;
@@ -118,7 +118,7 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   const C* tw4 = static_cast<const C*>(od.tw4);
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, k1 = e / W, j2 = cb * W + c;
-    dst[(int64_t)k1 * M2 + j2] = c_mul(res[c * ld + k1], tw4[j2 * k1]);
+    dst[(int64_t)k1 * M2 + j2] = c_mul(res[c * ld + (CT ? pad8(k1) : k1)], tw4[j2 * k1]);
   }
 }
 
@@ -151,25 +151,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
 // ---------------------------------------------------------------------------
 // Row pass of one block: the row pair {k1a, M1 - k1a} of order od. Both rows
 // hold every spectrum index k together with its mirror M - k, which the real
-// split needs. P2 > 0: compile-time row length; P2 == 0: runtime.
-template <class C, int P2>
+// split needs. Runtime row length (generic passes, ping-pong buffers).
+template <class C>
 __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& od, int kp, C* buf) {
-  constexpr bool CT = P2 > 0;
-  // Positions per thread: the double-word path reaches the runtime variant only
-  // for rows of at most 128 points (the plan checks this), FP64 for up to 512.
-  constexpr int PPT = CT ? (2 * P2 + kThreads - 1) / kThreads
-                         : (std::is_same<C, cdw>::value ? 1 : kRowPosPerThread);
+  // Positions per thread: the double-word path reaches this variant only for
+  // rows of at most 128 points (the plan checks this), FP64 for up to 512.
+  constexpr int PPT = std::is_same<C, cdw>::value ? 1 : kRowPosPerThread;
   const int d = od.d, R = od.R, M1 = od.M1, M = od.M;
-  const int M2 = CT ? P2 : od.M2;
-  const int ld = CT ? P2 + 1 : od.ld2;
-  const int G = CT ? ct_group(P2) : od.G;
+  const int M2 = od.M2;
+  const int ld = od.ld2;
+  const int G = od.G;
   const int k1a = kp, k1b = M1 - kp;
   const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
   const int NP = nrow * M2;
-  // Slots: transform (g, row) at buf + (2 g + row) ld in the compile-time
-  // layout, at buf + (g nrow + row) ld in the runtime layout.
+  // Slots: transform (g, row) at buf + (g nrow + row) ld.
   C* buf1 = buf + G * 2 * ld;
-  C* tw = CT ? buf + G * 2 * ld : buf1 + G * 2 * ld;
+  C* tw = buf1 + G * 2 * ld;
   const C* tw2 = static_cast<const C*>(od.tw2);
   const C* twL = static_cast<const C*>(od.twL);
   const C* src = static_cast<const C*>(P.scratch) + od.scr_off;
@@ -183,7 +180,7 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
   }
   C SN = c_zero(C{}), PrN = c_zero(C{});  // Nyquist index k = M (row 0 only)
   const bool nyq = (kp == 0 && threadIdx.x == 0);
-  const int slot_stride = CT ? 2 : nrow;
+  const int slot_stride = nrow;
 
   const int Vd = d * R;
   for (int q0 = 0; q0 < Vd; q0 += G) {
@@ -196,13 +193,7 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
       buf[(g * slot_stride + row) * ld + pos] = src[(int64_t)(m * R + r) * M + (int64_t)k1 * M2 + pos];
     }
     __syncthreads();
-    C* res;
-    if constexpr (CT) {
-      fft_ct<C, P2, 2 * ct_group(P2), kThreads>(buf, ld, tw);  // unused slots hold stale data
-      res = buf;
-    } else {
-      res = fft_batch(buf, buf1, M2, ld, gc * nrow, od.rp2, tw);
-    }
+    C* res = fft_batch(buf, buf1, M2, ld, gc * nrow, od.rp2, tw);
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
       const int p = threadIdx.x + i * kThreads;
@@ -258,13 +249,7 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
     buf[row * ld + pos] = c_conj(zpp);
   }
   __syncthreads();
-  C* res;
-  if constexpr (CT) {
-    fft_ct<C, P2, 2, kThreads>(buf, ld, tw);
-    res = buf;
-  } else {
-    res = fft_batch(buf, buf1, M2, ld, nrow, od.rp2, tw);
-  }
+  C* res = fft_batch(buf, buf1, M2, ld, nrow, od.rp2, tw);
   C* dst = static_cast<C*>(P.scratch2) + od.scr2_off;
   const C* tw4 = static_cast<const C*>(od.tw4);
   for (int p = threadIdx.x; p < NP; p += kThreads) {
@@ -274,24 +259,26 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
   }
 }
 
-// Row pass, compile-time row length, with the rows of the next chunk of
-// vectors streamed into a second shared-memory stage by bulk asynchronous
-// copies while the current chunk is transformed. Layout: two mbarriers, then
-// stage 0 and stage 1 (2 G transform slots of ld = P2 + 1 each), then the
-// twiddle table. Returns false (after setting the timeout status) if a copy
-// did not complete within P.spin_limit cycles.
+// Row pass, compile-time row length. The rows of each chunk of G vectors
+// (2 G transforms: both rows of the pair per vector) arrive by bulk
+// asynchronous copies in natural order in a staging area; the first radix
+// pass reads them from there and writes the padded work area, after which the
+// block issues the copies of the next chunk, so they land while the remaining
+// passes and the spectrum products of this chunk run. Layout: one mbarrier
+// (16 bytes), stage (2 G x P2), work (2 G transforms, ct_ld(P2, 2 G) apart),
+// twiddles (P2). If a copy does not complete within P.spin_limit cycles the
+// block sets the timeout status and returns.
 template <class C, int P2>
 __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderDesc& od, int kp,
                                                 unsigned char* smem_raw) {
   constexpr int G = ct_group(P2);
   constexpr int SLOTS = 2 * G;
-  constexpr int ld = P2 + 1;
+  constexpr int ld = ct_ld(P2, SLOTS);
   constexpr int PPT = (2 * P2 + kThreads - 1) / kThreads;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-  C* stage[2];
-  stage[0] = reinterpret_cast<C*>(smem_raw + 16);
-  stage[1] = stage[0] + SLOTS * ld;
-  C* tw = stage[1] + SLOTS * ld;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  C* stage = reinterpret_cast<C*>(smem_raw + 16);
+  C* work = stage + SLOTS * P2;
+  C* tw = work + SLOTS * ld;
   const int d = od.d, R = od.R, M1 = od.M1, M = od.M;
   const int k1a = kp, k1b = M1 - kp;
   const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
@@ -302,33 +289,27 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
   const int Vd = d * R;
   const int nchunk = (Vd + G - 1) / G;
 
-  // One thread issues the copies of chunk c into stage c & 1.
+  // One thread issues the copies of chunk c: transform (g, row) at stage + (2 g + row) P2.
   auto issue = [&](int c) {
     const int q0 = c * G, gc = min(G, Vd - q0);
-    uint64_t* bar = &bars[c & 1];
     mbar_arrive_expect_tx(bar, (uint32_t)(gc * nrow * P2 * sizeof(C)));
     for (int g = 0; g < gc; ++g) {
       const int q = q0 + g, r = q / d, m = q - r * d;
       for (int row = 0; row < nrow; ++row) {
         const int k1 = row ? k1b : k1a;
-        bulk_copy_g2s(stage[c & 1] + (2 * g + row) * ld,
-                      src + (int64_t)(m * R + r) * M + (int64_t)k1 * P2,
+        bulk_copy_g2s(stage + (2 * g + row) * P2, src + (int64_t)(m * R + r) * M + (int64_t)k1 * P2,
                       (uint32_t)(P2 * sizeof(C)), bar);
       }
     }
   };
 
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    mbar_init(bar, 1);
     mbar_init_fence();
   }
   for (int i = threadIdx.x; i < P2; i += kThreads) tw[i] = tw2[i];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    issue(0);
-    if (nchunk > 1) issue(1);
-  }
+  if (threadIdx.x == 0) issue(0);
 
   C S[PPT], Pr[PPT];
 #pragma unroll
@@ -341,13 +322,18 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
 
   for (int c = 0; c < nchunk; ++c) {
     const int q0 = c * G, gc = min(G, Vd - q0);
-    C* buf = stage[c & 1];
-    const bool ok = mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1), P.spin_limit);
+    // The barrier also orders the previous chunk's reads of work before the
+    // first pass overwrites it.
+    const bool ok = mbar_wait_bounded(bar, (uint32_t)(c & 1), P.spin_limit);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
       return;
     }
-    fft_ct<C, P2, SLOTS, kThreads>(buf, ld, tw);  // unused slots hold stale data
+    fft_ct_first<C, P2, SLOTS, kThreads>(stage, P2, work, ld, tw);  // unused slots hold stale data
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0 && c + 1 < nchunk) issue(c + 1);
+    fft_ct_rest<C, P2, SLOTS, kThreads>(work, ld, tw);
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
       const int p = threadIdx.x + i * kThreads;
@@ -357,9 +343,11 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
         int mrow, mpos;
         mirror_of(k1, row, pos, M1, P2, mrow, mpos);
         const C wL = twL[k1 + M1 * pos];
+        const int oa = row * ld + pad8(pos), ob = mrow * ld + pad8(mpos);
         for (int g = 0; g < gc; ++g) {
           const int q = q0 + g, r = q / d, m = q - r * d;
-          const C A = unpack2(buf[(2 * g + row) * ld + pos], buf[(2 * g + mrow) * ld + mpos], wL);
+          const C* bg = work + 2 * g * ld;
+          const C A = unpack2(bg[oa], bg[ob], wL);
           Pr[i] = (m == 0) ? A : c_mul(Pr[i], A);
           if (m == d - 1) S[i] = c_add(S[i], rank_weight(Pr[i], od, r));
         }
@@ -368,21 +356,18 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
     if (nyq) {
       for (int g = 0; g < gc; ++g) {
         const int q = q0 + g, r = q / d, m = q - r * d;
-        const C z0 = buf[(2 * g) * ld];
+        const C z0 = work[(2 * g) * ld];
         const C zc = c_conj(z0);
         const C A = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));  // 2 A[M]
         PrN = (m == 0) ? A : c_mul(PrN, A);
         if (m == d - 1) SN = c_add(SN, rank_weight(PrN, od, r));
       }
     }
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0 && c + 2 < nchunk) issue(c + 2);
   }
 
-  // Inverse, row half (as in rows_body), in stage 0; every copy has landed.
-  C* buf = stage[0];
-  C* sS = buf + 2 * ld;
+  // Inverse, row half (as in rows_body): S staged in the (idle) stage area,
+  // the packed sequence built in work.
+  C* sS = stage;
 #pragma unroll
   for (int i = 0; i < PPT; ++i) {
     const int p = threadIdx.x + i * kThreads;
@@ -399,16 +384,16 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
     const C Sk = sS[p];
     const C Sm = (k == 0) ? sS[NP] : c_conj(sS[mrow * P2 + mpos]);
     const C zpp = c_add(c_add(Sk, Sm), c_mul_pi(c_mul(c_conj(twL[k]), c_sub(Sk, Sm))));
-    buf[row * ld + pos] = c_conj(zpp);
+    work[row * ld + pad8(pos)] = c_conj(zpp);
   }
   __syncthreads();
-  fft_ct<C, P2, 2, kThreads>(buf, ld, tw);
+  fft_ct<C, P2, 2, kThreads>(work, ld, tw);
   C* dst = static_cast<C*>(P.scratch2) + od.scr2_off;
   const C* tw4 = static_cast<const C*>(od.tw4);
   for (int p = threadIdx.x; p < NP; p += kThreads) {
     const int row = p / P2, j2 = p - row * P2;
     const int k1 = row ? k1b : k1a;
-    dst[(int64_t)k1 * P2 + j2] = c_mul(buf[row * ld + j2], tw4[j2 * k1]);
+    dst[(int64_t)k1 * P2 + j2] = c_mul(work[row * ld + pad8(j2)], tw4[j2 * k1]);
   }
 }
 
@@ -422,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ Rh
   const OrderDesc& od = P.ord[P.rowperm[j]];
   const int kp = blockIdx.x - P.rowpre[j];
   if constexpr (!std::is_same<C, cdw>::value) {
-    rows_body<C, 0>(P, od, kp, buf);
+    rows_body<C>(P, od, kp, buf);
     return;
   }
   switch (od.ct2 ? od.M2 : 0) {
@@ -430,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ Rh
     case 128: rows_body_async<C, 128>(P, od, kp, smem_raw); break;
     case 256: rows_body_async<C, 256>(P, od, kp, smem_raw); break;
     case 512: rows_body_async<C, 512>(P, od, kp, smem_raw); break;
-    default: rows_body<C, 0>(P, od, kp, buf); break;
+    default: rows_body<C>(P, od, kp, buf); break;
   }
 }
 
@@ -442,7 +427,7 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   constexpr bool CT = P1 > 0;
   const int M1 = CT ? P1 : od.M1;
   const int W = CT ? ct_cols(P1) : od.W;
-  const int ld = CT ? P1 + 1 : od.ld1;
+  const int ld = CT ? ct_ld(P1, ct_cols(P1)) : od.ld1;
   const int M2 = od.M2, N = od.N;
   C* buf1 = buf + W * ld;
   C* tw = CT ? buf + W * ld : buf1 + W * ld;
@@ -451,7 +436,7 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   const C* src = static_cast<const C*>(P.scratch2) + od.scr2_off;
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, k1 = e / W;
-    buf[c * ld + k1] = src[(int64_t)k1 * M2 + cb * W + c];
+    buf[c * ld + (CT ? pad8(k1) : k1)] = src[(int64_t)k1 * M2 + cb * W + c];
   }
   __syncthreads();
   C* res;
@@ -466,7 +451,7 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
-    const C w = res[c * ld + j1];
+    const C w = res[c * ld + (CT ? pad8(j1) : j1)];
     const int k = 2 * j;  // sizes k (real part) and k + 1 (minus the imaginary part)
     if (k >= 1 && k <= N) out[k - 1] = cre(w) * scale;
     if (k + 1 <= N) out[k] = -cim(w) * scale;

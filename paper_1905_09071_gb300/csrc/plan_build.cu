@@ -261,14 +261,15 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     while (2 * W <= M2 && (int64_t)2 * W * od.M1 <= 2048) W *= 2;
     if (od.ct1) W = ct_cols(od.M1);
     od.W = W;
-    od.ld1 = od.M1 + 1;
-    od.ld2 = od.M2 + 1;
+    // The compile-time column kernels pad their transforms per column count.
+    od.ld1 = od.ct1 ? ct_ld(od.M1, W) : od.M1 + 1;
     od.ncolblk = M2 / W;
     od.nrowpair = od.M1 / 2 + 1;
     int G = std::max(1, 2048 / (2 * M2));
     G = std::min(G, std::max(1, od.nvec));
     G = std::min(G, 64);
     if (od.ct2) G = ct_group(od.M2);
+    od.ld2 = od.ct2 ? ct_ld(od.M2, 2 * G) : od.M2 + 1;
     if (dwp && !tt && !od.ct2 && 2 * od.M2 > kThreads)
       return fail(SAG_EUNSUPPORTED, "row length without a compile-time kernel above 128");
     od.G = G;
@@ -283,9 +284,11 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     chainpre.push_back(chainpre.back() + (tt ? (od.M + 1 + 255) / 256 : 0));
     // Compile-time kernels work in place (one buffer), the generic ones ping-pong.
     col_smem = std::max(col_smem, (size_t)((od.ct1 ? 1 : 2) * W * od.ld1 + od.M1) * csize);
-    // The compile-time row kernel double-buffers its input through bulk copies
-    // (two stages plus two mbarriers).
-    row_smem = std::max(row_smem, (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize + (od.ct2 ? 16 : 0));
+    // The compile-time row kernel stages its input (bulk copies, natural
+    // order) apart from the padded work area, behind one mbarrier; the
+    // runtime one ping-pongs.
+    row_smem = std::max(row_smem, od.ct2 ? (size_t)(2 * G * od.M2 + 2 * G * od.ld2 + od.M2) * csize + 16
+                                         : (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize);
     rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * G * 2 * od.ld2, 6 * od.ld2) * csize +
                                           (size_t)od.M2 * csize);
     // Vector-Jacobian product kernels (CP): ping-pong column blocks; row

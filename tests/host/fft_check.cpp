@@ -1,15 +1,21 @@
-// Host-side check of the library's FFT building blocks (csrc/dw.cuh, csrc/fft.cuh):
-// runs the Stockham passes sequentially on the CPU for the FP64 and double-word
-// complex types and prints, per length, the max-norm error relative to a
-// long-double direct DFT. Compiled by tests/test_fft_host.py with
-// -ffp-contract=off so that float operations stay separately rounded.
+// Host-side check of the library's FFT building blocks (csrc/dw.cuh, csrc/fft.cuh,
+// csrc/fft_ct.cuh): runs the Stockham passes sequentially on the CPU for the
+// FP64 and double-word complex types and prints, per length, the max-norm error
+// relative to a long-double direct DFT. With "ct" as the first argument it runs
+// the compile-time schedule instead, through the same index maps as the device
+// passes (padded shared-memory layout, in-place passes, natural-order first
+// pass), on several transforms side by side with unused slots set to NaN.
+// Compiled by tests/test_fft_host.py with -ffp-contract=off so that float
+// operations stay separately rounded.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <random>
+#include <string>
 #include <vector>
 
 #include "fft.cuh"
+#include "fft_ct.cuh"
 
 using namespace sag;
 
@@ -39,10 +45,119 @@ static std::vector<C> stockham(std::vector<C> a, int P, const std::vector<C>& tw
   return a;
 }
 
+// Compile-time schedule, emulated pass by pass: every butterfly's loads happen
+// before any store of the same pass, as in the device code (in place).
+template <class C, int P, int S, int Ns>
+static void ct_host_passes(std::vector<C>& buf, int ld, int count, const C* tw, const C* nat) {
+  constexpr ct_sched sc = make_ct_sched(P);
+  if constexpr (S < sc.n) {
+    constexpr int R = sc.r[S];
+    constexpr int NB = P / R;
+    std::vector<C> x((size_t)count * P);
+    for (int b = 0; b < count; ++b)
+      for (int j = 0; j < NB; ++j)
+        for (int t = 0; t < R; ++t) {
+          const long src = nat ? (long)b * P + ct_src<P, R, true>(j, t) : (long)b * ld + ct_src<P, R, false>(j, t);
+          const long lim = nat ? (long)count * P : (long)count * ld;
+          if (src < 0 || src >= lim) {
+            std::printf("read out of range P=%d pass %d\n", P, S);
+            std::exit(3);
+          }
+          x[((size_t)b * NB + j) * R + t] = nat ? nat[src] : buf[src];
+        }
+    for (int b = 0; b < count; ++b)
+      for (int j = 0; j < NB; ++j) {
+        C* xx = &x[((size_t)b * NB + j) * R];
+        if (Ns > 1)
+          for (int t = 1; t < R; ++t) xx[t] = c_mul(xx[t], tw[ct_twi<P, R, Ns>(j, t)]);
+        dft_r<R>(xx);
+        for (int t = 0; t < R; ++t) {
+          const int o = ct_dst<P, R, Ns>(j, t);
+          if (o < 0 || o >= ct_span(P) || (long)b * ld + o >= (long)count * ld) {
+            std::printf("write out of range P=%d pass %d\n", P, S);
+            std::exit(3);
+          }
+          buf[(size_t)b * ld + o] = xx[t];
+        }
+      }
+    ct_host_passes<C, P, S + 1, Ns * R>(buf, ld, count, tw, nullptr);
+  }
+}
+
+// count transforms of length P at ld = ct_ld(P, count); sin: the input comes
+// from a separate natural-order buffer. Returns the max relative error.
+template <int P>
+static long double ct_check(int count, bool sin, std::mt19937_64& g) {
+  const long double TWO_PI = 6.283185307179586476925286766559005768L;
+  std::uniform_real_distribution<double> u(-1.0, 1.0);
+  const int ld = ct_ld(P, count);
+  const cdw nan = cfrom(NAN, NAN, cdw{});
+  std::vector<cdw> buf((size_t)count * ld, nan), nat((size_t)count * P), tw(P);
+  std::vector<double> xr((size_t)count * P), xi((size_t)count * P);
+  for (int j = 0; j < P; ++j) {
+    const long double a = -TWO_PI * j / P;
+    tw[j] = cfrom((double)cosl(a), (double)sinl(a), cdw{});
+  }
+  for (int b = 0; b < count; ++b)
+    for (int j = 0; j < P; ++j) {
+      xr[(size_t)b * P + j] = u(g);
+      xi[(size_t)b * P + j] = u(g);
+      const cdw v = cfrom(xr[(size_t)b * P + j], xi[(size_t)b * P + j], cdw{});
+      if (sin) nat[(size_t)b * P + j] = v;
+      else buf[(size_t)b * ld + pad8(j)] = v;
+    }
+  ct_host_passes<cdw, P, 0, 1>(buf, ld, count, tw.data(), sin ? nat.data() : nullptr);
+  long double err = 0, nrm = 0;
+  for (int b = 0; b < count; ++b)
+    for (int k = 0; k < P; ++k) {
+      long double sr = 0, si = 0;
+      for (int j = 0; j < P; ++j) {
+        const long double a = -TWO_PI * (long double)(((long long)j * k) % P) / P;
+        const long double x0 = xr[(size_t)b * P + j], x1 = xi[(size_t)b * P + j];
+        sr += x0 * cosl(a) - x1 * sinl(a);
+        si += x0 * sinl(a) + x1 * cosl(a);
+      }
+      const cdw y = buf[(size_t)b * ld + pad8(k)];
+      nrm = fmaxl(nrm, sqrtl(sr * sr + si * si));
+      const long double e = hypotl(cre(y) - sr, cim(y) - si);
+      if (!(e == e)) return NAN;
+      err = fmaxl(err, e);
+    }
+  return err / nrm;
+}
+
+static long double ct_dispatch(int P, int count, bool sin, std::mt19937_64& g) {
+  switch (P) {
+    case 64: return ct_check<64>(count, sin, g);
+    case 96: return ct_check<96>(count, sin, g);
+    case 128: return ct_check<128>(count, sin, g);
+    case 192: return ct_check<192>(count, sin, g);
+    case 256: return ct_check<256>(count, sin, g);
+    case 384: return ct_check<384>(count, sin, g);
+    case 512: return ct_check<512>(count, sin, g);
+    case 768: return ct_check<768>(count, sin, g);
+    default: std::printf("unsupported %d\n", P); std::exit(2);
+  }
+}
+
 int main(int argc, char** argv) {
   const long double TWO_PI = 6.283185307179586476925286766559005768L;
   std::mt19937_64 g(1905);
   std::uniform_real_distribution<double> u(-1.0, 1.0);
+  if (argc > 1 && std::string(argv[1]) == "ct") {
+    // Layouts the kernels use: the column kernels (ct_cols(P) transforms side
+    // by side, padded input), the row kernel's chunks (2 ct_group(P)
+    // transforms from a natural-order stage) and its inverse (2 transforms).
+    for (int i = 2; i < argc; ++i) {
+      const int P = std::atoi(argv[i]);
+      std::printf("ct %d %d %d %.3Le\n", P, ct_cols(P), 0, ct_dispatch(P, ct_cols(P), false, g));
+      if ((P & (P - 1)) == 0 && P <= 512) {
+        std::printf("ct %d %d %d %.3Le\n", P, 2 * ct_group(P), 1, ct_dispatch(P, 2 * ct_group(P), true, g));
+        std::printf("ct %d %d %d %.3Le\n", P, 2, 0, ct_dispatch(P, 2, false, g));
+      }
+    }
+    return 0;
+  }
   for (int i = 1; i < argc; ++i) {
     const int P = std::atoi(argv[i]);
     std::vector<double> xr(P), xi(P);

@@ -3,7 +3,9 @@
 The radix-2/3/4/5/8 butterflies, the Stockham pass indexing and the
 double-word arithmetic of ``csrc/`` are compiled for the CPU and compared
 with a long-double direct DFT: FP64 must reach ~1e-16 and double-word FP32
-~1e-14 relative in max-norm at every length the library uses.
+~1e-14 relative in max-norm at every length the library uses. The same holds
+for the compile-time schedule run through its padded shared-memory index maps
+(every load lands on a written slot, every store inside its transform).
 """
 import os
 import shutil
@@ -49,3 +51,16 @@ def test_stockham_passes_match_direct_dft(fft_check):
     for P, e64, edw in rows:
         assert float(e64) < 1e-15, f"FP64 length {P}: {e64}"
         assert float(edw) < 2e-14, f"double-word length {P}: {edw}"
+
+
+CT_SIZES = [64, 96, 128, 192, 256, 384, 512, 768]
+
+
+def test_compile_time_passes_padded_layout(fft_check):
+    out = subprocess.run([fft_check, "ct"] + [str(s) for s in CT_SIZES], check=True,
+                         capture_output=True, text=True).stdout.split("\n")
+    rows = [ln.split() for ln in out if ln.startswith("ct ")]
+    # column layout for every length, row-chunk and inverse layouts for powers of two
+    assert len(rows) == len(CT_SIZES) + 2 * 4
+    for _, P, count, sin, err in rows:
+        assert float(err) < 2e-14, f"length {P}, {count} transforms, natural input {sin}: {err}"
