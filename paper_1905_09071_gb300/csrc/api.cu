@@ -90,15 +90,16 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
 }
 
 // Operation counts of the double-word arithmetic (FP32 instructions), as
-// written in dw.cuh: dw_add 11, dw_mul 7, one component of a complex product
-// (dot2) 19, so a complex add 22, a complex product 38, a real double-word
-// constant times a complex 14, a power-of-two scale 4. FP64 arithmetic: a
+// written in dw.cuh (results left unnormalised): dw_add 8, dw_mul 4, one
+// component of a complex product (dot2) 16, so a complex add 16, a complex
+// product 32, a real double-word constant times a complex 8, a power-of-two
+// scale 4. FP64 arithmetic: a
 // complex add 2, a complex product 4 (2 multiplies, 2 FMAs), a real times a
 // complex 2.
 struct OpCost {
   double cadd, cmul, kmul, scale;
 };
-constexpr OpCost kCostDW{22, 38, 14, 4};
+constexpr OpCost kCostDW{16, 32, 8, 4};
 constexpr OpCost kCostF64{2, 4, 2, 2};
 
 double dft_ops(int R, const OpCost& c) {
@@ -571,7 +572,7 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
   const bool dwp = pl->P.dwpath != 0;
   const OpCost& c = dwp ? kCostDW : kCostF64;
   const double Nt = (double)pl->Ntot, V = pl->P.Vtot;
-  const double load_mul = dwp ? 7.0 : 1.0;  // a = U n: dw_mul or one FP64 multiply
+  const double load_mul = dwp ? 4.0 : 1.0;  // a = U n: dw_mul or one FP64 multiply
   double o = 0.0, b = 0.0;
   int fp64 = dwp ? 0 : 1;
   double factor_elems = 0.0;  // sum over vectors of their length

@@ -1,13 +1,25 @@
 // Double-word ("float-float") arithmetic and the two complex scalar types the
 // FFT path is templated on.
 //
-// A dw value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
-// about 48 significant bits. The building blocks are the error-free transforms
-// of Dekker (1971) and Knuth (TAOCP vol. 2, Sec. 4.2.2): TwoSum, Fast2Sum, and
-// the FMA-based TwoProd; the composite operations follow the "sloppy" addition
-// and FMA multiplication analysed by Joldes, Muller and Popescu (2017), whose
-// error is bounded relative to |a| + |b| (resp. |a||b|), which is what a
-// normwise FFT error bound needs.
+// A dw value is the unevaluated sum hi + lo of two floats, about 48 significant
+// bits. The building blocks are the error-free transforms of Dekker (1971) and
+// Knuth (TAOCP vol. 2, Sec. 4.2.2): TwoSum, Fast2Sum, and the FMA-based
+// TwoProd; the composite operations follow the "sloppy" addition and FMA
+// multiplication analysed by Joldes, Muller and Popescu (2017), whose error is
+// bounded relative to |a| + |b| (resp. |a||b|), which is what a normwise FFT
+// error bound needs.
+//
+// Conversions from FP64 produce normalised pairs (|lo| <= ulp(hi)/2). The
+// arithmetic operations leave their result unnormalised: the final Fast2Sum
+// that would fold the error word into hi is skipped. That keeps every leading
+// sum and product error-free (TwoSum and TwoProd do not need normalised
+// inputs), and the error word only collects the rounding errors of the
+// leading operations plus the low words of the operands, each at most about
+// 2^-24 times the operands' magnitudes; the terms a normalised version would
+// add or drop are of the order 2^-48 |a| |b| (products) or 2^-48 (|a| + |b|)
+// (sums) as well. The error bounds stay normwise with a unit of about 2^-47
+// instead of 2^-48, for three FP32 operations fewer per addition and per
+// product.
 //
 // Every float operation below is written with an explicit round-to-nearest
 // intrinsic so the compiler can neither contract nor reassociate it; the
@@ -63,9 +75,7 @@ SAG_HD dw dw_add(dw a, dw b) {
   float s, e;
   two_sum(a.hi, b.hi, s, e);
   e = F_ADD(e, F_ADD(a.lo, b.lo));
-  dw r;
-  fast_two_sum(s, e, r.hi, r.lo);
-  return r;
+  return dw{s, e};
 }
 SAG_HD dw dw_neg(dw a) { return dw{-a.hi, -a.lo}; }
 SAG_HD dw dw_sub(dw a, dw b) { return dw_add(a, dw_neg(b)); }
@@ -74,9 +84,7 @@ SAG_HD dw dw_mul(dw a, dw b) {
   float e = F_FMA(a.hi, b.hi, -p);
   e = F_FMA(a.hi, b.lo, e);
   e = F_FMA(a.lo, b.hi, e);
-  dw r;
-  fast_two_sum(p, e, r.hi, r.lo);
-  return r;
+  return dw{p, e};
 }
 // a * 2^k for a power-of-two float scale (exact unless it under/overflows).
 SAG_HD dw dw_scale2(dw a, float p2) { return dw{F_MUL(a.hi, p2), F_MUL(a.lo, p2)}; }
@@ -126,9 +134,7 @@ SAG_HD dw dot2(dw x1, dw y1, dw x2, dw y2, bool sub) {
   t = F_FMA(x1.lo, y1.hi, t);
   t = F_FMA(x2h, y2.lo, t);
   t = F_FMA(x2l, y2.hi, t);
-  dw r;
-  fast_two_sum(s, t, r.hi, r.lo);
-  return r;
+  return dw{s, t};
 }
 SAG_HD cdw c_mul(cdw a, cdw b) {
   dw ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
