@@ -84,9 +84,43 @@ template <int P, int R, int Ns>
 SAG_CX int ct_dst(int j, int t) {
   return pad8_at<Ns, (Ns == 1 ? R : 0)>((j / Ns) * Ns * R + j % Ns, t);
 }
-template <int P, int R, int Ns>
+
+// Twiddles of the compile-time passes, one table per pass s >= 1 (the first
+// pass has span 1 and needs none), laid out [k][t - 1] for k = j mod Ns with
+// an odd row stride, so that the eight lanes of a 128-bit access phase (eight
+// consecutive k) read eight different bank groups. Entry (s, k, t) holds
+// omega_P^(t k P / (Ns R)); padding entries (radices with an even R - 1) are
+// never read.
+SAG_CX int ct_twstride(int R) { return (R - 1) % 2 ? R - 1 : R; }
+SAG_CX int ct_twp_off(int P, int S) {
+  const ct_sched sc = make_ct_sched(P);
+  int off = 0, Ns = sc.r[0];
+  for (int s = 1; s < S; ++s) {
+    off += Ns * ct_twstride(sc.r[s]);
+    Ns *= sc.r[s];
+  }
+  return off;
+}
+SAG_CX int ct_twp_size(int P) { return ct_twp_off(P, make_ct_sched(P).n); }
+// Index into the natural table (omega_P^e, e < P) of entry i of the pass
+// tables, or -1 for a padding entry.
+SAG_CX int ct_twp_src(int P, int i) {
+  const ct_sched sc = make_ct_sched(P);
+  int off = 0, Ns = sc.r[0];
+  for (int s = 1; s < sc.n; ++s) {
+    const int R = sc.r[s], st = ct_twstride(R);
+    if (i < off + Ns * st) {
+      const int k = (i - off) / st, t = (i - off) % st + 1;
+      return t < R ? t * k * (P / (Ns * R)) : -1;
+    }
+    off += Ns * st;
+    Ns *= R;
+  }
+  return -1;
+}
+template <int P, int S, int R, int Ns>
 SAG_CX int ct_twi(int j, int t) {
-  return t * (j % Ns) * (P / (Ns * R));
+  return ct_twp_off(P, S) + (j % Ns) * ct_twstride(R) + t - 1;
 }
 
 SAG_CX bool ct_supported(int P) {
@@ -100,7 +134,7 @@ SAG_CX bool ct_supported(int P) {
 // padded) and written padded at dst + b * dld. In place (src == dst) the block
 // synchronises between the loads and the stores; out of place it does not.
 // Ends with a barrier unless TAIL is false.
-template <class C, int P, int R, int Ns, int COUNT, int T, bool SIN, bool INPLACE, bool TAIL = true>
+template <class C, int P, int S, int R, int Ns, int COUNT, int T, bool SIN, bool INPLACE, bool TAIL = true>
 __device__ __forceinline__ void ct_pass(const C* src, int sld, C* dst, int dld, const C* tw) {
   constexpr int NB = P / R;
   constexpr int TOT = NB * COUNT;
@@ -124,7 +158,7 @@ __device__ __forceinline__ void ct_pass(const C* src, int sld, C* dst, int dld, 
       const int b = w / NB, j = w - b * NB;
       if (Ns > 1) {
 #pragma unroll
-        for (int t = 1; t < R; ++t) x[i][t] = c_mul(x[i][t], tw[ct_twi<P, R, Ns>(j, t)]);
+        for (int t = 1; t < R; ++t) x[i][t] = c_mul(x[i][t], tw[ct_twi<P, S, R, Ns>(j, t)]);
       }
       dft_r<R>(x[i]);
       C* ob = dst + b * dld;
@@ -140,13 +174,14 @@ __device__ __forceinline__ void ct_passes(C* buf, int ld, const C* tw) {
   constexpr ct_sched sc = make_ct_sched(P);
   if constexpr (S < sc.n) {
     constexpr int R = sc.r[S];
-    ct_pass<C, P, R, Ns, COUNT, T, false, true>(buf, ld, buf, ld, tw);
+    ct_pass<C, P, S, R, Ns, COUNT, T, false, true>(buf, ld, buf, ld, tw);
     ct_passes<C, P, COUNT, T, S + 1, Ns * R>(buf, ld, tw);
   }
 }
 
-// COUNT length-P forward transforms in place in the padded layout; the caller
-// has synchronised after filling buf; returns after a barrier.
+// COUNT length-P forward transforms in place in the padded layout; tw holds
+// the pass tables (ct_fill_twiddles); the caller has synchronised after
+// filling buf and tw; returns after a barrier.
 template <class C, int P, int COUNT, int T>
 __device__ __forceinline__ void fft_ct(C* buf, int ld, const C* tw) {
   static_assert(make_ct_sched(P).n > 0, "unsupported compile-time length");
@@ -162,12 +197,33 @@ template <class C, int P, int COUNT, int T>
 __device__ __forceinline__ void fft_ct_first(const C* src, int sld, C* dst, int dld, const C* tw) {
   static_assert(make_ct_sched(P).n > 1, "unsupported compile-time length");
   constexpr int R = make_ct_sched(P).r[0];
-  ct_pass<C, P, R, 1, COUNT, T, true, false, false>(src, sld, dst, dld, tw);
+  ct_pass<C, P, 0, R, 1, COUNT, T, true, false, false>(src, sld, dst, dld, tw);
 }
 template <class C, int P, int COUNT, int T>
 __device__ __forceinline__ void fft_ct_rest(C* buf, int ld, const C* tw) {
   constexpr int R = make_ct_sched(P).r[0];
   ct_passes<C, P, COUNT, T, 1, R>(buf, ld, tw);
+}
+
+template <class C, int P, int S, int Ns>
+__device__ __forceinline__ void ct_fill_pass(C* twp, const C* __restrict__ tw_nat) {
+  constexpr ct_sched sc = make_ct_sched(P);
+  if constexpr (S < sc.n) {
+    constexpr int R = sc.r[S], ST = ct_twstride(R), OFF = ct_twp_off(P, S);
+    for (int i = threadIdx.x; i < Ns * ST; i += blockDim.x) {
+      const int k = i / ST, t = i % ST + 1;
+      twp[OFF + i] = t < R ? tw_nat[t * k * (P / (Ns * R))] : c_zero(C{});
+    }
+    ct_fill_pass<C, P, S + 1, Ns * R>(twp, tw_nat);
+  }
+}
+
+// Fill the pass tables (ct_twp_size(P) entries, the layout ct_twp_src
+// describes) from the natural table of omega_P^e; the caller synchronises
+// before the first pass.
+template <class C, int P>
+__device__ __forceinline__ void ct_fill_twiddles(C* twp, const C* __restrict__ tw_nat) {
+  ct_fill_pass<C, P, 1, make_ct_sched(P).r[0]>(twp, tw_nat);
 }
 #endif
 

@@ -97,7 +97,9 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   C* buf1 = buf + W * ld;
   C* tw = CT ? buf + W * ld : buf1 + W * ld;
   const C* tw1 = static_cast<const C*>(od.tw1);
-  for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
+  if constexpr (CT) ct_fill_twiddles<C, P1>(tw, tw1);
+  else
+    for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
   const auto u = vec_ptr(P, v, C{});
   const auto nn = n_ptr(P, n, od.noff, C{});
   const int N = od.N;
@@ -115,10 +117,19 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
     res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
   }
   C* dst = static_cast<C*>(P.scratch) + od.scr_off + (int64_t)vloc * od.M;
-  const C* tw4 = static_cast<const C*>(od.tw4);
-  for (int e = threadIdx.x; e < W * M1; e += kThreads) {
-    const int c = e % W, k1 = e / W, j2 = cb * W + c;
-    dst[(int64_t)k1 * M2 + j2] = c_mul(res[c * ld + (CT ? pad8(k1) : k1)], tw4[j2 * k1]);
+  if constexpr (CT) {
+    // four-step twiddles of this column block, stored in the loop's order
+    const C* tw4c = static_cast<const C*>(od.tw4c) + (int64_t)cb * W * M1;
+    for (int e = threadIdx.x; e < W * M1; e += kThreads) {
+      const int c = e % W, k1 = e / W, j2 = cb * W + c;
+      dst[(int64_t)k1 * M2 + j2] = c_mul(res[c * ld + pad8(k1)], tw4c[e]);
+    }
+  } else {
+    const C* tw4 = static_cast<const C*>(od.tw4);
+    for (int e = threadIdx.x; e < W * M1; e += kThreads) {
+      const int c = e % W, k1 = e / W, j2 = cb * W + c;
+      dst[(int64_t)k1 * M2 + j2] = c_mul(res[c * ld + k1], tw4[j2 * k1]);
+    }
   }
 }
 
@@ -266,7 +277,7 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
 // block issues the copies of the next chunk, so they land while the remaining
 // passes and the spectrum products of this chunk run. Layout: one mbarrier
 // (16 bytes), stage (2 G x P2), work (2 G transforms, ct_ld(P2, 2 G) apart),
-// twiddles (P2). If a copy does not complete within P.spin_limit cycles the
+// pass twiddle tables (ct_twp_size(P2)). If a copy does not complete within P.spin_limit cycles the
 // block sets the timeout status and returns.
 template <class C, int P2>
 __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderDesc& od, int kp,
@@ -307,7 +318,7 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
     mbar_init(bar, 1);
     mbar_init_fence();
   }
-  for (int i = threadIdx.x; i < P2; i += kThreads) tw[i] = tw2[i];
+  ct_fill_twiddles<C, P2>(tw, tw2);
   __syncthreads();
   if (threadIdx.x == 0) issue(0);
 
@@ -432,7 +443,9 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   C* buf1 = buf + W * ld;
   C* tw = CT ? buf + W * ld : buf1 + W * ld;
   const C* tw1 = static_cast<const C*>(od.tw1);
-  for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
+  if constexpr (CT) ct_fill_twiddles<C, P1>(tw, tw1);
+  else
+    for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
   const C* src = static_cast<const C*>(P.scratch2) + od.scr2_off;
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, k1 = e / W;

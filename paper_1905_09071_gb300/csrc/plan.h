@@ -48,6 +48,8 @@ struct OrderDesc {
   const void* tw2;     // M2 entries omega_M2^k
   const void* tw4;     // M entries omega_M^e (four-step twiddle, e = j2 k1 < M)
   const void* twL;     // M entries omega_L^k, k < M (real-FFT split)
+  const void* tw4c;    // compile-time column kernels: omega_M^(j2 k1) in column-block
+                       // order (cb, k1, c) with j2 = cb W + c; M entries
   const float* rscale; // CP, double-word path: [R] power-of-two weight of rank term r
   double pscale;       // final FP64 scale of P^(d) (1/(L d!), factors of two), before the n scale
   double gscale;       // 2^-d / (L d!): final scale of a vector's cotangent before its exponents

@@ -72,6 +72,33 @@ struct TwiddleCache {
     *out = d;
     return cudaSuccess;
   }
+  // omega_M^(j2 k1) for M = M1 M2 in the order the compile-time column kernel
+  // reads it: column block cb (W columns), then k1, then column c, j2 = cb W + c.
+  std::map<std::tuple<int, int, int>, const void*> col_tables;
+  cudaError_t get_col(sag_plan_s* pl, int M1, int M2, int W, const void** out) {
+    auto key = std::make_tuple(M1, M2, W);
+    auto it = col_tables.find(key);
+    if (it != col_tables.end()) {
+      *out = it->second;
+      return cudaSuccess;
+    }
+    const int64_t M = (int64_t)M1 * M2;
+    std::vector<C> h(M);
+    int64_t i = 0;
+    for (int cb = 0; cb < M2 / W; ++cb)
+      for (int k1 = 0; k1 < M1; ++k1)
+        for (int c = 0; c < W; ++c) {
+          double cs, sn;
+          unit_root((int64_t)(cb * W + c) * k1, M, cs, sn);
+          h[i++] = to_c<C>(cs, sn);
+        }
+    C* d = nullptr;
+    cudaError_t e = pl->upload(&d, h);
+    if (e != cudaSuccess) return e;
+    col_tables[key] = d;
+    *out = d;
+    return cudaSuccess;
+  }
 };
 
 template <class C>
@@ -80,6 +107,8 @@ cudaError_t item_tables(sag_plan_s* pl, TwiddleCache<C>& tc, OrderDesc& od) {
   if (e == cudaSuccess) e = tc.get(pl, od.M2, od.M2, &od.tw2);
   if (e == cudaSuccess) e = tc.get(pl, od.M, od.M, &od.tw4);
   if (e == cudaSuccess) e = tc.get(pl, od.L, od.M, &od.twL);
+  od.tw4c = nullptr;
+  if (e == cudaSuccess && od.ct1) e = tc.get_col(pl, od.M1, od.M2, od.W, &od.tw4c);
   return e;
 }
 
@@ -283,11 +312,14 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     invpre.push_back(invpre.back() + od.ncolblk);
     chainpre.push_back(chainpre.back() + (tt ? (od.M + 1 + 255) / 256 : 0));
     // Compile-time kernels work in place (one buffer), the generic ones ping-pong.
-    col_smem = std::max(col_smem, (size_t)((od.ct1 ? 1 : 2) * W * od.ld1 + od.M1) * csize);
+    // (the compile-time kernels keep one table per radix pass, ct_twp_size entries)
+    col_smem = std::max(col_smem, od.ct1 ? (size_t)(W * od.ld1 + ct_twp_size(od.M1)) * csize
+                                         : (size_t)(2 * W * od.ld1 + od.M1) * csize);
     // The compile-time row kernel stages its input (bulk copies, natural
     // order) apart from the padded work area, behind one mbarrier; the
     // runtime one ping-pongs.
-    row_smem = std::max(row_smem, od.ct2 ? (size_t)(2 * G * od.M2 + 2 * G * od.ld2 + od.M2) * csize + 16
+    row_smem = std::max(row_smem, od.ct2 ? (size_t)(2 * G * od.M2 + 2 * G * od.ld2 + ct_twp_size(od.M2)) *
+                                                   csize + 16
                                          : (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize);
     rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * G * 2 * od.ld2, 6 * od.ld2) * csize +
                                           (size_t)od.M2 * csize);

@@ -69,7 +69,14 @@ static void ct_host_passes(std::vector<C>& buf, int ld, int count, const C* tw, 
       for (int j = 0; j < NB; ++j) {
         C* xx = &x[((size_t)b * NB + j) * R];
         if (Ns > 1)
-          for (int t = 1; t < R; ++t) xx[t] = c_mul(xx[t], tw[ct_twi<P, R, Ns>(j, t)]);
+          for (int t = 1; t < R; ++t) {
+            const int ti = ct_twi<P, S, R, Ns>(j, t);
+            if (ti < 0 || ti >= ct_twp_size(P) || ct_twp_src(P, ti) < 0) {
+              std::printf("twiddle index out of range P=%d pass %d\n", P, S);
+              std::exit(3);
+            }
+            xx[t] = c_mul(xx[t], tw[ti]);
+          }
         dft_r<R>(xx);
         for (int t = 0; t < R; ++t) {
           const int o = ct_dst<P, R, Ns>(j, t);
@@ -106,7 +113,11 @@ static long double ct_check(int count, bool sin, std::mt19937_64& g) {
       if (sin) nat[(size_t)b * P + j] = v;
       else buf[(size_t)b * ld + pad8(j)] = v;
     }
-  ct_host_passes<cdw, P, 0, 1>(buf, ld, count, tw.data(), sin ? nat.data() : nullptr);
+  // pass tables, as the kernels build them from the natural table
+  std::vector<cdw> twp(ct_twp_size(P), nan);
+  for (int i = 0; i < ct_twp_size(P); ++i)
+    if (ct_twp_src(P, i) >= 0) twp[i] = tw[ct_twp_src(P, i)];
+  ct_host_passes<cdw, P, 0, 1>(buf, ld, count, twp.data(), sin ? nat.data() : nullptr);
   long double err = 0, nrm = 0;
   for (int b = 0; b < count; ++b)
     for (int k = 0; k < P; ++k) {
