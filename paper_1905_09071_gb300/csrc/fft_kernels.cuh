@@ -23,8 +23,8 @@
 
 namespace sag {
 
-// ---- loading a = U o n, two sizes per complex point -------------------------
-// u, nn: the vector and the system's n, both indexed by size - 1; N sizes.
+// ---- loading a = U o n, two sizes per complex point (k even) ---------------
+// FP64: u, nn are the vector and the system's n, indexed by size - 1.
 __device__ __forceinline__ cd load_a_pair(const double* __restrict__ u, const double* __restrict__ nn,
                                           int N, int k, cd) {
   double re = 0.0, im = 0.0;
@@ -32,26 +32,24 @@ __device__ __forceinline__ cd load_a_pair(const double* __restrict__ u, const do
   if (k + 1 <= N) im = u[k] * nn[k];
   return cd{re, im};
 }
+// Double-word: u, nn indexed by size, zero at size 0 and N + 1 and 16-byte
+// aligned, so sizes k and k + 1 are one aligned 16-byte load of each.
 __device__ __forceinline__ cdw load_a_pair(const float2* __restrict__ u, const float2* __restrict__ nn,
                                            int N, int k, cdw) {
-  dw re{0.f, 0.f}, im{0.f, 0.f};
-  if (k >= 1 && k <= N) {
-    float2 a = u[k - 1], b = nn[k - 1];
-    re = dw_mul(dw{a.x, a.y}, dw{b.x, b.y});
-  }
-  if (k + 1 <= N) {
-    float2 a = u[k], b = nn[k];
-    im = dw_mul(dw{a.x, a.y}, dw{b.x, b.y});
-  }
-  return make_cdw(re, im);
+  if (k > N) return c_zero(cdw{});
+  const float4 a = __ldg(reinterpret_cast<const float4*>(u + k));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(nn + k));
+  return make_cdw(dw_mul(dw{a.x, a.y}, dw{b.x, b.y}), dw_mul(dw{a.z, a.w}, dw{b.z, b.w}));
 }
 __device__ __forceinline__ const double* vec_ptr(const RhsParams& P, int v, cd) { return P.U64 + P.voff[v]; }
-__device__ __forceinline__ const float2* vec_ptr(const RhsParams& P, int v, cdw) { return P.Udw + P.voff[v]; }
-__device__ __forceinline__ const double* n_ptr(const RhsParams&, const double* n, int64_t off, cd) {
-  return n + off;
+__device__ __forceinline__ const float2* vec_ptr(const RhsParams& P, int v, cdw) {
+  return P.Udw + P.vdwoff[v];
 }
-__device__ __forceinline__ const float2* n_ptr(const RhsParams& P, const double*, int64_t off, cdw) {
-  return P.ndw + off;
+__device__ __forceinline__ const double* n_ptr(const RhsParams&, const double* n, const OrderDesc& od, cd) {
+  return n + od.noff;
+}
+__device__ __forceinline__ const float2* n_ptr(const RhsParams& P, const double*, const OrderDesc& od, cdw) {
+  return P.ndw + od.ndwoff;
 }
 
 // Power-of-two weight of a rank term (double-word path keeps every factor
@@ -101,7 +99,7 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   else
     for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
   const auto u = vec_ptr(P, v, C{});
-  const auto nn = n_ptr(P, n, od.noff, C{});
+  const auto nn = n_ptr(P, n, od, C{});
   const int N = od.N;
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;

@@ -52,7 +52,7 @@ __global__ void k_nsplit(const __grid_constant__ RhsParams P, const double* __re
   const double mx = __longlong_as_double((long long)sc->nmax_bits);
   const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) + 1 : 0;
   const double* x = n + s.noff;
-  float2* out = P.ndw + s.noff;
+  float2* out = P.ndw + s.ndwoff + 1;  // element index = size
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.N; k += gridDim.x * blockDim.x) {
     const dw v = dw_from_double(scalbn(x[k], -e));
     out[k] = make_float2(v.hi, v.lo);

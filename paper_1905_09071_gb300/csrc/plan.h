@@ -29,6 +29,7 @@ struct OrderDesc {
   int nvec;            // factor vectors of this order (CP: d R; TT: nonzero core vectors)
   int N;               // sizes of the system
   int64_t noff;        // offset of the system's size 1 in packed state vectors
+  int64_t ndwoff;      // offset of the system's double-word n (RhsParams::ndw)
   int L, M, M1, M2;    // real FFT length, complex length, four-step factors
   int vbase;           // first global vector index (CP: v = vbase + m R + r)
   int W;               // columns per block in the column kernels
@@ -59,6 +60,7 @@ struct OrderDesc {
 struct SysDesc {
   int N, D, fmt;
   int64_t noff;        // packed offset of size 1
+  int64_t ndwoff;      // offset of its double-word n (element index = size)
   int vbeg, vend;      // its global vectors
   int ibeg, iend;      // its items (orders)
   int ndotchunk;       // inner-product chunks per vector
@@ -107,8 +109,13 @@ struct RhsParams {
   const int* rowperm;            // [nitems] items in row-kernel order, heaviest first (rowpre follows it)
   const double* U64;             // [Vtot][N_b] FP64 factors (vector v at voff[v])
   const int64_t* voff;           // [Vtot] offset of vector v in the factor arrays
-  const float2* Udw;             // double-word factors, scaled by 2^-e_v (same offsets)
-  float2* ndw;                   // [Ntot] double-word n scaled by 2^-e_n of its system
+  // Double-word copies, indexed by size: element 0 and element N + 1 (and one
+  // more for odd N) are zero, elements 1..N hold sizes 1..N, and every array
+  // starts on a 16-byte boundary, so that sizes (2j, 2j + 1) form one aligned
+  // 16-byte load.
+  const float2* Udw;             // factors scaled by 2^-e_v, vector v at vdwoff[v]
+  const int64_t* vdwoff;         // [Vtot]
+  float2* ndw;                   // n scaled by 2^-e_n of its system, at SysDesc::ndwoff
   void* scratch;                 // forward column output, all vectors (TT: then their spectra)
   void* scratch2;                // per item: spectral sum after the inverse row step
   void* spec_nyq;                // TT: [Vtot] Nyquist value of each vector's spectrum

@@ -182,13 +182,17 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   // ---- vectors: host copy of every nonzero factor vector, packed ----------
   std::vector<double> hf;          // concatenated vectors
   std::vector<int64_t> voff;       // offset of each vector in hf
+  std::vector<int64_t> vdwoff;     // offset of each vector in the double-word copy
   std::vector<int> vsys;           // system of each vector
   std::vector<int> vid;            // TT tables
   std::vector<SysDesc>& S = pl->systems;
   std::vector<OrderDesc>& I = pl->items;
   S.resize(B);
   pl->offsets.assign(B + 1, 0);
-  int64_t noff = 0;
+  int64_t noff = 0, ndwoff = 0, vdwtot = 0;
+  // Double-word arrays are indexed by size with zero slots at 0 and N + 1
+  // (one more for odd N, so that every array starts 16-byte aligned).
+  auto dwlen = [](int N) { return (int64_t)((N + 3) & ~1); };
   cudaError_t e;
   for (int b = 0; b < B; ++b) {
     const sag_system& s = sys[b];
@@ -205,6 +209,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     sd.D = s.D;
     sd.fmt = s.fmt;
     sd.noff = noff;
+    sd.ndwoff = ndwoff;
     sd.vbeg = (int)vsys.size();
     sd.ibeg = (int)I.size();
     sd.ndotchunk = (N + P.dotchunk - 1) / P.dotchunk;
@@ -216,10 +221,13 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       od.d = d;
       od.N = N;
       od.noff = noff;
+      od.ndwoff = ndwoff;
       od.fmt = s.fmt;
       od.vbase = (int)vsys.size();
       auto push_vector = [&](const double* x) {
         voff.push_back((int64_t)hf.size());
+        vdwoff.push_back(vdwtot);
+        vdwtot += dwlen(N);
         vsys.push_back(b);
         hf.insert(hf.end(), x, x + N);
         return (int)vsys.size() - 1;
@@ -254,10 +262,12 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     sd.vend = (int)vsys.size();
     sd.iend = (int)I.size();
     noff += N;
+    ndwoff += dwlen(N);
     pl->offsets[b + 1] = noff;
   }
   pl->Ntot = noff;
   pl->nfactor = (int64_t)hf.size();
+  pl->nfactor_dw = vdwtot;
   P.Ntot = noff;
   P.Vtot = (int)vsys.size();
   P.nitems = (int)I.size();
@@ -379,7 +389,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   // 2^(sum_l E_l) (TT) moves into the FP64 scale of P^(d).
   std::vector<int> ev(Vtot, 0);
   if (dwp) {
-    std::vector<float2> hdw(hf.size());
+    std::vector<float2> hdw((size_t)std::max<int64_t>(vdwtot, 1), make_float2(0.f, 0.f));
     for (int v = 0; v < Vtot; ++v) {
       const int N = S[vsys[v]].N;
       const double* x = hf.data() + voff[v];
@@ -390,14 +400,18 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       ev[v] = ex;
       for (int k = 0; k < N; ++k) {
         dw y = dw_from_double(std::ldexp(x[k], -ex));
-        hdw[voff[v] + k] = make_float2(y.hi, y.lo);
+        hdw[vdwoff[v] + 1 + k] = make_float2(y.hi, y.lo);
       }
     }
     float2* Udw = nullptr;
     if ((e = pl->upload(&Udw, hdw)) != cudaSuccess) return fail(SAG_ENOMEM, "cudaMalloc dw factors");
     P.Udw = Udw;
     float2* ndw = nullptr;
-    if ((e = pl->alloc(&ndw, (size_t)pl->Ntot)) != cudaSuccess) return fail(SAG_ENOMEM, "cudaMalloc n");
+    if ((e = pl->alloc(&ndw, (size_t)std::max<int64_t>(ndwoff, 1))) != cudaSuccess)
+      return fail(SAG_ENOMEM, "cudaMalloc n");
+    // the zero slots stay zero: the split kernel writes elements 1..N only
+    if ((e = cudaMemset(ndw, 0, (size_t)std::max<int64_t>(ndwoff, 1) * sizeof(float2))) != cudaSuccess)
+      return cuda_fail(e, "clear n");
     P.ndw = ndw;
   }
   std::vector<float> vweight(Vtot, 1.0f);
@@ -462,13 +476,15 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   int *d_colpre = nullptr, *d_rowpre = nullptr, *d_invpre = nullptr, *d_chainpre = nullptr,
       *d_epipre = nullptr, *d_vsys = nullptr, *d_rowperm = nullptr, *d_vid = nullptr;
   int64_t* d_voff = nullptr;
+  int64_t* d_vdwoff = nullptr;
   float* d_vw = nullptr;
   if (pl->upload(&d_ord, I) != cudaSuccess || pl->upload(&d_sys, S) != cudaSuccess ||
       pl->upload(&d_colpre, colpre) != cudaSuccess || pl->upload(&d_rowpre, rowpre) != cudaSuccess ||
       pl->upload(&d_invpre, invpre) != cudaSuccess || pl->upload(&d_chainpre, chainpre) != cudaSuccess ||
       pl->upload(&d_epipre, epipre) != cudaSuccess || pl->upload(&d_vsys, vsys) != cudaSuccess ||
       pl->upload(&d_rowperm, rowperm) != cudaSuccess || pl->upload(&d_vid, vid) != cudaSuccess ||
-      pl->upload(&d_voff, voff) != cudaSuccess || pl->upload(&d_vw, vweight) != cudaSuccess)
+      pl->upload(&d_voff, voff) != cudaSuccess || pl->upload(&d_vw, vweight) != cudaSuccess ||
+      pl->upload(&d_vdwoff, vdwoff) != cudaSuccess)
     return fail(SAG_ENOMEM, "cudaMalloc tables");
   P.ord = d_ord;
   P.sys = d_sys;
@@ -481,6 +497,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   P.rowperm = d_rowperm;
   P.vid = d_vid;
   P.voff = d_voff;
+  P.vdwoff = d_vdwoff;
   P.vweight = d_vw;
   const size_t Nt = (size_t)pl->Ntot;
   if (pl->alloc((unsigned char**)&P.spec_nyq, (size_t)Vtot * csize) != cudaSuccess ||
@@ -546,11 +563,12 @@ sag_status update_factors(sag_plan_s* pl, const double* factors, int on_device) 
   if ((e = cudaMemcpy((void*)P.U64, hf.data(), nf * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "upload factors");
   std::vector<int> ev(Vtot, 0);
-  std::vector<int64_t> voff(Vtot);
-  if ((e = cudaMemcpy(voff.data(), P.voff, sizeof(int64_t) * Vtot, cudaMemcpyDeviceToHost)) != cudaSuccess)
+  std::vector<int64_t> voff(Vtot), vdwoff(Vtot);
+  if ((e = cudaMemcpy(voff.data(), P.voff, sizeof(int64_t) * Vtot, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(vdwoff.data(), P.vdwoff, sizeof(int64_t) * Vtot, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "read layout");
   if (dwp) {
-    std::vector<float2> hdw(nf);
+    std::vector<float2> hdw((size_t)pl->nfactor_dw, make_float2(0.f, 0.f));
     for (const SysDesc& sd : pl->systems)
       for (int v = sd.vbeg; v < sd.vend; ++v) {
         const double* x = hf.data() + voff[v];
@@ -561,10 +579,11 @@ sag_status update_factors(sag_plan_s* pl, const double* factors, int on_device) 
         ev[v] = ex;
         for (int k = 0; k < sd.N; ++k) {
           dw y = dw_from_double(std::ldexp(x[k], -ex));
-          hdw[voff[v] + k] = make_float2(y.hi, y.lo);
+          hdw[vdwoff[v] + 1 + k] = make_float2(y.hi, y.lo);
         }
       }
-    if ((e = cudaMemcpy((void*)P.Udw, hdw.data(), nf * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpy((void*)P.Udw, hdw.data(), hdw.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
       return cuda_fail(e, "upload dw factors");
   }
   std::vector<int> vexcl(Vtot, 0);

@@ -33,6 +33,7 @@ struct sag_plan_s {
   int B = 0, prec = 0, rk = 0, sym = 1, fmt = 0;
   int64_t Ntot = 0;
   int64_t nfactor = 0;                    // factor values over all vectors (vector layout)
+  int64_t nfactor_dw = 0;                 // length of the padded double-word factor copy
   // integrate_vjp buffers, allocated on first use
   double* vjp_pool = nullptr;
   size_t vjp_pool_len = 0;
