@@ -123,6 +123,28 @@ SAG_CX int ct_twi(int j, int t) {
   return ct_twp_off(P, S) + (j % Ns) * ct_twstride(R) + t - 1;
 }
 
+// The same maps with a runtime span, for radix-8 passes (Ns a power of two):
+// used by the compact variant below.
+SAG_CX int ct_dst8_rt(int j, int t, int Ns) {
+  const int k = j & (Ns - 1);
+  return pad8((j - k) * 8 + k + t * Ns);
+}
+SAG_CX int ct_twi8_rt(int j, int t, int Ns, int twoff) {
+  return twoff + (j & (Ns - 1)) * ct_twstride(8) + t - 1;
+}
+// Number of leading radix-8 passes and their total span.
+SAG_CX int ct_n8(int P) {
+  const ct_sched sc = make_ct_sched(P);
+  int n = 0;
+  while (n < sc.n && sc.r[n] == 8) ++n;
+  return n;
+}
+SAG_CX int ct_ns8(int P) {
+  int v = 1;
+  for (int s = 0; s < ct_n8(P); ++s) v *= 8;
+  return v;
+}
+
 SAG_CX bool ct_supported(int P) {
   return P == 64 || P == 128 || P == 256 || P == 512 || P == 96 || P == 192 || P == 384 ||
          P == 768;
@@ -203,6 +225,60 @@ template <class C, int P, int COUNT, int T>
 __device__ __forceinline__ void fft_ct_rest(C* buf, int ld, const C* tw) {
   constexpr int R = make_ct_sched(P).r[0];
   ct_passes<C, P, COUNT, T, 1, R>(buf, ld, tw);
+}
+
+// Compact variant for kernels whose blocks each run once per SM (the cost
+// there is fetching the code, not issuing it): all radix-8 passes share one
+// pass body with the span Ns and the pass-table offset as runtime values;
+// only the radix-4/2/3 tail passes are specialised. Same arithmetic, same
+// layout, same tables as fft_ct.
+template <class C, int P, int COUNT, int T>
+__device__ __forceinline__ void ct_pass8_rt(C* buf, int ld, const C* tw, int Ns, int twoff) {
+  constexpr int R = 8;
+  constexpr int NB = P / R;
+  constexpr int TOT = NB * COUNT;
+  constexpr int PER = (TOT + T - 1) / T;
+  C x[PER][R];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int w = threadIdx.x + i * T;
+    if (TOT % T == 0 || w < TOT) {
+      const int b = w / NB, j = w - b * NB;
+      const C* ib = buf + b * ld;
+#pragma unroll
+      for (int t = 0; t < R; ++t) x[i][t] = ib[ct_src<P, R, false>(j, t)];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int w = threadIdx.x + i * T;
+    if (TOT % T == 0 || w < TOT) {
+      const int b = w / NB, j = w - b * NB;
+      if (Ns > 1) {
+#pragma unroll
+        for (int t = 1; t < R; ++t) x[i][t] = c_mul(x[i][t], tw[ct_twi8_rt(j, t, Ns, twoff)]);
+      }
+      dft_r<R>(x[i]);
+      C* ob = buf + b * ld;
+#pragma unroll
+      for (int t = 0; t < R; ++t) ob[ct_dst8_rt(j, t, Ns)] = x[i][t];
+    }
+  }
+  __syncthreads();
+}
+
+template <class C, int P, int COUNT, int T>
+__device__ __forceinline__ void fft_ct_compact(C* buf, int ld, const C* tw) {
+  constexpr int N8 = ct_n8(P);
+  static_assert(N8 >= 1, "compile-time lengths start with radix 8");
+  int Ns = 1;
+#pragma unroll 1
+  for (int s = 0; s < N8; ++s) {
+    ct_pass8_rt<C, P, COUNT, T>(buf, ld, tw, Ns, ct_twp_off(P, s));
+    Ns *= 8;
+  }
+  ct_passes<C, P, COUNT, T, N8, ct_ns8(P)>(buf, ld, tw);
 }
 
 template <class C, int P, int S, int Ns>

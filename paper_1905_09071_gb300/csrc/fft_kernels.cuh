@@ -452,7 +452,7 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   __syncthreads();
   C* res;
   if constexpr (CT) {
-    fft_ct<C, P1, ct_cols(P1), kThreads>(buf, ld, tw);
+    fft_ct_compact<C, P1, ct_cols(P1), kThreads>(buf, ld, tw);  // one block per SM: small code
     res = buf;
   } else {
     res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);

@@ -64,6 +64,12 @@ static void ct_host_passes(std::vector<C>& buf, int ld, int count, const C* tw, 
             std::exit(3);
           }
           x[((size_t)b * NB + j) * R + t] = nat ? nat[src] : buf[src];
+          // the compact variant's runtime maps agree with the compile-time ones
+          if (R == 8 && (ct_dst8_rt(j, t, Ns) != ct_dst<P, R, Ns>(j, t) ||
+                         (Ns > 1 && t > 0 && ct_twi8_rt(j, t, Ns, ct_twp_off(P, S)) != ct_twi<P, S, R, Ns>(j, t)))) {
+            std::printf("runtime map differs P=%d pass %d\n", P, S);
+            std::exit(3);
+          }
         }
     for (int b = 0; b < count; ++b)
       for (int j = 0; j < NB; ++j) {
