@@ -63,12 +63,45 @@ bool is_device_ptr(const void* p) {
 sag_status eval(sag_plan_t pl, const double* nin, EpiArgs A, cudaStream_t st, bool allow_hook = true) {
   A.part = pl->epi_part;
   cudaError_t e = enqueue_eval(pl->P, pl->L, nin, A, st, (pl->prof && allow_hook) ? &pl->hook : nullptr,
-                               &pl->side);
+                               &pl->side, &pl->groups);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return SAG_OK;
 }
 
 // The two stages of one explicit RK2 step (Heun or midpoint) on device state n.
+// Runs the work `enqueue` puts on a stream as a CUDA graph: captured once per
+// key on the plan's capture stream, then replayed on st.
+template <class F>
+sag_status replay(sag_plan_t pl, const sag_plan_s::GraphKey& k, cudaStream_t st, F enqueue) {
+  cudaGraphExec_t x = nullptr;
+  for (auto& it : pl->gcache)
+    if (it.first.kind == k.kind && it.first.p0 == k.p0 && it.first.p1 == k.p1 && it.first.dt == k.dt)
+      x = it.second;
+  cudaError_t e;
+  if (!x) {
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(e, "begin capture");
+    sag_status s = enqueue(pl->cap_stream);
+    e = cudaStreamEndCapture(pl->cap_stream, &g);
+    if (s != SAG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    if (pl->gcache.size() >= 4) {
+      cudaGraphExecDestroy(pl->gcache.front().second);
+      pl->gcache.erase(pl->gcache.begin());
+    }
+    pl->gcache.push_back({k, x});
+  }
+  if ((e = cudaGraphLaunch(x, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+  return SAG_OK;
+}
+
 sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaStream_t st,
                         bool allow_hook) {
   EpiArgs a{};
@@ -226,7 +259,10 @@ sag_status sag_rhs(sag_plan_t pl, const double* n, double* dndt, void* stream) {
   a.mode = EPI_RHS;
   a.nin = nd;
   a.out0 = oh ? pl->stage_b : dndt;
-  sag_status s = eval(pl, nd, a, st);
+  // per-kernel profiling launches kernel by kernel; otherwise a cached graph
+  sag_status s = pl->prof ? eval(pl, nd, a, st)
+                          : replay(pl, {1, nd, a.out0, 0.0}, st,
+                                   [&](cudaStream_t cs) { return eval(pl, nd, a, cs, false); });
   if (s != SAG_OK) return s;
   if (oh) {
     if ((e = cudaMemcpyAsync(dndt, pl->stage_b, nb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -249,7 +285,10 @@ sag_status sag_rk2_step(sag_plan_t pl, double* n, double dt, void* stream) {
       return cuda_fail(e, "copy n");
     nd = pl->stage_a;
   }
-  sag_status s = enqueue_step(pl, nd, dt, nullptr, st, true);
+  sag_status s = pl->prof ? enqueue_step(pl, nd, dt, nullptr, st, true)
+                          : replay(pl, {2, nd, nullptr, dt}, st, [&](cudaStream_t cs) {
+                              return enqueue_step(pl, nd, dt, nullptr, cs, false);
+                            });
   if (s != SAG_OK) return s;
   if (h) {
     if ((e = cudaMemcpyAsync(n, pl->stage_a, nb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)

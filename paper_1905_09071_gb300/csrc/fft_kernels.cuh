@@ -133,12 +133,13 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
 
 template <class C>
 __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__ RhsParams P,
-                                                      const double* __restrict__ n) {
+                                                      const double* __restrict__ n, int base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int it = find_segment(P.colpre, P.nitems, blockIdx.x);
+  const int bid = base + blockIdx.x;  // launches may cover a range of the colpre table
+  const int it = find_segment(P.colpre, P.nitems, bid);
   const OrderDesc& od = P.ord[it];
-  const int local = blockIdx.x - P.colpre[it];
+  const int local = bid - P.colpre[it];
   const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
   if constexpr (!std::is_same<C, cdw>::value) {
     fwd_col_body<C, 0>(P, od, vloc, cb, n, buf);
@@ -407,14 +408,15 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
 }
 
 template <class C>
-__global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ RhsParams P) {
+__global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ RhsParams P, int base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   // Items with the most vectors per row pair come first (rowperm), so that
-  // they are scheduled first.
-  const int j = find_segment(P.rowpre, P.nitems, blockIdx.x);
+  // they are scheduled first; launches may cover a range of the table.
+  const int bid = base + blockIdx.x;
+  const int j = find_segment(P.rowpre, P.nitems, bid);
   const OrderDesc& od = P.ord[P.rowperm[j]];
-  const int kp = blockIdx.x - P.rowpre[j];
+  const int kp = bid - P.rowpre[j];
   if constexpr (!std::is_same<C, cdw>::value) {
     rows_body<C>(P, od, kp, buf);
     return;
@@ -470,12 +472,13 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
 }
 
 template <class C>
-__global__ void __launch_bounds__(kThreads, 4) k_inv_col(const __grid_constant__ RhsParams P) {
+__global__ void __launch_bounds__(kThreads, 4) k_inv_col(const __grid_constant__ RhsParams P, int base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int oi = find_segment(P.invpre, P.nitems, blockIdx.x);
+  const int bid = base + blockIdx.x;  // launches may cover a range of the invpre table
+  const int oi = find_segment(P.invpre, P.nitems, bid);
   const OrderDesc& od = P.ord[oi];
-  const int cb = blockIdx.x - P.invpre[oi];
+  const int cb = bid - P.invpre[oi];
   if constexpr (!std::is_same<C, cdw>::value) {
     inv_col_body<C, 0>(P, od, oi, cb, buf);
     return;

@@ -330,7 +330,8 @@ __global__ void __launch_bounds__(1024) k_moments(const __grid_constant__ RhsPar
 
 // ---- launch of one evaluation ---------------------------------------------
 cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
-                         const EpiArgs& A, cudaStream_t st, LaunchHook* hook, const SideStream* side) {
+                         const EpiArgs& A, cudaStream_t st, LaunchHook* hook, const SideStream* side,
+                         const FftGroups* groups) {
   if (P.dwpath) {
     if (hook) hook->mark(KID_NMAX, st);
     k_nmax<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, nin);
@@ -351,8 +352,22 @@ cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* n
   if (hook) hook->mark(KID_COEF, st);
   k_coef<<<P.B, 256, L.coef_smem, ds>>>(P);
   if (fork && (e = cudaEventRecord(side->join, ds)) != cudaSuccess) return e;
-  e = P.dwpath ? enqueue_fft_dw(P, L, nin, st, hook) : enqueue_fft_f64(P, L, nin, st, hook);
-  if (e != cudaSuccess) return e;
+  if (fork && groups && groups->n > 1) {
+    // one FFT chain per group, each on its own stream after the split of n
+    for (int g = 0; g < groups->n; ++g) {
+      cudaStream_t gs = groups->s[g].stream;
+      if ((e = cudaStreamWaitEvent(gs, side->fork, 0)) != cudaSuccess) return e;
+      e = P.dwpath ? enqueue_fft_dw(P, L, nin, gs, nullptr, &groups->r[g])
+                   : enqueue_fft_f64(P, L, nin, gs, nullptr, &groups->r[g]);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaEventRecord(groups->s[g].join, gs)) != cudaSuccess) return e;
+    }
+    for (int g = 0; g < groups->n; ++g)
+      if ((e = cudaStreamWaitEvent(st, groups->s[g].join, 0)) != cudaSuccess) return e;
+  } else {
+    e = P.dwpath ? enqueue_fft_dw(P, L, nin, st, hook) : enqueue_fft_f64(P, L, nin, st, hook);
+    if (e != cudaSuccess) return e;
+  }
   if (fork && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return e;
   if (hook) hook->mark(KID_EPILOGUE, st);
   k_epilogue<<<L.epi_blocks, 256, L.epi_smem, st>>>(P, A);

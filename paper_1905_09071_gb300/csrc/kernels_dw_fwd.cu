@@ -5,9 +5,9 @@
 
 namespace sag {
 
-cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
-  (void)nin;
-  k_fwd_col<cdw><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin);
+cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
+                                int base, int blocks) {
+  if (blocks > 0) k_fwd_col<cdw><<<blocks, kThreads, L.col_smem, st>>>(P, nin, base);
   return cudaGetLastError();
 }
 

@@ -5,9 +5,8 @@
 
 namespace sag {
 
-cudaError_t launch_k_inv_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
-  (void)nin;
-  k_inv_col<cdw><<<L.inv_blocks, kThreads, L.inv_smem, st>>>(P);
+cudaError_t launch_k_inv_col_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, int base, int blocks) {
+  if (blocks > 0) k_inv_col<cdw><<<blocks, kThreads, L.inv_smem, st>>>(P, base);
   return cudaGetLastError();
 }
 

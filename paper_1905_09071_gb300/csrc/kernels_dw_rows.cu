@@ -5,9 +5,8 @@
 
 namespace sag {
 
-cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
-  (void)nin;
-  k_rows<cdw><<<L.row_blocks, kThreads, L.row_smem, st>>>(P);
+cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, int base, int blocks) {
+  if (blocks > 0) k_rows<cdw><<<blocks, kThreads, L.row_smem, st>>>(P, base);
   return cudaGetLastError();
 }
 

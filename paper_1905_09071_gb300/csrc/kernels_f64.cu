@@ -4,23 +4,25 @@
 namespace sag {
 
 cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                            LaunchHook* hook) {
+                            LaunchHook* hook, const FftRange* r) {
+  const FftRange all{0, L.col_blocks, 0, L.row_blocks, 0, L.inv_blocks};
+  const FftRange& R = r ? *r : all;
   if (hook) hook->mark(KID_FWD_COL, st);
-  k_fwd_col<cd><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin);
+  if (R.col1 > R.col0) k_fwd_col<cd><<<R.col1 - R.col0, kThreads, L.col_smem, st>>>(P, nin, R.col0);
   if (L.has_tt) {
-    cudaError_t e = launch_tt_stage<cd>(P, L, st, hook);
+    cudaError_t e = launch_tt_stage<cd>(P, L, st, hook);  // every item (no groups with TT)
     if (e != cudaSuccess) return e;
   } else {
     if (hook) hook->mark(KID_ROWS, st);
-    k_rows<cd><<<L.row_blocks, kThreads, L.row_smem, st>>>(P);
+    if (R.row1 > R.row0) k_rows<cd><<<R.row1 - R.row0, kThreads, L.row_smem, st>>>(P, R.row0);
   }
   if (hook) hook->mark(KID_INV_COL, st);
-  k_inv_col<cd><<<L.inv_blocks, kThreads, L.inv_smem, st>>>(P);
+  if (R.inv1 > R.inv0) k_inv_col<cd><<<R.inv1 - R.inv0, kThreads, L.inv_smem, st>>>(P, R.inv0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
-  k_fwd_col<cd><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin);
+  k_fwd_col<cd><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin, 0);
   return cudaGetLastError();
 }
 

@@ -4,11 +4,12 @@
 
 namespace sag {
 
-cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
+                                int base, int blocks);
 
 cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
                               cudaStream_t st) {
-  cudaError_t e = launch_k_fwd_col_dw(P, L, n, st);
+  cudaError_t e = launch_k_fwd_col_dw(P, L, n, st, 0, L.col_blocks);
   if (e != cudaSuccess) return e;
   k_gcol<cdw><<<L.inv_blocks, kThreads, L.vcol_smem, st>>>(P, g);
   k_rows_vjp<cdw><<<L.row_blocks, kThreads, L.vrow_smem, st>>>(P);

@@ -53,9 +53,24 @@ struct SideStream {
   cudaEvent_t fork, join;
 };
 
+// Block ranges [begin, end) of the three FFT kernels' tables (colpre, rowpre in
+// rowperm order, invpre) for one group of items.
+struct FftRange {
+  int col0, col1, row0, row1, inv0, inv1;
+};
+
+// FFT groups run on their own streams (graph branches) so that one order's
+// ALU-heavy row pass overlaps another order's memory-heavy column pass.
+constexpr int kMaxFftGroups = 4;
+struct FftGroups {
+  int n;                            // 0: one launch per kernel on the caller's stream
+  FftRange r[kMaxFftGroups];
+  SideStream s[kMaxFftGroups];      // stream, and the events that fork and join it
+};
+
 cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
                          const EpiArgs& A, cudaStream_t st, LaunchHook* hook = nullptr,
-                         const SideStream* side = nullptr);
+                         const SideStream* side = nullptr, const FftGroups* groups = nullptr);
 // Largest dynamic shared memory a block may use on the current device.
 inline int smem_limit() {
   int dev = 0, v = 48 * 1024;
@@ -77,10 +92,11 @@ inline cudaError_t allow_max_smem(F* func) {
 }
 
 cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, cudaStream_t st);
+// FFT stage over the block range r (nullptr: every item).
 cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                            LaunchHook* hook);
+                            LaunchHook* hook, const FftRange* r = nullptr);
 cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                           LaunchHook* hook);
+                           LaunchHook* hook, const FftRange* r = nullptr);
 cudaError_t setup_common_kernels(const LaunchCfg& L);
 // n -> double-word with its per-system power-of-two scale (resets nothing).
 cudaError_t enqueue_nsplit(const RhsParams& P, const LaunchCfg& L, const double* n, cudaStream_t st);

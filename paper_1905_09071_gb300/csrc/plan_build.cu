@@ -536,6 +536,23 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       (e = cudaEventCreateWithFlags(&pl->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&pl->side.join, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(e, "stream");
+  // A few CP items (one system): one FFT chain per item on its own stream,
+  // the heaviest (first in rowperm order) at the highest priority.
+  if (!tt && P.nitems >= 2 && P.nitems <= kMaxFftGroups) {
+    int least = 0, greatest = 0;
+    if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess) return cuda_fail(e, "stream");
+    for (int p = 0; p < P.nitems; ++p) {
+      const int i = rowperm[p];
+      pl->groups.r[p] = FftRange{colpre[i], colpre[i + 1], rowpre[p], rowpre[p + 1], invpre[i], invpre[i + 1]};
+      const int prio = std::min(least, greatest + p);
+      SideStream& s = pl->groups.s[p];
+      if ((e = cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "stream");
+      s.fork = nullptr;
+      pl->groups.n = p + 1;
+    }
+  }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "plan setup");
   return SAG_OK;
 }

@@ -55,8 +55,18 @@ struct sag_plan_s {
   size_t stage_diag_len = 0;
   cudaStream_t cap_stream = nullptr;
   sag::SideStream side{nullptr, nullptr, nullptr};
+  sag::FftGroups groups{};
   bool prof = false;
   sag::EventHook hook;
+  // Instantiated graphs of sag_rhs / sag_rk2_step calls, keyed by the call's
+  // kind, device pointers and dt (a few, most recent last).
+  struct GraphKey {
+    int kind;
+    const void* p0;
+    const void* p1;
+    double dt;
+  };
+  std::vector<std::pair<GraphKey, cudaGraphExec_t>> gcache;
   cudaGraphExec_t gexec = nullptr;
   const double* g_n = nullptr;
   double g_dt = 0.0;
@@ -80,10 +90,15 @@ struct sag_plan_s {
   }
   ~sag_plan_s() {
     if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& g : gcache) cudaGraphExecDestroy(g.second);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (side.stream) cudaStreamDestroy(side.stream);
     if (side.fork) cudaEventDestroy(side.fork);
     if (side.join) cudaEventDestroy(side.join);
+    for (int g = 0; g < groups.n; ++g) {
+      if (groups.s[g].stream) cudaStreamDestroy(groups.s[g].stream);
+      if (groups.s[g].join) cudaEventDestroy(groups.s[g].join);
+    }
     for (void* q : allocs) cudaFree(q);
     if (stage_diag) cudaFree(stage_diag);
     if (vjp_pool) cudaFree(vjp_pool);
