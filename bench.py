@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="timed region only: no parity check, kernel profile, e2e or CPU baseline "
                          "(for ncu captures); prints no JSON line")
+    ap.add_argument("--kernels", action="store_true",
+                    help="per-kernel pass only: K non-graph RK2 steps of the FP32-split path, each "
+                         "kernel launched once per right-hand side over every item and timed with "
+                         "CUDA events (the launches the roofline figures refer to; for ncu captures); "
+                         "prints the per-kernel table to stderr, no JSON line")
     ap.add_argument("--workload", default="throughput", choices=["throughput", "batched"],
                     help="batched: 256 independent systems in one plan vs a loop of plans")
     ap.add_argument("--systems", type=int, default=256)
@@ -275,6 +280,21 @@ def run_ours(args, world, rank, local):
     clocks = None
     precs = {"both": (sag.SAG_FP32_SPLIT, sag.SAG_FP64), "fp32_split": (sag.SAG_FP32_SPLIT,),
              "fp64": (sag.SAG_FP64,)}[args.prec]
+    if args.kernels:
+        pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT)
+        n = torch.tensor(s.n0, device="cuda")
+        pl.profile(True)
+        for _ in range(W):
+            pl.rk2_step(n, s.dt)
+        pl.profile_read()
+        for _ in range(K):
+            pl.rk2_step(n, s.dt)
+        prof = pl.profile_read()
+        assert pl.sync_status() == sag.SAG_OK
+        for name, (ms, cnt) in prof.items():
+            print(f"{name:12s} {cnt:6d} launches {1e3 * ms / cnt:9.1f} us/launch", file=sys.stderr)
+        pl.close()
+        return
     if args.quick:
         for prec in precs:
             pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec)
