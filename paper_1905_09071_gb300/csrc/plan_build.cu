@@ -536,9 +536,11 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       (e = cudaEventCreateWithFlags(&pl->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&pl->side.join, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(e, "stream");
-  // A few CP items (one system): one FFT chain per item on its own stream,
-  // the heaviest (first in rowperm order) at the highest priority.
-  if (!tt && P.nitems >= 2 && P.nitems <= kMaxFftGroups) {
+  // A few CP items (one system), double-word path: one FFT chain per item on
+  // its own stream, the heaviest (first in rowperm order) at the highest
+  // priority. (The FP64 kernels, bound by the FP64 pipe, gain nothing from
+  // the overlap and lose a little.)
+  if (!tt && dwp && P.nitems >= 2 && P.nitems <= kMaxFftGroups) {
     int least = 0, greatest = 0;
     if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess) return cuda_fail(e, "stream");
     for (int p = 0; p < P.nitems; ++p) {
