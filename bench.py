@@ -55,6 +55,8 @@ def parse():
                          "kernel launched once per right-hand side over every item and timed with "
                          "CUDA events (the launches the roofline figures refer to; for ncu captures); "
                          "prints the per-kernel table to stderr, no JSON line")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="plans with the fixed launch rules instead of the plan-time autotuner")
     ap.add_argument("--workload", default="throughput", choices=["throughput", "batched"],
                     help="batched: 256 independent systems in one plan vs a loop of plans")
     ap.add_argument("--systems", type=int, default=256)
@@ -275,6 +277,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     s = wl.random_power_cp()
     K, W = args.steps, args.warmup
+    tune = 0 if args.no_autotune else 1
     res = {}
     sampler = ClockSampler(local)
     clocks = None
@@ -297,7 +300,7 @@ def run_ours(args, world, rank, local):
         return
     if args.quick:
         for prec in precs:
-            pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec)
+            pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, autotune=tune)
             n = torch.tensor(s.n0, device="cuda")
             pl.integrate(n, s.dt, W)
             t = time_integrate(pl, n, s.dt, K, world)
@@ -308,7 +311,7 @@ def run_ours(args, world, rank, local):
     if args.prec != "both":
         raise SystemExit("--prec other than both needs --quick")
     for prec in precs:
-        pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec)
+        pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, autotune=tune)
         n = torch.tensor(s.n0, device="cuda")
         pl.integrate(n, s.dt, max(W, 3))
         torch.cuda.synchronize()
@@ -336,7 +339,7 @@ def run_ours(args, world, rank, local):
         pl.close()
 
     # end-to-end: the public call with host buffers (pinned), copies inside
-    pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT)
+    pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT, autotune=tune)
     host_n = torch.tensor(s.n0).pin_memory().numpy()
     for _ in range(max(W, 3)):
         pl.rk2_step(host_n, s.dt)
@@ -384,7 +387,10 @@ def run_ours(args, world, rank, local):
                    "timed": "sag_integrate: K Heun steps as CUDA-graph replays, inputs resident in HBM",
                    "l2": "working set (factor copies 151 MB + FFT workspace 243 MB) larger than the 129 MB L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "fft_geometry": dw["desc"]["orders"]},
+                   "fft_geometry": dw["desc"]["orders"],
+                   "fft_stream_groups": {"fp32_split": dw["desc"]["blocks"]["fft_groups"],
+                                         "fp64": f64["desc"]["blocks"]["fft_groups"],
+                                         "chosen_by": "fixed rule" if args.no_autotune else "plan-time autotuner"}},
         "rhs_evals_per_s": max(K, 10) / dw["t_rhs"],
         "error_vs_oracle": {"fp32_split": dw["err"], "fp64": f64["err"],
                             "metric": "max|x - oracle| / (max|P| + max|Q|), one RHS at n0"},
@@ -421,7 +427,8 @@ def run_batched(args, world, rank, local):
     dt = systems[0].dt
     desc = [(s.N, s.D, s.ranks, s.factors, sag.SAG_CP) for s in systems]
     n0 = np.concatenate([s.n0 for s in systems])
-    pl = sag.Plan.batch(desc, prec=sag.SAG_FP32_SPLIT)
+    pl = sag.Plan.batch(desc, prec=sag.SAG_FP32_SPLIT, autotune=0 if args.no_autotune else 1)
+    groups = pl.describe()["blocks"]["fft_groups"]
     n = torch.tensor(n0, device="cuda")
     pl.integrate(n, dt, W)
     t_batch = max_over_ranks(time_integrate(pl, n, dt, K, world), world)
@@ -454,6 +461,7 @@ def run_batched(args, world, rank, local):
            "dtype": "f32x2", "data": "synthetic",
            "config": {"workload": "batched_power_cp: B=%d, N in [1024, 32768] log-uniform, D in {3,4}, "
                                   "CP ranks in [4, 32], a in [-0.5, 0.5], Heun dt=1e-4" % len(systems),
+                      "fft_stream_groups": groups,
                       "total_sizes": int(n0.size), "vectors": int(sum(sum(d * r for d, r in
                                                                        zip(range(2, s.D + 1), s.ranks))
                                                                    for s in systems))},

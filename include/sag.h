@@ -87,7 +87,13 @@ typedef struct {
                             0: the kernel's last mode holds k, exactly as printed.
                             The two coincide for symmetric kernels (Sec. 1 assumes
                             symmetric coefficients). */
-  int32_t reserved;
+  int32_t autotune;      /* 0 (default): fixed launch rules. 1: at plan time, time the
+                            candidate launch layouts of the FFT stage (1 to 4 stream
+                            groups of consecutive orders/systems, each a branch of the
+                            graph) on this plan's own sizes and keep the fastest: a few
+                            right-hand sides per candidate on an internal stream with a
+                            synthetic n, synchronising. The results do not depend on
+                            the choice. */
 } sag_options;
 
 /* Fills *opt with the defaults. */

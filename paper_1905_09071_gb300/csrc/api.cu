@@ -169,7 +169,7 @@ void sag_default_options(sag_options* opt) {
   opt->prec = SAG_FP32_SPLIT;
   opt->rk = SAG_HEUN;
   opt->symmetrize_q = 1;
-  opt->reserved = 0;
+  opt->autotune = 0;
 }
 
 const char* sag_last_error(void) { return g_err.c_str(); }
@@ -714,6 +714,7 @@ sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
   }
   js += "], \"orders_total\": " + std::to_string(pl->items.size()) + ", \"blocks\": {\"fwd_col\": " +
         std::to_string(pl->L.col_blocks) + ", \"rows\": " + std::to_string(pl->L.row_blocks) +
+        ", \"fft_groups\": " + std::to_string(pl->fft_groups) +
         ", \"inv_col\": " + std::to_string(pl->L.inv_blocks) + ", \"epilogue\": " +
         std::to_string(pl->L.epi_blocks) + "}, \"device_bytes\": " + std::to_string(pl->bytes) + "}";
   std::snprintf(buf, len, "%s", js.c_str());

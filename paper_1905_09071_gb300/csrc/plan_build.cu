@@ -536,27 +536,180 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       (e = cudaEventCreateWithFlags(&pl->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&pl->side.join, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(e, "stream");
-  // A few CP items (one system), double-word path: one FFT chain per item on
-  // its own stream, the heaviest (first in rowperm order) at the highest
-  // priority. (The FP64 kernels, bound by the FP64 pipe, gain nothing from
-  // the overlap and lose a little.)
-  if (!tt && dwp && P.nitems >= 2 && P.nitems <= kMaxFftGroups) {
-    int least = 0, greatest = 0;
-    if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess) return cuda_fail(e, "stream");
-    for (int p = 0; p < P.nitems; ++p) {
-      const int i = rowperm[p];
-      pl->groups.r[p] = FftRange{colpre[i], colpre[i + 1], rowpre[p], rowpre[p + 1], invpre[i], invpre[i + 1]};
-      const int prio = std::min(least, greatest + p);
-      SideStream& s = pl->groups.s[p];
+  // Stream groups of the FFT stage. Default: in the double-word path, a plan
+  // with 2 to 4 CP items (one system) runs one FFT chain per item on its own
+  // stream (the FP64 kernels, bound by the FP64 pipe, gain nothing from the
+  // overlap and lose a little); else one launch per kernel. With autotune the
+  // plan times 1..4 groups instead.
+  pl->h_colpre = colpre;
+  pl->h_invpre = invpre;
+  pl->h_nrowpair.resize(I.size());
+  pl->h_nvec.resize(I.size());
+  pl->h_work.resize(I.size());
+  for (size_t i = 0; i < I.size(); ++i) {
+    pl->h_nrowpair[i] = I[i].nrowpair;
+    pl->h_nvec[i] = I[i].nvec;
+    pl->h_work[i] = (double)I[i].nvec * (double)I[i].M;
+  }
+  sag_status st = configure_fft_groups(pl, (!tt && dwp && P.nitems <= kMaxFftGroups) ? P.nitems : 1);
+  if (st == SAG_OK && opt.autotune && !tt && P.nitems >= 2) st = autotune_fft_groups(pl);
+  if (st != SAG_OK) return st;
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "plan setup");
+  return SAG_OK;
+}
+
+// Splits the items into G groups of consecutive items (balanced by FFT
+// points; G = number of items: one item each), orders the row blocks group by
+// group (heaviest group first, heaviest items first within it), uploads that
+// order and sets the groups' block ranges and streams (heaviest group at the
+// highest priority). G = 1: one launch per kernel over every item.
+sag_status configure_fft_groups(sag_plan_s* pl, int G) {
+  RhsParams& P = pl->P;
+  const int n = P.nitems;
+  G = std::max(1, std::min(G, std::min(n, (int)kMaxFftGroups)));
+  std::vector<int> cut(G + 1, 0);
+  cut[G] = n;
+  if (G == n) {
+    for (int g = 0; g <= G; ++g) cut[g] = g;
+  } else if (G > 1) {
+    double total = 0.0;
+    for (double w : pl->h_work) total += w;
+    double acc = 0.0;
+    int g = 1;
+    for (int i = 0; i < n && g < G; ++i) {
+      acc += pl->h_work[i];
+      // cut after item i once its share is reached, leaving an item for each later group
+      if (acc >= total * g / G && n - (i + 1) >= G - g) cut[g++] = i + 1;
+    }
+    for (; g < G; ++g) cut[g] = n - (G - g);  // (only when the shares were not reached)
+  }
+  std::vector<int> chunk(G);
+  std::vector<double> cw(G, 0.0);
+  for (int g = 0; g < G; ++g) {
+    chunk[g] = g;
+    for (int i = cut[g]; i < cut[g + 1]; ++i) cw[g] += pl->h_work[i];
+  }
+  std::stable_sort(chunk.begin(), chunk.end(), [&](int a, int b) { return cw[a] > cw[b]; });
+  std::vector<int> rowperm, rowpre(1, 0), rstart(G + 1, 0);
+  for (int c = 0; c < G; ++c) {
+    const int g = chunk[c];
+    std::vector<int> items;
+    for (int i = cut[g]; i < cut[g + 1]; ++i) items.push_back(i);
+    std::stable_sort(items.begin(), items.end(), [&](int a, int b) { return pl->h_nvec[a] > pl->h_nvec[b]; });
+    for (int i : items) {
+      rowperm.push_back(i);
+      rowpre.push_back(rowpre.back() + pl->h_nrowpair[i]);
+    }
+    rstart[c + 1] = (int)rowperm.size();
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpy((void*)P.rowperm, rowperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy((void*)P.rowpre, rowpre.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+    return cuda_fail(e, "row block order");
+  pl->groups.n = 0;
+  pl->fft_groups = G;
+  if (G == 1) return SAG_OK;
+  int least = 0, greatest = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess) return cuda_fail(e, "stream");
+  for (int c = 0; c < G; ++c) {
+    const int g = chunk[c];
+    const int i0 = cut[g], i1 = cut[g + 1];
+    pl->groups.r[c] = FftRange{pl->h_colpre[i0], pl->h_colpre[i1], rowpre[rstart[c]], rowpre[rstart[c + 1]],
+                               pl->h_invpre[i0], pl->h_invpre[i1]};
+    SideStream& s = pl->groups.s[c];
+    if (!s.stream) {
+      const int prio = std::min(least, greatest + c);
       if ((e = cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio)) != cudaSuccess ||
           (e = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "stream");
       s.fork = nullptr;
-      pl->groups.n = p + 1;
     }
   }
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "plan setup");
+  pl->groups.n = G;
   return SAG_OK;
+}
+
+namespace {
+
+// Mean time of one RK2 step (the two stages that sag_integrate replays, with
+// dt = 0 so that the state in the staging buffer does not change), replayed
+// as a graph with the plan's current groups.
+sag_status time_step_graph(sag_plan_s* pl, float* ms) {
+  EpiArgs a{};
+  a.mode = pl->rk == SAG_HEUN ? EPI_HEUN1 : EPI_MID1;
+  a.nin = pl->stage_a;
+  a.out0 = pl->nstar;
+  a.k1buf = pl->k1buf;
+  a.part = pl->epi_part;
+  EpiArgs b{};
+  b.mode = pl->rk == SAG_HEUN ? EPI_HEUN2 : EPI_MID2;
+  b.nin = pl->nstar;
+  b.nbase = pl->stage_a;
+  b.k1buf = pl->k1buf;
+  b.part = pl->epi_part;
+  cudaStream_t cs = pl->cap_stream;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune capture");
+  cudaError_t el = enqueue_eval(pl->P, pl->L, pl->stage_a, a, cs, nullptr, &pl->side, &pl->groups);
+  if (el == cudaSuccess) el = enqueue_eval(pl->P, pl->L, pl->nstar, b, cs, nullptr, &pl->side, &pl->groups);
+  e = cudaStreamEndCapture(cs, &g);
+  if (el != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(el != cudaSuccess ? el : e, "autotune capture");
+  }
+  e = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune instantiate");
+  if ((e = cudaEventCreate(&e0)) == cudaSuccess && (e = cudaEventCreate(&e1)) == cudaSuccess) {
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaGraphLaunch(x, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+    for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = cudaGraphLaunch(x, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGraphExecDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+  *ms /= 10.0f;
+  return SAG_OK;
+}
+
+}  // namespace
+
+// Times 1..4 stream groups on this plan (synthetic n = e^{-k/10} per system),
+// three sweeps over the candidates, each candidate's best time counting, and
+// keeps the fewest groups within 1% of the fastest.
+sag_status autotune_fft_groups(sag_plan_s* pl) {
+  std::vector<double> h((size_t)pl->Ntot);
+  for (const SysDesc& sd : pl->systems) {
+    double s = 0.0;
+    for (int k = 1; k <= sd.N; ++k) s += std::exp(-k / 10.0);
+    for (int k = 1; k <= sd.N; ++k) h[sd.noff + k - 1] = std::exp(-k / 10.0) / s;
+  }
+  cudaError_t e = cudaMemcpy(pl->stage_a, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune input");
+  const int gmax = std::min(pl->P.nitems, (int)kMaxFftGroups);
+  float t[kMaxFftGroups + 1];
+  for (int G = 1; G <= gmax; ++G) t[G] = 1e30f;
+  for (int sweep = 0; sweep < 3; ++sweep)
+    for (int G = 1; G <= gmax; ++G) {
+      sag_status s = configure_fft_groups(pl, G);
+      float ms = 0.0f;
+      if (s == SAG_OK) s = time_step_graph(pl, &ms);
+      if (s != SAG_OK) return s;
+      t[G] = std::min(t[G], ms);
+    }
+  float fastest = t[1];
+  for (int G = 2; G <= gmax; ++G) fastest = std::min(fastest, t[G]);
+  int best_g = 1;
+  while (t[best_g] > 1.01f * fastest) ++best_g;
+  return configure_fft_groups(pl, best_g);
 }
 
 }  // namespace sag

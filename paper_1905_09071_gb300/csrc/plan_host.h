@@ -56,6 +56,11 @@ struct sag_plan_s {
   cudaStream_t cap_stream = nullptr;
   sag::SideStream side{nullptr, nullptr, nullptr};
   sag::FftGroups groups{};
+  int fft_groups = 1;                     // stream groups of the FFT stage (1: one launch per kernel)
+  std::vector<int> h_colpre, h_invpre;    // host copies of the block tables, for regrouping
+  std::vector<int> h_nrowpair;
+  std::vector<double> h_work;             // FFT points per item, for balancing groups
+  std::vector<int> h_nvec;                // vectors per item (row blocks go heaviest first)
   bool prof = false;
   sag::EventHook hook;
   // Instantiated graphs of sag_rhs / sag_rk2_step calls, keyed by the call's
@@ -95,7 +100,7 @@ struct sag_plan_s {
     if (side.stream) cudaStreamDestroy(side.stream);
     if (side.fork) cudaEventDestroy(side.fork);
     if (side.join) cudaEventDestroy(side.join);
-    for (int g = 0; g < groups.n; ++g) {
+    for (int g = 0; g < sag::kMaxFftGroups; ++g) {
       if (groups.s[g].stream) cudaStreamDestroy(groups.s[g].stream);
       if (groups.s[g].join) cudaEventDestroy(groups.s[g].join);
     }
@@ -110,4 +115,8 @@ namespace sag {
 sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options& opt);
 sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, sag_plan_s* pl);
 sag_status update_factors(sag_plan_s* pl, const double* factors, int on_device);
+// Stream groups of the FFT stage (1..4; 1 = one launch per kernel) and the
+// plan-time search over them.
+sag_status configure_fft_groups(sag_plan_s* pl, int G);
+sag_status autotune_fft_groups(sag_plan_s* pl);
 }  // namespace sag

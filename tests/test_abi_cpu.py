@@ -37,7 +37,7 @@ def test_library_exports_every_declared_function(lib):
 def test_version_and_defaults(lib):
     assert b"sm_103a" in lib.sag_version()
     assert sag.default_options() == {"prec": sag.SAG_FP32_SPLIT, "rk": sag.SAG_HEUN,
-                                     "symmetrize_q": 1}
+                                     "symmetrize_q": 1, "autotune": 0}
 
 
 def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=True, out=True):

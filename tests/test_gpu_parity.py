@@ -318,3 +318,24 @@ def test_plans_with_different_footprints_coexist():
                 pl.rhs(n, out)
                 torch.cuda.synchronize()
                 assert pl.sync_status() == sag.SAG_OK
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_autotuned_plan_gives_the_same_results(prec):
+    # The autotuner only changes how the FFT stage is split into launches and
+    # streams: right-hand side and trajectory are bitwise the same.
+    import torch
+    s = wl.random_cp(4, 5000, [4, 3, 2], seed=61)
+    outs = []
+    for autotune in (0, 1):
+        with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, autotune=autotune) as pl:
+            assert 1 <= pl.describe()["blocks"]["fft_groups"] <= 3
+            n = dev(s.n0)
+            out = torch.empty_like(n)
+            pl.rhs(n, out)
+            pl.integrate(n, 1e-3, 3)
+            torch.cuda.synchronize()
+            outs.append((out.cpu().numpy(), n.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])

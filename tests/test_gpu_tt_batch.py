@@ -166,6 +166,23 @@ def test_batched_equals_one_plan_per_system():
             assert np.array_equal(out[off[b]:off[b + 1]], y.cpu().numpy()), b
 
 
+def test_autotuned_batch_gives_the_same_results():
+    systems = mixed_batch()
+    res = []
+    for autotune in (0, 1):
+        with sag.Plan.batch([(s.N, s.D, s.ranks, s.factors, FMT[s.fmt]) for s in systems],
+                            autotune=autotune) as pl:
+            assert 1 <= pl.describe()["blocks"]["fft_groups"] <= 4
+            n = dev(packed(systems))
+            out = torch.empty_like(n)
+            pl.rhs(n, out)
+            pl.integrate(n, 1e-3, 2)
+            torch.cuda.synchronize()
+            res.append((out.cpu().numpy(), n.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_batched_integrate_diagnostics_layout(prec):
     systems = [wl.constant_monodisperse(3, 64), wl.random_cp(3, 50, [2, 2], seed=46),
