@@ -57,8 +57,10 @@ def parse():
                          "prints the per-kernel table to stderr, no JSON line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plans with the fixed launch rules instead of the plan-time autotuner")
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "batched"],
-                    help="batched: 256 independent systems in one plan vs a loop of plans")
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "batched", "paper"],
+                    help="batched: 256 independent systems in one plan vs a loop of plans; "
+                         "paper: the shape of the paper's experiment (pure ternary Brownian "
+                         "kernel, N = 2^19, TT and CP forms, 100 RK2 steps)")
     ap.add_argument("--systems", type=int, default=256)
     return ap.parse_args()
 
@@ -471,6 +473,53 @@ def run_batched(args, world, rank, local):
     print(json.dumps(out), flush=True)
 
 
+def run_paper(args, world, rank, local):
+    """The paper's own experiment shape (Sec. 3, Table 1): pure ternary
+    aggregation, 3-D generalized Brownian kernel, N = 2^19, 100 RK2 steps, in
+    TT form (ranks 1, 3, 3, 1) and CP form (rank 6), both precisions."""
+    import torch
+    from paper_1905_09071_gb300 import sag, workloads as wl
+    torch.cuda.set_device(local)
+    N = 1 << 19
+    K, W = 100, max(args.warmup, 1)
+    tune = 0 if args.no_autotune else 1
+    res = {}
+    rhs_at_n0 = {}
+    for fmt in ("tt", "cp"):
+        s = wl.paper_ternary(N, fmt)
+        for pname, prec in (("fp32_split", sag.SAG_FP32_SPLIT), ("fp64", sag.SAG_FP64)):
+            pl = sag.Plan(s.N, s.D, s.ranks, s.factors, fmt=sag.SAG_TT if fmt == "tt" else sag.SAG_CP,
+                          prec=prec, autotune=tune)
+            n = torch.tensor(s.n0, device="cuda")
+            out = torch.empty_like(n)
+            pl.rhs(n, out)
+            rhs_at_n0[(fmt, pname)] = out.cpu().numpy()
+            pl.integrate(n, s.dt, W)
+            t = max_over_ranks(time_integrate(pl, n, s.dt, K, world), world)
+            assert pl.sync_status() == sag.SAG_OK
+            err = parity_error(pl, s) if (fmt == "cp" and rank == 0) else None
+            res[(fmt, pname)] = {"seconds_for_100_steps": t, "steps_per_s": K * world / t,
+                                 "error_vs_oracle": err}
+            pl.close()
+    if rank != 0:
+        return
+    ref = rhs_at_n0[("cp", "fp64")]
+    scale = np.abs(ref).max()
+    tt_vs_cp = {p: float(np.abs(rhs_at_n0[("tt", p)] - ref).max() / scale) for p in ("fp32_split", "fp64")}
+    out = {"metric": "paper-shape RK2 steps/s (pure ternary Brownian kernel, N=2^19, 100 steps)",
+           "value": res[("tt", "fp32_split")]["steps_per_s"], "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": W, "higher_is_better": True, "scaling": "weak", "data": "synthetic",
+           "config": {"workload": "paper_ternary: D=3 (d=3 term only), N=2^19, mu=(1/3,-1/3,0), "
+                                  "n_k ~ exp(-k/10), Heun dt=1e-3 (the paper states none of mu, the "
+                                  "start or the step)"},
+           "runs": {f"{f}_{p}": v for (f, p), v in res.items()},
+           "tt_vs_cp_rhs_at_n0": tt_vs_cp,
+           "context": {"paper_table1_128_cores_seconds": 12.22, "paper_table1_1_core_seconds": 257.80,
+                       "note": "Table 1: the same kernel family and N on CPU cores (MKL ClusterFFT, "
+                               "MPI), mu and precision not stated"}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -480,6 +529,8 @@ def main():
     world, rank, local = dist_setup(args)
     if args.workload == "batched":
         run_batched(args, world, rank, local)
+    elif args.workload == "paper":
+        run_paper(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -106,6 +106,8 @@ void sag_default_options(sag_options* opt);
  * core vectors that are identically zero are skipped) and allocates the
  * workspace. Every kernel of an evaluation then covers all B systems in one
  * launch. Limits: N <= 2^22, d N <= 2^24, CP ranks <= 4096, TT ranks <= 16.
+ * A CP rank of 0 leaves that order out (for example a purely ternary system:
+ * D = 3 with R_2 = 0); every system needs one order of rank >= 1.
  * opt may be NULL (defaults). On success *out holds the plan. */
 sag_status sag_plan(const sag_system* sys, int32_t B, const sag_options* opt, sag_plan_t* out);
 

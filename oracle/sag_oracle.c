@@ -52,8 +52,9 @@ static double factorial(int d) {
 static int ranks_ok(int fmt, int D, int N, const int* ranks) {
   if (D < 2 || D > ORC_MAXD || N < 1 || !ranks) return 0;
   if (fmt == ORC_CP) {
+    /* rank 0: the order is absent (its sums over r are empty) */
     for (int d = 2; d <= D; ++d)
-      if (ranks[d - 2] < 1) return 0;
+      if (ranks[d - 2] < 0) return 0;
     return 1;
   }
   if (fmt == ORC_TT) {

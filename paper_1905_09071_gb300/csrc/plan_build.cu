@@ -147,17 +147,21 @@ sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options&
     if (s.fmt != SAG_CP && s.fmt != SAG_TT) return fail(SAG_EINVAL, "unknown format" + at);
     if (s.fmt != sys[0].fmt) return fail(SAG_EUNSUPPORTED, "all systems of a plan must share one format" + at);
     const int32_t* rk = s.rank;
+    int present = 0;
     for (int d = 2; d <= s.D; ++d) {
       if (s.fmt == SAG_CP) {
-        if (rk[0] < 1 || rk[0] > 4096) return fail(SAG_EINVAL, "CP rank out of [1, 4096]" + at);
+        if (rk[0] < 0 || rk[0] > 4096) return fail(SAG_EINVAL, "CP rank out of [0, 4096]" + at);
+        present += rk[0] > 0;
         rk += 1;
       } else {
         if (rk[0] != 1 || rk[d] != 1) return fail(SAG_EINVAL, "TT ranks must start and end with 1" + at);
         for (int l = 1; l < d; ++l)
           if (rk[l] < 1 || rk[l] > kMaxTTRank) return fail(SAG_EINVAL, "TT rank out of [1, 16]" + at);
+        present += 1;
         rk += d + 1;
       }
     }
+    if (present == 0) return fail(SAG_EINVAL, "every CP rank is 0: the system has no kernel" + at);
     if (factor_count(s) > ((int64_t)1 << 34)) return fail(SAG_EINVAL, "factor array too large" + at);
   }
   return SAG_OK;
@@ -216,6 +220,10 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     const int32_t* rk = s.rank;
     int64_t soff = 0;  // offset in the caller's factor array
     for (int d = 2; d <= s.D; ++d) {
+      if (s.fmt == SAG_CP && rk[0] == 0) {  // rank 0: the order is absent
+        rk += 1;
+        continue;
+      }
       OrderDesc od{};
       od.sys = b;
       od.d = d;

@@ -187,6 +187,28 @@ def brownian_tt(D: int, N: int, mu, n0=None, decay: float = 10.0) -> System:
                   meta={"mu": list(mu)})
 
 
+def paper_ternary(N: int = 1 << 19, fmt: str = "tt", mu=(1 / 3, -1 / 3, 0.0), decay: float = 10.0,
+                  dt: float = 1e-3) -> System:
+    """The shape of the paper's own experiment (Sec. 3): pure ternary
+    aggregation (only the d = 3 term) with the 3-D generalized Brownian kernel
+    of Eq. ch3.eq17, C(i, j, l) = sum over permutations s of (i^mu_s1 j^mu_s2
+    l^mu_s3). The paper does not state mu, the start or the step; these
+    defaults are ours. fmt "tt": the Theorem-1 cores (ranks 1, 3, 3, 1) and an
+    all-zero d = 2 order (ranks 1, 1, 1); fmt "cp": rank 0 for d = 2 and one
+    rank-one term per permutation (rank 6) for d = 3."""
+    i = sizes(N)
+    n0 = normalised(np.exp(-i / decay))
+    if fmt == "tt":
+        r3, c3 = brownian_tt_cores(list(mu), N)
+        return System(3, N, "tt", [1, 1, 1] + r3, np.concatenate([np.zeros(2 * N), c3]), n0, dt=dt,
+                      name=f"paper_ternary_tt_N{N}", meta={"mu": list(mu)})
+    import itertools
+    perms = list(itertools.permutations(range(3)))
+    U = np.stack([np.stack([i ** mu[p[m]] for p in perms]) for m in range(3)])  # [3][6][N]
+    ranks, f = cp_from_vectors(3, N, {2: np.zeros((2, 0, N)), 3: U})
+    return System(3, N, "cp", [0, 6], f, n0, dt=dt, name=f"paper_ternary_cp_N{N}", meta={"mu": list(mu)})
+
+
 def random_tt(D: int, N: int, ranks_per_order: dict, seed: int, lo: float = 0.2,
               hi: float = 1.0) -> System:
     """Dense positive TT cores: ranks_per_order[d] = [1, R_1, ..., R_{d-1}, 1]."""

@@ -56,7 +56,8 @@ def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=
     (dict(N=0), sag.SAG_EINVAL),
     (dict(D=1, ranks=()), sag.SAG_EINVAL),
     (dict(D=9, ranks=(1,) * 7), sag.SAG_EINVAL),
-    (dict(ranks=(2, 0)), sag.SAG_EINVAL),
+    (dict(ranks=(2, -1)), sag.SAG_EINVAL),
+    (dict(ranks=(0, 0)), sag.SAG_EINVAL),  # rank 0 leaves an order out, but one must remain
     (dict(fmt=7), sag.SAG_EINVAL),
     (dict(B=0), sag.SAG_EINVAL),
     (dict(factors=False), sag.SAG_EINVAL),

@@ -339,3 +339,27 @@ def test_autotuned_plan_gives_the_same_results(prec):
             outs.append((out.cpu().numpy(), n.cpu().numpy()))
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("make", [
+    lambda: wl.paper_ternary(300, "cp"),
+    lambda: wl.paper_ternary(300, "tt"),
+    lambda: wl.random_cp(4, 257, [2, 0, 1], seed=62),
+], ids=["ternary_cp", "ternary_tt", "D4_no_d3"])
+def test_absent_orders(make, prec):
+    # Orders left out (CP rank 0, or an all-zero TT order) contribute nothing.
+    import torch
+    s = make()
+    fmt = sag.SAG_TT if s.fmt == "tt" else sag.SAG_CP
+    ofmt = oracle.TT if s.fmt == "tt" else oracle.CP
+    p_ref, q_ref = oracle.rhs(s.n0, s.D, s.ranks, s.factors, mode=oracle.DIRECT, fmt=ofmt)
+    scale = np.abs(p_ref).max() + np.abs(q_ref).max()
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, fmt=fmt, prec=prec) as pl:
+        n = dev(s.n0)
+        p, q = torch.empty_like(n), torch.empty_like(n)
+        pl.rhs_parts(n, p, q)
+        torch.cuda.synchronize()
+    assert nerr(p.cpu().numpy(), p_ref, scale) < TOL[prec]
+    assert nerr(q.cpu().numpy(), q_ref, scale) < TOL[prec]

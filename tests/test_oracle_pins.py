@@ -374,3 +374,24 @@ def test_integrate_vjp_matches_central_differences(method):
     d_f = (L(s.n0, s.factors + h * uf) - L(s.n0, s.factors - h * uf)) / (2 * h)
     assert abs(d_n - gn0 @ un) < 1e-7 * abs(d_n)
     assert abs(d_f - gU @ uf) < 1e-7 * abs(d_f)
+
+
+def test_paper_ternary_forms_agree():
+    # Pure ternary Brownian kernel (only the d = 3 term; the d = 2 order is
+    # absent: CP rank 0, or an all-zero TT order): brute force over the kernel
+    # entries of both forms, and the direct modes, agree.
+    s = wl.paper_ternary(40, "cp")
+    t = wl.paper_ternary(40, "tt")
+    pb, qb = oracle.rhs(s.n0, s.D, s.ranks, s.factors, mode=oracle.BRUTE)
+    scale = np.abs(pb).max() + np.abs(qb).max()
+    for sysm, fmt in ((s, oracle.CP), (t, oracle.TT)):
+        for mode in (oracle.BRUTE, oracle.DIRECT):
+            p, q = oracle.rhs(sysm.n0, sysm.D, sysm.ranks, sysm.factors, mode=mode, fmt=fmt)
+            assert np.abs(p - pb).max() / scale < 1e-14
+            assert np.abs(q - qb).max() / scale < 1e-14
+    # the d = 2 order contributes nothing: a D = 3 system whose d = 2 factors
+    # are zero gives the same right-hand side
+    z = wl.cp_from_vectors(3, 40, {2: np.zeros((2, 1, 40)),
+                                  3: s.factors.reshape(3, 6, 40)})
+    p, q = oracle.rhs(s.n0, 3, z[0], z[1], mode=oracle.DIRECT)
+    assert np.abs(p - pb).max() / scale < 1e-14 and np.abs(q - qb).max() / scale < 1e-14
