@@ -639,7 +639,7 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
       break;
     case KID_FWD_COL:
       for (const OrderDesc& od : pl->items)
-        o += (double)od.nvec * (od.M2 * fft_ops(od.M1, od.rp1, c) + (double)od.M * c.cmul +
+        o += (double)od.nu * (od.M2 * fft_ops(od.M1, od.rp1, c) + (double)od.M * c.cmul +
                                 2.0 * std::min<double>(od.M, od.N) * load_mul);
       b = 8.0 * factor_elems + 8.0 * Nt;
       break;
@@ -706,7 +706,8 @@ sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
   for (size_t i = 0; i < shown; ++i) {
     const OrderDesc& od = pl->items[i];
     js += std::string(i ? ", " : "") + "{\"sys\": " + std::to_string(od.sys) + ", \"d\": " +
-          std::to_string(od.d) + ", \"vectors\": " + std::to_string(od.nvec) + ", \"L\": " +
+          std::to_string(od.d) + ", \"vectors\": " + std::to_string(od.nvec) +
+          ", \"transformed\": " + std::to_string(od.nu) + ", \"L\": " +
           std::to_string(od.L) + ", \"M1\": " + std::to_string(od.M1) + ", \"M2\": " +
           std::to_string(od.M2) + ", \"radix_M1\": " + rps(od.rp1) + ", \"radix_M2\": " + rps(od.rp2) +
           ", \"W\": " + std::to_string(od.W) + ", \"G\": " + std::to_string(od.G) +

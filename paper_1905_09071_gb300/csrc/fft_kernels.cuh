@@ -59,6 +59,11 @@ __device__ __forceinline__ cdw rank_weight(cdw x, const OrderDesc& od, int r) {
   return c_scale2(x, od.rscale[r]);
 }
 
+// Spectrum slot of CP vector m R + r of an order (duplicates share one).
+__device__ __forceinline__ int cp_slot(const RhsParams& P, const OrderDesc& od, int q) {
+  return od.umap_off < 0 ? q : P.umap[od.umap_off + q];
+}
+
 // Twice the spectrum of a real sequence from its half-length packed transform:
 // 2 A[k] = (Z[k] + conj Z[M-k]) - i omega_L^k (Z[k] - conj Z[M-k]).
 template <class C>
@@ -81,17 +86,18 @@ __device__ __forceinline__ void mirror_of(int k1, int row, int pos, int M1, int 
 }
 
 // ---------------------------------------------------------------------------
-// Forward column pass of one block: vector vloc of order od, column block cb.
-// P1 > 0: compile-time length, in place; P1 == 0: runtime length, ping-pong.
+// Forward column pass of one block: the order's vector lv (local index) into
+// spectrum slot `slot`, column block cb. P1 > 0: compile-time length, in
+// place; P1 == 0: runtime length, ping-pong.
 template <class C, int P1>
-__device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc& od, int vloc,
+__device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc& od, int slot, int lv,
                                              int cb, const double* __restrict__ n, C* buf) {
   constexpr bool CT = P1 > 0;
   const int M1 = CT ? P1 : od.M1;
   const int W = CT ? ct_cols(P1) : od.W;
   const int ld = CT ? ct_ld(P1, ct_cols(P1)) : od.ld1;
   const int M2 = od.M2;
-  const int v = od.vbase + vloc;
+  const int v = od.vbase + lv;
   C* buf1 = buf + W * ld;
   C* tw = CT ? buf + W * ld : buf1 + W * ld;
   const C* tw1 = static_cast<const C*>(od.tw1);
@@ -114,7 +120,7 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   } else {
     res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
   }
-  C* dst = static_cast<C*>(P.scratch) + od.scr_off + (int64_t)vloc * od.M;
+  C* dst = static_cast<C*>(P.scratch) + od.scr_off + (int64_t)slot * od.M;
   if constexpr (CT) {
     // four-step twiddles of this column block, stored in the loop's order
     const C* tw4c = static_cast<const C*>(od.tw4c) + (int64_t)cb * W * M1;
@@ -131,30 +137,34 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   }
 }
 
+// all = 0: each order's distinct vectors (colpre; duplicates share a slot);
+// all = 1: every vector into its own slot (colpre_all; the adjoint).
 template <class C>
 __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__ RhsParams P,
-                                                      const double* __restrict__ n, int base) {
+                                                      const double* __restrict__ n, int base, int all) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int bid = base + blockIdx.x;  // launches may cover a range of the colpre table
-  const int it = find_segment(P.colpre, P.nitems, bid);
+  const int* pre = all ? P.colpre_all : P.colpre;
+  const int bid = base + blockIdx.x;  // launches may cover a range of the table
+  const int it = find_segment(pre, P.nitems, bid);
   const OrderDesc& od = P.ord[it];
-  const int local = bid - P.colpre[it];
+  const int local = bid - pre[it];
   const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
+  const int lv = (all || od.umap_off < 0) ? vloc : P.ulist[od.umap_off + vloc];
   if constexpr (!std::is_same<C, cdw>::value) {
-    fwd_col_body<C, 0>(P, od, vloc, cb, n, buf);
+    fwd_col_body<C, 0>(P, od, vloc, lv, cb, n, buf);
     return;
   }
   switch (od.ct1 ? od.M1 : 0) {
-    case 64: fwd_col_body<C, 64>(P, od, vloc, cb, n, buf); break;
-    case 96: fwd_col_body<C, 96>(P, od, vloc, cb, n, buf); break;
-    case 128: fwd_col_body<C, 128>(P, od, vloc, cb, n, buf); break;
-    case 192: fwd_col_body<C, 192>(P, od, vloc, cb, n, buf); break;
-    case 256: fwd_col_body<C, 256>(P, od, vloc, cb, n, buf); break;
-    case 384: fwd_col_body<C, 384>(P, od, vloc, cb, n, buf); break;
-    case 512: fwd_col_body<C, 512>(P, od, vloc, cb, n, buf); break;
-    case 768: fwd_col_body<C, 768>(P, od, vloc, cb, n, buf); break;
-    default: fwd_col_body<C, 0>(P, od, vloc, cb, n, buf); break;
+    case 64: fwd_col_body<C, 64>(P, od, vloc, lv, cb, n, buf); break;
+    case 96: fwd_col_body<C, 96>(P, od, vloc, lv, cb, n, buf); break;
+    case 128: fwd_col_body<C, 128>(P, od, vloc, lv, cb, n, buf); break;
+    case 192: fwd_col_body<C, 192>(P, od, vloc, lv, cb, n, buf); break;
+    case 256: fwd_col_body<C, 256>(P, od, vloc, lv, cb, n, buf); break;
+    case 384: fwd_col_body<C, 384>(P, od, vloc, lv, cb, n, buf); break;
+    case 512: fwd_col_body<C, 512>(P, od, vloc, lv, cb, n, buf); break;
+    case 768: fwd_col_body<C, 768>(P, od, vloc, lv, cb, n, buf); break;
+    default: fwd_col_body<C, 0>(P, od, vloc, lv, cb, n, buf); break;
   }
 }
 
@@ -200,7 +210,7 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
       const int row = p / M2, pos = p - row * M2;
       const int q = q0 + g, r = q / d, m = q - r * d;
       const int k1 = row ? k1b : k1a;
-      buf[(g * slot_stride + row) * ld + pos] = src[(int64_t)(m * R + r) * M + (int64_t)k1 * M2 + pos];
+      buf[(g * slot_stride + row) * ld + pos] = src[(int64_t)cp_slot(P, od, m * R + r) * M + (int64_t)k1 * M2 + pos];
     }
     __syncthreads();
     C* res = fft_batch(buf, buf1, M2, ld, gc * nrow, od.rp2, tw);
@@ -307,7 +317,7 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
       const int q = q0 + g, r = q / d, m = q - r * d;
       for (int row = 0; row < nrow; ++row) {
         const int k1 = row ? k1b : k1a;
-        bulk_copy_g2s(stage + (2 * g + row) * P2, src + (int64_t)(m * R + r) * M + (int64_t)k1 * P2,
+        bulk_copy_g2s(stage + (2 * g + row) * P2, src + (int64_t)cp_slot(P, od, m * R + r) * M + (int64_t)k1 * P2,
                       (uint32_t)(P2 * sizeof(C)), bar);
       }
     }

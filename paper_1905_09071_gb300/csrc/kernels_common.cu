@@ -171,6 +171,9 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
         right[l - 1][a] = acc;
       }
     }
+    // Core entries that share a vector (bitwise-identical entries of one
+    // core) add their weights; this thread owns the order's vectors.
+    for (int v = od.vbase; v < od.vbase + od.nvec; ++v) P.coef[v] = 0.0;
     for (int l = 1; l <= d; ++l) {
       const int ra = od.ttr[l - 1], rb = od.ttr[l];
       const double wl = P.sym ? 1.0 / d : (l == d ? 1.0 : 0.0);
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
           const int w = vid[offs[l] + a * rb + bb];
           if (w < 0) continue;
           const double lr = left[l - 1][a] * right[l][bb];
-          P.coef[w] = -inv_factorial(d - 1) * wl * lr;
+          P.coef[w] += -inv_factorial(d - 1) * wl * lr;
           g[0] += t[w - sy.vbeg] * lr * inv_factorial(d);
         }
     }

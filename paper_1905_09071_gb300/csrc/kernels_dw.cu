@@ -5,7 +5,7 @@
 namespace sag {
 
 cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                                int base, int blocks);
+                                int base, int blocks, int all);
 cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, int base, int blocks);
 cudaError_t launch_k_inv_col_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, int base, int blocks);
 cudaError_t launch_tt_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, LaunchHook* hook);
@@ -19,7 +19,7 @@ cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double*
   const FftRange all{0, L.col_blocks, 0, L.row_blocks, 0, L.inv_blocks};
   const FftRange& R = r ? *r : all;
   if (hook) hook->mark(KID_FWD_COL, st);
-  cudaError_t e = launch_k_fwd_col_dw(P, L, nin, st, R.col0, R.col1 - R.col0);
+  cudaError_t e = launch_k_fwd_col_dw(P, L, nin, st, R.col0, R.col1 - R.col0, 0);
   if (e != cudaSuccess) return e;
   if (L.has_tt) {
     if ((e = launch_tt_dw(P, L, st, hook)) != cudaSuccess) return e;  // every item (no groups with TT)

@@ -6,8 +6,8 @@
 namespace sag {
 
 cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                                int base, int blocks) {
-  if (blocks > 0) k_fwd_col<cdw><<<blocks, kThreads, L.col_smem, st>>>(P, nin, base);
+                                int base, int blocks, int all) {
+  if (blocks > 0) k_fwd_col<cdw><<<blocks, kThreads, L.col_smem, st>>>(P, nin, base, all);
   return cudaGetLastError();
 }
 

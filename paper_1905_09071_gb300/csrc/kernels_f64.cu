@@ -8,7 +8,7 @@ cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double
   const FftRange all{0, L.col_blocks, 0, L.row_blocks, 0, L.inv_blocks};
   const FftRange& R = r ? *r : all;
   if (hook) hook->mark(KID_FWD_COL, st);
-  if (R.col1 > R.col0) k_fwd_col<cd><<<R.col1 - R.col0, kThreads, L.col_smem, st>>>(P, nin, R.col0);
+  if (R.col1 > R.col0) k_fwd_col<cd><<<R.col1 - R.col0, kThreads, L.col_smem, st>>>(P, nin, R.col0, 0);
   if (L.has_tt) {
     cudaError_t e = launch_tt_stage<cd>(P, L, st, hook);  // every item (no groups with TT)
     if (e != cudaSuccess) return e;
@@ -22,7 +22,7 @@ cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double
 }
 
 cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
-  k_fwd_col<cd><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, nin, 0);
+  k_fwd_col<cd><<<L.col_blocks_all, kThreads, L.col_smem, st>>>(P, nin, 0, 1);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ cudaError_t launch_vjp_fft_f64(const RhsParams& P, const LaunchCfg& L, const dou
   if (e != cudaSuccess) return e;
   k_gcol<cd><<<L.inv_blocks, kThreads, L.vcol_smem, st>>>(P, g);
   k_rows_vjp<cd><<<L.row_blocks, kThreads, L.vrow_smem, st>>>(P);
-  k_inv_col_vjp<cd><<<L.col_blocks, kThreads, L.vcol_smem, st>>>(P);
+  k_inv_col_vjp<cd><<<L.col_blocks_all, kThreads, L.vcol_smem, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@ namespace sag {
 struct LaunchCfg {
   int prep_blocks;
   int col_blocks, row_blocks, inv_blocks, epi_blocks;
+  int col_blocks_all;  // column blocks over every vector (the adjoint's passes)
   int chain_blocks;
   int has_tt;           // the plan's systems use TT kernels (one format per plan)
   size_t col_smem, row_smem, inv_smem, epi_smem, coef_smem, rowtt_smem;

@@ -35,6 +35,9 @@ struct OrderDesc {
   int W;               // columns per block in the column kernels
   int ld1, ld2;        // shared-memory leading dimensions (M1 + 1, M2 + 1)
   int ncolblk;         // M2 / W
+  int nu;              // vectors the forward pass transforms: CP, its distinct vectors
+                       // (bitwise); TT, every stored vector (duplicates share one already)
+  int umap_off;        // CP with duplicates: offset of its maps in RhsParams::umap/ulist; -1: none
   int nrowpair;        // floor(M1 / 2) + 1 row pairs {k1, M1 - k1}
   int G;               // vectors per chunk in the row kernel
   int ct1, ct2;        // 1: the column (M1) / row (M2) transforms use the compile-time kernels
@@ -100,7 +103,10 @@ struct RhsParams {
   int maxdotchunk;               // most chunks of any vector
   const OrderDesc* ord;          // [nitems]
   const SysDesc* sys;            // [B]
-  const int* colpre;             // [nitems + 1] forward/inverse column kernel blocks
+  const int* colpre;             // [nitems + 1] forward column kernel blocks (nu per item)
+  const int* colpre_all;         // [nitems + 1] column blocks over every vector (nvec per item; the adjoint)
+  const int* umap;               // CP items with duplicates: spectrum slot of vector m R + r (d R entries)
+  const int* ulist;              // the same items: vector (m R + r) transformed into slot u (nu entries)
   const int* rowpre;             // [nitems + 1] row kernel blocks, in rowperm order
   const int* invpre;             // [nitems + 1] inverse column kernel blocks
   const int* chainpre;           // [nitems + 1] TT chain kernel blocks

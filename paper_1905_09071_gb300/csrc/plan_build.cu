@@ -189,6 +189,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   std::vector<int64_t> vdwoff;     // offset of each vector in the double-word copy
   std::vector<int> vsys;           // system of each vector
   std::vector<int> vid;            // TT tables
+  std::vector<int> umap, ulist;    // CP duplicate maps
   std::vector<SysDesc>& S = pl->systems;
   std::vector<OrderDesc>& I = pl->items;
   S.resize(B);
@@ -244,6 +245,36 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
         od.R = rk[0];
         od.nvec = d * od.R;
         for (int v = 0; v < od.nvec; ++v) push_vector(src.data() + soff + (int64_t)v * N);
+        // Bitwise-identical vectors of the order are transformed once: slot
+        // umap[v] holds the spectrum of vector ulist[umap[v]].
+        std::vector<int> um(od.nvec), ul;
+        std::map<uint64_t, std::vector<int>> seen;
+        for (int v = 0; v < od.nvec; ++v) {
+          const double* x = src.data() + soff + (int64_t)v * N;
+          uint64_t h = 1469598103934665603ull;  // FNV-1a over the bytes
+          const unsigned char* bytes = reinterpret_cast<const unsigned char*>(x);
+          for (size_t k = 0; k < (size_t)N * sizeof(double); ++k) h = (h ^ bytes[k]) * 1099511628211ull;
+          int found = -1;
+          for (int u : seen[h])
+            if (std::memcmp(x, src.data() + soff + (int64_t)ul[u] * N, (size_t)N * sizeof(double)) == 0) {
+              found = u;
+              break;
+            }
+          if (found < 0) {
+            found = (int)ul.size();
+            ul.push_back(v);
+            seen[h].push_back(found);
+          }
+          um[v] = found;
+        }
+        od.nu = (int)ul.size();
+        od.umap_off = -1;
+        if (od.nu < od.nvec) {
+          od.umap_off = (int)umap.size();
+          umap.insert(umap.end(), um.begin(), um.end());
+          ulist.insert(ulist.end(), ul.begin(), ul.end());
+          ulist.resize(umap.size(), 0);  // both tables indexed from umap_off
+        }
         soff += (int64_t)od.nvec * N;
         rk += 1;
       } else {
@@ -251,17 +282,32 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
         for (int l = 0; l <= d; ++l) od.ttr[l] = rk[l];
         od.vid_off = (int)vid.size();
         int cnt = 0;
-        for (int l = 1; l <= d; ++l)
+        for (int l = 1; l <= d; ++l) {
+          // within one core, bitwise-identical vectors share one id (their
+          // power-of-two weight depends on the core only)
+          std::vector<std::pair<const double*, int>> core;
           for (int a = 0; a < rk[l - 1]; ++a)
             for (int c = 0; c < rk[l]; ++c) {
               const double* x = src.data() + soff;
               soff += N;
               bool nz = false;
               for (int k = 0; k < N && !nz; ++k) nz = x[k] != 0.0;
-              vid.push_back(nz ? push_vector(x) : -1);
-              cnt += nz ? 1 : 0;
+              int id = -1;
+              if (nz) {
+                for (const auto& pc : core)
+                  if (std::memcmp(x, pc.first, (size_t)N * sizeof(double)) == 0) id = pc.second;
+                if (id < 0) {
+                  id = push_vector(x);
+                  core.push_back({x, id});
+                  ++cnt;
+                }
+              }
+              vid.push_back(id);
             }
+        }
         od.nvec = cnt;
+        od.nu = cnt;
+        od.umap_off = -1;
         rk += d + 1;
         for (int l = 0; l <= d; ++l) P.tt_rmax = std::max(P.tt_rmax, od.ttr[l]);
       }
@@ -285,7 +331,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   // ---- FFT geometry of each item ------------------------------------------
   int64_t scr = 0, scr2 = 0, pdo = 0;
   size_t col_smem = 0, row_smem = 0, rowtt_smem = 0;
-  std::vector<int> colpre(1, 0), invpre(1, 0), chainpre(1, 0);
+  std::vector<int> colpre(1, 0), colpre_all(1, 0), invpre(1, 0), chainpre(1, 0);
   for (OrderDesc& od : I) {
     const int d = od.d;
     const int64_t L = choose_fft_length(std::max<int64_t>((int64_t)d * od.N, 16));
@@ -326,7 +372,8 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     scr2 += od.M;
     od.pd_off = pdo;
     pdo += od.N;
-    colpre.push_back(colpre.back() + od.nvec * od.ncolblk);
+    colpre.push_back(colpre.back() + od.nu * od.ncolblk);
+    colpre_all.push_back(colpre_all.back() + od.nvec * od.ncolblk);
     invpre.push_back(invpre.back() + od.ncolblk);
     chainpre.push_back(chainpre.back() + (tt ? (od.M + 1 + 255) / 256 : 0));
     // Compile-time kernels work in place (one buffer), the generic ones ping-pong.
@@ -371,6 +418,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   for (const SysDesc& sd : S) maxN = std::max(maxN, sd.N);
   L.prep_blocks = std::max(1, std::min(64, (maxN + 255) / 256));
   L.col_blocks = colpre.back();
+  L.col_blocks_all = colpre_all.back();
   L.row_blocks = rowpre.back();
   L.inv_blocks = invpre.back();
   L.chain_blocks = chainpre.back();
@@ -481,13 +529,16 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   P.scratch2 = scratch2;
   OrderDesc* d_ord = nullptr;
   SysDesc* d_sys = nullptr;
-  int *d_colpre = nullptr, *d_rowpre = nullptr, *d_invpre = nullptr, *d_chainpre = nullptr,
+  int *d_colpre = nullptr, *d_colpre_all = nullptr, *d_umap = nullptr, *d_ulist = nullptr,
+      *d_rowpre = nullptr, *d_invpre = nullptr, *d_chainpre = nullptr,
       *d_epipre = nullptr, *d_vsys = nullptr, *d_rowperm = nullptr, *d_vid = nullptr;
   int64_t* d_voff = nullptr;
   int64_t* d_vdwoff = nullptr;
   float* d_vw = nullptr;
   if (pl->upload(&d_ord, I) != cudaSuccess || pl->upload(&d_sys, S) != cudaSuccess ||
       pl->upload(&d_colpre, colpre) != cudaSuccess || pl->upload(&d_rowpre, rowpre) != cudaSuccess ||
+      pl->upload(&d_colpre_all, colpre_all) != cudaSuccess || pl->upload(&d_umap, umap) != cudaSuccess ||
+      pl->upload(&d_ulist, ulist) != cudaSuccess ||
       pl->upload(&d_invpre, invpre) != cudaSuccess || pl->upload(&d_chainpre, chainpre) != cudaSuccess ||
       pl->upload(&d_epipre, epipre) != cudaSuccess || pl->upload(&d_vsys, vsys) != cudaSuccess ||
       pl->upload(&d_rowperm, rowperm) != cudaSuccess || pl->upload(&d_vid, vid) != cudaSuccess ||
@@ -497,6 +548,9 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   P.ord = d_ord;
   P.sys = d_sys;
   P.colpre = d_colpre;
+  P.colpre_all = d_colpre_all;
+  P.umap = d_umap;
+  P.ulist = d_ulist;
   P.rowpre = d_rowpre;
   P.invpre = d_invpre;
   P.chainpre = d_chainpre;

@@ -187,9 +187,9 @@ template <class C>
 __global__ void __launch_bounds__(kThreads) k_inv_col_vjp(const __grid_constant__ RhsParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int it = find_segment(P.colpre, P.nitems, blockIdx.x);
+  const int it = find_segment(P.colpre_all, P.nitems, blockIdx.x);
   const OrderDesc& od = P.ord[it];
-  const int local = blockIdx.x - P.colpre[it];
+  const int local = blockIdx.x - P.colpre_all[it];
   const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
   const int v = od.vbase + vloc;
   const int W = od.W, M1 = od.M1, M2 = od.M2, ld = od.ld1, N = od.N;

@@ -363,3 +363,25 @@ def test_absent_orders(make, prec):
         torch.cuda.synchronize()
     assert nerr(p.cpu().numpy(), p_ref, scale) < TOL[prec]
     assert nerr(q.cpu().numpy(), q_ref, scale) < TOL[prec]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_duplicate_vectors_are_transformed_once(prec):
+    # The Brownian kernel's CP form repeats three functions (1, i^{1/3},
+    # i^{-1/3}) over its rank terms: the forward pass transforms each once per
+    # order, and the right-hand side still matches the oracle.
+    import torch
+    s = wl.brownian_cp(3, 1500)
+    p_ref, q_ref = oracle.rhs(s.n0, s.D, s.ranks, s.factors, mode=oracle.DIRECT)
+    scale = np.abs(p_ref).max() + np.abs(q_ref).max()
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec) as pl:
+        orders = pl.describe()["orders"]
+        assert [o["transformed"] for o in orders] == [3, 3]
+        assert [o["vectors"] for o in orders] == [8, 27]
+        n = dev(s.n0)
+        p, q = torch.empty_like(n), torch.empty_like(n)
+        pl.rhs_parts(n, p, q)
+        torch.cuda.synchronize()
+    assert nerr(p.cpu().numpy(), p_ref, scale) < TOL[prec]
+    assert nerr(q.cpu().numpy(), q_ref, scale) < TOL[prec]
