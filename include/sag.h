@@ -183,7 +183,7 @@ sag_status sag_sync_status(sag_plan_t plan, void* stream);
  * launch stream. sag_profile_read waits for that work, adds each kernel's
  * total time (ms) and launch count to ms[id] and launches[id] for
  * id < min(n, SAG_NUM_KERNELS), and forgets the records. */
-#define SAG_NUM_KERNELS 12
+#define SAG_NUM_KERNELS 13
 sag_status sag_profile_enable(sag_plan_t plan, int32_t on);
 sag_status sag_profile_read(sag_plan_t plan, double* ms, int64_t* launches, int32_t n);
 /* Name of kernel id (0 <= id < SAG_NUM_KERNELS), or NULL. */

@@ -601,7 +601,8 @@ sag_status sag_profile_read(sag_plan_t pl, double* ms, int64_t* launches, int32_
 const char* sag_kernel_name(int32_t id) {
   static const char* names[KID_COUNT] = {"k_nmax",    "k_nsplit",      "k_dot",       "k_fwd_col",
                                          "k_rows",    "k_inv_col",     "k_epilogue",  "k_moments",
-                                         "k_coef",    "k_rows_tt_fwd", "k_tt_chain",  "k_rows_tt_inv"};
+                                         "k_coef",    "k_rows_tt_fwd", "k_tt_chain",  "k_rows_tt_inv",
+                                         "k_qterm"};
   return (id >= 0 && id < KID_COUNT) ? names[id] : nullptr;
 }
 
@@ -673,9 +674,14 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
       b = 0.0;
       for (const OrderDesc& od : pl->items) b += 8.0 * od.N;  // P^(d) written
       break;
-    case KID_EPILOGUE:  // w = sum_v coef_v U_v(k); rhs = p + n w; stage update
-      o = factor_elems + 8 * Nt;
-      b = 8 * factor_elems + 8.0 * pl->items.size() / std::max(1, pl->B) * Nt + 3 * 8 * Nt;
+    case KID_QTERM:  // q = n (sum_v coef_v U_v(k))
+      o = factor_elems + Nt;
+      b = 8 * factor_elems + 2 * 8 * Nt;
+      fp64 = 1;
+      break;
+    case KID_EPILOGUE:  // rhs = p + q; stage update; moments
+      o = 8 * Nt;
+      b = 8.0 * pl->items.size() / std::max(1, pl->B) * Nt + 4 * 8 * Nt;
       fp64 = 1;
       break;
     case KID_MOMENTS:

@@ -195,10 +195,11 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
 // rhs_k = sum_d P^(d)_k + n_k sum_v coef_v U_v(k), then the Runge-Kutta stage.
 // The last block of each system to finish reduces that system's block
 // partials in a fixed order and evaluates its outflow gflux - sum_{k<=N} k P_k.
-__global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsParams P, EpiArgs A) {
+// q_k = n_k sum_v coef_v U_v(k): one pass over the FP64 factors. It needs
+// only the loss weights, so it runs on the side branch beside the FFT kernels.
+__global__ void __launch_bounds__(256) k_qterm(const __grid_constant__ RhsParams P,
+                                               const double* __restrict__ nin) {
   extern __shared__ double esh[];  // [vectors of the system] coef
-  __shared__ double red[32 * 4];
-  __shared__ int is_last;
   const int b = find_segment(P.epipre, P.B, blockIdx.x);
   const SysDesc sy = P.sys[b];
   const int blk = blockIdx.x - P.epipre[b];
@@ -206,6 +207,28 @@ __global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsPar
   double* coef = esh;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) coef[i] = P.coef[sy.vbeg + i];
   __syncthreads();
+  const int k = blk * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  // A system's vectors are stored back to back, N sizes each.
+  const double* Ub = P.U64 + P.voff[sy.vbeg] + k;
+  double w0 = 0.0, w1 = 0.0;
+  int i = 0;
+  for (; i + 1 < nv; i += 2) {
+    w0 = fma(coef[i], Ub[(int64_t)i * N], w0);
+    w1 = fma(coef[i + 1], Ub[(int64_t)(i + 1) * N], w1);
+  }
+  if (i < nv) w0 = fma(coef[i], Ub[(int64_t)i * N], w0);
+  const int64_t g = sy.noff + k;
+  P.qbuf[g] = nin[g] * (w0 + w1);
+}
+
+__global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsParams P, EpiArgs A) {
+  __shared__ double red[32 * 4];
+  __shared__ int is_last;
+  const int b = find_segment(P.epipre, P.B, blockIdx.x);
+  const SysDesc sy = P.sys[b];
+  const int blk = blockIdx.x - P.epipre[b];
+  const int N = sy.N;
 
   double part[3] = {0.0, 0.0, 0.0};  // sum k p_k, M0 and M1 of the new state
   const int k = blk * blockDim.x + threadIdx.x;
@@ -213,17 +236,8 @@ __global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsPar
     const int64_t g = sy.noff + k;
     double p = 0.0;
     for (int it = sy.ibeg; it < sy.iend; ++it) p += P.pd[P.ord[it].pd_off + k];
-    // A system's vectors are stored back to back, N sizes each.
-    const double* Ub = P.U64 + P.voff[sy.vbeg] + k;
-    double w0 = 0.0, w1 = 0.0;
-    int i = 0;
-    for (; i + 1 < nv; i += 2) {
-      w0 = fma(coef[i], Ub[(int64_t)i * N], w0);
-      w1 = fma(coef[i + 1], Ub[(int64_t)(i + 1) * N], w1);
-    }
-    if (i < nv) w0 = fma(coef[i], Ub[(int64_t)i * N], w0);
     const double nk = A.nin[g];
-    const double q = nk * (w0 + w1);
+    const double q = P.qbuf[g];
     const double rhs = p + q;
     if (!isfinite(rhs)) atomicOr(P.status, kStatusNonFinite);
     const double size = (double)(k + 1);
@@ -354,6 +368,8 @@ cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* n
   k_dot<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, ds>>>(P, nin);
   if (hook) hook->mark(KID_COEF, st);
   k_coef<<<P.B, 256, L.coef_smem, ds>>>(P);
+  if (hook) hook->mark(KID_QTERM, st);
+  k_qterm<<<L.epi_blocks, 256, L.epi_smem, ds>>>(P, nin);
   if (fork && (e = cudaEventRecord(side->join, ds)) != cudaSuccess) return e;
   if (fork && groups && groups->n > 1) {
     // one FFT chain per group, each on its own stream after the split of n
@@ -373,7 +389,7 @@ cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* n
   }
   if (fork && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return e;
   if (hook) hook->mark(KID_EPILOGUE, st);
-  k_epilogue<<<L.epi_blocks, 256, L.epi_smem, st>>>(P, A);
+  k_epilogue<<<L.epi_blocks, 256, 0, st>>>(P, A);
   if (hook) hook->mark(-1, st);
   return cudaGetLastError();
 }
@@ -390,7 +406,7 @@ cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, c
 }
 
 cudaError_t setup_common_kernels(const LaunchCfg& L) {
-  cudaError_t e = allow_max_smem(k_epilogue);
+  cudaError_t e = allow_max_smem(k_qterm);
   if (e == cudaSuccess)
     e = allow_max_smem(k_coef);
   return e;

@@ -37,7 +37,7 @@ struct EpiArgs {
 enum KernelId : int {
   KID_NMAX = 0, KID_NSPLIT = 1, KID_DOT = 2, KID_FWD_COL = 3, KID_ROWS = 4, KID_INV_COL = 5,
   KID_EPILOGUE = 6, KID_MOMENTS = 7, KID_COEF = 8, KID_ROWS_TT = 9, KID_TT_CHAIN = 10,
-  KID_ROWS_TT_INV = 11, KID_COUNT = 12
+  KID_ROWS_TT_INV = 11, KID_QTERM = 12, KID_COUNT = 13
 };
 
 // Optional hook called before each kernel launch (id) and once after the last

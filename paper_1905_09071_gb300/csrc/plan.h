@@ -133,6 +133,7 @@ struct RhsParams {
   double* dot_t;                 // [Vtot][maxdotchunk] partial <k U, n>
   double* coef;                  // [Vtot] loss weights: q_k = n_k sum_v coef_v U_v(k)
   double* epi_part;              // [epilogue blocks][4] block partials
+  double* qbuf;                  // [Ntot] loss term q of the current evaluation
   // vector-Jacobian product workspace (CP)
   float2* gdw;                   // [Ntot] double-word cotangent scaled by 2^-e_g of its system
   double* gabuf;                 // cotangent of each a = U o n (vector layout, voff)

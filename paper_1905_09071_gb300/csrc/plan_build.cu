@@ -572,7 +572,8 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       pl->alloc(&P.sc, (size_t)B) != cudaSuccess || pl->alloc(&P.status, 1) != cudaSuccess ||
       pl->alloc(&pl->nstar, Nt) != cudaSuccess || pl->alloc(&pl->k1buf, Nt) != cudaSuccess ||
       pl->alloc(&pl->stage_a, Nt) != cudaSuccess || pl->alloc(&pl->stage_b, Nt) != cudaSuccess ||
-      pl->alloc(&pl->stage_c, Nt) != cudaSuccess || pl->alloc(&pl->dev_outflow, (size_t)B) != cudaSuccess)
+      pl->alloc(&pl->stage_c, Nt) != cudaSuccess || pl->alloc(&pl->dev_outflow, (size_t)B) != cudaSuccess ||
+      pl->alloc(&P.qbuf, Nt) != cudaSuccess)
     return fail(SAG_ENOMEM, "cudaMalloc workspace");
   P.epi_part = pl->epi_part;
   if (!tt) {

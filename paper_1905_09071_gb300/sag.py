@@ -29,7 +29,7 @@ EXPORTS = [
     "sag_kernel_work", "sag_plan_describe", "sag_loss_noalloc", "sag_rhs_vjp", "sag_integrate_vjp",
     "sag_plan_update_factors", "sag_plan_factor_count",
 ]
-SAG_NUM_KERNELS = 12
+SAG_NUM_KERNELS = 13
 
 _STATUS_NAMES = {0: "SAG_OK", 1: "SAG_EINVAL", 2: "SAG_ENOMEM", 3: "SAG_ECUDA",
                  4: "SAG_EUNSUPPORTED", 5: "SAG_ETIMEOUT", 6: "SAG_ENONFINITE"}
