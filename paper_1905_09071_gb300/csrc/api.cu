@@ -639,9 +639,9 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
       fp64 = 1;
       break;
     case KID_FWD_COL:
-      for (const OrderDesc& od : pl->items)
-        o += (double)od.nu * (od.M2 * fft_ops(od.M1, od.rp1, c) + (double)od.M * c.cmul +
-                                2.0 * std::min<double>(od.M, od.N) * load_mul);
+      for (const OrderDesc& od : pl->items)  // a pair costs what two single vectors cost
+        o += (od.pair ? 2.0 * od.npair : (double)od.nu) *
+             (od.M2 * fft_ops(od.M1, od.rp1, c) + (double)od.M * c.cmul + 2.0 * std::min<double>(od.M, od.N) * load_mul);
       b = 8.0 * factor_elems + 8.0 * Nt;
       break;
     case KID_ROWS:
@@ -649,9 +649,13 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
         const double Vd = od.nvec, M = od.M;
         const double unpack = 4 * c.cadd + c.cmul;
         const double repack = 4 * c.cadd + c.cmul;
-        o += Vd * od.M1 * fft_ops(od.M2, od.rp2, c)             // forward rows of every vector
-             + Vd * M * unpack                                    // real split
-             + (Vd - od.R) * M * c.cmul                           // product over the modes
+        if (od.pair)  // rows of 2 M2 points per pair; separation: 2 complex adds per pair and index
+          o += (double)od.npair * od.M1 * fft_ops(2 * od.M2, make_radix_plan(2 * od.M2), c) +
+               (double)od.npair * M * 2 * c.cadd;
+        else
+          o += Vd * od.M1 * fft_ops(od.M2, od.rp2, c)  // forward rows of every vector
+               + Vd * M * unpack;                        // real split
+        o += (Vd - od.R) * M * c.cmul                           // product over the modes
              + (double)od.R * M * (c.cadd + (dwp ? c.scale : 0))  // rank sum
              + M * repack + od.M1 * fft_ops(od.M2, od.rp2, c)     // inverse rows
              + M * c.cmul;                                        // four-step twiddle
@@ -713,7 +717,8 @@ sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
     const OrderDesc& od = pl->items[i];
     js += std::string(i ? ", " : "") + "{\"sys\": " + std::to_string(od.sys) + ", \"d\": " +
           std::to_string(od.d) + ", \"vectors\": " + std::to_string(od.nvec) +
-          ", \"transformed\": " + std::to_string(od.nu) + ", \"L\": " +
+          ", \"transformed\": " + std::to_string(od.pair ? 2 * od.npair : od.nu) +
+          ", \"pairs\": " + std::to_string(od.pair) + ", \"L\": " +
           std::to_string(od.L) + ", \"M1\": " + std::to_string(od.M1) + ", \"M2\": " +
           std::to_string(od.M2) + ", \"radix_M1\": " + rps(od.rp1) + ", \"radix_M2\": " + rps(od.rp2) +
           ", \"W\": " + std::to_string(od.W) + ", \"G\": " + std::to_string(od.G) +

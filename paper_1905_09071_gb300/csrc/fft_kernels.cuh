@@ -139,6 +139,49 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
 
 // all = 0: each order's distinct vectors (colpre; duplicates share a slot);
 // all = 1: every vector into its own slot (colpre_all; the adjoint).
+// Forward column pass of a pair (double-word, compile-time length): vectors
+// q = 2 pr, 2 pr + 1 of the order (rank-major, vector m R + r for q = r d + m)
+// as the real and imaginary parts of one sequence indexed by size, j = 2 M2 j1
+// + j2, so each complex point holds one size of each vector; column block cb
+// of the M1 x 2 M2 geometry. A missing second vector (odd count) is zero.
+template <class C, int P1>
+__device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const OrderDesc& od, int pr, int cb,
+                                                  C* buf) {
+  constexpr int W = ct_cols(P1);
+  constexpr int ld = ct_ld(P1, W);
+  const int M2p = 2 * od.M2, N = od.N, d = od.d, R = od.R;
+  C* tw = buf + W * ld;
+  ct_fill_twiddles<C, P1>(tw, static_cast<const C*>(od.tw1));
+  const int q1 = 2 * pr, q2 = q1 + 1;
+  const float2* u1 = P.Udw + P.vdwoff[od.vbase + (q1 % d) * R + q1 / d];
+  const float2* u2 = q2 < od.nvec ? P.Udw + P.vdwoff[od.vbase + (q2 % d) * R + q2 / d] : nullptr;
+  const float2* nn = P.ndw + od.ndwoff;  // indexed by size, zero at 0
+  for (int e = threadIdx.x; e < W * P1; e += kThreads) {
+    const int c = e % W, j1 = e / W;
+    const int j = M2p * j1 + cb * W + c;
+    C z = c_zero(C{});
+    if (j <= N) {
+      const float2 nb = __ldg(nn + j), a1 = __ldg(u1 + j);
+      const dw nv{nb.x, nb.y};
+      dw im{0.f, 0.f};
+      if (u2) {
+        const float2 a2 = __ldg(u2 + j);
+        im = dw_mul(dw{a2.x, a2.y}, nv);
+      }
+      z = make_cdw(dw_mul(dw{a1.x, a1.y}, nv), im);
+    }
+    buf[c * ld + pad8(j1)] = z;
+  }
+  __syncthreads();
+  fft_ct<C, P1, W, kThreads>(buf, ld, tw);
+  C* dst = static_cast<C*>(P.scratch) + od.scr_off + (int64_t)pr * 2 * od.M;
+  const C* tw4c = static_cast<const C*>(od.tw4c_p) + (int64_t)cb * W * P1;
+  for (int e = threadIdx.x; e < W * P1; e += kThreads) {
+    const int c = e % W, k1 = e / W, j2 = cb * W + c;
+    dst[(int64_t)k1 * M2p + j2] = c_mul(buf[c * ld + pad8(k1)], tw4c[e]);
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__ RhsParams P,
                                                       const double* __restrict__ n, int base, int all) {
@@ -149,6 +192,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
   const int it = find_segment(pre, P.nitems, bid);
   const OrderDesc& od = P.ord[it];
   const int local = bid - pre[it];
+  if constexpr (std::is_same<C, cdw>::value) {
+    if (!all && od.pair) {
+      const int pr = local / od.ncolblk_p, cbp = local - pr * od.ncolblk_p;
+      switch (od.M1) {
+        case 64: fwd_col_pair_body<C, 64>(P, od, pr, cbp, buf); break;
+        case 96: fwd_col_pair_body<C, 96>(P, od, pr, cbp, buf); break;
+        case 128: fwd_col_pair_body<C, 128>(P, od, pr, cbp, buf); break;
+        case 192: fwd_col_pair_body<C, 192>(P, od, pr, cbp, buf); break;
+        case 256: fwd_col_pair_body<C, 256>(P, od, pr, cbp, buf); break;
+        case 384: fwd_col_pair_body<C, 384>(P, od, pr, cbp, buf); break;
+        case 512: fwd_col_pair_body<C, 512>(P, od, pr, cbp, buf); break;
+        case 768: fwd_col_pair_body<C, 768>(P, od, pr, cbp, buf); break;
+        default: break;  // the plan sets pair only with a compile-time column length
+      }
+      return;
+    }
+  }
   const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
   const int lv = (all || od.umap_off < 0) ? vloc : P.ulist[od.umap_off + vloc];
   if constexpr (!std::is_same<C, cdw>::value) {
@@ -417,6 +477,137 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
   }
 }
 
+// Row pass of the pair form (double-word, rows of P2p = 2 M2 points): block
+// kp owns rows {k1, M1 - k1} of every pair's L-geometry transform, which hold
+// every index k = k1 + M1 pos of row k1 together with its mirror L - k. The
+// two vectors of a pair separate as 2 A1 = Z + conj Z(L-k) and
+// 2 A2 = -i (Z - conj Z(L-k)); products and rank sums run over the P2p
+// positions of row k1 only (row M1 - k1 is their Hermitian mirror). The
+// inverse's row half then needs S(k) and S(k + M) of each M-geometry row,
+// both in row k1 or, conjugated, in its mirror. Layout: one mbarrier (16
+// bytes), stage (2 G x P2p), work (2 G transforms, ct_ld(P2p, 2 G) apart), pass
+// tables of P2p, pass tables of M2 (the inverse rows).
+template <class C, int P2p>
+__device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDesc& od, int kp,
+                                               unsigned char* smem_raw) {
+  constexpr int M2c = P2p / 2;
+  constexpr int G = ct_group(P2p);  // pairs per chunk
+  constexpr int SLOTS = 2 * G;
+  constexpr int ld = ct_ld(P2p, SLOTS);
+  constexpr int ldi = ct_ld(M2c, 2);
+  static_assert(2 * ldi <= SLOTS * ld, "inverse rows fit the work area");
+  constexpr int PPT = (P2p + kThreads - 1) / kThreads;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  C* stage = reinterpret_cast<C*>(smem_raw + 16);
+  C* work = stage + SLOTS * P2p;
+  C* tw = work + SLOTS * ld;
+  C* twi = tw + ct_twp_size(P2p);
+  const int d = od.d, R = od.R, M1 = od.M1, M = od.M;
+  const int k1a = kp, k1b = M1 - kp;
+  const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
+  const C* twL = static_cast<const C*>(od.twL);
+  const C* src = static_cast<const C*>(P.scratch) + od.scr_off;  // pair p at src + 2 M p
+  const int Vd = d * R, np = od.npair;
+  const int nchunk = (np + G - 1) / G;
+
+  auto issue = [&](int c) {
+    const int p0 = c * G, gc = min(G, np - p0);
+    mbar_arrive_expect_tx(bar, (uint32_t)(gc * nrow * P2p * sizeof(C)));
+    for (int g = 0; g < gc; ++g)
+      for (int row = 0; row < nrow; ++row) {
+        const int k1 = row ? k1b : k1a;
+        bulk_copy_g2s(stage + (2 * g + row) * P2p, src + (int64_t)(p0 + g) * 2 * M + (int64_t)k1 * P2p,
+                      (uint32_t)(P2p * sizeof(C)), bar);
+      }
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  ct_fill_twiddles<C, P2p>(tw, static_cast<const C*>(od.tw2p));
+  ct_fill_twiddles<C, M2c>(twi, static_cast<const C*>(od.tw2));
+  __syncthreads();
+  if (threadIdx.x == 0) issue(0);
+
+  C S[PPT], Pr[PPT];
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    S[i] = c_zero(C{});
+    Pr[i] = c_zero(C{});
+  }
+  auto accumulate = [&](int i, const C& A, int q) {
+    const int r = q / d, m = q - r * d;
+    Pr[i] = (m == 0) ? A : c_mul(Pr[i], A);
+    if (m == d - 1) S[i] = c_add(S[i], rank_weight(Pr[i], od, r));
+  };
+
+  for (int c = 0; c < nchunk; ++c) {
+    const int p0 = c * G, gc = min(G, np - p0);
+    const bool ok = mbar_wait_bounded(bar, (uint32_t)(c & 1), P.spin_limit);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
+      return;
+    }
+    fft_ct_first<C, P2p, SLOTS, kThreads>(stage, P2p, work, ld, tw);  // unused slots hold stale data
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0 && c + 1 < nchunk) issue(c + 1);
+    fft_ct_rest<C, P2p, SLOTS, kThreads>(work, ld, tw);
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int p = threadIdx.x + i * kThreads;
+      if (p < P2p) {
+        int mrow, mpos;
+        mirror_of(k1a, 0, p, M1, P2p, mrow, mpos);
+        const int oa = pad8(p), ob = mrow * ld + pad8(mpos);
+        for (int g = 0; g < gc; ++g) {
+          const C* bg = work + 2 * g * ld;
+          const C z = bg[oa], zc = c_conj(bg[ob]);
+          const int q = 2 * (p0 + g);
+          accumulate(i, c_add(z, zc), q);
+          if (q + 1 < Vd) accumulate(i, c_mul_mi(c_sub(z, zc)), q + 1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // Inverse, row half: S of row k1 staged in the (idle) stage area; the packed
+  // sequences of M-geometry rows k1 (and M1 - k1) built in work.
+  C* sS = stage;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = threadIdx.x + i * kThreads;
+    if (p < P2p) sS[p] = S[i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nrow * M2c; e += kThreads) {
+    const int row = e / M2c, k2 = e - row * M2c;
+    const int k1 = row ? k1b : k1a;
+    const int k = k1 + M1 * k2;
+    C Sk, SkM;  // S(k), S(k + M)
+    if (row == 0) {
+      Sk = sS[k2];
+      SkM = sS[k2 + M2c];
+    } else {
+      Sk = c_conj(sS[P2p - 1 - k2]);
+      SkM = c_conj(sS[M2c - 1 - k2]);
+    }
+    const C zpp = c_add(c_add(Sk, SkM), c_mul_pi(c_mul(c_conj(twL[k]), c_sub(Sk, SkM))));
+    work[row * ldi + pad8(k2)] = c_conj(zpp);
+  }
+  __syncthreads();
+  fft_ct<C, M2c, 2, kThreads>(work, ldi, twi);
+  C* dst = static_cast<C*>(P.scratch2) + od.scr2_off;
+  const C* tw4 = static_cast<const C*>(od.tw4);
+  for (int e = threadIdx.x; e < nrow * M2c; e += kThreads) {
+    const int row = e / M2c, j2 = e - row * M2c;
+    const int k1 = row ? k1b : k1a;
+    dst[(int64_t)k1 * M2c + j2] = c_mul(work[row * ldi + pad8(j2)], tw4[j2 * k1]);
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ RhsParams P, int base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -429,6 +620,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ Rh
   const int kp = bid - P.rowpre[j];
   if constexpr (!std::is_same<C, cdw>::value) {
     rows_body<C>(P, od, kp, buf);
+    return;
+  }
+  if (od.pair) {
+    switch (2 * od.M2) {
+      case 128: rows_body_pair<C, 128>(P, od, kp, smem_raw); break;
+      case 256: rows_body_pair<C, 256>(P, od, kp, smem_raw); break;
+      case 512: rows_body_pair<C, 512>(P, od, kp, smem_raw); break;
+      default: break;  // the plan sets pair only for these row lengths
+    }
     return;
   }
   switch (od.ct2 ? od.M2 : 0) {

@@ -54,6 +54,16 @@ struct OrderDesc {
   const void* twL;     // M entries omega_L^k, k < M (real-FFT split)
   const void* tw4c;    // compile-time column kernels: omega_M^(j2 k1) in column-block
                        // order (cb, k1, c) with j2 = cb W + c; M entries
+  // Pair form of the forward pass (CP, double-word, compile-time kernels, no
+  // duplicate vectors): vectors q = 2p, 2p + 1 (rank-major, q = r d + m) are
+  // the real and imaginary parts of one length-L sequence, transformed as
+  // M1 rows of 2 M2 points; the row pass separates their spectra.
+  int pair;            // 1: the forward pass runs on pairs
+  int npair;           // ceil(nvec / 2)
+  int ncolblk_p;       // 2 M2 / W column blocks per pair
+  int ld2p;            // work-area stride of the pair row transforms
+  const void* tw2p;    // omega_{2 M2}^k, k < 2 M2
+  const void* tw4c_p;  // omega_L^(j2 k1) for j2 < 2 M2 in column-block order
   const float* rscale; // CP, double-word path: [R] power-of-two weight of rank term r
   double pscale;       // final FP64 scale of P^(d) (1/(L d!), factors of two), before the n scale
   double gscale;       // 2^-d / (L d!): final scale of a vector's cotangent before its exponents

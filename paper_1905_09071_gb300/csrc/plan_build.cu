@@ -109,6 +109,10 @@ cudaError_t item_tables(sag_plan_s* pl, TwiddleCache<C>& tc, OrderDesc& od) {
   if (e == cudaSuccess) e = tc.get(pl, od.L, od.M, &od.twL);
   od.tw4c = nullptr;
   if (e == cudaSuccess && od.ct1) e = tc.get_col(pl, od.M1, od.M2, od.W, &od.tw4c);
+  od.tw2p = nullptr;
+  od.tw4c_p = nullptr;
+  if (e == cudaSuccess && od.pair) e = tc.get(pl, 2 * od.M2, 2 * od.M2, &od.tw2p);
+  if (e == cudaSuccess && od.pair) e = tc.get_col(pl, od.M1, 2 * od.M2, od.W, &od.tw4c_p);
   return e;
 }
 
@@ -366,13 +370,24 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     if (dwp && !tt && !od.ct2 && 2 * od.M2 > kThreads)
       return fail(SAG_EUNSUPPORTED, "row length without a compile-time kernel above 128");
     od.G = G;
+    // Pairs (see OrderDesc): rows of 2 M2 points with a compile-time kernel.
+    od.pair = 0;
+    od.npair = 0;
+    od.ncolblk_p = 0;
+    od.ld2p = 0;
+    if (od.ct1 && od.ct2 && !tt && od.umap_off < 0 && 2 * od.M2 <= 512 && ct_supported(2 * od.M2)) {
+      od.pair = 1;
+      od.npair = (od.nvec + 1) / 2;
+      od.ncolblk_p = 2 * M2 / W;
+      od.ld2p = ct_ld(2 * od.M2, 2 * ct_group(2 * od.M2));
+    }
     od.scr_off = scr;
-    scr += (int64_t)od.nvec * od.M;
+    scr += (int64_t)std::max(od.nvec, 2 * od.npair) * od.M;
     od.scr2_off = scr2;
     scr2 += od.M;
     od.pd_off = pdo;
     pdo += od.N;
-    colpre.push_back(colpre.back() + od.nu * od.ncolblk);
+    colpre.push_back(colpre.back() + (od.pair ? od.npair * od.ncolblk_p : od.nu * od.ncolblk));
     colpre_all.push_back(colpre_all.back() + od.nvec * od.ncolblk);
     invpre.push_back(invpre.back() + od.ncolblk);
     chainpre.push_back(chainpre.back() + (tt ? (od.M + 1 + 255) / 256 : 0));
@@ -386,6 +401,11 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     row_smem = std::max(row_smem, od.ct2 ? (size_t)(2 * G * od.M2 + 2 * G * od.ld2 + ct_twp_size(od.M2)) *
                                                    csize + 16
                                          : (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize);
+    if (od.pair) {  // stage and work of 2 G' transforms of 2 M2 points, pass tables of 2 M2 and of M2
+      const int Gp = ct_group(2 * od.M2);
+      row_smem = std::max(row_smem, (size_t)(2 * Gp * 2 * od.M2 + 2 * Gp * od.ld2p + ct_twp_size(2 * od.M2) +
+                                             ct_twp_size(od.M2)) * csize + 16);
+    }
     rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * G * 2 * od.ld2, 6 * od.ld2) * csize +
                                           (size_t)od.M2 * csize);
     // Vector-Jacobian product kernels (CP): ping-pong column blocks; row
