@@ -145,18 +145,68 @@ SAG_CX int ct_ns8(int P) {
   return v;
 }
 
+// Pass tables in global memory (read through L1, so laid out for coalescing
+// rather than for banks): pass s >= 1 holds omega_P^(t k P / (Ns R)) at
+// ct_twg_off(P, s) + (t - 1) Ns + k, k < Ns, 1 <= t < R.
+SAG_CX int ct_twg_off(int P, int S) {
+  const ct_sched sc = make_ct_sched(P);
+  int off = 0, Ns = sc.r[0];
+  for (int s = 1; s < S; ++s) {
+    off += Ns * (sc.r[s] - 1);
+    Ns *= sc.r[s];
+  }
+  return off;
+}
+SAG_CX int ct_twg_size(int P) { return ct_twg_off(P, make_ct_sched(P).n); }
+// Natural-table exponent of entry i of the global pass tables.
+SAG_CX int ct_twg_src(int P, int i) {
+  const ct_sched sc = make_ct_sched(P);
+  int off = 0, Ns = sc.r[0];
+  for (int s = 1; s < sc.n; ++s) {
+    const int R = sc.r[s];
+    if (i < off + Ns * (R - 1)) {
+      const int t = (i - off) / Ns + 1, k = (i - off) % Ns;
+      return t * k * (P / (Ns * R));
+    }
+    off += Ns * (R - 1);
+    Ns *= R;
+  }
+  return -1;
+}
+template <int P, int S, int R, int Ns>
+SAG_CX int ct_twg(int j, int t) {
+  return ct_twg_off(P, S) + (t - 1) * Ns + j % Ns;
+}
+
 SAG_CX bool ct_supported(int P) {
   return P == 64 || P == 128 || P == 256 || P == 512 || P == 96 || P == 192 || P == 384 ||
          P == 768;
 }
 
 #if defined(__CUDACC__)
+// Twiddle t of butterfly j: from the shared-memory pass tables (bank layout)
+// or, GT, from the global ones (ct_twg layout, read-only path).
+__device__ __forceinline__ cdw ld_ro(const cdw* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return cdw{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ cd ld_ro(const cd* p) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return cd{v.x, v.y};
+}
+template <class C, bool GT, int P, int S, int R, int Ns>
+__device__ __forceinline__ C tw_at(const C* tw, int j, int t) {
+  if constexpr (GT) return ld_ro(tw + ct_twg<P, S, R, Ns>(j, t));
+  else return tw[ct_twi<P, S, R, Ns>(j, t)];
+}
+
 // One pass of radix R and span Ns over COUNT transforms of length P, T
 // threads: transform b is read at src + b * sld (natural order if SIN, else
 // padded) and written padded at dst + b * dld. In place (src == dst) the block
 // synchronises between the loads and the stores; out of place it does not.
 // Ends with a barrier unless TAIL is false.
-template <class C, int P, int S, int R, int Ns, int COUNT, int T, bool SIN, bool INPLACE, bool TAIL = true>
+template <class C, int P, int S, int R, int Ns, int COUNT, int T, bool SIN, bool INPLACE, bool TAIL = true,
+          bool GT = false>
 __device__ __forceinline__ void ct_pass(const C* src, int sld, C* dst, int dld, const C* tw) {
   constexpr int NB = P / R;
   constexpr int TOT = NB * COUNT;
@@ -180,7 +230,7 @@ __device__ __forceinline__ void ct_pass(const C* src, int sld, C* dst, int dld, 
       const int b = w / NB, j = w - b * NB;
       if (Ns > 1) {
 #pragma unroll
-        for (int t = 1; t < R; ++t) x[i][t] = c_mul(x[i][t], tw[ct_twi<P, S, R, Ns>(j, t)]);
+        for (int t = 1; t < R; ++t) x[i][t] = c_mul(x[i][t], tw_at<C, GT, P, S, R, Ns>(tw, j, t));
       }
       dft_r<R>(x[i]);
       C* ob = dst + b * dld;
@@ -191,23 +241,23 @@ __device__ __forceinline__ void ct_pass(const C* src, int sld, C* dst, int dld, 
   if constexpr (TAIL) __syncthreads();
 }
 
-template <class C, int P, int COUNT, int T, int S, int Ns>
+template <class C, int P, int COUNT, int T, int S, int Ns, bool GT = false>
 __device__ __forceinline__ void ct_passes(C* buf, int ld, const C* tw) {
   constexpr ct_sched sc = make_ct_sched(P);
   if constexpr (S < sc.n) {
     constexpr int R = sc.r[S];
-    ct_pass<C, P, S, R, Ns, COUNT, T, false, true>(buf, ld, buf, ld, tw);
-    ct_passes<C, P, COUNT, T, S + 1, Ns * R>(buf, ld, tw);
+    ct_pass<C, P, S, R, Ns, COUNT, T, false, true, true, GT>(buf, ld, buf, ld, tw);
+    ct_passes<C, P, COUNT, T, S + 1, Ns * R, GT>(buf, ld, tw);
   }
 }
 
 // COUNT length-P forward transforms in place in the padded layout; tw holds
 // the pass tables (ct_fill_twiddles); the caller has synchronised after
 // filling buf and tw; returns after a barrier.
-template <class C, int P, int COUNT, int T>
+template <class C, int P, int COUNT, int T, bool GT = false>
 __device__ __forceinline__ void fft_ct(C* buf, int ld, const C* tw) {
   static_assert(make_ct_sched(P).n > 0, "unsupported compile-time length");
-  ct_passes<C, P, COUNT, T, 0, 1>(buf, ld, tw);
+  ct_passes<C, P, COUNT, T, 0, 1, GT>(buf, ld, tw);
 }
 
 // The same transforms in two steps: fft_ct_first reads natural-order input
@@ -215,16 +265,16 @@ __device__ __forceinline__ void fft_ct(C* buf, int ld, const C* tw) {
 // at the end (src may be refilled once the block has synchronised);
 // fft_ct_rest then runs the remaining passes in place in dst, starting after
 // the caller's barrier, and returns after a barrier.
-template <class C, int P, int COUNT, int T>
+template <class C, int P, int COUNT, int T, bool GT = false>
 __device__ __forceinline__ void fft_ct_first(const C* src, int sld, C* dst, int dld, const C* tw) {
   static_assert(make_ct_sched(P).n > 1, "unsupported compile-time length");
   constexpr int R = make_ct_sched(P).r[0];
-  ct_pass<C, P, 0, R, 1, COUNT, T, true, false, false>(src, sld, dst, dld, tw);
+  ct_pass<C, P, 0, R, 1, COUNT, T, true, false, false, GT>(src, sld, dst, dld, tw);
 }
-template <class C, int P, int COUNT, int T>
+template <class C, int P, int COUNT, int T, bool GT = false>
 __device__ __forceinline__ void fft_ct_rest(C* buf, int ld, const C* tw) {
   constexpr int R = make_ct_sched(P).r[0];
-  ct_passes<C, P, COUNT, T, 1, R>(buf, ld, tw);
+  ct_passes<C, P, COUNT, T, 1, R, GT>(buf, ld, tw);
 }
 
 // Compact variant for kernels whose blocks each run once per SM (the cost

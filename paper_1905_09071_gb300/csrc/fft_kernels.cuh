@@ -485,8 +485,9 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
 // positions of row k1 only (row M1 - k1 is their Hermitian mirror). The
 // inverse's row half then needs S(k) and S(k + M) of each M-geometry row,
 // both in row k1 or, conjugated, in its mirror. Layout: one mbarrier (16
-// bytes), stage (2 G x P2p), work (2 G transforms, ct_ld(P2p, 2 G) apart), pass
-// tables of P2p, pass tables of M2 (the inverse rows).
+// bytes), stage (2 G x P2p), work (2 G transforms, ct_ld(P2p, 2 G) apart). The
+// pass twiddles come from global tables (ct_twg layout), which keeps the block
+// at three per SM for 512-point rows.
 template <class C, int P2p>
 __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDesc& od, int kp,
                                                unsigned char* smem_raw) {
@@ -500,8 +501,8 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   C* stage = reinterpret_cast<C*>(smem_raw + 16);
   C* work = stage + SLOTS * P2p;
-  C* tw = work + SLOTS * ld;
-  C* twi = tw + ct_twp_size(P2p);
+  const C* tw = static_cast<const C*>(od.tw2p);
+  const C* twi = static_cast<const C*>(od.twg2);
   const int d = od.d, R = od.R, M1 = od.M1, M = od.M;
   const int k1a = kp, k1b = M1 - kp;
   const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
@@ -525,8 +526,6 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
     mbar_init(bar, 1);
     mbar_init_fence();
   }
-  ct_fill_twiddles<C, P2p>(tw, static_cast<const C*>(od.tw2p));
-  ct_fill_twiddles<C, M2c>(twi, static_cast<const C*>(od.tw2));
   __syncthreads();
   if (threadIdx.x == 0) issue(0);
 
@@ -549,11 +548,11 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
       if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
       return;
     }
-    fft_ct_first<C, P2p, SLOTS, kThreads>(stage, P2p, work, ld, tw);  // unused slots hold stale data
+    fft_ct_first<C, P2p, SLOTS, kThreads, true>(stage, P2p, work, ld, tw);  // unused slots hold stale data
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0 && c + 1 < nchunk) issue(c + 1);
-    fft_ct_rest<C, P2p, SLOTS, kThreads>(work, ld, tw);
+    fft_ct_rest<C, P2p, SLOTS, kThreads, true>(work, ld, tw);
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
       const int p = threadIdx.x + i * kThreads;
@@ -598,7 +597,7 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
     work[row * ldi + pad8(k2)] = c_conj(zpp);
   }
   __syncthreads();
-  fft_ct<C, M2c, 2, kThreads>(work, ldi, twi);
+  fft_ct<C, M2c, 2, kThreads, true>(work, ldi, twi);
   C* dst = static_cast<C*>(P.scratch2) + od.scr2_off;
   const C* tw4 = static_cast<const C*>(od.tw4);
   for (int e = threadIdx.x; e < nrow * M2c; e += kThreads) {

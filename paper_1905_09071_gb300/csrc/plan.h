@@ -62,7 +62,8 @@ struct OrderDesc {
   int npair;           // ceil(nvec / 2)
   int ncolblk_p;       // 2 M2 / W column blocks per pair
   int ld2p;            // work-area stride of the pair row transforms
-  const void* tw2p;    // omega_{2 M2}^k, k < 2 M2
+  const void* tw2p;    // pass tables of the 2 M2-point rows, global layout (ct_twg)
+  const void* twg2;    // pass tables of the M2-point inverse rows, global layout
   const void* tw4c_p;  // omega_L^(j2 k1) for j2 < 2 M2 in column-block order
   const float* rscale; // CP, double-word path: [R] power-of-two weight of rank term r
   double pscale;       // final FP64 scale of P^(d) (1/(L d!), factors of two), before the n scale

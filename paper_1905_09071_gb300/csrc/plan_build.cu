@@ -72,6 +72,27 @@ struct TwiddleCache {
     *out = d;
     return cudaSuccess;
   }
+  // Pass tables of a compile-time length P in the global layout (ct_twg).
+  std::map<int, const void*> pass_tables;
+  cudaError_t get_pass(sag_plan_s* pl, int P, const void** out) {
+    auto it = pass_tables.find(P);
+    if (it != pass_tables.end()) {
+      *out = it->second;
+      return cudaSuccess;
+    }
+    std::vector<C> h(std::max(1, ct_twg_size(P)));
+    for (int i = 0; i < ct_twg_size(P); ++i) {
+      double c, s;
+      unit_root(ct_twg_src(P, i), P, c, s);
+      h[i] = to_c<C>(c, s);
+    }
+    C* d = nullptr;
+    cudaError_t e = pl->upload(&d, h);
+    if (e != cudaSuccess) return e;
+    pass_tables[P] = d;
+    *out = d;
+    return cudaSuccess;
+  }
   // omega_M^(j2 k1) for M = M1 M2 in the order the compile-time column kernel
   // reads it: column block cb (W columns), then k1, then column c, j2 = cb W + c.
   std::map<std::tuple<int, int, int>, const void*> col_tables;
@@ -110,8 +131,10 @@ cudaError_t item_tables(sag_plan_s* pl, TwiddleCache<C>& tc, OrderDesc& od) {
   od.tw4c = nullptr;
   if (e == cudaSuccess && od.ct1) e = tc.get_col(pl, od.M1, od.M2, od.W, &od.tw4c);
   od.tw2p = nullptr;
+  od.twg2 = nullptr;
   od.tw4c_p = nullptr;
-  if (e == cudaSuccess && od.pair) e = tc.get(pl, 2 * od.M2, 2 * od.M2, &od.tw2p);
+  if (e == cudaSuccess && od.pair) e = tc.get_pass(pl, 2 * od.M2, &od.tw2p);
+  if (e == cudaSuccess && od.pair) e = tc.get_pass(pl, od.M2, &od.twg2);
   if (e == cudaSuccess && od.pair) e = tc.get_col(pl, od.M1, 2 * od.M2, od.W, &od.tw4c_p);
   return e;
 }
@@ -401,10 +424,9 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     row_smem = std::max(row_smem, od.ct2 ? (size_t)(2 * G * od.M2 + 2 * G * od.ld2 + ct_twp_size(od.M2)) *
                                                    csize + 16
                                          : (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize);
-    if (od.pair) {  // stage and work of 2 G' transforms of 2 M2 points, pass tables of 2 M2 and of M2
+    if (od.pair) {  // stage and work of 2 G' transforms of 2 M2 points (pass tables in global memory)
       const int Gp = ct_group(2 * od.M2);
-      row_smem = std::max(row_smem, (size_t)(2 * Gp * 2 * od.M2 + 2 * Gp * od.ld2p + ct_twp_size(2 * od.M2) +
-                                             ct_twp_size(od.M2)) * csize + 16);
+      row_smem = std::max(row_smem, (size_t)(2 * Gp * 2 * od.M2 + 2 * Gp * od.ld2p) * csize + 16);
     }
     rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * G * 2 * od.ld2, 6 * od.ld2) * csize +
                                           (size_t)od.M2 * csize);

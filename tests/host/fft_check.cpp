@@ -81,6 +81,12 @@ static void ct_host_passes(std::vector<C>& buf, int ld, int count, const C* tw, 
               std::printf("twiddle index out of range P=%d pass %d\n", P, S);
               std::exit(3);
             }
+            // the global-memory layout names the same twiddle
+            const int tg = ct_twg<P, S, R, Ns>(j, t);
+            if (tg < 0 || tg >= ct_twg_size(P) || ct_twg_src(P, tg) != ct_twp_src(P, ti)) {
+              std::printf("global twiddle table differs P=%d pass %d\n", P, S);
+              std::exit(3);
+            }
             xx[t] = c_mul(xx[t], tw[ti]);
           }
         dft_r<R>(xx);
