@@ -99,10 +99,9 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   const int M2 = od.M2;
   const int v = od.vbase + lv;
   C* buf1 = buf + W * ld;
-  C* tw = CT ? buf + W * ld : buf1 + W * ld;
+  C* tw = buf1 + W * ld;  // runtime length only: the natural table in shared memory
   const C* tw1 = static_cast<const C*>(od.tw1);
-  if constexpr (CT) ct_fill_twiddles<C, P1>(tw, tw1);
-  else
+  if constexpr (!CT)
     for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
   const auto u = vec_ptr(P, v, C{});
   const auto nn = n_ptr(P, n, od, C{});
@@ -115,7 +114,8 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   __syncthreads();
   C* res;
   if constexpr (CT) {
-    fft_ct<C, P1, ct_cols(P1), kThreads>(buf, ld, tw);
+    // pass tables from global memory (no per-block fill)
+    fft_ct<C, P1, ct_cols(P1), kThreads, true>(buf, ld, static_cast<const C*>(od.twg1));
     res = buf;
   } else {
     res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
@@ -150,8 +150,7 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
   constexpr int W = ct_cols(P1);
   constexpr int ld = ct_ld(P1, W);
   const int M2p = 2 * od.M2, N = od.N, d = od.d, R = od.R;
-  C* tw = buf + W * ld;
-  ct_fill_twiddles<C, P1>(tw, static_cast<const C*>(od.tw1));
+  const C* tw = static_cast<const C*>(od.twg1);  // pass tables, global layout
   const int q1 = 2 * pr, q2 = q1 + 1;
   const float2* u1 = P.Udw + P.vdwoff[od.vbase + (q1 % d) * R + q1 / d];
   const float2* u2 = q2 < od.nvec ? P.Udw + P.vdwoff[od.vbase + (q2 % d) * R + q2 / d] : nullptr;
@@ -173,7 +172,7 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
     buf[c * ld + pad8(j1)] = z;
   }
   __syncthreads();
-  fft_ct<C, P1, W, kThreads>(buf, ld, tw);
+  fft_ct<C, P1, W, kThreads, true>(buf, ld, tw);
   C* dst = static_cast<C*>(P.scratch) + od.scr_off + (int64_t)pr * 2 * od.M;
   const C* tw4c = static_cast<const C*>(od.tw4c_p) + (int64_t)cb * W * P1;
   for (int e = threadIdx.x; e < W * P1; e += kThreads) {

@@ -64,6 +64,7 @@ struct OrderDesc {
   int ld2p;            // work-area stride of the pair row transforms
   const void* tw2p;    // pass tables of the 2 M2-point rows, global layout (ct_twg)
   const void* twg2;    // pass tables of the M2-point inverse rows, global layout
+  const void* twg1;    // compile-time columns: pass tables of M1, global layout
   const void* tw4c_p;  // omega_L^(j2 k1) for j2 < 2 M2 in column-block order
   const float* rscale; // CP, double-word path: [R] power-of-two weight of rank term r
   double pscale;       // final FP64 scale of P^(d) (1/(L d!), factors of two), before the n scale

@@ -132,7 +132,9 @@ cudaError_t item_tables(sag_plan_s* pl, TwiddleCache<C>& tc, OrderDesc& od) {
   if (e == cudaSuccess && od.ct1) e = tc.get_col(pl, od.M1, od.M2, od.W, &od.tw4c);
   od.tw2p = nullptr;
   od.twg2 = nullptr;
+  od.twg1 = nullptr;
   od.tw4c_p = nullptr;
+  if (e == cudaSuccess && od.ct1) e = tc.get_pass(pl, od.M1, &od.twg1);
   if (e == cudaSuccess && od.pair) e = tc.get_pass(pl, 2 * od.M2, &od.tw2p);
   if (e == cudaSuccess && od.pair) e = tc.get_pass(pl, od.M2, &od.twg2);
   if (e == cudaSuccess && od.pair) e = tc.get_col(pl, od.M1, 2 * od.M2, od.W, &od.tw4c_p);
