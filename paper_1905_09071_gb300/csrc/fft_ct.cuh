@@ -282,7 +282,7 @@ __device__ __forceinline__ void fft_ct_rest(C* buf, int ld, const C* tw) {
 // pass body with the span Ns and the pass-table offset as runtime values;
 // only the radix-4/2/3 tail passes are specialised. Same arithmetic, same
 // layout, same tables as fft_ct.
-template <class C, int P, int COUNT, int T>
+template <class C, int P, int COUNT, int T, bool GT = false>
 __device__ __forceinline__ void ct_pass8_rt(C* buf, int ld, const C* tw, int Ns, int twoff) {
   constexpr int R = 8;
   constexpr int NB = P / R;
@@ -307,7 +307,9 @@ __device__ __forceinline__ void ct_pass8_rt(C* buf, int ld, const C* tw, int Ns,
       const int b = w / NB, j = w - b * NB;
       if (Ns > 1) {
 #pragma unroll
-        for (int t = 1; t < R; ++t) x[i][t] = c_mul(x[i][t], tw[ct_twi8_rt(j, t, Ns, twoff)]);
+        for (int t = 1; t < R; ++t)
+          x[i][t] = c_mul(x[i][t], GT ? ld_ro(tw + twoff + (t - 1) * Ns + (j & (Ns - 1)))
+                                      : tw[ct_twi8_rt(j, t, Ns, twoff)]);
       }
       dft_r<R>(x[i]);
       C* ob = buf + b * ld;
@@ -318,17 +320,17 @@ __device__ __forceinline__ void ct_pass8_rt(C* buf, int ld, const C* tw, int Ns,
   __syncthreads();
 }
 
-template <class C, int P, int COUNT, int T>
+template <class C, int P, int COUNT, int T, bool GT = false>
 __device__ __forceinline__ void fft_ct_compact(C* buf, int ld, const C* tw) {
   constexpr int N8 = ct_n8(P);
   static_assert(N8 >= 1, "compile-time lengths start with radix 8");
   int Ns = 1;
 #pragma unroll 1
   for (int s = 0; s < N8; ++s) {
-    ct_pass8_rt<C, P, COUNT, T>(buf, ld, tw, Ns, ct_twp_off(P, s));
+    ct_pass8_rt<C, P, COUNT, T, GT>(buf, ld, tw, Ns, GT ? ct_twg_off(P, s) : ct_twp_off(P, s));
     Ns *= 8;
   }
-  ct_passes<C, P, COUNT, T, N8, ct_ns8(P)>(buf, ld, tw);
+  ct_passes<C, P, COUNT, T, N8, ct_ns8(P), GT>(buf, ld, tw);
 }
 
 template <class C, int P, int S, int Ns>

@@ -344,8 +344,8 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
 // pass reads them from there and writes the padded work area, after which the
 // block issues the copies of the next chunk, so they land while the remaining
 // passes and the spectrum products of this chunk run. Layout: one mbarrier
-// (16 bytes), stage (2 G x P2), work (2 G transforms, ct_ld(P2, 2 G) apart),
-// pass twiddle tables (ct_twp_size(P2)). If a copy does not complete within P.spin_limit cycles the
+// (16 bytes), stage (2 G x P2), work (2 G transforms, ct_ld(P2, 2 G) apart);
+// the pass twiddle tables are read from global memory. If a copy does not complete within P.spin_limit cycles the
 // block sets the timeout status and returns.
 template <class C, int P2>
 __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderDesc& od, int kp,
@@ -357,12 +357,11 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   C* stage = reinterpret_cast<C*>(smem_raw + 16);
   C* work = stage + SLOTS * P2;
-  C* tw = work + SLOTS * ld;
+  const C* tw = static_cast<const C*>(od.twg2);  // pass tables, global memory
   const int d = od.d, R = od.R, M1 = od.M1, M = od.M;
   const int k1a = kp, k1b = M1 - kp;
   const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
   const int NP = nrow * P2;
-  const C* tw2 = static_cast<const C*>(od.tw2);
   const C* twL = static_cast<const C*>(od.twL);
   const C* src = static_cast<const C*>(P.scratch) + od.scr_off;
   const int Vd = d * R;
@@ -386,7 +385,6 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
     mbar_init(bar, 1);
     mbar_init_fence();
   }
-  ct_fill_twiddles<C, P2>(tw, tw2);
   __syncthreads();
   if (threadIdx.x == 0) issue(0);
 
@@ -408,11 +406,11 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
       if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
       return;
     }
-    fft_ct_first<C, P2, SLOTS, kThreads>(stage, P2, work, ld, tw);  // unused slots hold stale data
+    fft_ct_first<C, P2, SLOTS, kThreads, true>(stage, P2, work, ld, tw);  // unused slots hold stale data
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0 && c + 1 < nchunk) issue(c + 1);
-    fft_ct_rest<C, P2, SLOTS, kThreads>(work, ld, tw);
+    fft_ct_rest<C, P2, SLOTS, kThreads, true>(work, ld, tw);
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
       const int p = threadIdx.x + i * kThreads;
@@ -466,7 +464,7 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
     work[row * ld + pad8(pos)] = c_conj(zpp);
   }
   __syncthreads();
-  fft_ct<C, P2, 2, kThreads>(work, ld, tw);
+  fft_ct<C, P2, 2, kThreads, true>(work, ld, tw);
   C* dst = static_cast<C*>(P.scratch2) + od.scr2_off;
   const C* tw4 = static_cast<const C*>(od.tw4);
   for (int p = threadIdx.x; p < NP; p += kThreads) {
@@ -649,10 +647,9 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   const int ld = CT ? ct_ld(P1, ct_cols(P1)) : od.ld1;
   const int M2 = od.M2, N = od.N;
   C* buf1 = buf + W * ld;
-  C* tw = CT ? buf + W * ld : buf1 + W * ld;
+  C* tw = buf1 + W * ld;  // runtime length only: the natural table in shared memory
   const C* tw1 = static_cast<const C*>(od.tw1);
-  if constexpr (CT) ct_fill_twiddles<C, P1>(tw, tw1);
-  else
+  if constexpr (!CT)
     for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
   const C* src = static_cast<const C*>(P.scratch2) + od.scr2_off;
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
@@ -662,7 +659,8 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   __syncthreads();
   C* res;
   if constexpr (CT) {
-    fft_ct_compact<C, P1, ct_cols(P1), kThreads>(buf, ld, tw);  // one block per SM: small code
+    // one block per SM: small code, pass tables straight from global memory
+    fft_ct_compact<C, P1, ct_cols(P1), kThreads, true>(buf, ld, static_cast<const C*>(od.twg1));
     res = buf;
   } else {
     res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);

@@ -136,7 +136,7 @@ cudaError_t item_tables(sag_plan_s* pl, TwiddleCache<C>& tc, OrderDesc& od) {
   od.tw4c_p = nullptr;
   if (e == cudaSuccess && od.ct1) e = tc.get_pass(pl, od.M1, &od.twg1);
   if (e == cudaSuccess && od.pair) e = tc.get_pass(pl, 2 * od.M2, &od.tw2p);
-  if (e == cudaSuccess && od.pair) e = tc.get_pass(pl, od.M2, &od.twg2);
+  if (e == cudaSuccess && od.ct2) e = tc.get_pass(pl, od.M2, &od.twg2);
   if (e == cudaSuccess && od.pair) e = tc.get_col(pl, od.M1, 2 * od.M2, od.W, &od.tw4c_p);
   return e;
 }
@@ -416,19 +416,20 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     colpre_all.push_back(colpre_all.back() + od.nvec * od.ncolblk);
     invpre.push_back(invpre.back() + od.ncolblk);
     chainpre.push_back(chainpre.back() + (tt ? (od.M + 1 + 255) / 256 : 0));
-    // Compile-time kernels work in place (one buffer), the generic ones ping-pong.
-    // (the compile-time kernels keep one table per radix pass, ct_twp_size entries)
-    col_smem = std::max(col_smem, od.ct1 ? (size_t)(W * od.ld1 + ct_twp_size(od.M1)) * csize
+    // Compile-time kernels work in place (one buffer, pass tables in global
+    // memory), the generic ones ping-pong and keep the natural table.
+    col_smem = std::max(col_smem, od.ct1 ? (size_t)(W * od.ld1) * csize
                                          : (size_t)(2 * W * od.ld1 + od.M1) * csize);
-    // The compile-time row kernel stages its input (bulk copies, natural
-    // order) apart from the padded work area, behind one mbarrier; the
-    // runtime one ping-pongs.
-    row_smem = std::max(row_smem, od.ct2 ? (size_t)(2 * G * od.M2 + 2 * G * od.ld2 + ct_twp_size(od.M2)) *
-                                                   csize + 16
-                                         : (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize);
-    if (od.pair) {  // stage and work of 2 G' transforms of 2 M2 points (pass tables in global memory)
+    // The compile-time row kernels stage their input (bulk copies, natural
+    // order) apart from the padded work area, behind one mbarrier: 2 G
+    // transforms of M2 points, or in the pair form 2 G' transforms of 2 M2
+    // points. The runtime one ping-pongs.
+    if (od.pair) {
       const int Gp = ct_group(2 * od.M2);
       row_smem = std::max(row_smem, (size_t)(2 * Gp * 2 * od.M2 + 2 * Gp * od.ld2p) * csize + 16);
+    } else {
+      row_smem = std::max(row_smem, od.ct2 ? (size_t)(2 * G * od.M2 + 2 * G * od.ld2) * csize + 16
+                                           : (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize);
     }
     rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * G * 2 * od.ld2, 6 * od.ld2) * csize +
                                           (size_t)od.M2 * csize);

@@ -65,6 +65,12 @@ static void ct_host_passes(std::vector<C>& buf, int ld, int count, const C* tw, 
           }
           x[((size_t)b * NB + j) * R + t] = nat ? nat[src] : buf[src];
           // the compact variant's runtime maps agree with the compile-time ones
+          // (and the compact pass's global-table index: ct_twg_off(P, S) + (t - 1) Ns + j mod Ns)
+          if (R == 8 && Ns > 1 && t > 0 &&
+              ct_twg_off(P, S) + (t - 1) * Ns + (j & (Ns - 1)) != ct_twg<P, S, R, Ns>(j, t)) {
+            std::printf("runtime global map differs P=%d pass %d\n", P, S);
+            std::exit(3);
+          }
           if (R == 8 && (ct_dst8_rt(j, t, Ns) != ct_dst<P, R, Ns>(j, t) ||
                          (Ns > 1 && t > 0 && ct_twi8_rt(j, t, Ns, ct_twp_off(P, S)) != ct_twi<P, S, R, Ns>(j, t)))) {
             std::printf("runtime map differs P=%d pass %d\n", P, S);
