@@ -11,7 +11,10 @@
 // the same Stockham butterfly as the generic path (fft.cuh).
 #pragma once
 
+#include <type_traits>
+
 #include "fft.cuh"
+#include "fft_aligned.cuh"
 
 #if defined(__CUDACC__)
 #define SAG_CX __host__ __device__ constexpr
@@ -183,6 +186,21 @@ SAG_CX bool ct_supported(int P) {
          P == 768;
 }
 
+// The butterfly of a compile-time pass: inputs t >= 1 multiplied by tw(t)
+// when TW, then the radix-R DFT. Double-word radix-2/4/8 butterflies run in
+// the grid-aligned arithmetic of fft_aligned.cuh, the others in dw.cuh's.
+template <int R, bool TW, class C, class TWF>
+SAG_HD void ct_bfly(C* x, TWF tw) {
+  if constexpr (std::is_same<C, cdw>::value && (R == 2 || R == 4 || R == 8)) {
+    g_bfly<R, TW>(x, tw);
+  } else {
+    if constexpr (TW)
+#pragma unroll
+      for (int t = 1; t < R; ++t) x[t] = c_mul(x[t], tw(t));
+    dft_r<R>(x);
+  }
+}
+
 #if defined(__CUDACC__)
 // Twiddle t of butterfly j: from the shared-memory pass tables (bank layout)
 // or, GT, from the global ones (ct_twg layout, read-only path).
@@ -228,11 +246,7 @@ __device__ __forceinline__ void ct_pass(const C* src, int sld, C* dst, int dld, 
     const int w = threadIdx.x + i * T;
     if (TOT % T == 0 || w < TOT) {
       const int b = w / NB, j = w - b * NB;
-      if (Ns > 1) {
-#pragma unroll
-        for (int t = 1; t < R; ++t) x[i][t] = c_mul(x[i][t], tw_at<C, GT, P, S, R, Ns>(tw, j, t));
-      }
-      dft_r<R>(x[i]);
+      ct_bfly<R, (Ns > 1)>(x[i], [&](int t) { return tw_at<C, GT, P, S, R, Ns>(tw, j, t); });
       C* ob = dst + b * dld;
 #pragma unroll
       for (int t = 0; t < R; ++t) ob[ct_dst<P, R, Ns>(j, t)] = x[i][t];
@@ -305,13 +319,12 @@ __device__ __forceinline__ void ct_pass8_rt(C* buf, int ld, const C* tw, int Ns,
     const int w = threadIdx.x + i * T;
     if (TOT % T == 0 || w < TOT) {
       const int b = w / NB, j = w - b * NB;
-      if (Ns > 1) {
-#pragma unroll
-        for (int t = 1; t < R; ++t)
-          x[i][t] = c_mul(x[i][t], GT ? ld_ro(tw + twoff + (t - 1) * Ns + (j & (Ns - 1)))
-                                      : tw[ct_twi8_rt(j, t, Ns, twoff)]);
-      }
-      dft_r<R>(x[i]);
+      // Ns = 1 only in the first pass, which has no twiddles (ones in the tables)
+      auto twf = [&](int t) {
+        return GT ? ld_ro(tw + twoff + (t - 1) * Ns + (j & (Ns - 1))) : tw[ct_twi8_rt(j, t, Ns, twoff)];
+      };
+      if (Ns > 1) ct_bfly<R, true>(x[i], twf);
+      else ct_bfly<R, false>(x[i], twf);
       C* ob = buf + b * ld;
 #pragma unroll
       for (int t = 0; t < R; ++t) ob[ct_dst8_rt(j, t, Ns)] = x[i][t];

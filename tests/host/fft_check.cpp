@@ -80,6 +80,7 @@ static void ct_host_passes(std::vector<C>& buf, int ld, int count, const C* tw, 
     for (int b = 0; b < count; ++b)
       for (int j = 0; j < NB; ++j) {
         C* xx = &x[((size_t)b * NB + j) * R];
+        std::vector<C> w(R);
         if (Ns > 1)
           for (int t = 1; t < R; ++t) {
             const int ti = ct_twi<P, S, R, Ns>(j, t);
@@ -93,9 +94,11 @@ static void ct_host_passes(std::vector<C>& buf, int ld, int count, const C* tw, 
               std::printf("global twiddle table differs P=%d pass %d\n", P, S);
               std::exit(3);
             }
-            xx[t] = c_mul(xx[t], tw[ti]);
+            w[t] = tw[ti];
           }
-        dft_r<R>(xx);
+        // the device passes' butterfly (grid-aligned for double-word radix 2/4/8)
+        if (Ns > 1) ct_bfly<R, true>(xx, [&](int t) { return w[t]; });
+        else ct_bfly<R, false>(xx, [&](int t) { return w[t]; });
         for (int t = 0; t < R; ++t) {
           const int o = ct_dst<P, R, Ns>(j, t);
           if (o < 0 || o >= ct_span(P) || (long)b * ld + o >= (long)count * ld) {

@@ -62,5 +62,9 @@ def test_compile_time_passes_padded_layout(fft_check):
     rows = [ln.split() for ln in out if ln.startswith("ct ")]
     # column layout for every length, row-chunk and inverse layouts for powers of two
     assert len(rows) == len(CT_SIZES) + 2 * 4
+    # Double-word radix-2/4/8 butterflies of the compile-time passes round
+    # their high words to a per-butterfly grid (low words at about 2^-43 of
+    # the butterfly's largest input, against 2^-47 of each value for plain
+    # double-word operations): about 2e-13 here, against 5e-15 before.
     for _, P, count, sin, err in rows:
-        assert float(err) < 2e-14, f"length {P}, {count} transforms, natural input {sin}: {err}"
+        assert float(err) < 1e-12, f"length {P}, {count} transforms, natural input {sin}: {err}"
