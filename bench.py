@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--prec", default="both", choices=["both", "fp32_split", "fp64"],
+    ap.add_argument("--prec", default="all", choices=["all", "both", "fp32_split", "fp32_split_exact", "fp64"],
                     help="paths to run (profiling runs use one)")
     ap.add_argument("--quick", action="store_true",
                     help="timed region only: no parity check, kernel profile, e2e or CPU baseline "
@@ -286,8 +286,9 @@ def run_ours(args, world, rank, local):
     res = {}
     sampler = ClockSampler(local)
     clocks = None
-    precs = {"both": (sag.SAG_FP32_SPLIT, sag.SAG_FP64), "fp32_split": (sag.SAG_FP32_SPLIT,),
-             "fp64": (sag.SAG_FP64,)}[args.prec]
+    everything = (sag.SAG_FP32_SPLIT, sag.SAG_FP32_SPLIT_EXACT, sag.SAG_FP64)
+    precs = {"all": everything, "both": everything, "fp32_split": (sag.SAG_FP32_SPLIT,),
+             "fp32_split_exact": (sag.SAG_FP32_SPLIT_EXACT,), "fp64": (sag.SAG_FP64,)}[args.prec]
     if args.kernels:
         pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT)
         n = torch.tensor(s.n0, device="cuda")
@@ -313,8 +314,8 @@ def run_ours(args, world, rank, local):
             print(f"prec {prec}: {K / t:.1f} RK2 steps/s", file=sys.stderr)
             pl.close()
         return
-    if args.prec != "both":
-        raise SystemExit("--prec other than both needs --quick")
+    if args.prec not in ("all", "both"):
+        raise SystemExit("--prec other than all needs --quick")
     for prec in precs:
         pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, autotune=tune)
         n = torch.tensor(s.n0, device="cuda")
@@ -359,7 +360,7 @@ def run_ours(args, world, rank, local):
 
     if rank != 0:
         return
-    dw, f64 = res[sag.SAG_FP32_SPLIT], res[sag.SAG_FP64]
+    dw, dwx, f64 = res[sag.SAG_FP32_SPLIT], res[sag.SAG_FP32_SPLIT_EXACT], res[sag.SAG_FP64]
     value = K * world / dw["t"]
     # dominant kernel of the headline path and its roofline
     name, (ms, cnt) = max(dw["prof"].items(), key=lambda kv: kv[1][0])
@@ -397,8 +398,11 @@ def run_ours(args, world, rank, local):
                                          "fp64": f64["desc"]["blocks"]["fft_groups"],
                                          "chosen_by": "fixed rule" if args.no_autotune else "plan-time autotuner"}},
         "rhs_evals_per_s": max(K, 10) / dw["t_rhs"],
-        "error_vs_oracle": {"fp32_split": dw["err"], "fp64": f64["err"],
+        "error_vs_oracle": {"fp32_split": dw["err"], "fp32_split_exact": dwx["err"], "fp64": f64["err"],
                             "metric": "max|x - oracle| / (max|P| + max|Q|), one RHS at n0"},
+        "fp32_split_exact": {"value": K * world / dwx["t"], "unit": UNIT, "ms_per_step": dwx["t"] / K * 1e3,
+                             "rhs_evals_per_s": max(K, 10) / dwx["t_rhs"],
+                             "note": "every FFT butterfly in plain double-word arithmetic"},
         "fp64": {"value": K * world / f64["t"], "unit": UNIT, "ms_per_step": f64["t"] / K * 1e3,
                  "rhs_evals_per_s": max(K, 10) / f64["t_rhs"]},
         "speedup_vs_fp64": f64["t"] / dw["t"],

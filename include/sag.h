@@ -52,10 +52,18 @@ typedef enum {
 
 typedef enum { SAG_CP = 0, SAG_TT = 1 } sag_format;
 
-/* SAG_FP64: every FFT in FP64. SAG_FP32_SPLIT: FFTs in double-word FP32
- * (hi + lo pairs, about 48 bits); the loss inner products, the Runge-Kutta
- * accumulation and the diagnostics stay FP64 in both. */
-typedef enum { SAG_FP64 = 0, SAG_FP32_SPLIT = 1 } sag_precision;
+/* SAG_FP64: every FFT in FP64.
+ * SAG_FP32_SPLIT: FFTs in double-word FP32 (hi + lo pairs); the radix-2/3/4/8
+ * butterflies first round their inputs' high words to one grid per butterfly,
+ * so that their additions are exact in the high word (about 2^-43 of the
+ * butterfly's largest input per rounding; right-hand sides to about 1e-13
+ * relative in max-norm).
+ * SAG_FP32_SPLIT_EXACT: the same with every butterfly in plain double-word
+ * arithmetic (about 2^-47 per value; right-hand sides to about 1e-15), at about
+ * 20% lower throughput.
+ * The loss inner products, the Runge-Kutta accumulation and the diagnostics
+ * stay FP64 in all three. */
+typedef enum { SAG_FP64 = 0, SAG_FP32_SPLIT = 1, SAG_FP32_SPLIT_EXACT = 2 } sag_precision;
 
 /* Second-order explicit Runge-Kutta variant (Sec. 3 names the order only):
  * Heun  n+ = n + dt/2 (F(n) + F(n + dt F(n)));

@@ -110,6 +110,7 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
   a.out0 = pl->nstar;
   a.dt = dt;
   a.mode = pl->rk == SAG_HEUN ? EPI_HEUN1 : EPI_MID1;
+  a.flux = diag != nullptr;  // the outflow is only reported through diag
   sag_status s = eval(pl, n, a, st, allow_hook);
   if (s != SAG_OK) return s;
   EpiArgs b{};
@@ -119,6 +120,7 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
   b.diag = diag;
   b.dt = dt;
   b.mode = pl->rk == SAG_HEUN ? EPI_HEUN2 : EPI_MID2;
+  b.flux = a.flux;
   return eval(pl, pl->nstar, b, st, allow_hook);
 }
 
@@ -129,11 +131,19 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
 // scale 4. FP64 arithmetic: a
 // complex add 2, a complex product 4 (2 multiplies, 2 FMAs), a real times a
 // complex 2.
+// The double-word FFT butterflies of radix 2, 3, 4 and 8 run in the
+// grid-aligned arithmetic of fft_aligned.cuh instead (grid = true): rounding
+// an input's high words to the grid 8 per complex value, a twiddle product
+// rounded to the grid 24, a complex add 4, a real constant product 5; the
+// radix-2/3/4/8 DFTs then cost 8, 38, 32 and 124 (max-abs and exponent
+// operations not counted).
 struct OpCost {
   double cadd, cmul, kmul, scale;
+  bool grid;
 };
-constexpr OpCost kCostDW{16, 32, 8, 4};
-constexpr OpCost kCostF64{2, 4, 2, 2};
+constexpr OpCost kCostDW{16, 32, 8, 4, true};
+constexpr OpCost kCostDWX{16, 32, 8, 4, false};  // SAG_FP32_SPLIT_EXACT: plain double-word butterflies
+constexpr OpCost kCostF64{2, 4, 2, 2, false};
 
 double dft_ops(int R, const OpCost& c) {
   switch (R) {
@@ -149,12 +159,20 @@ double dft_ops(int R, const OpCost& c) {
 // schedule of fft_ct.cuh has the same radices in another order, hence the
 // same butterfly count; only the twiddle-free first pass differs, which is
 // ignored here).
+double bfly_ops(int R, bool twiddled, const OpCost& c) {
+  if (c.grid && R != 5) {
+    const double dft = R == 2 ? 8 : R == 3 ? 38 : R == 4 ? 32 : 124;
+    return 8 + (R - 1) * (twiddled ? 24 : 8) + dft;
+  }
+  return dft_ops(R, c) + (twiddled ? (R - 1) * c.cmul : 0.0);
+}
+
 double fft_ops(int P, const radix_plan& rp, const OpCost& c) {
   double ops = 0.0;
   int Ns = 1;
   for (int s = 0; s < rp.n; ++s) {
     const int R = rp.r[s];
-    ops += (double)(P / R) * (dft_ops(R, c) + (Ns > 1 ? (R - 1) * c.cmul : 0.0));
+    ops += (double)(P / R) * bfly_ops(R, Ns > 1, c);
     Ns *= R;
   }
   return ops;
@@ -228,6 +246,7 @@ sag_status sag_rhs_parts(sag_plan_t pl, const double* n, double* p, double* q, d
   a.pout = ph ? pl->stage_b : p;
   a.qout = qh ? pl->stage_c : q;
   a.outflow_out = outflow ? (oh ? pl->dev_outflow : outflow) : nullptr;
+  a.flux = outflow != nullptr;
   sag_status s = eval(pl, nd, a, st);
   if (s != SAG_OK) return s;
   if (ph && (e = cudaMemcpyAsync(p, pl->stage_b, nb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -610,7 +629,7 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
   if (!pl || !ops || !ops_fp64 || !bytes) return fail(SAG_EINVAL, "NULL argument");
   if (id < 0 || id >= KID_COUNT) return fail(SAG_EINVAL, "kernel id out of range");
   const bool dwp = pl->P.dwpath != 0;
-  const OpCost& c = dwp ? kCostDW : kCostF64;
+  const OpCost& c = dwp ? (pl->P.exact ? kCostDWX : kCostDW) : kCostF64;
   const double Nt = (double)pl->Ntot, V = pl->P.Vtot;
   const double load_mul = dwp ? 4.0 : 1.0;  // a = U n: dw_mul or one FP64 multiply
   double o = 0.0, b = 0.0;
@@ -710,7 +729,7 @@ sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
   };
   std::string js = "{\"B\": " + std::to_string(P.B) + ", \"Ntot\": " + std::to_string(pl->Ntot) +
                    ", \"format\": \"" + (pl->fmt == SAG_TT ? "tt" : "cp") + "\", \"precision\": \"" +
-                   (P.dwpath ? "fp32_split" : "fp64") + "\", \"vectors\": " + std::to_string(P.Vtot) +
+                   (P.dwpath ? (P.exact ? "fp32_split_exact" : "fp32_split") : "fp64") + "\", \"vectors\": " + std::to_string(P.Vtot) +
                    ", \"orders\": [";
   const size_t shown = std::min<size_t>(pl->items.size(), 16);
   for (size_t i = 0; i < shown; ++i) {

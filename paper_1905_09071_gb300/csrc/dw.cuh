@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #if defined(__CUDA_ARCH__)
 #define SAG_HD __host__ __device__ __forceinline__
 #define F_ADD(a, b) __fadd_rn((a), (b))
@@ -54,6 +56,21 @@ struct dw {
 struct __align__(16) cdw {
   float rh, rl, ih, il;  // re = rh + rl, im = ih + il
 };
+
+// The same double-word complex value for the path whose FFT butterflies all
+// run in the double-word operations below (cdw's radix-2/3/4/8 butterflies are
+// grid-aligned, fft_aligned.cuh). A distinct type so that the two paths'
+// kernels are distinct instantiations; every cdw operation applies to it and
+// converts back.
+struct __align__(16) cdwx : cdw {
+  cdwx() = default;
+  SAG_HD cdwx(const cdw& a) : cdw(a) {}
+};
+static_assert(sizeof(cdwx) == sizeof(cdw), "cdwx shares cdw's layout");
+
+template <class C> struct is_dw : std::false_type {};
+template <> struct is_dw<cdw> : std::true_type {};
+template <> struct is_dw<cdwx> : std::true_type {};
 
 struct __align__(16) cd {
   double re, im;
@@ -162,6 +179,7 @@ SAG_HD cd c_mul(cd a, cd b) {
 // Real scalar of each complex type, and conversions from FP64.
 template <class C> struct real_of;
 template <> struct real_of<cdw> { using type = dw; };
+template <> struct real_of<cdwx> { using type = dw; };
 template <> struct real_of<cd> { using type = double; };
 
 SAG_HD void from_double(double x, dw& out) { out = dw_from_double(x); }

@@ -13,6 +13,8 @@
 // from one table of P entries.
 #pragma once
 
+#include <type_traits>
+
 #include "dw.cuh"
 
 namespace sag {
@@ -110,8 +112,16 @@ SAG_HD void dft_r(C* x) {
   else dft8(x);
 }
 
+}  // namespace sag
+
+#include "fft_aligned.cuh"
+
+namespace sag {
+
 // One Stockham butterfly: transform-local index j of a length-P transform,
 // pass radix R, span Ns. `in` and `out` point at the transform's first element.
+// Double-word radix-2/3/4/8 butterflies run in grid-aligned arithmetic
+// (fft_aligned.cuh).
 template <int R, class C>
 SAG_HD void stockham_bfly(const C* in, C* out, int P, int Ns, int j, const C* tw) {
   const int stride = P / R;
@@ -120,11 +130,17 @@ SAG_HD void stockham_bfly(const C* in, C* out, int P, int Ns, int j, const C* tw
   C x[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) x[t] = in[j + t * stride];
-  if (Ns > 1) {
+  if constexpr (std::is_same<C, cdw>::value && g_radix<R>()) {
+    auto twf = [&](int t) { return tw[t * k * twstep]; };
+    if (Ns > 1) g_bfly<R, true>(x, twf);
+    else g_bfly<R, false>(x, twf);
+  } else {
+    if (Ns > 1) {
 #pragma unroll
-    for (int t = 1; t < R; ++t) x[t] = c_mul(x[t], tw[t * k * twstep]);
+      for (int t = 1; t < R; ++t) x[t] = c_mul(x[t], tw[t * k * twstep]);
+    }
+    dft_r<R>(x);
   }
-  dft_r<R>(x);
   const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
   for (int t = 0; t < R; ++t) out[base + t * Ns] = x[t];

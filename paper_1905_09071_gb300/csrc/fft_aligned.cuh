@@ -1,5 +1,5 @@
-// Grid-aligned double-word butterflies (radix 2, 4 and 8) for the
-// compile-time FFT passes.
+// Grid-aligned double-word butterflies (radix 2, 3, 4 and 8) for the FFT
+// passes.
 //
 // Most of a double-word butterfly's work is additions, and an error-free
 // double-word addition costs eight float operations (TwoSum on the high words,
@@ -15,7 +15,8 @@
 // adds at most R of them, so every intermediate and output component stays
 // below 8 sqrt2 2^(e+1) < 2^(e+5). With q = 2^(e-19), every multiple of q below
 // 2^24 q = 2^(e+5) is a float, so sums and differences of grid values are
-// exact. A value v with |v| <= 2^22 q is rounded to the grid by one addition of
+// exact. (Radix 3 also halves a sum, exactly, onto the grid q/2; its values
+// stay below 3 sqrt2 2^(e+1) < 2^(e+4) = 2^24 q/2.) A value v with |v| <= 2^22 q is rounded to the grid by one addition of
 // the constant C = 1.5 2^23 q (v + C lies in [2^23 q, 2^24 q), whose float
 // spacing is q) and one subtraction of C; with an FMA the product x y is
 // rounded to the grid directly, and a second FMA gives its remainder
@@ -32,12 +33,14 @@
 //
 // Valid for |components| below 2^123 (the grid constant's exponent must not
 // overflow); the FFT inputs are scaled to magnitudes near 1.
+//
+// Included by fft.cuh after its small-DFT constants, which it uses.
 #pragma once
 
 #include <stdint.h>
 #include <string.h>
 
-#include "fft.cuh"
+#include "dw.cuh"
 
 namespace sag {
 
@@ -140,17 +143,27 @@ SAG_HD void g_dft4v(cdw y0, cdw y1, cdw y2, cdw y3, cdw& Y0, cdw& Y1, cdw& Y2, c
   Y3 = g_sub(s1, s3);
 }
 
-// The same splittings as dft2/dft4/dft8 of fft.cuh, on grid pairs.
+// The same splittings as dft2/dft3/dft4/dft8 of fft.cuh, on grid pairs.
 template <int R>
 SAG_HD void g_dft(cdw* x, float C) {
-  if constexpr (R == 2) {
+  if constexpr (R == 3) {
+    const cdw t1 = g_add(x[1], x[2]);
+    const cdw t2 = g_sub(x[0], c_scale2(t1, 0.5f));
+    const cdw d = g_sub(x[1], x[2]);
+    cdw t3;  // -i (x1 - x2) sqrt3/2
+    g_kmul(d.ih, d.il, K_SQRT3_2.hi, K_SQRT3_2.lo, C, t3.rh, t3.rl);
+    g_kmul(d.rh, d.rl, -K_SQRT3_2.hi, -K_SQRT3_2.lo, C, t3.ih, t3.il);
+    x[0] = g_add(x[0], t1);
+    x[1] = g_add(t2, t3);
+    x[2] = g_sub(t2, t3);
+  } else if constexpr (R == 2) {
     const cdw a = x[0], b = x[1];
     x[0] = g_add(a, b);
     x[1] = g_sub(a, b);
   } else if constexpr (R == 4) {
     g_dft4v(x[0], x[1], x[2], x[3], x[0], x[1], x[2], x[3]);
   } else {
-    static_assert(R == 8, "grid butterflies exist for radix 2, 4 and 8");
+    static_assert(R == 8, "grid butterflies exist for radix 2, 3, 4 and 8");
     const cdw a0 = g_add(x[0], x[4]), b0 = g_sub(x[0], x[4]);
     const cdw a1 = g_add(x[1], x[5]), b1 = g_rot8<false>(g_sub(x[1], x[5]), C);
     const cdw a2 = g_add(x[2], x[6]), b2 = c_mul_mi(g_sub(x[2], x[6]));
@@ -166,12 +179,16 @@ SAG_HD float g_maxabs(const cdw* x) {
   float m[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) m[t] = f_amax(x[t].rh, x[t].ih);
+  if constexpr (R == 3) return fmaxf(m[0], fmaxf(m[1], m[2]));
 #pragma unroll
   for (int w = R / 2; w >= 1; w /= 2)
 #pragma unroll
     for (int t = 0; t < w; ++t) m[t] = fmaxf(m[t], m[t + w]);
   return m[0];
 }
+
+template <int R>
+constexpr bool g_radix() { return R == 2 || R == 3 || R == 4 || R == 8; }
 
 // Radix-R butterfly: inputs t >= 1 multiplied by tw(t) when TW, then the DFT,
 // in grid arithmetic.

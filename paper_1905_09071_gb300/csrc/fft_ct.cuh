@@ -14,7 +14,6 @@
 #include <type_traits>
 
 #include "fft.cuh"
-#include "fft_aligned.cuh"
 
 #if defined(__CUDACC__)
 #define SAG_CX __host__ __device__ constexpr
@@ -187,11 +186,11 @@ SAG_CX bool ct_supported(int P) {
 }
 
 // The butterfly of a compile-time pass: inputs t >= 1 multiplied by tw(t)
-// when TW, then the radix-R DFT. Double-word radix-2/4/8 butterflies run in
+// when TW, then the radix-R DFT. Double-word radix-2/3/4/8 butterflies run in
 // the grid-aligned arithmetic of fft_aligned.cuh, the others in dw.cuh's.
 template <int R, bool TW, class C, class TWF>
 SAG_HD void ct_bfly(C* x, TWF tw) {
-  if constexpr (std::is_same<C, cdw>::value && (R == 2 || R == 4 || R == 8)) {
+  if constexpr (std::is_same<C, cdw>::value && g_radix<R>()) {
     g_bfly<R, TW>(x, tw);
   } else {
     if constexpr (TW)
@@ -204,9 +203,10 @@ SAG_HD void ct_bfly(C* x, TWF tw) {
 #if defined(__CUDACC__)
 // Twiddle t of butterfly j: from the shared-memory pass tables (bank layout)
 // or, GT, from the global ones (ct_twg layout, read-only path).
-__device__ __forceinline__ cdw ld_ro(const cdw* p) {
+template <class C, typename std::enable_if<is_dw<C>::value, int>::type = 0>
+__device__ __forceinline__ C ld_ro(const C* p) {
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-  return cdw{v.x, v.y, v.z, v.w};
+  return C(cdw{v.x, v.y, v.z, v.w});
 }
 __device__ __forceinline__ cd ld_ro(const cd* p) {
   const double2 v = __ldg(reinterpret_cast<const double2*>(p));

@@ -85,6 +85,27 @@ __device__ __forceinline__ void mirror_of(int k1, int row, int pos, int M1, int 
   }
 }
 
+// Epilogue of the compile-time column kernels: element e = c + W k1 of the
+// block's W columns times its four-step twiddle tw4c[e], stored at row k1,
+// column cb W + c of a row length `rowlen`. Each thread's W P1 / kThreads
+// twiddles are loaded together first (the FFT's registers are free by now),
+// so their L2 latency is paid once.
+template <class C, int P1>
+__device__ __forceinline__ void col_store_ct(const C* res, int ld, const C* __restrict__ tw4c, C* dst,
+                                             int rowlen, int cb) {
+  constexpr int W = ct_cols(P1), PE = W * P1 / kThreads;
+  static_assert((W * P1) % kThreads == 0, "a column block is a whole number of thread sweeps");
+  C w4[PE];
+#pragma unroll
+  for (int i = 0; i < PE; ++i) w4[i] = ld_ro(tw4c + threadIdx.x + i * kThreads);
+#pragma unroll
+  for (int i = 0; i < PE; ++i) {
+    const int e = threadIdx.x + i * kThreads;
+    const int c = e % W, k1 = e / W;
+    dst[(int64_t)k1 * rowlen + cb * W + c] = c_mul(res[c * ld + pad8(k1)], w4[i]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Forward column pass of one block: the order's vector lv (local index) into
 // spectrum slot `slot`, column block cb. P1 > 0: compile-time length, in
@@ -123,11 +144,7 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   C* dst = static_cast<C*>(P.scratch) + od.scr_off + (int64_t)slot * od.M;
   if constexpr (CT) {
     // four-step twiddles of this column block, stored in the loop's order
-    const C* tw4c = static_cast<const C*>(od.tw4c) + (int64_t)cb * W * M1;
-    for (int e = threadIdx.x; e < W * M1; e += kThreads) {
-      const int c = e % W, k1 = e / W, j2 = cb * W + c;
-      dst[(int64_t)k1 * M2 + j2] = c_mul(res[c * ld + pad8(k1)], tw4c[e]);
-    }
+    col_store_ct<C, P1>(res, ld, static_cast<const C*>(od.tw4c) + (int64_t)cb * W * M1, dst, M2, cb);
   } else {
     const C* tw4 = static_cast<const C*>(od.tw4);
     for (int e = threadIdx.x; e < W * M1; e += kThreads) {
@@ -174,11 +191,7 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
   __syncthreads();
   fft_ct<C, P1, W, kThreads, true>(buf, ld, tw);
   C* dst = static_cast<C*>(P.scratch) + od.scr_off + (int64_t)pr * 2 * od.M;
-  const C* tw4c = static_cast<const C*>(od.tw4c_p) + (int64_t)cb * W * P1;
-  for (int e = threadIdx.x; e < W * P1; e += kThreads) {
-    const int c = e % W, k1 = e / W, j2 = cb * W + c;
-    dst[(int64_t)k1 * M2p + j2] = c_mul(buf[c * ld + pad8(k1)], tw4c[e]);
-  }
+  col_store_ct<C, P1>(buf, ld, static_cast<const C*>(od.tw4c_p) + (int64_t)cb * W * P1, dst, M2p, cb);
 }
 
 template <class C>
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
   const int it = find_segment(pre, P.nitems, bid);
   const OrderDesc& od = P.ord[it];
   const int local = bid - pre[it];
-  if constexpr (std::is_same<C, cdw>::value) {
+  if constexpr (is_dw<C>::value) {
     if (!all && od.pair) {
       const int pr = local / od.ncolblk_p, cbp = local - pr * od.ncolblk_p;
       switch (od.M1) {
@@ -210,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
   }
   const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
   const int lv = (all || od.umap_off < 0) ? vloc : P.ulist[od.umap_off + vloc];
-  if constexpr (!std::is_same<C, cdw>::value) {
+  if constexpr (!is_dw<C>::value) {
     fwd_col_body<C, 0>(P, od, vloc, lv, cb, n, buf);
     return;
   }
@@ -235,7 +248,7 @@ template <class C>
 __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& od, int kp, C* buf) {
   // Positions per thread: the double-word path reaches this variant only for
   // rows of at most 128 points (the plan checks this), FP64 for up to 512.
-  constexpr int PPT = std::is_same<C, cdw>::value ? 1 : kRowPosPerThread;
+  constexpr int PPT = is_dw<C>::value ? 1 : kRowPosPerThread;
   const int d = od.d, R = od.R, M1 = od.M1, M = od.M;
   const int M2 = od.M2;
   const int ld = od.ld2;
@@ -286,7 +299,7 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
           const int q = q0 + g, r = q / d, m = q - r * d;
           const C A = unpack2(res[(g * slot_stride + row) * ld + pos],
                               res[(g * slot_stride + mrow) * ld + mpos], wL);
-          Pr[i] = (m == 0) ? A : c_mul(Pr[i], A);
+          Pr[i] = (m == 0) ? A : C(c_mul(Pr[i], A));
           if (m == d - 1) S[i] = c_add(S[i], rank_weight(Pr[i], od, r));
         }
       }
@@ -297,7 +310,7 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
         const C z0 = res[(g * slot_stride) * ld];
         const C zc = c_conj(z0);
         const C A = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));  // 2 A[M]
-        PrN = (m == 0) ? A : c_mul(PrN, A);
+        PrN = (m == 0) ? A : C(c_mul(PrN, A));
         if (m == d - 1) SN = c_add(SN, rank_weight(PrN, od, r));
       }
     }
@@ -425,7 +438,7 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
           const int q = q0 + g, r = q / d, m = q - r * d;
           const C* bg = work + 2 * g * ld;
           const C A = unpack2(bg[oa], bg[ob], wL);
-          Pr[i] = (m == 0) ? A : c_mul(Pr[i], A);
+          Pr[i] = (m == 0) ? A : C(c_mul(Pr[i], A));
           if (m == d - 1) S[i] = c_add(S[i], rank_weight(Pr[i], od, r));
         }
       }
@@ -436,7 +449,7 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
         const C z0 = work[(2 * g) * ld];
         const C zc = c_conj(z0);
         const C A = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));  // 2 A[M]
-        PrN = (m == 0) ? A : c_mul(PrN, A);
+        PrN = (m == 0) ? A : C(c_mul(PrN, A));
         if (m == d - 1) SN = c_add(SN, rank_weight(PrN, od, r));
       }
     }
@@ -534,7 +547,7 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
   }
   auto accumulate = [&](int i, const C& A, int q) {
     const int r = q / d, m = q - r * d;
-    Pr[i] = (m == 0) ? A : c_mul(Pr[i], A);
+    Pr[i] = (m == 0) ? A : C(c_mul(Pr[i], A));
     if (m == d - 1) S[i] = c_add(S[i], rank_weight(Pr[i], od, r));
   };
 
@@ -614,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ Rh
   const int j = find_segment(P.rowpre, P.nitems, bid);
   const OrderDesc& od = P.ord[P.rowperm[j]];
   const int kp = bid - P.rowpre[j];
-  if constexpr (!std::is_same<C, cdw>::value) {
+  if constexpr (!is_dw<C>::value) {
     rows_body<C>(P, od, kp, buf);
     return;
   }
@@ -685,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_col(const __grid_constant__
   const int oi = find_segment(P.invpre, P.nitems, bid);
   const OrderDesc& od = P.ord[oi];
   const int cb = bid - P.invpre[oi];
-  if constexpr (!std::is_same<C, cdw>::value) {
+  if constexpr (!is_dw<C>::value) {
     inv_col_body<C, 0>(P, od, oi, cb, buf);
     return;
   }
@@ -854,7 +867,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_tt_inv(const __grid_constant_
     int mrow, mpos;
     mirror_of(k1, row, pos, M1, M2, mrow, mpos);
     const C Sk = sS[p];
-    const C Sm = (k == 0) ? SM : c_conj(sS[mrow * M2 + mpos]);
+    const C Sm = (k == 0) ? SM : C(c_conj(sS[mrow * M2 + mpos]));
     const C zpp = c_add(c_add(Sk, Sm), c_mul_pi(c_mul(c_conj(twL[k]), c_sub(Sk, Sm))));
     bufa[row * ld + pos] = c_conj(zpp);
   }

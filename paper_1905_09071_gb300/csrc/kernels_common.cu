@@ -67,8 +67,10 @@ __global__ void k_nsplit(const __grid_constant__ RhsParams P, const double* __re
 // acc1 = sum x_i and acc2 = sum (i + 1) x_i (a running sum of running sums),
 // so t = base acc1 + 256 (acc2 - acc1) costs one FMA and one add per size.
 // Grid: (vectors, most chunks of any vector).
+// The first moments t are needed only for the outflow diagnostic (flux = 1);
+// without them the kernel does half the FP64 work.
 __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ RhsParams P,
-                                             const double* __restrict__ n) {
+                                             const double* __restrict__ n, int flux) {
   __shared__ double sh[64];
   const int v = blockIdx.x, c = blockIdx.y;
   const SysDesc s = P.sys[P.vsys[v]];
@@ -79,16 +81,20 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ RhsParams P
   const int first = k0 + threadIdx.x;
   const int cnt = first < k1 ? (k1 - first + 255) / 256 : 0;
   double acc1 = 0.0, acc2 = 0.0;
-  for (int i = cnt - 1; i >= 0; --i) {
-    const int k = first + i * 256;
-    acc1 = fma(u[k], x[k], acc1);
-    acc2 += acc1;
+  if (flux) {
+    for (int i = cnt - 1; i >= 0; --i) {
+      const int k = first + i * 256;
+      acc1 = fma(u[k], x[k], acc1);
+      acc2 += acc1;
+    }
+  } else {
+    for (int i = cnt - 1; i >= 0; --i) acc1 = fma(u[first + i * 256], x[first + i * 256], acc1);
   }
-  double acc[2] = {acc1, (double)(first + 1) * acc1 + 256.0 * (acc2 - acc1)};
+  double acc[2] = {acc1, flux ? (double)(first + 1) * acc1 + 256.0 * (acc2 - acc1) : 0.0};
   block_sum<2>(acc, sh);
   if (threadIdx.x == 0) {
     P.dot_s[(int64_t)v * P.maxdotchunk + c] = acc[0];
-    P.dot_t[(int64_t)v * P.maxdotchunk + c] = acc[1];
+    if (flux) P.dot_t[(int64_t)v * P.maxdotchunk + c] = acc[1];
   }
 }
 
@@ -100,8 +106,9 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ RhsParams P
 //   coef_v = -1/(d-1)! w_l (e_0 M_1 ... M_{l-1})[a] (M_{l+1} ... M_d e_0)[b],
 //   w_l = 1/d (symmetrised) or [l = d] (last mode).
 // gflux = sum_d 1/d! sum_{i in [1,N]^d} |i| C_i prod n: the same products with
-// one s replaced by the first moment t.
-__global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams P) {
+// one s replaced by the first moment t (only with flux = 1; else t = 0 and
+// gflux = 0, and the outflow derived from it is not meaningful).
+__global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams P, int flux) {
   extern __shared__ double csh[];  // [vectors of the system] s, then t
   __shared__ double red[32];
   const int b = blockIdx.x;
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
     double a = 0.0, c2 = 0.0;
     for (int c = 0; c < nc; ++c) {
       a += P.dot_s[base + c];
-      c2 += P.dot_t[base + c];
+      if (flux) c2 += P.dot_t[base + c];
     }
     s[i] = a;
     t[i] = c2;
@@ -365,9 +372,9 @@ cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* n
     if ((e = cudaStreamWaitEvent(ds, side->fork, 0)) != cudaSuccess) return e;
   }
   if (hook) hook->mark(KID_DOT, st);
-  k_dot<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, ds>>>(P, nin);
+  k_dot<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, ds>>>(P, nin, A.flux);
   if (hook) hook->mark(KID_COEF, st);
-  k_coef<<<P.B, 256, L.coef_smem, ds>>>(P);
+  k_coef<<<P.B, 256, L.coef_smem, ds>>>(P, A.flux);
   if (hook) hook->mark(KID_QTERM, st);
   k_qterm<<<L.epi_blocks, 256, L.epi_smem, ds>>>(P, nin);
   if (fork && (e = cudaEventRecord(side->join, ds)) != cudaSuccess) return e;

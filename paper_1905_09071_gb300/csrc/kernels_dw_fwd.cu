@@ -1,18 +1,23 @@
-// k_fwd_col for the double-word FP32 path (own translation unit: the
-// compile-time length variants make it the slowest file to compile).
+// k_fwd_col for a double-word FP32 path (own translation unit: the
+// compile-time length variants make it the slowest file to compile). The
+// element type is SAG_DW_C: cdw here, cdwx in kernels_dwx_fwd.cu.
 #include "fft_kernels.cuh"
 #include "launch.h"
+
+#ifndef SAG_DW_C
+#define SAG_DW_C cdw
+#endif
 
 namespace sag {
 
 cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                                int base, int blocks, int all) {
-  if (blocks > 0) k_fwd_col<cdw><<<blocks, kThreads, L.col_smem, st>>>(P, nin, base, all);
+                                int base, int blocks, int all, SAG_DW_C) {
+  if (blocks > 0) k_fwd_col<SAG_DW_C><<<blocks, kThreads, L.col_smem, st>>>(P, nin, base, all);
   return cudaGetLastError();
 }
 
-cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L) {
-  return allow_max_smem(k_fwd_col<cdw>);
+cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L, SAG_DW_C) {
+  return allow_max_smem(k_fwd_col<SAG_DW_C>);
 }
 
 }  // namespace sag

@@ -1,17 +1,23 @@
-// k_rows for the double-word FP32 path (own translation unit: the
-// compile-time length variants make it the slowest file to compile).
+// k_rows for a double-word FP32 path (own translation unit: the
+// compile-time length variants make it the slowest file to compile). The
+// element type is SAG_DW_C: cdw here, cdwx in kernels_dwx_rows.cu.
 #include "fft_kernels.cuh"
 #include "launch.h"
 
+#ifndef SAG_DW_C
+#define SAG_DW_C cdw
+#endif
+
 namespace sag {
 
-cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, int base, int blocks) {
-  if (blocks > 0) k_rows<cdw><<<blocks, kThreads, L.row_smem, st>>>(P, base);
+cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, int base, int blocks,
+                             SAG_DW_C) {
+  if (blocks > 0) k_rows<SAG_DW_C><<<blocks, kThreads, L.row_smem, st>>>(P, base);
   return cudaGetLastError();
 }
 
-cudaError_t setup_k_rows_dw(const LaunchCfg& L) {
-  return allow_max_smem(k_rows<cdw>);
+cudaError_t setup_k_rows_dw(const LaunchCfg& L, SAG_DW_C) {
+  return allow_max_smem(k_rows<SAG_DW_C>);
 }
 
 }  // namespace sag

@@ -1,0 +1,4 @@
+// The plain double-word path's instantiation of kernels_dw_inv.cu (element
+// type cdwx: every FFT butterfly in dw.cuh arithmetic).
+#define SAG_DW_C cdwx
+#include "kernels_dw_inv.cu"

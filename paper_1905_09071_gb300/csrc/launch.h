@@ -31,6 +31,7 @@ struct EpiArgs {
   double* part;         // [epi_blocks][4] block partials
   double dt;
   int mode;
+  int flux;             // 1: compute the outflow (diag or outflow_out wanted)
 };
 
 // Kernel ids for profiling (order of sag_kernel_name).
@@ -108,9 +109,31 @@ cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n,
 cudaError_t enqueue_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n,
                           cudaStream_t st);
 cudaError_t setup_vjp_common(const LaunchCfg& L);
-cudaError_t setup_vjp_fft_dw(const LaunchCfg& L);
 cudaError_t setup_vjp_fft_f64(const LaunchCfg& L);
 cudaError_t setup_fft_kernels_f64(const LaunchCfg& L);
+// Both double-word paths' FFT and adjoint kernels.
 cudaError_t setup_fft_kernels_dw(const LaunchCfg& L);
+
+// Double-word kernels per element type: cdw (grid-aligned butterflies,
+// kernels_dw_*.cu) and cdwx (plain double-word, kernels_dwx_*.cu); the last
+// argument only selects the type.
+#define SAG_DW_DECLS(C)                                                                                    \
+  cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st, \
+                                  int base, int blocks, int all, C);                                     \
+  cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, int base, int blocks, \
+                               C);                                                                       \
+  cudaError_t launch_k_inv_col_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, int base,        \
+                                  int blocks, C);                                                        \
+  cudaError_t launch_tt_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, LaunchHook* hook, C);  \
+  cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,  \
+                                cudaStream_t st, C);                                                     \
+  cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L, C);                                                 \
+  cudaError_t setup_k_rows_dw(const LaunchCfg& L, C);                                                    \
+  cudaError_t setup_k_inv_col_dw(const LaunchCfg& L, C);                                                 \
+  cudaError_t setup_tt_dw(const LaunchCfg& L, C);                                                        \
+  cudaError_t setup_vjp_fft_dw(const LaunchCfg& L, C);
+SAG_DW_DECLS(cdw)
+SAG_DW_DECLS(cdwx)
+#undef SAG_DW_DECLS
 
 }  // namespace sag

@@ -108,6 +108,7 @@ enum EpiMode : int {
 
 struct RhsParams {
   int B, nitems, Vtot, sym, dwpath;
+  int exact;                     // double-word path with plain double-word butterflies (cdwx)
   int64_t Ntot;                  // packed state length
   int tt_rmax;                   // largest TT rank of the plan (chain kernel variant)
   long long spin_limit;          // clock cycles a bounded device-side wait may take

@@ -162,7 +162,8 @@ sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options&
   if (!sys) return fail(SAG_EINVAL, "sys is NULL");
   if (B < 1) return fail(SAG_EINVAL, "B must be >= 1");
   if (B > 65535) return fail(SAG_EINVAL, "B must be <= 65535");
-  if (opt.prec != SAG_FP64 && opt.prec != SAG_FP32_SPLIT) return fail(SAG_EINVAL, "unknown precision");
+  if (opt.prec != SAG_FP64 && opt.prec != SAG_FP32_SPLIT && opt.prec != SAG_FP32_SPLIT_EXACT)
+    return fail(SAG_EINVAL, "unknown precision");
   if (opt.rk != SAG_HEUN && opt.rk != SAG_MIDPOINT) return fail(SAG_EINVAL, "unknown RK2 variant");
   if (opt.symmetrize_q != 0 && opt.symmetrize_q != 1) return fail(SAG_EINVAL, "symmetrize_q must be 0 or 1");
   for (int b = 0; b < B; ++b) {
@@ -197,7 +198,7 @@ sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options&
 }
 
 sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, sag_plan_s* pl) {
-  const bool dwp = opt.prec == SAG_FP32_SPLIT;
+  const bool dwp = opt.prec == SAG_FP32_SPLIT || opt.prec == SAG_FP32_SPLIT_EXACT;
   const bool tt = sys[0].fmt == SAG_TT;
   const size_t csize = dwp ? sizeof(cdw) : sizeof(cd);
   pl->B = B;
@@ -209,6 +210,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   P.B = B;
   P.sym = opt.symmetrize_q;
   P.dwpath = dwp ? 1 : 0;
+  P.exact = opt.prec == SAG_FP32_SPLIT_EXACT ? 1 : 0;
   P.spin_limit = 4000000000LL;  // about 2 s at the maximum SM clock
   P.dotchunk = 8192;
 
@@ -637,7 +639,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   e = setup_common_kernels(L);
   if (e == cudaSuccess) e = dwp ? setup_fft_kernels_dw(L) : setup_fft_kernels_f64(L);
   if (e == cudaSuccess) e = setup_vjp_common(L);
-  if (e == cudaSuccess) e = dwp ? setup_vjp_fft_dw(L) : setup_vjp_fft_f64(L);
+  if (e == cudaSuccess && !dwp) e = setup_vjp_fft_f64(L);  // the dw paths' are in setup_fft_kernels_dw
   if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
   if ((e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&pl->side.stream, cudaStreamNonBlocking)) != cudaSuccess ||

@@ -18,7 +18,7 @@ from . import build as _build
 
 SAG_OK, SAG_EINVAL, SAG_ENOMEM, SAG_ECUDA, SAG_EUNSUPPORTED, SAG_ETIMEOUT, SAG_ENONFINITE = range(7)
 SAG_CP, SAG_TT = 0, 1
-SAG_FP64, SAG_FP32_SPLIT = 0, 1
+SAG_FP64, SAG_FP32_SPLIT, SAG_FP32_SPLIT_EXACT = 0, 1, 2
 SAG_HEUN, SAG_MIDPOINT = 0, 1
 
 # Every function include/sag.h declares.

@@ -24,7 +24,8 @@ sys.path.insert(0, ROOT)
 import oracle  # noqa: E402
 from paper_1905_09071_gb300 import sag, workloads as wl  # noqa: E402
 
-PRECS = (("fp64", sag.SAG_FP64), ("fp32_split", sag.SAG_FP32_SPLIT))
+PRECS = (("fp64", sag.SAG_FP64), ("fp32_split", sag.SAG_FP32_SPLIT),
+         ("fp32_split_exact", sag.SAG_FP32_SPLIT_EXACT))
 
 
 def dev(x):

@@ -63,6 +63,7 @@ def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=
     (dict(factors=False), sag.SAG_EINVAL),
     (dict(out=False), sag.SAG_EINVAL),
     (dict(opt=(9, 0, 1, 0)), sag.SAG_EINVAL),
+    (dict(opt=(3, 0, 1, 0)), sag.SAG_EINVAL),  # precisions are 0, 1 and 2
     (dict(opt=(0, 4, 1, 0)), sag.SAG_EINVAL),
     (dict(opt=(0, 0, 2, 0)), sag.SAG_EINVAL),
 ])

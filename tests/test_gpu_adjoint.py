@@ -11,9 +11,9 @@ from paper_1905_09071_gb300 import sag, workloads as wl
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRECS = [sag.SAG_FP64, sag.SAG_FP32_SPLIT]
+PRECS = [sag.SAG_FP64, sag.SAG_FP32_SPLIT, sag.SAG_FP32_SPLIT_EXACT]
 # relative max-norm tolerances of cotangents
-TOL = {sag.SAG_FP64: 1e-11, sag.SAG_FP32_SPLIT: 1e-9}
+TOL = {sag.SAG_FP64: 1e-11, sag.SAG_FP32_SPLIT: 1e-9, sag.SAG_FP32_SPLIT_EXACT: 1e-11}
 
 
 @pytest.fixture(scope="module", autouse=True)

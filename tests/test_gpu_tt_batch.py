@@ -14,8 +14,8 @@ from paper_1905_09071_gb300 import sag, workloads as wl
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {sag.SAG_FP64: 1e-12, sag.SAG_FP32_SPLIT: 1e-10}
-PRECS = [sag.SAG_FP64, sag.SAG_FP32_SPLIT]
+TOL = {sag.SAG_FP64: 1e-12, sag.SAG_FP32_SPLIT: 1e-10, sag.SAG_FP32_SPLIT_EXACT: 1e-12}
+PRECS = [sag.SAG_FP64, sag.SAG_FP32_SPLIT, sag.SAG_FP32_SPLIT_EXACT]
 FMT = {"cp": sag.SAG_CP, "tt": sag.SAG_TT}
 OFMT = {"cp": oracle.CP, "tt": oracle.TT}
 
