@@ -57,10 +57,12 @@ def parse():
                          "prints the per-kernel table to stderr, no JSON line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plans with the fixed launch rules instead of the plan-time autotuner")
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "batched", "paper"],
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "batched", "paper", "adjoint"],
                     help="batched: 256 independent systems in one plan vs a loop of plans; "
                          "paper: the shape of the paper's experiment (pure ternary Brownian "
-                         "kernel, N = 2^19, TT and CP forms, 100 RK2 steps)")
+                         "kernel, N = 2^19, TT and CP forms, 100 RK2 steps); "
+                         "adjoint: the kernel-fitting gradient (D=3, N=8192, CP rank 9, 200 Heun "
+                         "steps, checkpoints every 20) against the forward run")
     ap.add_argument("--systems", type=int, default=256)
     return ap.parse_args()
 
@@ -527,6 +529,72 @@ def run_paper(args, world, rank, local):
     print(json.dumps(out), flush=True)
 
 
+def run_adjoint(args, world, rank, local):
+    """The kernel-fitting problem's gradient: loss ||n(T) - n_target||^2 after
+    200 Heun steps of dt 1e-3 (D = 3, N = 8192, CP rank 9 per order), its
+    gradient with respect to n0 and every factor by the discrete adjoint with
+    checkpoints every 20 steps (sag_integrate_vjp), timed against the forward
+    integration alone, in each precision."""
+    import torch
+    from paper_1905_09071_gb300 import sag, workloads as wl
+    torch.cuda.set_device(local)
+    p = wl.adjoint_fit_problem()
+    D, N, ranks, dt, steps, ckpt = p["D"], p["N"], p["ranks"], p["dt"], p["steps"], p["ckpt"]
+    reps, W = max(1, min(args.steps, 10)), max(args.warmup, 1)
+    with sag.Plan(N, D, ranks, p["target_factors"], prec=sag.SAG_FP64) as tp:
+        nt = torch.tensor(p["n0"], device="cuda")
+        tp.integrate(nt, dt, steps)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for pname, prec in (("fp32_split", sag.SAG_FP32_SPLIT), ("fp32_split_exact", sag.SAG_FP32_SPLIT_EXACT),
+                        ("fp64", sag.SAG_FP64)):
+        with sag.Plan(N, D, ranks, p["factors0"], prec=prec) as pl:
+            n0 = torch.tensor(p["n0"], device="cuda")
+            n = n0.clone()
+            pl.integrate(n, dt, steps)
+            g = 2.0 * (n - nt)
+            gn = torch.empty_like(n0)
+            gU = torch.empty(p["factors0"].size, dtype=torch.float64, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(W):
+                pl.integrate_vjp(n0, dt, steps, g, gn, gU, ckpt=ckpt)
+            barrier(world)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                pl.integrate_vjp(n0, dt, steps, g, gn, gU, ckpt=ckpt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_vjp = max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps, world)
+            x = n0.clone()
+            pl.integrate(x, dt, steps)
+            barrier(world)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                x.copy_(n0)
+                pl.integrate(x, dt, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_fwd = max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps, world)
+            assert pl.sync_status() == sag.SAG_OK
+            res[pname] = {"gradients_per_s": world / t_vjp, "ms_per_gradient": t_vjp * 1e3,
+                          "ms_forward_200_steps": t_fwd * 1e3, "gradient_over_forward": t_vjp / t_fwd,
+                          "grad_norm_n0": float(torch.linalg.norm(gn)),
+                          "grad_norm_factors": float(torch.linalg.norm(gU))}
+    if rank != 0:
+        return
+    out = {"metric": "adjoint: loss gradients/s (D=3, N=8192, CP rank 9, 200 Heun steps, checkpoints every 20)",
+           "value": res["fp32_split"]["gradients_per_s"], "unit": "gradients/s", "n_gpus": world,
+           "steps": reps, "warmup": W, "higher_is_better": True, "scaling": "weak", "data": "synthetic",
+           "config": {"workload": "adjoint_fit_problem: Brownian CP padded to rank 9, FP32-rounded initial "
+                                  "factors, target from factors scaled by 1 + 0.05 N(0,1), n_k ~ exp(-k), "
+                                  "Heun dt=1e-3; gradient of ||n(T) - n_target||^2 with respect to n0 and "
+                                  "every factor (sag_integrate_vjp, recomputation from checkpoints)"},
+           "runs": res}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -538,6 +606,8 @@ def main():
         run_batched(args, world, rank, local)
     elif args.workload == "paper":
         run_paper(args, world, rank, local)
+    elif args.workload == "adjoint":
+        run_adjoint(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

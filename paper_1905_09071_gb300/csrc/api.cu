@@ -75,7 +75,8 @@ template <class F>
 sag_status replay(sag_plan_t pl, const sag_plan_s::GraphKey& k, cudaStream_t st, F enqueue) {
   cudaGraphExec_t x = nullptr;
   for (auto& it : pl->gcache)
-    if (it.first.kind == k.kind && it.first.p0 == k.p0 && it.first.p1 == k.p1 && it.first.dt == k.dt)
+    if (it.first.kind == k.kind && it.first.p0 == k.p0 && it.first.p1 == k.p1 && it.first.dt == k.dt &&
+        it.first.p2 == k.p2 && it.first.i0 == k.i0)
       x = it.second;
   cudaError_t e;
   if (!x) {
@@ -92,7 +93,7 @@ sag_status replay(sag_plan_t pl, const sag_plan_s::GraphKey& k, cudaStream_t st,
     e = cudaGraphInstantiate(&x, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-    if (pl->gcache.size() >= 4) {
+    if (pl->gcache.size() >= 8) {
       cudaGraphExecDestroy(pl->gcache.front().second);
       pl->gcache.erase(pl->gcache.begin());
     }
@@ -497,13 +498,29 @@ sag_status sag_integrate_vjp(sag_plan_t pl, const double* n0, double dt, int64_t
   double* gud;
   if ((s = stage(pl, g_U, (size_t)pl->nfactor, false, &gud, &pl->stage_g, &pl->stage_g_len, st)) != SAG_OK)
     return s;
+  // Each phase of a segment (its forward steps, the recomputation of its
+  // states, its reverse steps) runs as one cached CUDA graph: the buffers are
+  // the same for every segment of a given length, only the checkpoint copies
+  // between phases differ. With per-kernel profiling on, kernels launch
+  // directly.
+  auto phase = [&](int kind, const void* p, int64_t len, auto&& body) -> sag_status {
+    if (pl->prof) return body(st);
+    return replay(pl, {kind, p, gud, dt, seg, len * 65536 + ckpt}, st, body);
+  };
   // Forward sweep, keeping the state at the start of every segment.
   if ((e = cudaMemcpyAsync(x, n0, nb, in_kind, st)) != cudaSuccess) return cuda_fail(e, "copy n0");
-  for (int64_t t = 0; t < steps; ++t) {
-    if (t % ckpt == 0 && (e = cudaMemcpyAsync(ck + (size_t)(t / ckpt) * Nt, x, nb, cudaMemcpyDeviceToDevice,
-                                              st)) != cudaSuccess)
+  for (int64_t c = 0; c < nck && steps > 0; ++c) {
+    const int64_t len = std::min<int64_t>(ckpt, steps - c * ckpt);
+    if ((e = cudaMemcpyAsync(ck + (size_t)c * Nt, x, nb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "checkpoint");
-    if ((s = enqueue_step(pl, x, dt, nullptr, st, false)) != SAG_OK) return s;
+    s = phase(3, x, len, [&](cudaStream_t cs) -> sag_status {
+      for (int64_t t = 0; t < len; ++t) {
+        sag_status r = enqueue_step(pl, x, dt, nullptr, cs, false);
+        if (r != SAG_OK) return r;
+      }
+      return SAG_OK;
+    });
+    if (s != SAG_OK) return s;
   }
   // Reverse sweep: recompute each segment's states, then step backwards.
   const cudaMemcpyKind g_kind = is_device_ptr(g_final) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -515,33 +532,46 @@ sag_status sag_integrate_vjp(sag_plan_t pl, const double* n0, double dt, int64_t
   const double w1 = heun ? 0.5 * dt : 0.0;  // weight of k1 in the update
   const double w2 = heun ? 0.5 * dt : dt;   // weight of k2 in the update
   for (int64_t c = nck - 1; c >= 0 && steps > 0; --c) {
-    const int64_t t0 = c * ckpt, t1 = std::min<int64_t>(t0 + ckpt, steps);
+    const int64_t t0 = c * ckpt, len = std::min<int64_t>(ckpt, steps - t0);
     if ((e = cudaMemcpyAsync(seg, ck + (size_t)c * Nt, nb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "restore");
-    for (int64_t t = t0; t + 1 < t1; ++t) {
-      double* cur = seg + (size_t)(t - t0) * Nt;
-      double* nxt = cur + Nt;
-      if ((e = cudaMemcpyAsync(nxt, cur, nb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-        return cuda_fail(e, "recompute");
-      if ((s = enqueue_step(pl, nxt, dt, nullptr, st, false)) != SAG_OK) return s;
+    if (len > 1) {
+      s = phase(4, seg, len, [&](cudaStream_t cs) -> sag_status {
+        for (int64_t t = 0; t + 1 < len; ++t) {
+          double* cur = seg + (size_t)t * Nt;
+          double* nxt = cur + Nt;
+          cudaError_t r = cudaMemcpyAsync(nxt, cur, nb, cudaMemcpyDeviceToDevice, cs);
+          if (r != cudaSuccess) return cuda_fail(r, "recompute");
+          sag_status q = enqueue_step(pl, nxt, dt, nullptr, cs, false);
+          if (q != SAG_OK) return q;
+        }
+        return SAG_OK;
+      });
+      if (s != SAG_OK) return s;
     }
-    for (int64_t t = t1 - 1; t >= t0; --t) {
-      double* n = seg + (size_t)(t - t0) * Nt;
-      EpiArgs a{};
-      a.nin = n;
-      a.k1buf = pl->k1buf;
-      a.out0 = pl->nstar;
-      a.dt = dt;
-      a.mode = heun ? EPI_HEUN1 : EPI_MID1;
-      if ((s = eval(pl, n, a, st, false)) != SAG_OK) return s;  // n* of this step
-      if ((e = enqueue_axpby(gk, w2, gbar, 0.0, nullptr, (int64_t)Nt, st)) != cudaSuccess ||
-          (e = enqueue_vjp(pl->P, pl->L, pl->nstar, gk, gA, gud, 1, st)) != cudaSuccess ||
-          (e = enqueue_axpby(gk, w1, gbar, h1, gA, (int64_t)Nt, st)) != cudaSuccess ||
-          (e = enqueue_vjp(pl->P, pl->L, n, gk, gB, gud, 1, st)) != cudaSuccess ||
-          (e = enqueue_axpby(gbar, 1.0, gbar, 1.0, gA, (int64_t)Nt, st)) != cudaSuccess ||
-          (e = enqueue_axpby(gbar, 1.0, gbar, 1.0, gB, (int64_t)Nt, st)) != cudaSuccess)
-        return cuda_fail(e, "adjoint step");
-    }
+    s = phase(5, seg, len, [&](cudaStream_t cs) -> sag_status {
+      for (int64_t t = len - 1; t >= 0; --t) {
+        double* n = seg + (size_t)t * Nt;
+        EpiArgs a{};
+        a.nin = n;
+        a.k1buf = pl->k1buf;
+        a.out0 = pl->nstar;
+        a.dt = dt;
+        a.mode = heun ? EPI_HEUN1 : EPI_MID1;
+        sag_status q = eval(pl, n, a, cs, false);  // n* of this step
+        if (q != SAG_OK) return q;
+        cudaError_t r;
+        if ((r = enqueue_axpby(gk, w2, gbar, 0.0, nullptr, (int64_t)Nt, cs)) != cudaSuccess ||
+            (r = enqueue_vjp(pl->P, pl->L, pl->nstar, gk, gA, gud, 1, cs)) != cudaSuccess ||
+            (r = enqueue_axpby(gk, w1, gbar, h1, gA, (int64_t)Nt, cs)) != cudaSuccess ||
+            (r = enqueue_vjp(pl->P, pl->L, n, gk, gB, gud, 1, cs)) != cudaSuccess ||
+            (r = enqueue_axpby(gbar, 1.0, gbar, 1.0, gA, (int64_t)Nt, cs)) != cudaSuccess ||
+            (r = enqueue_axpby(gbar, 1.0, gbar, 1.0, gB, (int64_t)Nt, cs)) != cudaSuccess)
+          return cuda_fail(r, "adjoint step");
+      }
+      return SAG_OK;
+    });
+    if (s != SAG_OK) return s;
   }
   if (g_n0) {
     const cudaMemcpyKind out_kind = is_device_ptr(g_n0) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

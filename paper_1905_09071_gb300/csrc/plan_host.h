@@ -70,6 +70,8 @@ struct sag_plan_s {
     const void* p0;
     const void* p1;
     double dt;
+    const void* p2 = nullptr;
+    int64_t i0 = 0;
   };
   std::vector<std::pair<GraphKey, cudaGraphExec_t>> gcache;
   cudaGraphExec_t gexec = nullptr;
