@@ -112,6 +112,9 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
   a.dt = dt;
   a.mode = pl->rk == SAG_HEUN ? EPI_HEUN1 : EPI_MID1;
   a.flux = diag != nullptr;  // the outflow is only reported through diag
+  // The first stage writes n*'s double-word copy at n's scale, so the second
+  // evaluation starts at its FFTs (the scale is renewed every step).
+  a.split_next = pl->P.dwpath;
   sag_status s = eval(pl, n, a, st, allow_hook);
   if (s != SAG_OK) return s;
   EpiArgs b{};
@@ -122,6 +125,7 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
   b.dt = dt;
   b.mode = pl->rk == SAG_HEUN ? EPI_HEUN2 : EPI_MID2;
   b.flux = a.flux;
+  b.presplit = pl->P.dwpath;
   return eval(pl, pl->nstar, b, st, allow_hook);
 }
 

@@ -258,10 +258,12 @@ __global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsPar
         break;
       case EPI_HEUN1:
         A.k1buf[g] = rhs;
-        A.out0[g] = nk + A.dt * rhs;
+        nn = nk + A.dt * rhs;
+        A.out0[g] = nn;
         break;
       case EPI_MID1:
-        A.out0[g] = nk + 0.5 * A.dt * rhs;
+        nn = nk + 0.5 * A.dt * rhs;
+        A.out0[g] = nn;
         break;
       case EPI_HEUN2:
         nn = A.nbase[g] + 0.5 * A.dt * (A.k1buf[g] + rhs);
@@ -272,11 +274,23 @@ __global__ void __launch_bounds__(256) k_epilogue(const __grid_constant__ RhsPar
         A.nbase[g] = nn;
         break;
     }
+    if (A.split_next) {
+      // the stage state's double-word copy for the next evaluation, at this
+      // evaluation's scale 2^-e_n (the next one skips k_nmax and k_nsplit)
+      const dw v = dw_from_double(scalbn(nn, -P.sc[b].e_n));
+      P.ndw[sy.ndwoff + 1 + k] = make_float2(v.hi, v.lo);
+    }
     part[1] = nn;
     part[2] = size * nn;
   }
-  block_sum<3>(part, red);
   SysScalars* sc = &P.sc[b];
+  if (!A.flux) {
+    // No diagnostics or outflow wanted: no moment sums. Clear the max of n for
+    // the next evaluation's k_nmax (this evaluation's k_nsplit has run).
+    if (blk == 0 && threadIdx.x == 0) sc->nmax_bits = 0ull;
+    return;
+  }
+  block_sum<3>(part, red);
   if (threadIdx.x == 0) {
     A.part[blockIdx.x * 4 + 0] = part[0];
     A.part[blockIdx.x * 4 + 1] = part[1];
@@ -356,7 +370,7 @@ __global__ void __launch_bounds__(1024) k_moments(const __grid_constant__ RhsPar
 cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* nin,
                          const EpiArgs& A, cudaStream_t st, LaunchHook* hook, const SideStream* side,
                          const FftGroups* groups) {
-  if (P.dwpath) {
+  if (P.dwpath && !A.presplit) {
     if (hook) hook->mark(KID_NMAX, st);
     k_nmax<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, nin);
     if (hook) hook->mark(KID_NSPLIT, st);

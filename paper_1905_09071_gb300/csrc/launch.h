@@ -32,6 +32,8 @@ struct EpiArgs {
   double dt;
   int mode;
   int flux;             // 1: compute the outflow (diag or outflow_out wanted)
+  int split_next;       // first stages (double-word path): also write out0's double-word copy
+  int presplit;         // the double-word copy of nin is current: skip k_nmax and k_nsplit
 };
 
 // Kernel ids for profiling (order of sag_kernel_name).

@@ -752,12 +752,14 @@ sag_status time_step_graph(sag_plan_s* pl, float* ms) {
   a.out0 = pl->nstar;
   a.k1buf = pl->k1buf;
   a.part = pl->epi_part;
+  a.split_next = pl->P.dwpath;  // as enqueue_step does
   EpiArgs b{};
   b.mode = pl->rk == SAG_HEUN ? EPI_HEUN2 : EPI_MID2;
   b.nin = pl->nstar;
   b.nbase = pl->stage_a;
   b.k1buf = pl->k1buf;
   b.part = pl->epi_part;
+  b.presplit = pl->P.dwpath;
   cudaStream_t cs = pl->cap_stream;
   cudaGraph_t g = nullptr;
   cudaGraphExec_t x = nullptr;
