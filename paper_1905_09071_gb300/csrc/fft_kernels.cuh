@@ -194,7 +194,7 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
   col_store_ct<C, P1>(buf, ld, static_cast<const C*>(od.tw4c_p) + (int64_t)cb * W * P1, dst, M2p, cb);
 }
 
-template <class C>
+template <class C, int KIND = kKindGeneral>
 __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__ RhsParams P,
                                                       const double* __restrict__ n, int base, int all) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -204,6 +204,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
   const int it = find_segment(pre, P.nitems, bid);
   const OrderDesc& od = P.ord[it];
   const int local = bid - pre[it];
+  if constexpr (KIND >= kKindPair) {  // every block of the launch: a pair at this column length
+    const int pr = local / od.ncolblk_p, cbp = local - pr * od.ncolblk_p;
+    fwd_col_pair_body<C, ct_len(KIND - kKindPair)>(P, od, pr, cbp, buf);
+    return;
+  } else if constexpr (KIND != kKindGeneral) {  // single vectors, one length form
+    const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
+    const int lv = (all || od.umap_off < 0) ? vloc : P.ulist[od.umap_off + vloc];
+    fwd_col_body<C, KIND == kKindRuntime ? 0 : ct_len(KIND - kKindCt)>(P, od, vloc, lv, cb, n, buf);
+    return;
+  }
   if constexpr (is_dw<C>::value) {
     if (!all && od.pair) {
       const int pr = local / od.ncolblk_p, cbp = local - pr * od.ncolblk_p;
@@ -617,7 +627,7 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
   }
 }
 
-template <class C>
+template <class C, int KIND = kKindGeneral>
 __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ RhsParams P, int base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -627,6 +637,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ Rh
   const int j = find_segment(P.rowpre, P.nitems, bid);
   const OrderDesc& od = P.ord[P.rowperm[j]];
   const int kp = bid - P.rowpre[j];
+  if constexpr (KIND >= kKindPair) {
+    rows_body_pair<C, ct_len(KIND - kKindPair)>(P, od, kp, smem_raw);
+    return;
+  } else if constexpr (KIND >= kKindCt) {
+    rows_body_async<C, ct_len(KIND - kKindCt)>(P, od, kp, smem_raw);
+    return;
+  } else if constexpr (KIND == kKindRuntime) {
+    rows_body<C>(P, od, kp, buf);
+    return;
+  }
   if constexpr (!is_dw<C>::value) {
     rows_body<C>(P, od, kp, buf);
     return;
@@ -690,7 +710,7 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   }
 }
 
-template <class C>
+template <class C, int KIND = kKindGeneral>
 __global__ void __launch_bounds__(kThreads, 4) k_inv_col(const __grid_constant__ RhsParams P, int base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -698,6 +718,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_col(const __grid_constant__
   const int oi = find_segment(P.invpre, P.nitems, bid);
   const OrderDesc& od = P.ord[oi];
   const int cb = bid - P.invpre[oi];
+  if constexpr (KIND >= kKindCt) {
+    inv_col_body<C, ct_len(KIND - kKindCt)>(P, od, oi, cb, buf);
+    return;
+  } else if constexpr (KIND == kKindRuntime) {
+    inv_col_body<C, 0>(P, od, oi, cb, buf);
+    return;
+  }
   if constexpr (!is_dw<C>::value) {
     inv_col_body<C, 0>(P, od, oi, cb, buf);
     return;

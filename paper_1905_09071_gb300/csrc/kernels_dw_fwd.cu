@@ -1,6 +1,11 @@
 // k_fwd_col for a double-word FP32 path (own translation unit: the
 // compile-time length variants make it the slowest file to compile). The
-// element type is SAG_DW_C: cdw here, cdwx in kernels_dwx_fwd.cu.
+// element type is SAG_DW_C: cdw here, cdwx in kernels_dwx_fwd.cu. Each run of
+// column blocks of one specialisation (KIND, fft_ct.cuh) gets its own
+// instantiation.
+#include <array>
+#include <utility>
+
 #include "fft_kernels.cuh"
 #include "launch.h"
 
@@ -10,14 +15,48 @@
 
 namespace sag {
 
+namespace {
+
+using FwdLaunch = void (*)(const RhsParams&, const double*, int, int, int, size_t, cudaStream_t);
+using Setup = cudaError_t (*)();
+
+template <int K>
+void fwd_kind(const RhsParams& P, const double* nin, int base, int blocks, int all, size_t smem,
+              cudaStream_t st) {
+  k_fwd_col<SAG_DW_C, K><<<blocks, kThreads, smem, st>>>(P, nin, base, all);
+}
+template <int K>
+cudaError_t fwd_setup() {
+  return allow_max_smem(k_fwd_col<SAG_DW_C, K>);
+}
+template <int... K>
+constexpr std::array<FwdLaunch, sizeof...(K)> fwd_launches(std::integer_sequence<int, K...>) {
+  return {{&fwd_kind<K>...}};
+}
+template <int... K>
+constexpr std::array<Setup, sizeof...(K)> fwd_setups(std::integer_sequence<int, K...>) {
+  return {{&fwd_setup<K>...}};
+}
+constexpr auto kFwd = fwd_launches(std::make_integer_sequence<int, kKindCount>{});
+constexpr auto kFwdSetup = fwd_setups(std::make_integer_sequence<int, kKindCount>{});
+
+}  // namespace
+
 cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
                                 int base, int blocks, int all, SAG_DW_C) {
-  if (blocks > 0) k_fwd_col<SAG_DW_C><<<blocks, kThreads, L.col_smem, st>>>(P, nin, base, all);
-  return cudaGetLastError();
+  return for_kind_runs(all ? L.col_all : L.col, base, base + blocks, [&](int kind, int b0, int b1) {
+    kFwd[kind](P, nin, b0, b1 - b0, all, L.col_smem, st);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L, SAG_DW_C) {
-  return allow_max_smem(k_fwd_col<SAG_DW_C>);
+  (void)L;
+  for (Setup s : kFwdSetup) {
+    const cudaError_t e = s();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace sag

@@ -8,7 +8,16 @@
 namespace sag {
 
 // Grid and shared-memory sizes of one plan, computed once at plan time.
+// The entries of one block table (items in table order) with the kernel
+// specialisation (KIND, fft_ct.cuh) each entry's blocks run.
+struct KindTable {
+  const int* pre = nullptr;   // [n + 1] block prefix (host copy)
+  const int* kind = nullptr;  // [n] specialisation of each entry
+  int n = 0;
+};
+
 struct LaunchCfg {
+  KindTable col, col_all, row;  // forward columns (pairs or distinct vectors; every vector), rows
   int prep_blocks;
   int col_blocks, row_blocks, inv_blocks, epi_blocks;
   int col_blocks_all;  // column blocks over every vector (the adjoint's passes)
@@ -42,6 +51,40 @@ enum KernelId : int {
   KID_EPILOGUE = 6, KID_MOMENTS = 7, KID_COEF = 8, KID_ROWS_TT = 9, KID_TT_CHAIN = 10,
   KID_ROWS_TT_INV = 11, KID_QTERM = 12, KID_COUNT = 13
 };
+
+// Splits the blocks [b0, b1) of table t into runs of equal specialisation
+// and calls launch(kind, r0, r1) for each; with more than kMaxKindRuns runs
+// (a batch of systems with mixed lengths) it launches the run-time
+// dispatching kernel over the whole range instead (kind kKindGeneral).
+constexpr int kMaxKindRuns = 8;
+template <class F>
+cudaError_t for_kind_runs(const KindTable& t, int b0, int b1, F&& launch) {
+  if (b1 <= b0) return cudaSuccess;
+  int rk[kMaxKindRuns], r0[kMaxKindRuns], r1[kMaxKindRuns], nr = 0;
+  bool general = t.kind == nullptr;
+  for (int i = 0; i < t.n && !general; ++i) {
+    const int a = t.pre[i] > b0 ? t.pre[i] : b0, z = t.pre[i + 1] < b1 ? t.pre[i + 1] : b1;
+    if (a >= z) continue;
+    if (nr > 0 && rk[nr - 1] == t.kind[i] && r1[nr - 1] == a) {
+      r1[nr - 1] = z;
+      continue;
+    }
+    if (nr == kMaxKindRuns) {
+      general = true;
+      break;
+    }
+    rk[nr] = t.kind[i];
+    r0[nr] = a;
+    r1[nr] = z;
+    ++nr;
+  }
+  if (general) return launch(kKindGeneral, b0, b1);
+  for (int r = 0; r < nr; ++r) {
+    const cudaError_t e = launch(rk[r], r0[r], r1[r]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 // Optional hook called before each kernel launch (id) and once after the last
 // one (id = -1), on the launch stream.

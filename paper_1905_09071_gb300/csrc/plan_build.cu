@@ -652,7 +652,21 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   // overlap and lose a little); else one launch per kernel. With autotune the
   // plan times 1..4 groups instead.
   pl->h_colpre = colpre;
+  pl->h_colpre_all = colpre_all;
   pl->h_invpre = invpre;
+  // Kernel specialisation of each item's column blocks (the row table's
+  // follow its order, set by configure_fft_groups).
+  pl->h_colkind.resize(I.size());
+  pl->h_colkind_all.resize(I.size());
+  for (size_t i = 0; i < I.size(); ++i) {
+    const OrderDesc& od = I[i];
+    const int ct = od.ct1 ? kKindCt + ct_index(od.M1) : kKindRuntime;
+    pl->h_colkind[i] = !dwp ? kKindGeneral : od.pair ? kKindPair + ct_index(od.M1) : ct;
+    pl->h_colkind_all[i] = dwp ? ct : kKindGeneral;
+  }
+  const int ni = (int)I.size();
+  pl->L.col = KindTable{pl->h_colpre.data(), pl->h_colkind.data(), ni};
+  pl->L.col_all = KindTable{pl->h_colpre_all.data(), pl->h_colkind_all.data(), ni};
   pl->h_nrowpair.resize(I.size());
   pl->h_nvec.resize(I.size());
   pl->h_work.resize(I.size());
@@ -717,6 +731,19 @@ sag_status configure_fft_groups(sag_plan_s* pl, int G) {
       (e = cudaMemcpy((void*)P.rowpre, rowpre.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice)) !=
           cudaSuccess)
     return cuda_fail(e, "row block order");
+  // Row kernel specialisation per row-table entry (kKindGeneral for TT plans,
+  // whose rows run other kernels, and for FP64).
+  pl->h_rowperm = rowperm;
+  pl->h_rowpre = rowpre;
+  pl->h_rowkind.resize(n);
+  for (int j = 0; j < n; ++j) {
+    const OrderDesc& od = pl->items[rowperm[j]];
+    int kind = kKindGeneral;
+    if (P.dwpath && pl->fmt != SAG_TT)
+      kind = od.pair ? kKindPair + ct_index(2 * od.M2) : od.ct2 ? kKindCt + ct_index(od.M2) : kKindRuntime;
+    pl->h_rowkind[j] = kind;
+  }
+  pl->L.row = KindTable{pl->h_rowpre.data(), pl->h_rowkind.data(), n};
   pl->groups.n = 0;
   pl->fft_groups = G;
   if (G == 1) return SAG_OK;

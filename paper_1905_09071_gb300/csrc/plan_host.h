@@ -58,6 +58,8 @@ struct sag_plan_s {
   sag::FftGroups groups{};
   int fft_groups = 1;                     // stream groups of the FFT stage (1: one launch per kernel)
   std::vector<int> h_colpre, h_invpre;    // host copies of the block tables, for regrouping
+  std::vector<int> h_colpre_all, h_rowpre, h_rowperm;
+  std::vector<int> h_colkind, h_colkind_all, h_rowkind;  // kernel specialisations (LaunchCfg)
   std::vector<int> h_nrowpair;
   std::vector<double> h_work;             // FFT points per item, for balancing groups
   std::vector<int> h_nvec;                // vectors per item (row blocks go heaviest first)
