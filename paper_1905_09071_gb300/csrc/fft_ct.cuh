@@ -273,13 +273,86 @@ __device__ __forceinline__ void ct_pass(const C* src, int sld, C* dst, int dld, 
   if constexpr (TAIL) __syncthreads();
 }
 
-template <class C, int P, int COUNT, int T, int S, int Ns, bool GT = false>
+// Passes S .. END - 1 (END = -1: to the last pass), in place.
+template <class C, int P, int COUNT, int T, int S, int Ns, bool GT = false, int END = -1>
 __device__ __forceinline__ void ct_passes(C* buf, int ld, const C* tw) {
   constexpr ct_sched sc = make_ct_sched(P);
-  if constexpr (S < sc.n) {
+  constexpr int E = END < 0 ? sc.n : END;
+  if constexpr (S < E) {
     constexpr int R = sc.r[S];
     ct_pass<C, P, S, R, Ns, COUNT, T, false, true, true, GT>(buf, ld, buf, ld, tw);
-    ct_passes<C, P, COUNT, T, S + 1, Ns * R, GT>(buf, ld, tw);
+    ct_passes<C, P, COUNT, T, S + 1, Ns * R, GT, END>(buf, ld, tw);
+  }
+}
+
+// Span (product of the radices before it) of the last pass.
+SAG_CX int ct_last_ns(int P) {
+  const ct_sched sc = make_ct_sched(P);
+  int ns = 1;
+  for (int s = 0; s + 1 < sc.n; ++s) ns *= sc.r[s];
+  return ns;
+}
+
+// First and last passes with their data in global memory, for COUNT
+// transforms that sit side by side in the source and destination (the
+// columns of a column block). Thread w takes transform b = w mod COUNT and
+// butterfly j = w / COUNT, so consecutive threads touch neighbouring columns
+// (coalesced global accesses); in the padded layout this map is free of
+// bank conflicts as well.
+//
+// ct_pass_first_from: pass 0 with input element i of transform b from
+// load(b, i) (natural order), written padded to dst + b * dld; ends with a
+// barrier.
+template <class C, int P, int COUNT, int T, class LD>
+__device__ __forceinline__ void ct_pass_first_from(LD&& load, C* dst, int dld) {
+  constexpr ct_sched sc = make_ct_sched(P);
+  constexpr int R = sc.r[0];
+  constexpr int NB = P / R;
+  constexpr int TOT = NB * COUNT;
+  constexpr int PER = (TOT + T - 1) / T;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int w = threadIdx.x + i * T;
+    if (TOT % T == 0 || w < TOT) {
+      const int b = w % COUNT, j = w / COUNT;
+      C x[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) x[t] = load(b, j + t * NB);
+      ct_bfly<R, false>(x, [&](int) { return C{}; });
+      C* ob = dst + b * dld;
+#pragma unroll
+      for (int t = 0; t < R; ++t) ob[ct_dst<P, R, 1>(j, t)] = x[t];
+    }
+  }
+  __syncthreads();
+}
+
+// ct_pass_last_to: the last pass of transforms held padded at src + b * sld
+// (after the earlier passes and a barrier), output element k of transform b
+// handed to store(b, k, value); no barrier.
+template <class C, int P, int COUNT, int T, bool GT, class ST>
+__device__ __forceinline__ void ct_pass_last_to(const C* src, int sld, const C* tw, ST&& store) {
+  constexpr ct_sched sc = make_ct_sched(P);
+  constexpr int S = sc.n - 1;
+  constexpr int R = sc.r[S];
+  constexpr int Ns = ct_last_ns(P);
+  constexpr int NB = P / R;
+  constexpr int TOT = NB * COUNT;
+  constexpr int PER = (TOT + T - 1) / T;
+  static_assert(Ns == NB, "the last pass spans the whole transform");
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int w = threadIdx.x + i * T;
+    if (TOT % T == 0 || w < TOT) {
+      const int b = w % COUNT, j = w / COUNT;
+      const C* ib = src + b * sld;
+      C x[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) x[t] = ib[ct_src<P, R, false>(j, t)];
+      ct_bfly<R, (Ns > 1)>(x, [&](int t) { return tw_at<C, GT, P, S, R, Ns>(tw, j, t); });
+#pragma unroll
+      for (int t = 0; t < R; ++t) store(b, j + t * Ns, x[t]);
+    }
   }
 }
 

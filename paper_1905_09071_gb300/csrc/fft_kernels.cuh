@@ -166,32 +166,38 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
                                                   C* buf) {
   constexpr int W = ct_cols(P1);
   constexpr int ld = ct_ld(P1, W);
+  constexpr ct_sched sc = make_ct_sched(P1);
   const int M2p = 2 * od.M2, N = od.N, d = od.d, R = od.R;
   const C* tw = static_cast<const C*>(od.twg1);  // pass tables, global layout
   const int q1 = 2 * pr, q2 = q1 + 1;
   const float2* u1 = P.Udw + P.vdwoff[od.vbase + (q1 % d) * R + q1 / d];
   const float2* u2 = q2 < od.nvec ? P.Udw + P.vdwoff[od.vbase + (q2 % d) * R + q2 / d] : nullptr;
   const float2* nn = P.ndw + od.ndwoff;  // indexed by size, zero at 0
-  for (int e = threadIdx.x; e < W * P1; e += kThreads) {
-    const int c = e % W, j1 = e / W;
-    const int j = M2p * j1 + cb * W + c;
-    C z = c_zero(C{});
-    if (j <= N) {
-      const float2 nb = __ldg(nn + j), a1 = __ldg(u1 + j);
-      const dw nv{nb.x, nb.y};
-      dw im{0.f, 0.f};
-      if (u2) {
-        const float2 a2 = __ldg(u2 + j);
-        im = dw_mul(dw{a2.x, a2.y}, nv);
-      }
-      z = make_cdw(dw_mul(dw{a1.x, a1.y}, nv), im);
-    }
-    buf[c * ld + pad8(j1)] = z;
-  }
-  __syncthreads();
-  fft_ct<C, P1, W, kThreads, true>(buf, ld, tw);
+  // Pass 0 straight from the factors and n: point j1 of column c is size
+  // j = 2 M2 j1 + cb W + c, z = (u1 n, u2 n) there (zero beyond N).
+  ct_pass_first_from<C, P1, W, kThreads>(
+      [&](int c, int j1) -> C {
+        const int j = M2p * j1 + cb * W + c;
+        if (j > N) return c_zero(C{});
+        const float2 nb = __ldg(nn + j), a1 = __ldg(u1 + j);
+        const dw nv{nb.x, nb.y};
+        dw im{0.f, 0.f};
+        if (u2) {
+          const float2 a2 = __ldg(u2 + j);
+          im = dw_mul(dw{a2.x, a2.y}, nv);
+        }
+        return make_cdw(dw_mul(dw{a1.x, a1.y}, nv), im);
+      },
+      buf, ld);
+  ct_passes<C, P1, W, kThreads, 1, sc.r[0], true, sc.n - 1>(buf, ld, tw);  // middle passes, in place
+  // The last pass hands each output k1 of column c, times its four-step
+  // twiddle, straight to the workspace (row k1, column cb W + c of the
+  // M1 x 2 M2 geometry).
   C* dst = static_cast<C*>(P.scratch) + od.scr_off + (int64_t)pr * 2 * od.M;
-  col_store_ct<C, P1>(buf, ld, static_cast<const C*>(od.tw4c_p) + (int64_t)cb * W * P1, dst, M2p, cb);
+  const C* tw4c = static_cast<const C*>(od.tw4c_p) + (int64_t)cb * W * P1;
+  ct_pass_last_to<C, P1, W, kThreads, true>(buf, ld, tw, [&](int c, int k1, C v) {
+    dst[(int64_t)k1 * M2p + cb * W + c] = c_mul(v, ld_ro(tw4c + c + W * k1));
+  });
 }
 
 template <class C, int KIND = kKindGeneral>
