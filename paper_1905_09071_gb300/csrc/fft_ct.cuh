@@ -125,28 +125,6 @@ SAG_CX int ct_twi(int j, int t) {
   return ct_twp_off(P, S) + (j % Ns) * ct_twstride(R) + t - 1;
 }
 
-// The same maps with a runtime span, for radix-8 passes (Ns a power of two):
-// used by the compact variant below.
-SAG_CX int ct_dst8_rt(int j, int t, int Ns) {
-  const int k = j & (Ns - 1);
-  return pad8((j - k) * 8 + k + t * Ns);
-}
-SAG_CX int ct_twi8_rt(int j, int t, int Ns, int twoff) {
-  return twoff + (j & (Ns - 1)) * ct_twstride(8) + t - 1;
-}
-// Number of leading radix-8 passes and their total span.
-SAG_CX int ct_n8(int P) {
-  const ct_sched sc = make_ct_sched(P);
-  int n = 0;
-  while (n < sc.n && sc.r[n] == 8) ++n;
-  return n;
-}
-SAG_CX int ct_ns8(int P) {
-  int v = 1;
-  for (int s = 0; s < ct_n8(P); ++s) v *= 8;
-  return v;
-}
-
 // Pass tables in global memory (read through L1, so laid out for coalescing
 // rather than for banks): pass s >= 1 holds omega_P^(t k P / (Ns R)) at
 // ct_twg_off(P, s) + (t - 1) Ns + k, k < Ns, 1 <= t < R.
@@ -357,8 +335,9 @@ __device__ __forceinline__ void ct_pass_last_to(const C* src, int sld, const C* 
 }
 
 // COUNT length-P forward transforms in place in the padded layout; tw holds
-// the pass tables (ct_fill_twiddles); the caller has synchronised after
-// filling buf and tw; returns after a barrier.
+// the pass tables (global layout when GT, else the shared-memory layout
+// ct_twp_src describes); the caller has synchronised after filling buf;
+// returns after a barrier.
 template <class C, int P, int COUNT, int T, bool GT = false>
 __device__ __forceinline__ void fft_ct(C* buf, int ld, const C* tw) {
   static_assert(make_ct_sched(P).n > 0, "unsupported compile-time length");
@@ -382,81 +361,6 @@ __device__ __forceinline__ void fft_ct_rest(C* buf, int ld, const C* tw) {
   ct_passes<C, P, COUNT, T, 1, R, GT>(buf, ld, tw);
 }
 
-// Compact variant for kernels whose blocks each run once per SM (the cost
-// there is fetching the code, not issuing it): all radix-8 passes share one
-// pass body with the span Ns and the pass-table offset as runtime values;
-// only the radix-4/2/3 tail passes are specialised. Same arithmetic, same
-// layout, same tables as fft_ct.
-template <class C, int P, int COUNT, int T, bool GT = false>
-__device__ __forceinline__ void ct_pass8_rt(C* buf, int ld, const C* tw, int Ns, int twoff) {
-  constexpr int R = 8;
-  constexpr int NB = P / R;
-  constexpr int TOT = NB * COUNT;
-  constexpr int PER = (TOT + T - 1) / T;
-  C x[PER][R];
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int w = threadIdx.x + i * T;
-    if (TOT % T == 0 || w < TOT) {
-      const int b = w / NB, j = w - b * NB;
-      const C* ib = buf + b * ld;
-#pragma unroll
-      for (int t = 0; t < R; ++t) x[i][t] = ib[ct_src<P, R, false>(j, t)];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int w = threadIdx.x + i * T;
-    if (TOT % T == 0 || w < TOT) {
-      const int b = w / NB, j = w - b * NB;
-      // Ns = 1 only in the first pass, which has no twiddles (ones in the tables)
-      auto twf = [&](int t) {
-        return GT ? ld_ro(tw + twoff + (t - 1) * Ns + (j & (Ns - 1))) : tw[ct_twi8_rt(j, t, Ns, twoff)];
-      };
-      if (Ns > 1) ct_bfly<R, true>(x[i], twf);
-      else ct_bfly<R, false>(x[i], twf);
-      C* ob = buf + b * ld;
-#pragma unroll
-      for (int t = 0; t < R; ++t) ob[ct_dst8_rt(j, t, Ns)] = x[i][t];
-    }
-  }
-  __syncthreads();
-}
-
-template <class C, int P, int COUNT, int T, bool GT = false>
-__device__ __forceinline__ void fft_ct_compact(C* buf, int ld, const C* tw) {
-  constexpr int N8 = ct_n8(P);
-  static_assert(N8 >= 1, "compile-time lengths start with radix 8");
-  int Ns = 1;
-#pragma unroll 1
-  for (int s = 0; s < N8; ++s) {
-    ct_pass8_rt<C, P, COUNT, T, GT>(buf, ld, tw, Ns, GT ? ct_twg_off(P, s) : ct_twp_off(P, s));
-    Ns *= 8;
-  }
-  ct_passes<C, P, COUNT, T, N8, ct_ns8(P), GT>(buf, ld, tw);
-}
-
-template <class C, int P, int S, int Ns>
-__device__ __forceinline__ void ct_fill_pass(C* twp, const C* __restrict__ tw_nat) {
-  constexpr ct_sched sc = make_ct_sched(P);
-  if constexpr (S < sc.n) {
-    constexpr int R = sc.r[S], ST = ct_twstride(R), OFF = ct_twp_off(P, S);
-    for (int i = threadIdx.x; i < Ns * ST; i += blockDim.x) {
-      const int k = i / ST, t = i % ST + 1;
-      twp[OFF + i] = t < R ? tw_nat[t * k * (P / (Ns * R))] : c_zero(C{});
-    }
-    ct_fill_pass<C, P, S + 1, Ns * R>(twp, tw_nat);
-  }
-}
-
-// Fill the pass tables (ct_twp_size(P) entries, the layout ct_twp_src
-// describes) from the natural table of omega_P^e; the caller synchronises
-// before the first pass.
-template <class C, int P>
-__device__ __forceinline__ void ct_fill_twiddles(C* twp, const C* __restrict__ tw_nat) {
-  ct_fill_pass<C, P, 1, make_ct_sched(P).r[0]>(twp, tw_nat);
-}
 #endif
 
 }  // namespace sag

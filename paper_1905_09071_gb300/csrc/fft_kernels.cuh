@@ -691,25 +691,34 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
   if constexpr (!CT)
     for (int i = threadIdx.x; i < M1; i += kThreads) tw[i] = tw1[i];
   const C* src = static_cast<const C*>(P.scratch2) + od.scr2_off;
-  for (int e = threadIdx.x; e < W * M1; e += kThreads) {
-    const int c = e % W, k1 = e / W;
-    buf[c * ld + (CT ? pad8(k1) : k1)] = src[(int64_t)k1 * M2 + cb * W + c];
-  }
-  __syncthreads();
-  C* res;
-  if constexpr (CT) {
-    // one block per SM: small code, pass tables straight from global memory
-    fft_ct_compact<C, P1, ct_cols(P1), kThreads, true>(buf, ld, static_cast<const C*>(od.twg1));
-    res = buf;
-  } else {
-    res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
-  }
   const double scale = ldexp(od.pscale, P.dwpath ? od.d * P.sc[od.sys].e_n : 0);
   double* out = P.pd + od.pd_off;
+  if constexpr (CT) {
+    // First pass straight from the spectrum rows, last pass straight to the
+    // kept outputs (column c, point j1 is index j = M2 j1 + cb W + c: sizes
+    // 2 j and 2 j + 1); pass tables from global memory.
+    constexpr ct_sched sc = make_ct_sched(P1);
+    const C* twg = static_cast<const C*>(od.twg1);
+    ct_pass_first_from<C, P1, ct_cols(P1), kThreads>(
+        [&](int c, int k1) -> C { return ld_ro(src + (int64_t)k1 * M2 + cb * W + c); }, buf, ld);
+    ct_passes<C, P1, ct_cols(P1), kThreads, 1, sc.r[0], true, sc.n - 1>(buf, ld, twg);
+    ct_pass_last_to<C, P1, ct_cols(P1), kThreads, true>(buf, ld, twg, [&](int c, int j1, C w) {
+      const int k = 2 * (M2 * j1 + cb * W + c);
+      if (k >= 1 && k <= N) out[k - 1] = cre(w) * scale;
+      if (k + 1 <= N) out[k] = -cim(w) * scale;
+    });
+    return;
+  }
+  for (int e = threadIdx.x; e < W * M1; e += kThreads) {
+    const int c = e % W, k1 = e / W;
+    buf[c * ld + k1] = src[(int64_t)k1 * M2 + cb * W + c];
+  }
+  __syncthreads();
+  C* res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
-    const C w = res[c * ld + (CT ? pad8(j1) : j1)];
+    const C w = res[c * ld + j1];
     const int k = 2 * j;  // sizes k (real part) and k + 1 (minus the imaginary part)
     if (k >= 1 && k <= N) out[k - 1] = cre(w) * scale;
     if (k + 1 <= N) out[k] = -cim(w) * scale;
