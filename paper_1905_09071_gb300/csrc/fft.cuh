@@ -103,12 +103,29 @@ SAG_HD void dft5(C* x) {
   x[3] = c_sub(a2, c_mul_mi(b2));
 }
 
+// Six points by the prime-factor split 6 = 2 x 3 (no internal twiddles):
+// with n = (3 n1 + 2 n2) mod 6 the 3-point DFTs of (x0, x2, x4) and
+// (x3, x5, x1) give Y0, Y1, and X[(3 k1 + 4 k2) mod 6] = Y0[k2] +- Y1[k2].
+template <class C>
+SAG_HD void dft6(C* x) {
+  C y0[3] = {x[0], x[2], x[4]}, y1[3] = {x[3], x[5], x[1]};
+  dft3(y0);
+  dft3(y1);
+  x[0] = c_add(y0[0], y1[0]);
+  x[3] = c_sub(y0[0], y1[0]);
+  x[4] = c_add(y0[1], y1[1]);
+  x[1] = c_sub(y0[1], y1[1]);
+  x[2] = c_add(y0[2], y1[2]);
+  x[5] = c_sub(y0[2], y1[2]);
+}
+
 template <int R, class C>
 SAG_HD void dft_r(C* x) {
   if constexpr (R == 2) dft2(x);
   else if constexpr (R == 3) dft3(x);
   else if constexpr (R == 4) dft4(x);
   else if constexpr (R == 5) dft5(x);
+  else if constexpr (R == 6) dft6(x);
   else dft8(x);
 }
 

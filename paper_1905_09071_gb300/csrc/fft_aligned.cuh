@@ -1,4 +1,4 @@
-// Grid-aligned double-word butterflies (radix 2, 3, 4 and 8) for the FFT
+// Grid-aligned double-word butterflies (radix 2, 3, 4, 6 and 8) for the FFT
 // passes.
 //
 // Most of a double-word butterfly's work is additions, and an error-free
@@ -16,7 +16,9 @@
 // below 8 sqrt2 2^(e+1) < 2^(e+5). With q = 2^(e-19), every multiple of q below
 // 2^24 q = 2^(e+5) is a float, so sums and differences of grid values are
 // exact. (Radix 3 also halves a sum, exactly, onto the grid q/2; its values
-// stay below 3 sqrt2 2^(e+1) < 2^(e+4) = 2^24 q/2.) A value v with |v| <= 2^22 q is rounded to the grid by one addition of
+// stay below 3 sqrt2 2^(e+1) < 2^(e+4) = 2^24 q/2. Radix 6, two radix-3 DFTs
+// combined by sums and differences, reaches 6 sqrt2 2^(e+1) on that half
+// grid, so it rounds to the grid 2q: values below 2^24 q = 2^(e+5).) A value v with |v| <= 2^22 q is rounded to the grid by one addition of
 // the constant C = 1.5 2^23 q (v + C lies in [2^23 q, 2^24 q), whose float
 // spacing is q) and one subtraction of C; with an FMA the product x y is
 // rounded to the grid directly, and a second FMA gives its remainder
@@ -143,7 +145,7 @@ SAG_HD void g_dft4v(cdw y0, cdw y1, cdw y2, cdw y3, cdw& Y0, cdw& Y1, cdw& Y2, c
   Y3 = g_sub(s1, s3);
 }
 
-// The same splittings as dft2/dft3/dft4/dft8 of fft.cuh, on grid pairs.
+// The same splittings as dft2/dft3/dft4/dft6/dft8 of fft.cuh, on grid pairs.
 template <int R>
 SAG_HD void g_dft(cdw* x, float C) {
   if constexpr (R == 3) {
@@ -156,6 +158,16 @@ SAG_HD void g_dft(cdw* x, float C) {
     x[0] = g_add(x[0], t1);
     x[1] = g_add(t2, t3);
     x[2] = g_sub(t2, t3);
+  } else if constexpr (R == 6) {  // prime-factor split, as dft6 of fft.cuh
+    cdw y0[3] = {x[0], x[2], x[4]}, y1[3] = {x[3], x[5], x[1]};
+    g_dft<3>(y0, C);
+    g_dft<3>(y1, C);
+    x[0] = g_add(y0[0], y1[0]);
+    x[3] = g_sub(y0[0], y1[0]);
+    x[4] = g_add(y0[1], y1[1]);
+    x[1] = g_sub(y0[1], y1[1]);
+    x[2] = g_add(y0[2], y1[2]);
+    x[5] = g_sub(y0[2], y1[2]);
   } else if constexpr (R == 2) {
     const cdw a = x[0], b = x[1];
     x[0] = g_add(a, b);
@@ -163,7 +175,7 @@ SAG_HD void g_dft(cdw* x, float C) {
   } else if constexpr (R == 4) {
     g_dft4v(x[0], x[1], x[2], x[3], x[0], x[1], x[2], x[3]);
   } else {
-    static_assert(R == 8, "grid butterflies exist for radix 2, 3, 4 and 8");
+    static_assert(R == 8, "grid butterflies exist for radix 2, 3, 4, 6 and 8");
     const cdw a0 = g_add(x[0], x[4]), b0 = g_sub(x[0], x[4]);
     const cdw a1 = g_add(x[1], x[5]), b1 = g_rot8<false>(g_sub(x[1], x[5]), C);
     const cdw a2 = g_add(x[2], x[6]), b2 = c_mul_mi(g_sub(x[2], x[6]));
@@ -180,6 +192,7 @@ SAG_HD float g_maxabs(const cdw* x) {
 #pragma unroll
   for (int t = 0; t < R; ++t) m[t] = f_amax(x[t].rh, x[t].ih);
   if constexpr (R == 3) return fmaxf(m[0], fmaxf(m[1], m[2]));
+  if constexpr (R == 6) return fmaxf(fmaxf(fmaxf(m[0], m[3]), fmaxf(m[1], m[4])), fmaxf(m[2], m[5]));
 #pragma unroll
   for (int w = R / 2; w >= 1; w /= 2)
 #pragma unroll
@@ -188,13 +201,14 @@ SAG_HD float g_maxabs(const cdw* x) {
 }
 
 template <int R>
-constexpr bool g_radix() { return R == 2 || R == 3 || R == 4 || R == 8; }
+constexpr bool g_radix() { return R == 2 || R == 3 || R == 4 || R == 6 || R == 8; }
 
 // Radix-R butterfly: inputs t >= 1 multiplied by tw(t) when TW, then the DFT,
 // in grid arithmetic.
 template <int R, bool TW, class TWF>
 SAG_HD void g_bfly(cdw* x, TWF tw) {
-  const float C = grid_const(g_maxabs<R>(x));
+  // radix 6: one grid step coarser (constant 2 C), see the header
+  const float C = grid_const(g_maxabs<R>(x)) * (R == 6 ? 2.0f : 1.0f);
   x[0] = g_snapc(x[0], C);
 #pragma unroll
   for (int t = 1; t < R; ++t) {

@@ -34,6 +34,10 @@ SAG_CX ct_sched make_ct_sched(int P) {
   if (P % 3 == 0) { odd = 3; P /= 3; }
   while (P % 8 == 0) { s.r[s.n++] = 8; P /= 8; }
   if (P == 4) { s.r[s.n++] = 4; P = 1; }
+  if (P == 2 && odd == 3) {  // a 2 and the 3 as one radix-6 pass
+    s.r[s.n++] = 6;
+    return s;
+  }
   if (P == 2) { s.r[s.n++] = 2; P = 1; }
   if (odd == 3) s.r[s.n++] = 3;
   if (P != 1) s.n = -1;

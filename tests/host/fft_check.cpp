@@ -108,31 +108,31 @@ static void ct_host_passes(std::vector<C>& buf, int ld, int count, const C* tw, 
 
 // count transforms of length P at ld = ct_ld(P, count); sin: the input comes
 // from a separate natural-order buffer. Returns the max relative error.
-template <int P>
+template <int P, class C = cdw>
 static long double ct_check(int count, bool sin, std::mt19937_64& g) {
   const long double TWO_PI = 6.283185307179586476925286766559005768L;
   std::uniform_real_distribution<double> u(-1.0, 1.0);
   const int ld = ct_ld(P, count);
-  const cdw nan = cfrom(NAN, NAN, cdw{});
-  std::vector<cdw> buf((size_t)count * ld, nan), nat((size_t)count * P), tw(P);
+  const C nan = cfrom(NAN, NAN, C{});
+  std::vector<C> buf((size_t)count * ld, nan), nat((size_t)count * P), tw(P);
   std::vector<double> xr((size_t)count * P), xi((size_t)count * P);
   for (int j = 0; j < P; ++j) {
     const long double a = -TWO_PI * j / P;
-    tw[j] = cfrom((double)cosl(a), (double)sinl(a), cdw{});
+    tw[j] = cfrom((double)cosl(a), (double)sinl(a), C{});
   }
   for (int b = 0; b < count; ++b)
     for (int j = 0; j < P; ++j) {
       xr[(size_t)b * P + j] = u(g);
       xi[(size_t)b * P + j] = u(g);
-      const cdw v = cfrom(xr[(size_t)b * P + j], xi[(size_t)b * P + j], cdw{});
+      const C v = cfrom(xr[(size_t)b * P + j], xi[(size_t)b * P + j], C{});
       if (sin) nat[(size_t)b * P + j] = v;
       else buf[(size_t)b * ld + pad8(j)] = v;
     }
   // pass tables, as the kernels build them from the natural table
-  std::vector<cdw> twp(ct_twp_size(P), nan);
+  std::vector<C> twp(ct_twp_size(P), nan);
   for (int i = 0; i < ct_twp_size(P); ++i)
     if (ct_twp_src(P, i) >= 0) twp[i] = tw[ct_twp_src(P, i)];
-  ct_host_passes<cdw, P, 0, 1>(buf, ld, count, twp.data(), sin ? nat.data() : nullptr);
+  ct_host_passes<C, P, 0, 1>(buf, ld, count, twp.data(), sin ? nat.data() : nullptr);
   long double err = 0, nrm = 0;
   for (int b = 0; b < count; ++b)
     for (int k = 0; k < P; ++k) {
@@ -143,7 +143,7 @@ static long double ct_check(int count, bool sin, std::mt19937_64& g) {
         sr += x0 * cosl(a) - x1 * sinl(a);
         si += x0 * sinl(a) + x1 * cosl(a);
       }
-      const cdw y = buf[(size_t)b * ld + pad8(k)];
+      const C y = buf[(size_t)b * ld + pad8(k)];
       nrm = fmaxl(nrm, sqrtl(sr * sr + si * si));
       const long double e = hypotl(cre(y) - sr, cim(y) - si);
       if (!(e == e)) return NAN;
@@ -152,16 +152,17 @@ static long double ct_check(int count, bool sin, std::mt19937_64& g) {
   return err / nrm;
 }
 
+template <class C = cdw>
 static long double ct_dispatch(int P, int count, bool sin, std::mt19937_64& g) {
   switch (P) {
-    case 64: return ct_check<64>(count, sin, g);
-    case 96: return ct_check<96>(count, sin, g);
-    case 128: return ct_check<128>(count, sin, g);
-    case 192: return ct_check<192>(count, sin, g);
-    case 256: return ct_check<256>(count, sin, g);
-    case 384: return ct_check<384>(count, sin, g);
-    case 512: return ct_check<512>(count, sin, g);
-    case 768: return ct_check<768>(count, sin, g);
+    case 64: return ct_check<64, C>(count, sin, g);
+    case 96: return ct_check<96, C>(count, sin, g);
+    case 128: return ct_check<128, C>(count, sin, g);
+    case 192: return ct_check<192, C>(count, sin, g);
+    case 256: return ct_check<256, C>(count, sin, g);
+    case 384: return ct_check<384, C>(count, sin, g);
+    case 512: return ct_check<512, C>(count, sin, g);
+    case 768: return ct_check<768, C>(count, sin, g);
     default: std::printf("unsupported %d\n", P); std::exit(2);
   }
 }
@@ -177,6 +178,8 @@ int main(int argc, char** argv) {
     for (int i = 2; i < argc; ++i) {
       const int P = std::atoi(argv[i]);
       std::printf("ct %d %d %d %.3Le\n", P, ct_cols(P), 0, ct_dispatch(P, ct_cols(P), false, g));
+      // FP64 through the same passes (the plain DFTs of fft.cuh, radix 6 included)
+      std::printf("ct64 %d %d %d %.3Le\n", P, ct_cols(P), 0, ct_dispatch<cd>(P, ct_cols(P), false, g));
       if ((P & (P - 1)) == 0 && P <= 512) {
         std::printf("ct %d %d %d %.3Le\n", P, 2 * ct_group(P), 1, ct_dispatch(P, 2 * ct_group(P), true, g));
         std::printf("ct %d %d %d %.3Le\n", P, 2, 0, ct_dispatch(P, 2, false, g));

@@ -61,6 +61,11 @@ def test_compile_time_passes_padded_layout(fft_check):
     out = subprocess.run([fft_check, "ct"] + [str(s) for s in CT_SIZES], check=True,
                          capture_output=True, text=True).stdout.split("\n")
     rows = [ln.split() for ln in out if ln.startswith("ct ")]
+    # the same passes in FP64 (the plain small DFTs, radix 6 included)
+    rows64 = [ln.split() for ln in out if ln.startswith("ct64 ")]
+    assert len(rows64) == len(CT_SIZES)
+    for _, P, count, sin, err in rows64:
+        assert float(err) < 1e-15, f"FP64 length {P}: {err}"
     # column layout for every length, row-chunk and inverse layouts for powers of two
     assert len(rows) == len(CT_SIZES) + 2 * 4
     # Double-word radix-2/4/8 butterflies of the compile-time passes round
