@@ -156,20 +156,29 @@ double dft_ops(int R, const OpCost& c) {
     case 3: return 6 * c.cadd + c.kmul + c.scale;
     case 4: return 8 * c.cadd;
     case 5: return 16 * c.cadd + 8 * c.kmul;
+    case 6: return 2 * (6 * c.cadd + c.kmul + c.scale) + 6 * c.cadd;  // two 3-point DFTs, 6 adds
     default: return 26 * c.cadd + 2 * c.kmul;  // radix 8: 8 + 2 + 16 adds, 2 constant products
   }
 }
 
-// One length-P transform with the given radix schedule (the compile-time
-// schedule of fft_ct.cuh has the same radices in another order, hence the
-// same butterfly count; only the twiddle-free first pass differs, which is
-// ignored here).
+// One length-P transform with the given radix schedule: the compile-time
+// schedule of fft_ct.cuh (ct_plan) for the lengths the kernels specialise,
+// else the runtime one.
 double bfly_ops(int R, bool twiddled, const OpCost& c) {
   if (c.grid && R != 5) {
-    const double dft = R == 2 ? 8 : R == 3 ? 38 : R == 4 ? 32 : 124;
+    const double dft = R == 2 ? 8 : R == 3 ? 38 : R == 4 ? 32 : R == 6 ? 100 : 124;
     return 8 + (R - 1) * (twiddled ? 24 : 8) + dft;
   }
   return dft_ops(R, c) + (twiddled ? (R - 1) * c.cmul : 0.0);
+}
+
+radix_plan ct_plan(int P, bool ct, const radix_plan& rt) {
+  if (!ct) return rt;
+  const ct_sched sc = make_ct_sched(P);
+  radix_plan rp{};
+  rp.n = sc.n;
+  for (int s = 0; s < sc.n; ++s) rp.r[s] = sc.r[s];
+  return rp;
 }
 
 double fft_ops(int P, const radix_plan& rp, const OpCost& c) {
@@ -694,7 +703,7 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
     case KID_FWD_COL:
       for (const OrderDesc& od : pl->items)  // a pair costs what two single vectors cost
         o += (od.pair ? 2.0 * od.npair : (double)od.nu) *
-             (od.M2 * fft_ops(od.M1, od.rp1, c) + (double)od.M * c.cmul + 2.0 * std::min<double>(od.M, od.N) * load_mul);
+             (od.M2 * fft_ops(od.M1, ct_plan(od.M1, dwp && od.ct1, od.rp1), c) + (double)od.M * c.cmul + 2.0 * std::min<double>(od.M, od.N) * load_mul);
       b = 8.0 * factor_elems + 8.0 * Nt;
       break;
     case KID_ROWS:
@@ -703,31 +712,31 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
         const double unpack = 4 * c.cadd + c.cmul;
         const double repack = 4 * c.cadd + c.cmul;
         if (od.pair)  // rows of 2 M2 points per pair; separation: 2 complex adds per pair and index
-          o += (double)od.npair * od.M1 * fft_ops(2 * od.M2, make_radix_plan(2 * od.M2), c) +
+          o += (double)od.npair * od.M1 * fft_ops(2 * od.M2, ct_plan(2 * od.M2, true, make_radix_plan(2 * od.M2)), c) +
                (double)od.npair * M * 2 * c.cadd;
         else
-          o += Vd * od.M1 * fft_ops(od.M2, od.rp2, c)  // forward rows of every vector
+          o += Vd * od.M1 * fft_ops(od.M2, ct_plan(od.M2, dwp && od.ct2, od.rp2), c)  // forward rows of every vector
                + Vd * M * unpack;                        // real split
         o += (Vd - od.R) * M * c.cmul                           // product over the modes
              + (double)od.R * M * (c.cadd + (dwp ? c.scale : 0))  // rank sum
-             + M * repack + od.M1 * fft_ops(od.M2, od.rp2, c)     // inverse rows
+             + M * repack + od.M1 * fft_ops(od.M2, ct_plan(od.M2, dwp && od.ct2, od.rp2), c)     // inverse rows
              + M * c.cmul;                                        // four-step twiddle
       }
       b = 0.0;  // reads and writes only the FFT workspace
       break;
     case KID_ROWS_TT:
       for (const OrderDesc& od : pl->items)
-        o += (double)od.nvec * (od.M1 * fft_ops(od.M2, od.rp2, c) + (double)od.M * (4 * c.cadd + c.cmul));
+        o += (double)od.nvec * (od.M1 * fft_ops(od.M2, ct_plan(od.M2, dwp && od.ct2, od.rp2), c) + (double)od.M * (4 * c.cadd + c.cmul));
       break;
     case KID_TT_CHAIN:
       for (const OrderDesc& od : pl->items) o += (double)od.nvec * (od.M + 1) * (c.cmul + c.cadd);
       break;
     case KID_ROWS_TT_INV:
       for (const OrderDesc& od : pl->items)
-        o += (double)od.M * (4 * c.cadd + 2 * c.cmul) + od.M1 * fft_ops(od.M2, od.rp2, c);
+        o += (double)od.M * (4 * c.cadd + 2 * c.cmul) + od.M1 * fft_ops(od.M2, ct_plan(od.M2, dwp && od.ct2, od.rp2), c);
       break;
     case KID_INV_COL:
-      for (const OrderDesc& od : pl->items) o += od.M2 * fft_ops(od.M1, od.rp1, c);
+      for (const OrderDesc& od : pl->items) o += od.M2 * fft_ops(od.M1, ct_plan(od.M1, dwp && od.ct1, od.rp1), c);
       b = 0.0;
       for (const OrderDesc& od : pl->items) b += 8.0 * od.N;  // P^(d) written
       break;
