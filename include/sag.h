@@ -181,6 +181,17 @@ sag_status sag_plan_update_factors(sag_plan_t plan, const double* factors, int32
 /* Number of factor values in the plan's vector layout. */
 sag_status sag_plan_factor_count(sag_plan_t plan, int64_t* count);
 
+/* Clock-cycle limit of the plan's device-side waits (the row kernels' waits on
+ * their own bulk copies); cycles <= 0 restores the default, 4e9 (about 2 s at
+ * the maximum SM clock). A wait that runs out latches SAG_ETIMEOUT for
+ * sag_sync_status, lets the block's copies in flight land (a second wait of at
+ * most the default) and ends the block; that evaluation's results are not
+ * valid, and the context stays usable. With `unmet` nonzero every such wait
+ * targets a barrier that nothing completes, so each runs out after `cycles`:
+ * a test of that path without any fault. Synchronises the device and drops
+ * the plan's cached graphs. */
+sag_status sag_plan_set_wait_limit(sag_plan_t plan, int64_t cycles, int32_t unmet);
+
 /* Waits for `stream`, then returns and clears the plan's latched device-side
  * status (SAG_OK, SAG_ENONFINITE or SAG_ETIMEOUT). */
 sag_status sag_sync_status(sag_plan_t plan, void* stream);

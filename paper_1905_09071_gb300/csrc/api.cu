@@ -613,6 +613,22 @@ sag_status sag_plan_factor_count(sag_plan_t pl, int64_t* count) {
   return SAG_OK;
 }
 
+sag_status sag_plan_set_wait_limit(sag_plan_t pl, int64_t cycles, int32_t unmet) {
+  if (!pl) return fail(SAG_EINVAL, "NULL plan");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  pl->P.spin_limit = cycles > 0 ? (long long)cycles : kDefaultSpinLimit;
+  pl->P.wait_unmet = unmet ? 1 : 0;
+  // captured graphs hold the old limit in their kernel parameters
+  for (auto& g : pl->gcache) cudaGraphExecDestroy(g.second);
+  pl->gcache.clear();
+  if (pl->gexec) {
+    cudaGraphExecDestroy(pl->gexec);
+    pl->gexec = nullptr;
+  }
+  return SAG_OK;
+}
+
 sag_status sag_sync_status(sag_plan_t pl, void* stream) {
   if (!pl) return fail(SAG_EINVAL, "NULL plan");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

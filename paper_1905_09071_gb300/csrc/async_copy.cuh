@@ -58,6 +58,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Clock cycles a block that gave up waiting still waits for its own copies in
+// flight before it exits (about 2 s at the maximum SM clock).
+constexpr long long kDrainLimit = 4000000000LL;
+
 // Waits for phase `parity` of the barrier; false if `limit` cycles pass first.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
@@ -65,6 +69,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+
+// A block whose wait gave up: latch the timeout status, then let the copies
+// it has in flight on `bar` (phase `parity`) land before it exits. Called by
+// one thread; out of line, as it runs at most once.
+static __device__ __noinline__ void timeout_drain(unsigned* status, unsigned bit, uint64_t* bar,
+                                                  uint32_t parity) {
+  atomicOr(status, bit);
+  mbar_wait_bounded(bar, parity, kDrainLimit);
 }
 
 }  // namespace sag

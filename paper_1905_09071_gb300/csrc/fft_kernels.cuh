@@ -374,8 +374,11 @@ __device__ __forceinline__ void rows_body(const RhsParams& P, const OrderDesc& o
 // block issues the copies of the next chunk, so they land while the remaining
 // passes and the spectrum products of this chunk run. Layout: one mbarrier
 // (16 bytes), stage (2 G x P2), work (2 G transforms, ct_ld(P2, 2 G) apart);
-// the pass twiddle tables are read from global memory. If a copy does not complete within P.spin_limit cycles the
-// block sets the timeout status and returns.
+// the pass twiddle tables are read from global memory. If a copy does not
+// complete within P.spin_limit cycles the block sets the timeout status, waits
+// (bounded by kDrainLimit) for the copies it has in flight, and returns. The
+// header's second 8 bytes hold a barrier nothing arrives at, which the waits
+// target instead when P.wait_unmet is set (a test of that path).
 template <class C, int P2>
 __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderDesc& od, int kp,
                                                 unsigned char* smem_raw) {
@@ -412,6 +415,7 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
 
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);  // the barrier nothing arrives at (P.wait_unmet)
     mbar_init_fence();
   }
   __syncthreads();
@@ -430,9 +434,12 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
     const int q0 = c * G, gc = min(G, Vd - q0);
     // The barrier also orders the previous chunk's reads of work before the
     // first pass overwrites it.
-    const bool ok = mbar_wait_bounded(bar, (uint32_t)(c & 1), P.spin_limit);
+    // (a test of the timeout path waits on the barrier nothing completes)
+    const bool ok = mbar_wait_bounded(P.wait_unmet ? bar + 1 : bar, (uint32_t)(c & 1), P.spin_limit);
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
+      // Timed out: latch the status, then let this chunk's copies land (a
+      // second bounded wait) before the block's shared memory is released.
+      if (threadIdx.x == 0) timeout_drain(P.status, kStatusTimeout, bar, (uint32_t)(c & 1));
       return;
     }
     fft_ct_first<C, P2, SLOTS, kThreads, true>(stage, P2, work, ld, tw);  // unused slots hold stale data
@@ -550,6 +557,7 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
 
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);  // the barrier nothing arrives at (P.wait_unmet)
     mbar_init_fence();
   }
   __syncthreads();
@@ -569,9 +577,12 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
 
   for (int c = 0; c < nchunk; ++c) {
     const int p0 = c * G, gc = min(G, np - p0);
-    const bool ok = mbar_wait_bounded(bar, (uint32_t)(c & 1), P.spin_limit);
+    // (a test of the timeout path waits on the barrier nothing completes)
+    const bool ok = mbar_wait_bounded(P.wait_unmet ? bar + 1 : bar, (uint32_t)(c & 1), P.spin_limit);
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
+      // Timed out: latch the status, then let this chunk's copies land (a
+      // second bounded wait) before the block's shared memory is released.
+      if (threadIdx.x == 0) timeout_drain(P.status, kStatusTimeout, bar, (uint32_t)(c & 1));
       return;
     }
     fft_ct_first<C, P2p, SLOTS, kThreads, true>(stage, P2p, work, ld, tw);  // unused slots hold stale data

@@ -15,6 +15,7 @@ constexpr int kMaxD = 8;
 constexpr int kThreads = 256;        // block size of the FFT kernels
 constexpr int kRowPosPerThread = 4;  // row kernel: positions owned per thread (2 rows x M2 <= 1024)
 constexpr int kMaxTTRank = 16;       // largest TT rank R_lambda the chain kernel holds in registers
+constexpr long long kDefaultSpinLimit = 4000000000LL;  // device-side wait limit, cycles (about 2 s)
 
 // One order d of one system: its FFT geometry and where its data lives.
 //
@@ -112,6 +113,7 @@ struct RhsParams {
   int64_t Ntot;                  // packed state length
   int tt_rmax;                   // largest TT rank of the plan (chain kernel variant)
   long long spin_limit;          // clock cycles a bounded device-side wait may take
+  int wait_unmet;                // test of the timeout path: waits target a barrier nothing completes
   int dotchunk;                  // sizes per inner-product chunk
   int maxdotchunk;               // most chunks of any vector
   const OrderDesc* ord;          // [nitems]

@@ -211,7 +211,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   P.sym = opt.symmetrize_q;
   P.dwpath = dwp ? 1 : 0;
   P.exact = opt.prec == SAG_FP32_SPLIT_EXACT ? 1 : 0;
-  P.spin_limit = 4000000000LL;  // about 2 s at the maximum SM clock
+  P.spin_limit = kDefaultSpinLimit;
   P.dotchunk = 8192;
 
   // ---- vectors: host copy of every nonzero factor vector, packed ----------

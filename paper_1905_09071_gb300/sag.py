@@ -27,7 +27,7 @@ EXPORTS = [
     "sag_rhs_parts", "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_plan_destroy",
     "sag_last_error", "sag_version", "sag_profile_enable", "sag_profile_read", "sag_kernel_name",
     "sag_kernel_work", "sag_plan_describe", "sag_loss_noalloc", "sag_rhs_vjp", "sag_integrate_vjp",
-    "sag_plan_update_factors", "sag_plan_factor_count",
+    "sag_plan_update_factors", "sag_plan_factor_count", "sag_plan_set_wait_limit",
 ]
 SAG_NUM_KERNELS = 13
 
@@ -98,11 +98,13 @@ def load(build_if_missing: bool = True):
         lib.sag_integrate_vjp.argtypes = [vp, vp, f64, i64, i64, vp, vp, vp, vp]
         lib.sag_plan_update_factors.argtypes = [vp, vp, i32]
         lib.sag_plan_factor_count.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.sag_plan_set_wait_limit.argtypes = [vp, i64, i32]
         lib.sag_loss_noalloc.restype = ctypes.c_int
         for name in ("sag_plan", "sag_plan_layout", "sag_plan_bytes", "sag_rhs", "sag_rhs_parts",
                      "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_profile_enable",
                      "sag_profile_read", "sag_kernel_work", "sag_plan_describe", "sag_rhs_vjp",
-                     "sag_integrate_vjp", "sag_plan_update_factors", "sag_plan_factor_count"):
+                     "sag_integrate_vjp", "sag_plan_update_factors", "sag_plan_factor_count",
+                     "sag_plan_set_wait_limit"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -235,6 +237,12 @@ class Plan:
         """Returns the latched device status (SAG_OK, SAG_ENONFINITE, ...), clearing it."""
         st = self._lib.sag_sync_status(self._h, _stream(stream))
         return int(st)
+
+    def set_wait_limit(self, cycles: int = 0, unmet: bool = False):
+        """Clock-cycle limit of the device-side waits (0: the default); with
+        unmet, every such wait targets a barrier nothing completes (a test of
+        the timeout path; see include/sag.h)."""
+        _check(self._lib.sag_plan_set_wait_limit(self._h, int(cycles), int(bool(unmet))))
 
     def profile(self, on: bool = True):
         """Turns per-kernel event timing on or off (non-graph launches only)."""
