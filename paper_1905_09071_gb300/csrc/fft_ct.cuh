@@ -164,26 +164,26 @@ SAG_CX int ct_twg(int j, int t) {
 
 // Kernel specialisations (the KIND template argument of k_fwd_col, k_rows and
 // k_inv_col): 0 dispatches on the item at run time; 1 is the runtime-length
-// path; 2 + i the compile-time length ct_len(i); for k_fwd_col 10 + i the
-// pair form at column length ct_len(i); for k_rows 10 + i the pair form at row
+// path; 2 + i the compile-time length ct_len(i); for k_fwd_col 11 + i the
+// pair form at column length ct_len(i); for k_rows 11 + i the pair form at row
 // length ct_len(i). The host launches each run of equal kind of the forward
 // columns and the rows with its own instantiation, so that a kernel holds one
 // path's code and registers (measured: 7% faster than one kernel for every
 // path). The inverse columns, about one block per SM, stay one launch.
 SAG_CX int ct_len(int i) {
-  return i == 0 ? 64 : i == 1 ? 96 : i == 2 ? 128 : i == 3 ? 192 : i == 4 ? 256 : i == 5 ? 384 : i == 6 ? 512 : 768;
+  return i == 0 ? 64 : i == 1 ? 96 : i == 2 ? 128 : i == 3 ? 192 : i == 4 ? 256 : i == 5 ? 384 : i == 6 ? 512
+       : i == 7 ? 768 : 1536;
 }
+constexpr int kCtLengths = 9;
 SAG_CX int ct_index(int P) {
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < kCtLengths; ++i)
     if (ct_len(i) == P) return i;
   return -1;
 }
-constexpr int kKindGeneral = 0, kKindRuntime = 1, kKindCt = 2, kKindPair = 10, kKindCount = 18;
+constexpr int kKindGeneral = 0, kKindRuntime = 1, kKindCt = 2, kKindPair = kKindCt + kCtLengths,
+              kKindCount = kKindPair + kCtLengths;
 
-SAG_CX bool ct_supported(int P) {
-  return P == 64 || P == 128 || P == 256 || P == 512 || P == 96 || P == 192 || P == 384 ||
-         P == 768;
-}
+SAG_CX bool ct_supported(int P) { return ct_index(P) >= 0; }
 
 // The butterfly of a compile-time pass: inputs t >= 1 multiplied by tw(t)
 // when TW, then the radix-R DFT. Double-word radix-2/3/4/8 butterflies run in

@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
     case 384: fwd_col_body<C, 384>(P, od, vloc, lv, cb, n, buf); break;
     case 512: fwd_col_body<C, 512>(P, od, vloc, lv, cb, n, buf); break;
     case 768: fwd_col_body<C, 768>(P, od, vloc, lv, cb, n, buf); break;
+    case 1536: fwd_col_body<C, 1536>(P, od, vloc, lv, cb, n, buf); break;
     default: fwd_col_body<C, 0>(P, od, vloc, lv, cb, n, buf); break;
   }
 }
@@ -764,6 +765,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_col(const __grid_constant__
     case 384: inv_col_body<C, 384>(P, od, oi, cb, buf); break;
     case 512: inv_col_body<C, 512>(P, od, oi, cb, buf); break;
     case 768: inv_col_body<C, 768>(P, od, oi, cb, buf); break;
+    case 1536: inv_col_body<C, 1536>(P, od, oi, cb, buf); break;
     default: inv_col_body<C, 0>(P, od, oi, cb, buf); break;
   }
 }

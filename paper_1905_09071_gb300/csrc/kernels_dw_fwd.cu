@@ -20,14 +20,18 @@ namespace {
 using FwdLaunch = void (*)(const RhsParams&, const double*, int, int, int, size_t, cudaStream_t);
 using Setup = cudaError_t (*)();
 
+// The pair form exists for column lengths up to 768 (its rows are at most 512
+// points, so the 1536-point columns never pair); that kind maps to kKindGeneral.
+constexpr int fwd_kind_of(int K) { return K == kKindPair + ct_index(1536) ? kKindGeneral : K; }
+
 template <int K>
 void fwd_kind(const RhsParams& P, const double* nin, int base, int blocks, int all, size_t smem,
               cudaStream_t st) {
-  k_fwd_col<SAG_DW_C, K><<<blocks, kThreads, smem, st>>>(P, nin, base, all);
+  k_fwd_col<SAG_DW_C, fwd_kind_of(K)><<<blocks, kThreads, smem, st>>>(P, nin, base, all);
 }
 template <int K>
 cudaError_t fwd_setup() {
-  return allow_max_smem(k_fwd_col<SAG_DW_C, K>);
+  return allow_max_smem(k_fwd_col<SAG_DW_C, fwd_kind_of(K)>);
 }
 template <int... K>
 constexpr std::array<FwdLaunch, sizeof...(K)> fwd_launches(std::integer_sequence<int, K...>) {
