@@ -40,7 +40,7 @@ SM_MAX_MHZ = 2070.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -90,6 +90,15 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # nvidia-smi takes a moment to start: let its first sample land before
+        # the timed region begins, so every sample falls inside or right at it.
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            with open(self.path) as fh:
+                if fh.readline():
+                    break
+            time.sleep(0.02)
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -209,7 +218,8 @@ def run_reference(args, world, rank):
         return
     from paper_1905_09071_gb300 import workloads as wl
     s = wl.random_power_cp()
-    sec_per_rhs, samples, cores = oracle_sample(s, seconds=0.0, max_samples=args.steps,
+    # K samples, or as many as about 90 s of host time allows
+    sec_per_rhs, samples, cores = oracle_sample(s, seconds=90.0, max_samples=args.steps,
                                                 warmup=args.warmup)
     value = 1.0 / (2.0 * sec_per_rhs)
     sample = (f"{samples} timed steps; each step = the oracle's direct-mode right-hand side of a "
