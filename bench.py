@@ -302,7 +302,9 @@ def run_ours(args, world, rank, local):
     precs = {"all": everything, "both": everything, "fp32_split": (sag.SAG_FP32_SPLIT,),
              "fp32_split_exact": (sag.SAG_FP32_SPLIT_EXACT,), "fp64": (sag.SAG_FP64,)}[args.prec]
     if args.kernels:
-        pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT)
+        # the timed run's plan: the same autotuned splits and stream groups
+        pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT, autotune=tune)
+        print("fft splits:", [[o["M1"], o["M2"]] for o in pl.describe()["orders"]], file=sys.stderr)
         n = torch.tensor(s.n0, device="cuda")
         pl.profile(True)
         for _ in range(W):
@@ -406,6 +408,7 @@ def run_ours(args, world, rank, local):
                    "l2": "working set (factor copies 151 MB + FFT workspace 243 MB) larger than the 129 MB L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "fft_geometry": dw["desc"]["orders"],
+                   "fft_split_candidates": dw["desc"].get("geometry_autotune", []),
                    "fft_stream_groups": {"fp32_split": dw["desc"]["blocks"]["fft_groups"],
                                          "fp64": f64["desc"]["blocks"]["fft_groups"],
                                          "chosen_by": "fixed rule" if args.no_autotune else "plan-time autotuner"}},

@@ -95,13 +95,26 @@ typedef struct {
                             0: the kernel's last mode holds k, exactly as printed.
                             The two coincide for symmetric kernels (Sec. 1 assumes
                             symmetric coefficients). */
-  int32_t autotune;      /* 0 (default): fixed launch rules. 1: at plan time, time the
-                            candidate launch layouts of the FFT stage (1 to 4 stream
-                            groups of consecutive orders/systems, each a branch of the
-                            graph) on this plan's own sizes and keep the fastest: a few
-                            right-hand sides per candidate on an internal stream with a
-                            synthetic n, synchronising. The results do not depend on
-                            the choice. */
+  int32_t autotune;      /* 0 (default): fixed rules. 1: at plan time, time candidates on
+                            this plan's own sizes and keep the fastest, each timed as
+                            graph-replayed RK2 steps on an internal stream with a
+                            synthetic n (synchronising):
+                            - the launch layout of the FFT stage: 1 to 4 stream groups
+                              of consecutive orders/systems, each a branch of the
+                              graph. The results do not depend on this choice;
+                            - for a double-word CP plan of 1 to 4 orders, the
+                              four-step split of each order's FFT, M = L/2 = M1 M2:
+                              the rule's M2 or half of it, where both give compile-
+                              time column and row kernels. Whole candidate plans are
+                              built, so the plan call takes longer and briefly holds
+                              two plans' device memory. The split changes the order of
+                              the FFT's roundings, so results differ within the
+                              precision's error bound. */
+  int32_t max_m2;        /* 0 (default): the rule, M2 = the largest power of two with
+                            M2^2 <= M, M2 <= 512 and M2 dividing M. Otherwise a
+                            power of two in [4, 512] that caps M2 (shorter rows, longer
+                            columns; for tests and tuning). A column length M1 above
+                            4096 is SAG_EUNSUPPORTED. */
 } sag_options;
 
 /* Fills *opt with the defaults. */

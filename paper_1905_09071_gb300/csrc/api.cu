@@ -202,6 +202,7 @@ void sag_default_options(sag_options* opt) {
   opt->rk = SAG_HEUN;
   opt->symmetrize_q = 1;
   opt->autotune = 0;
+  opt->max_m2 = 0;
 }
 
 const char* sag_last_error(void) { return g_err.c_str(); }
@@ -220,6 +221,7 @@ sag_status sag_plan(const sag_system* sys, int32_t B, const sag_options* opt, sa
   sag_plan_s* pl = new (std::nothrow) sag_plan_s();
   if (!pl) return fail(SAG_ENOMEM, "host allocation");
   s = build_plan(sys, B, o, pl);
+  if (s == SAG_OK && o.autotune) s = autotune_geometry(sys, B, o, &pl);
   if (s != SAG_OK) {
     delete pl;
     return s;
@@ -806,7 +808,8 @@ sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
         std::to_string(pl->L.col_blocks) + ", \"rows\": " + std::to_string(pl->L.row_blocks) +
         ", \"fft_groups\": " + std::to_string(pl->fft_groups) +
         ", \"inv_col\": " + std::to_string(pl->L.inv_blocks) + ", \"epilogue\": " +
-        std::to_string(pl->L.epi_blocks) + "}, \"device_bytes\": " + std::to_string(pl->bytes) + "}";
+        std::to_string(pl->L.epi_blocks) + "}, \"device_bytes\": " + std::to_string(pl->bytes) +
+        ", \"geometry_autotune\": [" + pl->tune_log + "]}";
   std::snprintf(buf, len, "%s", js.c_str());
   return SAG_OK;
 }

@@ -166,6 +166,9 @@ sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options&
     return fail(SAG_EINVAL, "unknown precision");
   if (opt.rk != SAG_HEUN && opt.rk != SAG_MIDPOINT) return fail(SAG_EINVAL, "unknown RK2 variant");
   if (opt.symmetrize_q != 0 && opt.symmetrize_q != 1) return fail(SAG_EINVAL, "symmetrize_q must be 0 or 1");
+  if (opt.autotune != 0 && opt.autotune != 1) return fail(SAG_EINVAL, "autotune must be 0 or 1");
+  if (opt.max_m2 != 0 && (opt.max_m2 < 4 || opt.max_m2 > 512 || (opt.max_m2 & (opt.max_m2 - 1)) != 0))
+    return fail(SAG_EINVAL, "max_m2 must be 0 or a power of two in [4, 512]");
   for (int b = 0; b < B; ++b) {
     const sag_system& s = sys[b];
     const std::string at = B > 1 ? " (system " + std::to_string(b) + ")" : "";
@@ -369,8 +372,13 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     if (L > (int64_t)1 << 24) return fail(SAG_EUNSUPPORTED, "FFT length above 2^24 (d N too large)");
     od.L = (int)L;
     od.M = (int)(L / 2);
+    // Four-step split M = M1 M2: M2 by the rule (capped by max_m2), or the
+    // geometry autotuner's choice for this item.
+    const int m2cap = opt.max_m2 > 0 ? opt.max_m2 : 512;
     int M2 = 1;
-    while ((int64_t)(2 * M2) * (2 * M2) <= od.M && 2 * M2 <= 512 && od.M % (2 * M2) == 0) M2 *= 2;
+    while ((int64_t)(2 * M2) * (2 * M2) <= od.M && 2 * M2 <= m2cap && od.M % (2 * M2) == 0) M2 *= 2;
+    const size_t ix = (size_t)(&od - I.data());
+    if (ix < pl->m2_pref.size() && pl->m2_pref[ix] > 0 && od.M % pl->m2_pref[ix] == 0) M2 = pl->m2_pref[ix];
     od.M2 = M2;
     od.M1 = od.M / M2;
     if (od.M1 > 4096) return fail(SAG_EUNSUPPORTED, "FFT column length above 4096");
@@ -397,12 +405,15 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     if (dwp && !tt && !od.ct2 && 2 * od.M2 > kThreads)
       return fail(SAG_EUNSUPPORTED, "row length without a compile-time kernel above 128");
     od.G = G;
-    // Pairs (see OrderDesc): rows of 2 M2 points with a compile-time kernel.
+    // Pairs (see OrderDesc): rows of 2 M2 points with a compile-time kernel,
+    // columns of at most 768 points (the pair column kernels' lengths; the
+    // rule never pairs 1536-point columns, whose rows are 2 x 512 points).
     od.pair = 0;
     od.npair = 0;
     od.ncolblk_p = 0;
     od.ld2p = 0;
-    if (od.ct1 && od.ct2 && !tt && od.umap_off < 0 && 2 * od.M2 <= 512 && ct_supported(2 * od.M2)) {
+    if (od.ct1 && od.ct2 && !tt && od.umap_off < 0 && od.M1 <= 768 && 2 * od.M2 <= 512 &&
+        ct_supported(2 * od.M2)) {
       od.pair = 1;
       od.npair = (od.nvec + 1) / 2;
       od.ncolblk_p = 2 * M2 / W;
@@ -821,10 +832,11 @@ sag_status time_step_graph(sag_plan_s* pl, float* ms) {
 
 }  // namespace
 
-// Times 1..4 stream groups on this plan (synthetic n = e^{-k/10} per system),
-// three sweeps over the candidates, each candidate's best time counting, and
-// keeps the fewest groups within 1% of the fastest.
-sag_status autotune_fft_groups(sag_plan_s* pl) {
+namespace {
+
+// The autotuners' input: n = e^{-k/10} per system, normalised to M0 = 1, in
+// the plan's input staging buffer.
+sag_status load_tuning_input(sag_plan_s* pl) {
   std::vector<double> h((size_t)pl->Ntot);
   for (const SysDesc& sd : pl->systems) {
     double s = 0.0;
@@ -832,7 +844,17 @@ sag_status autotune_fft_groups(sag_plan_s* pl) {
     for (int k = 1; k <= sd.N; ++k) h[sd.noff + k - 1] = std::exp(-k / 10.0) / s;
   }
   cudaError_t e = cudaMemcpy(pl->stage_a, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "autotune input");
+  return e == cudaSuccess ? SAG_OK : cuda_fail(e, "autotune input");
+}
+
+}  // namespace
+
+// Times 1..4 stream groups on this plan (synthetic n = e^{-k/10} per system),
+// three sweeps over the candidates, each candidate's best time counting, and
+// keeps the fewest groups within 1% of the fastest.
+sag_status autotune_fft_groups(sag_plan_s* pl) {
+  sag_status st = load_tuning_input(pl);
+  if (st != SAG_OK) return st;
   const int gmax = std::min(pl->P.nitems, (int)kMaxFftGroups);
   float t[kMaxFftGroups + 1];
   for (int G = 1; G <= gmax; ++G) t[G] = 1e30f;
@@ -849,6 +871,108 @@ sag_status autotune_fft_groups(sag_plan_s* pl) {
   int best_g = 1;
   while (t[best_g] > 1.01f * fastest) ++best_g;
   return configure_fft_groups(pl, best_g);
+}
+
+namespace {
+
+// An alternative four-step split M = M1 M2 for the pair form: both the
+// column length M1 (at most 768) and the pair rows' 2 M2 points have
+// compile-time kernels, and a column block's W columns fit in M2 columns.
+bool pair_split_ok(int M, int M2) {
+  if (M2 < 4 || M % (2 * M2) != 0) return false;
+  const int M1 = M / M2;
+  return ct_supported(M1) && M1 <= 768 && ct_supported(M2) && ct_supported(2 * M2) && 2 * M2 <= 512 &&
+         M2 >= ct_cols(M1);
+}
+
+// Best of three timings of one graph-replayed RK2 step on the tuning input.
+sag_status time_plan(sag_plan_s* pl, float* ms) {
+  sag_status st = load_tuning_input(pl);
+  *ms = 1e30f;
+  for (int rep = 0; rep < 3 && st == SAG_OK; ++rep) {
+    float t = 0.0f;
+    st = time_step_graph(pl, &t);
+    *ms = std::min(*ms, t);
+  }
+  return st;
+}
+
+// Appends one candidate (its splits [M1, M2] per order, time, verdict) to log.
+void log_geometry(std::string& log, const sag_plan_s* of, float ms, bool kept) {
+  std::string js = "{\"splits\": [";
+  for (size_t i = 0; i < of->items.size(); ++i)
+    js += std::string(i ? ", " : "") + "[" + std::to_string(of->items[i].M1) + ", " +
+          std::to_string(of->items[i].M2) + "]";
+  char t[32];
+  std::snprintf(t, sizeof t, "%.4f", ms);
+  js += std::string("], \"ms_per_step\": ") + t + ", \"kept\": " + (kept ? "true" : "false") + "}";
+  log += (log.empty() ? "" : ", ") + js;
+}
+
+}  // namespace
+
+// Coordinate search over the four-step split of each order of a double-word
+// CP plan with 1 to 4 orders (the pair form): for each order in turn, a
+// whole plan is built with that order's M2 halved (where both lengths still
+// have compile-time kernels, so that the candidate keeps the pair form) and
+// timed as graph-replayed RK2 steps against the best plan so far; a candidate
+// replaces it when it is more than 1% faster. The kept plan's describe()
+// lists every candidate with its time.
+sag_status autotune_geometry(const sag_system* sys, int32_t B, const sag_options& opt, sag_plan_s** plp) {
+  sag_plan_s* best = *plp;
+  const int n = (int)best->items.size();
+  if (!best->P.dwpath || best->fmt != SAG_CP || n > kMaxFftGroups) return SAG_OK;
+  std::vector<int> pref(n);
+  bool any = false;
+  for (int i = 0; i < n; ++i) {
+    const OrderDesc& od = best->items[i];
+    pref[i] = od.M2;
+    any = any || (od.pair && pair_split_ok(od.M, od.M2 / 2));
+  }
+  if (!any) return SAG_OK;
+  float best_ms = 0.0f;
+  sag_status st = time_plan(best, &best_ms);
+  if (st != SAG_OK) return st;
+  std::string log;
+  log_geometry(log, best, best_ms, true);
+  for (int i = 0; i < n; ++i) {
+    const OrderDesc& od = best->items[i];
+    const int alt = od.M2 / 2;
+    if (!od.pair || !pair_split_ok(od.M, alt)) continue;
+    sag_plan_s* cand = new (std::nothrow) sag_plan_s();
+    if (!cand) return fail(SAG_ENOMEM, "host allocation");
+    cand->m2_pref = pref;
+    cand->m2_pref[i] = alt;
+    float ms = 0.0f;
+    st = build_plan(sys, B, opt, cand);
+    // A candidate that cannot be built (device memory) or that lost the
+    // pair form is skipped; the plan so far stays valid.
+    if (st != SAG_OK || !cand->items[i].pair || cand->items[i].M2 != alt) {
+      cudaDeviceSynchronize();
+      delete cand;
+      continue;
+    }
+    st = time_plan(cand, &ms);
+    if (st != SAG_OK) {
+      cudaDeviceSynchronize();
+      delete cand;
+      return st;
+    }
+    const bool keep = ms < 0.99f * best_ms;
+    log_geometry(log, cand, ms, keep);
+    cudaDeviceSynchronize();
+    if (keep) {
+      delete best;
+      best = cand;
+      *plp = best;  // the caller owns the plan kept so far
+      best_ms = ms;
+      pref[i] = alt;
+    } else {
+      delete cand;
+    }
+  }
+  best->tune_log = log;
+  return SAG_OK;
 }
 
 }  // namespace sag

@@ -57,6 +57,8 @@ struct sag_plan_s {
   sag::SideStream side{nullptr, nullptr, nullptr};
   sag::FftGroups groups{};
   int fft_groups = 1;                     // stream groups of the FFT stage (1: one launch per kernel)
+  std::vector<int> m2_pref;               // per item: M2 of its four-step split (0: the rule)
+  std::string tune_log;                   // candidates the geometry autotuner timed (JSON objects)
   std::vector<int> h_colpre, h_invpre;    // host copies of the block tables, for regrouping
   std::vector<int> h_colpre_all, h_rowpre, h_rowperm;
   std::vector<int> h_colkind, h_colkind_all, h_rowkind;  // kernel specialisations (LaunchCfg)
@@ -123,4 +125,7 @@ sag_status update_factors(sag_plan_s* pl, const double* factors, int on_device);
 // plan-time search over them.
 sag_status configure_fft_groups(sag_plan_s* pl, int G);
 sag_status autotune_fft_groups(sag_plan_s* pl);
+// Plan-time search over the four-step split of each order (sag_options.autotune):
+// may replace *pl by a plan built with other splits.
+sag_status autotune_geometry(const sag_system* sys, int32_t B, const sag_options& opt, sag_plan_s** pl);
 }  // namespace sag

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_function(lib):
 def test_version_and_defaults(lib):
     assert b"sm_103a" in lib.sag_version()
     assert sag.default_options() == {"prec": sag.SAG_FP32_SPLIT, "rk": sag.SAG_HEUN,
-                                     "symmetrize_q": 1, "autotune": 0}
+                                     "symmetrize_q": 1, "autotune": 0, "max_m2": 0}
 
 
 def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=True, out=True):
@@ -66,6 +66,11 @@ def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=
     (dict(opt=(3, 0, 1, 0)), sag.SAG_EINVAL),  # precisions are 0, 1 and 2
     (dict(opt=(0, 4, 1, 0)), sag.SAG_EINVAL),
     (dict(opt=(0, 0, 2, 0)), sag.SAG_EINVAL),
+    (dict(opt=(1, 0, 1, 2)), sag.SAG_EINVAL),  # autotune is 0 or 1
+    (dict(opt=(1, 0, 1, 0, 2)), sag.SAG_EINVAL),  # max_m2: 0 or a power of two in [4, 512]
+    (dict(opt=(1, 0, 1, 0, 96)), sag.SAG_EINVAL),
+    (dict(opt=(1, 0, 1, 0, 1024)), sag.SAG_EINVAL),
+    (dict(opt=(1, 0, 1, 0, -4)), sag.SAG_EINVAL),
 ])
 def test_plan_rejects_bad_arguments(kw, status):
     st, msg = _plan_status(**kw)

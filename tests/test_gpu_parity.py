@@ -31,8 +31,10 @@ def dev(x):
     return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
 
 
-def gpu_parts(s, n0, prec, sym=1, rk=sag.SAG_HEUN):
-    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, symmetrize_q=sym, rk=rk) as pl:
+def gpu_parts(s, n0, prec, sym=1, rk=sag.SAG_HEUN, check=None, **kw):
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, symmetrize_q=sym, rk=rk, **kw) as pl:
+        if check:
+            check(pl.describe())
         n = dev(n0)
         p, q = torch.empty_like(n), torch.empty_like(n)
         o = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -129,6 +131,58 @@ def test_full_size_sampled_parity(throughput_case, prec):
     p, q, _, r = gpu_parts(s, s.n0, prec)
     scale = np.abs(p).max() + np.abs(q_ref).max()
     assert np.abs(p).max() <= 1.0001 * np.abs(p_pre).max() + 1e-300  # the maximum is in the prefix
+    assert nerr(p[:K], p_pre, scale) < TOL[prec]
+    assert nerr(q, q_ref, scale) < TOL[prec]
+    assert nerr(r[:K], p_pre + q_ref[:K], scale) < TOL[prec]
+
+
+# Four-step splits M = M1 M2 with M2 capped: pair-form columns of 512 and 768
+# points and a run-time-length 1024-point column (max_m2 = 128); 1024 and
+# 2048-point run-time columns and a compile-time 1536-point column of single
+# vectors (max_m2 = 64).
+CAPPED_SPLITS = {128: [[512, 128, 1], [768, 128, 1], [1024, 128, 0]],
+                 64: [[1024, 64, 0], [1536, 64, 0], [2048, 64, 0]]}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("max_m2", sorted(CAPPED_SPLITS))
+def test_capped_row_length_parity(throughput_case, prec, max_m2):
+    s, K, p_pre, q_ref = throughput_case
+
+    def check(desc):
+        got = [[o["M1"], o["M2"], o["pairs"]] for o in desc["orders"]]
+        want = [[m1, m2, pr if prec != sag.SAG_FP64 else 0] for m1, m2, pr in CAPPED_SPLITS[max_m2]]
+        assert got == want
+
+    p, q, _, r = gpu_parts(s, s.n0, prec, max_m2=max_m2, check=check)
+    scale = np.abs(p).max() + np.abs(q_ref).max()
+    assert nerr(p[:K], p_pre, scale) < TOL[prec]
+    assert nerr(q, q_ref, scale) < TOL[prec]
+    assert nerr(r[:K], p_pre + q_ref[:K], scale) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [sag.SAG_FP32_SPLIT, sag.SAG_FP32_SPLIT_EXACT])
+def test_geometry_autotuner(throughput_case, prec):
+    # The rule's splits are timed first, then d = 2 and d = 3 with M2 halved
+    # (d = 4 would need a 1024-point compile-time column kernel); the plan
+    # keeps the last candidate marked kept, and its results match the oracle.
+    s, K, p_pre, q_ref = throughput_case
+    seen = {}
+
+    def check(desc):
+        seen.update(desc)
+
+    p, q, _, r = gpu_parts(s, s.n0, prec, autotune=1, check=check)
+    log = seen["geometry_autotune"]
+    assert len(log) == 3
+    assert log[0]["splits"] == [[256, 256], [384, 256], [512, 256]] and log[0]["kept"]
+    assert log[1]["splits"] == [[512, 128], [384, 256], [512, 256]]
+    assert log[2]["splits"][1] == [768, 128] and log[2]["splits"][2] == [512, 256]
+    assert all(e["ms_per_step"] > 0 for e in log)
+    chosen = [[o["M1"], o["M2"]] for o in seen["orders"]]
+    assert chosen == [e for e in log if e["kept"]][-1]["splits"]
+    assert all(o["pairs"] == 1 for o in seen["orders"])
+    scale = np.abs(p).max() + np.abs(q_ref).max()
     assert nerr(p[:K], p_pre, scale) < TOL[prec]
     assert nerr(q, q_ref, scale) < TOL[prec]
     assert nerr(r[:K], p_pre + q_ref[:K], scale) < TOL[prec]
@@ -333,14 +387,17 @@ def test_plans_with_different_footprints_coexist():
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", PRECS)
 def test_autotuned_plan_gives_the_same_results(prec):
-    # The autotuner only changes how the FFT stage is split into launches and
-    # streams: right-hand side and trajectory are bitwise the same.
+    # The stream-group autotuner only changes how the FFT stage is split into
+    # launches and streams: right-hand side and trajectory are bitwise the
+    # same. (These lengths have no compile-time pair kernels, so the split
+    # autotuner has no candidates.)
     import torch
     s = wl.random_cp(4, 5000, [4, 3, 2], seed=61)
     outs = []
     for autotune in (0, 1):
         with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, autotune=autotune) as pl:
             assert 1 <= pl.describe()["blocks"]["fft_groups"] <= 3
+            assert pl.describe()["geometry_autotune"] == []
             n = dev(s.n0)
             out = torch.empty_like(n)
             pl.rhs(n, out)
