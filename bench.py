@@ -57,6 +57,9 @@ def parse():
                          "prints the per-kernel table to stderr, no JSON line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plans with the fixed launch rules instead of the plan-time autotuner")
+    ap.add_argument("--m2", default=None,
+                    help="with --kernels: the four-step M2 of each order, comma-separated (the splits an "
+                         "autotuned plan reports), instead of tuning; profilers perturb the tuner's timings")
     ap.add_argument("--workload", default="throughput", choices=["throughput", "batched", "paper", "adjoint"],
                     help="batched: 256 independent systems in one plan vs a loop of plans; "
                          "paper: the shape of the paper's experiment (pure ternary Brownian "
@@ -302,8 +305,13 @@ def run_ours(args, world, rank, local):
     precs = {"all": everything, "both": everything, "fp32_split": (sag.SAG_FP32_SPLIT,),
              "fp32_split_exact": (sag.SAG_FP32_SPLIT_EXACT,), "fp64": (sag.SAG_FP64,)}[args.prec]
     if args.kernels:
-        # the timed run's plan: the same autotuned splits and stream groups
-        pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT, autotune=tune)
+        # the timed run's plan: the same autotuned splits and stream groups,
+        # or the splits given by --m2 with the rule's stream groups
+        if args.m2:
+            pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT,
+                          m2=[int(x) for x in args.m2.split(",")])
+        else:
+            pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT, autotune=tune)
         print("fft splits:", [[o["M1"], o["M2"]] for o in pl.describe()["orders"]], file=sys.stderr)
         n = torch.tensor(s.n0, device="cuda")
         pl.profile(True)

@@ -115,6 +115,15 @@ typedef struct {
                             power of two in [4, 512] that caps M2 (shorter rows, longer
                             columns; for tests and tuning). A column length M1 above
                             4096 is SAG_EUNSUPPORTED. */
+  const int32_t* m2;     /* NULL (default), or n_m2 host values: the four-step M2 of each
+                            order of the plan, in the order sag_plan_describe lists
+                            them (systems in turn, orders d = 2..D with a nonzero CP
+                            rank; every order of a TT system). 0 keeps the rule for
+                            that order; otherwise a power of two in [4, 512] dividing
+                            M = L/2, with M1 = M / M2 <= 4096. This reproduces the
+                            splits an autotuned plan reports, without tuning again;
+                            it replaces max_m2 and the split search. */
+  int32_t n_m2;          /* entries of m2: the plan's order count, else SAG_EINVAL */
 } sag_options;
 
 /* Fills *opt with the defaults. */

@@ -203,6 +203,8 @@ void sag_default_options(sag_options* opt) {
   opt->symmetrize_q = 1;
   opt->autotune = 0;
   opt->max_m2 = 0;
+  opt->m2 = nullptr;
+  opt->n_m2 = 0;
 }
 
 const char* sag_last_error(void) { return g_err.c_str(); }

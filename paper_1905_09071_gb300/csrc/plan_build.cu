@@ -169,6 +169,13 @@ sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options&
   if (opt.autotune != 0 && opt.autotune != 1) return fail(SAG_EINVAL, "autotune must be 0 or 1");
   if (opt.max_m2 != 0 && (opt.max_m2 < 4 || opt.max_m2 > 512 || (opt.max_m2 & (opt.max_m2 - 1)) != 0))
     return fail(SAG_EINVAL, "max_m2 must be 0 or a power of two in [4, 512]");
+  if ((opt.m2 == nullptr) != (opt.n_m2 == 0) || opt.n_m2 < 0)
+    return fail(SAG_EINVAL, "m2 and n_m2 go together (NULL and 0, or n_m2 >= 1 values)");
+  for (int i = 0; i < opt.n_m2; ++i) {
+    const int u = opt.m2[i];
+    if (u != 0 && (u < 4 || u > 512 || (u & (u - 1)) != 0))
+      return fail(SAG_EINVAL, "m2 entries must be 0 or powers of two in [4, 512]");
+  }
   for (int b = 0; b < B; ++b) {
     const sag_system& s = sys[b];
     const std::string at = B > 1 ? " (system " + std::to_string(b) + ")" : "";
@@ -363,6 +370,8 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   if (Vtot == 0) return fail(SAG_EINVAL, "every kernel is identically zero");
 
   // ---- FFT geometry of each item ------------------------------------------
+  if (opt.m2 && opt.n_m2 != (int)I.size())
+    return fail(SAG_EINVAL, "m2 needs one entry per order of the plan (" + std::to_string(I.size()) + ")");
   int64_t scr = 0, scr2 = 0, pdo = 0;
   size_t col_smem = 0, row_smem = 0, rowtt_smem = 0;
   std::vector<int> colpre(1, 0), colpre_all(1, 0), invpre(1, 0), chainpre(1, 0);
@@ -378,6 +387,12 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     int M2 = 1;
     while ((int64_t)(2 * M2) * (2 * M2) <= od.M && 2 * M2 <= m2cap && od.M % (2 * M2) == 0) M2 *= 2;
     const size_t ix = (size_t)(&od - I.data());
+    if (opt.m2 && opt.m2[ix] > 0) {
+      if (od.M % opt.m2[ix] != 0 || od.M / opt.m2[ix] > 4096)
+        return fail(SAG_EINVAL, "m2 entry " + std::to_string(ix) + " must divide M = " + std::to_string(od.M) +
+                                    " with M / M2 <= 4096");
+      M2 = opt.m2[ix];
+    }
     if (ix < pl->m2_pref.size() && pl->m2_pref[ix] > 0 && od.M % pl->m2_pref[ix] == 0) M2 = pl->m2_pref[ix];
     od.M2 = M2;
     od.M1 = od.M / M2;
@@ -921,7 +936,7 @@ void log_geometry(std::string& log, const sag_plan_s* of, float ms, bool kept) {
 sag_status autotune_geometry(const sag_system* sys, int32_t B, const sag_options& opt, sag_plan_s** plp) {
   sag_plan_s* best = *plp;
   const int n = (int)best->items.size();
-  if (!best->P.dwpath || best->fmt != SAG_CP || n > kMaxFftGroups) return SAG_OK;
+  if (opt.m2 || !best->P.dwpath || best->fmt != SAG_CP || n > kMaxFftGroups) return SAG_OK;
   std::vector<int> pref(n);
   bool any = false;
   for (int i = 0; i < n; ++i) {

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_function(lib):
 def test_version_and_defaults(lib):
     assert b"sm_103a" in lib.sag_version()
     assert sag.default_options() == {"prec": sag.SAG_FP32_SPLIT, "rk": sag.SAG_HEUN,
-                                     "symmetrize_q": 1, "autotune": 0, "max_m2": 0}
+                                     "symmetrize_q": 1, "autotune": 0, "max_m2": 0, "m2": None}
 
 
 def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=True, out=True):
@@ -71,11 +71,21 @@ def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=
     (dict(opt=(1, 0, 1, 0, 96)), sag.SAG_EINVAL),
     (dict(opt=(1, 0, 1, 0, 1024)), sag.SAG_EINVAL),
     (dict(opt=(1, 0, 1, 0, -4)), sag.SAG_EINVAL),
+    (dict(opt=(1, 0, 1, 0, 0, None, 2)), sag.SAG_EINVAL),  # n_m2 without m2
 ])
 def test_plan_rejects_bad_arguments(kw, status):
     st, msg = _plan_status(**kw)
     assert st == status
     assert msg
+
+
+@pytest.mark.parametrize("m2,n", [([256, 96], 2), ([2, 0], 2), ([0, 1024], 2), ([256], 0)])
+def test_plan_rejects_bad_m2(m2, n):
+    arr = np.array(m2, dtype=np.int32)
+    opt = (sag.SAG_FP32_SPLIT, sag.SAG_HEUN, 1, 0, 0, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n)
+    st, msg = _plan_status(opt=opt)
+    assert st == sag.SAG_EINVAL
+    assert "m2" in msg
 
 
 def test_batched_plan_rejects_mixed_formats_and_bad_tt_ranks(lib):

@@ -188,6 +188,33 @@ def test_geometry_autotuner(throughput_case, prec):
     assert nerr(r[:K], p_pre + q_ref[:K], scale) < TOL[prec]
 
 
+def test_m2_reproduces_tuned_splits(throughput_case):
+    # Passing back the splits an autotuned plan reports builds the same
+    # geometry without tuning, with bitwise the same right-hand side.
+    s, K, p_pre, q_ref = throughput_case
+    outs, splits = [], None
+    for kw in (dict(autotune=1), "m2"):
+        if kw == "m2":
+            kw = dict(m2=splits)
+        with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT, **kw) as pl:
+            desc = pl.describe()
+            got = [o["M2"] for o in desc["orders"]]
+            if splits is None:
+                splits = got
+            else:
+                assert got == splits and desc["geometry_autotune"] == []
+            n = dev(s.n0)
+            out = torch.empty_like(n)
+            pl.rhs(n, out)
+            torch.cuda.synchronize()
+            outs.append(out.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    with pytest.raises(sag.SagError):  # one entry per order
+        sag.Plan(s.N, s.D, s.ranks, s.factors, m2=splits[:2])
+    with pytest.raises(sag.SagError):  # M2 must divide M = L/2 = 65536 (d = 2) with M1 <= 4096
+        sag.Plan(s.N, s.D, s.ranks, s.factors, m2=[8, 0, 0])
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("kernel", ["constant", "product"])
 def test_full_length_fft_geometric_closed_form(kernel, prec):
