@@ -207,9 +207,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int* pre = all ? P.colpre_all : P.colpre;
   const int bid = base + blockIdx.x;  // launches may cover a range of the table
-  const int it = find_segment(pre, P.nitems, bid);
+  const int pos = find_segment(pre, P.nitems, bid);
+  const int it = all ? pos : P.colperm[pos];  // colpre runs in colperm order
   const OrderDesc& od = P.ord[it];
-  const int local = bid - pre[it];
+  const int local = bid - pre[pos];
   if constexpr (KIND >= kKindPair) {  // every block of the launch: a pair at this column length
     const int pr = local / od.ncolblk_p, cbp = local - pr * od.ncolblk_p;
     fwd_col_pair_body<C, ct_len(KIND - kKindPair)>(P, od, pr, cbp, buf);

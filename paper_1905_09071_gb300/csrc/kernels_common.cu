@@ -90,11 +90,17 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ RhsParams P
   } else {
     for (int i = cnt - 1; i >= 0; --i) acc1 = fma(u[first + i * 256], x[first + i * 256], acc1);
   }
-  double acc[2] = {acc1, flux ? (double)(first + 1) * acc1 + 256.0 * (acc2 - acc1) : 0.0};
-  block_sum<2>(acc, sh);
-  if (threadIdx.x == 0) {
-    P.dot_s[(int64_t)v * P.maxdotchunk + c] = acc[0];
-    if (flux) P.dot_t[(int64_t)v * P.maxdotchunk + c] = acc[1];
+  if (flux) {
+    double acc[2] = {acc1, (double)(first + 1) * acc1 + 256.0 * (acc2 - acc1)};
+    block_sum<2>(acc, sh);
+    if (threadIdx.x == 0) {
+      P.dot_s[(int64_t)v * P.maxdotchunk + c] = acc[0];
+      P.dot_t[(int64_t)v * P.maxdotchunk + c] = acc[1];
+    }
+  } else {  // one reduction instead of two: the FP64 adds of the tree count
+    double acc[1] = {acc1};
+    block_sum<1>(acc, sh);
+    if (threadIdx.x == 0) P.dot_s[(int64_t)v * P.maxdotchunk + c] = acc[0];
   }
 }
 

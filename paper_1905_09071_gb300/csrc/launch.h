@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "plan.h"
 
 namespace sag {
@@ -54,9 +56,11 @@ enum KernelId : int {
 
 // Splits the blocks [b0, b1) of table t into runs of equal specialisation
 // and calls launch(kind, r0, r1) for each; with more than kMaxKindRuns runs
-// (a batch of systems with mixed lengths) it launches the run-time
-// dispatching kernel over the whole range instead (kind kKindGeneral).
-constexpr int kMaxKindRuns = 8;
+// it launches the run-time dispatching kernel over the whole range instead
+// (kind kKindGeneral). Plans whose items alternate between many kinds (a
+// batch of systems with mixed lengths) order their block tables by kind
+// (kind_order), so that they stay within one run per kind.
+constexpr int kMaxKindRuns = kKindCount;
 template <class F>
 cudaError_t for_kind_runs(const KindTable& t, int b0, int b1, F&& launch) {
   if (b1 <= b0) return cudaSuccess;
@@ -84,6 +88,20 @@ cudaError_t for_kind_runs(const KindTable& t, int b0, int b1, F&& launch) {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Order of a block table's entries: the identity when kinds[] (in item order)
+// forms at most kMaxKindRuns runs of equal kind, else the items stably sorted
+// by kind. Returns whether it sorted.
+inline bool kind_order(const int* kinds, int n, int* order) {
+  int runs = 0;
+  for (int i = 0; i < n; ++i) {
+    order[i] = i;
+    runs += (i == 0 || kinds[i] != kinds[i - 1]);
+  }
+  if (runs <= kMaxKindRuns) return false;
+  std::stable_sort(order, order + n, [&](int a, int b) { return kinds[a] < kinds[b]; });
+  return true;
 }
 
 // Optional hook called before each kernel launch (id) and once after the last

@@ -118,7 +118,8 @@ struct RhsParams {
   int maxdotchunk;               // most chunks of any vector
   const OrderDesc* ord;          // [nitems]
   const SysDesc* sys;            // [B]
-  const int* colpre;             // [nitems + 1] forward column kernel blocks (nu per item)
+  const int* colpre;             // [nitems + 1] forward column kernel blocks (nu per item), in colperm order
+  const int* colperm;            // [nitems] items in forward-column table order (by kernel kind in mixed batches)
   const int* colpre_all;         // [nitems + 1] column blocks over every vector (nvec per item; the adjoint)
   const int* umap;               // CP items with duplicates: spectrum slot of vector m R + r (d R entries)
   const int* ulist;              // the same items: vector (m R + r) transformed into slot u (nu entries)

@@ -602,14 +602,31 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   P.scratch2 = scratch2;
   OrderDesc* d_ord = nullptr;
   SysDesc* d_sys = nullptr;
-  int *d_colpre = nullptr, *d_colpre_all = nullptr, *d_umap = nullptr, *d_ulist = nullptr,
+  // Forward-column table order: the items' natural order, or the items sorted
+  // by kernel specialisation when that order alternates between more kinds
+  // than the launcher issues launches for (mixed batches); the table then
+  // holds one run per kind. colpre follows this order.
+  std::vector<int> colkind_nat(I.size()), colperm(I.size());
+  for (size_t i = 0; i < I.size(); ++i) {
+    const OrderDesc& od = I[i];
+    const int ct = od.ct1 ? kKindCt + ct_index(od.M1) : kKindRuntime;
+    colkind_nat[i] = !dwp ? kKindGeneral : od.pair ? kKindPair + ct_index(od.M1) : ct;
+  }
+  pl->col_sorted = kind_order(colkind_nat.data(), (int)I.size(), colperm.data());
+  std::vector<int> colpre_t(1, 0), colkind_t;
+  for (int i : colperm) {
+    colpre_t.push_back(colpre_t.back() + colpre[i + 1] - colpre[i]);
+    colkind_t.push_back(colkind_nat[i]);
+  }
+  int *d_colpre = nullptr, *d_colpre_all = nullptr, *d_umap = nullptr, *d_ulist = nullptr, *d_colperm = nullptr,
       *d_rowpre = nullptr, *d_invpre = nullptr, *d_chainpre = nullptr,
       *d_epipre = nullptr, *d_vsys = nullptr, *d_rowperm = nullptr, *d_vid = nullptr;
   int64_t* d_voff = nullptr;
   int64_t* d_vdwoff = nullptr;
   float* d_vw = nullptr;
   if (pl->upload(&d_ord, I) != cudaSuccess || pl->upload(&d_sys, S) != cudaSuccess ||
-      pl->upload(&d_colpre, colpre) != cudaSuccess || pl->upload(&d_rowpre, rowpre) != cudaSuccess ||
+      pl->upload(&d_colpre, colpre_t) != cudaSuccess || pl->upload(&d_colperm, colperm) != cudaSuccess ||
+      pl->upload(&d_rowpre, rowpre) != cudaSuccess ||
       pl->upload(&d_colpre_all, colpre_all) != cudaSuccess || pl->upload(&d_umap, umap) != cudaSuccess ||
       pl->upload(&d_ulist, ulist) != cudaSuccess ||
       pl->upload(&d_invpre, invpre) != cudaSuccess || pl->upload(&d_chainpre, chainpre) != cudaSuccess ||
@@ -621,6 +638,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   P.ord = d_ord;
   P.sys = d_sys;
   P.colpre = d_colpre;
+  P.colperm = d_colperm;
   P.colpre_all = d_colpre_all;
   P.umap = d_umap;
   P.ulist = d_ulist;
@@ -677,18 +695,17 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   // stream (the FP64 kernels, bound by the FP64 pipe, gain nothing from the
   // overlap and lose a little); else one launch per kernel. With autotune the
   // plan times 1..4 groups instead.
-  pl->h_colpre = colpre;
+  pl->h_colpre = colpre_t;
   pl->h_colpre_all = colpre_all;
   pl->h_invpre = invpre;
-  // Kernel specialisation of each item's column blocks (the row table's
-  // follow its order, set by configure_fft_groups).
-  pl->h_colkind.resize(I.size());
+  // Kernel specialisation of the column table entries (table order; the row
+  // table's follow its order, set by configure_fft_groups). The adjoint's
+  // table over every vector keeps the item order.
+  pl->h_colkind = colkind_t;
   pl->h_colkind_all.resize(I.size());
   for (size_t i = 0; i < I.size(); ++i) {
     const OrderDesc& od = I[i];
-    const int ct = od.ct1 ? kKindCt + ct_index(od.M1) : kKindRuntime;
-    pl->h_colkind[i] = !dwp ? kKindGeneral : od.pair ? kKindPair + ct_index(od.M1) : ct;
-    pl->h_colkind_all[i] = dwp ? ct : kKindGeneral;
+    pl->h_colkind_all[i] = dwp ? (od.ct1 ? kKindCt + ct_index(od.M1) : kKindRuntime) : kKindGeneral;
   }
   const int ni = (int)I.size();
   pl->L.col = KindTable{pl->h_colpre.data(), pl->h_colkind.data(), ni};
@@ -717,6 +734,7 @@ sag_status configure_fft_groups(sag_plan_s* pl, int G) {
   RhsParams& P = pl->P;
   const int n = P.nitems;
   G = std::max(1, std::min(G, std::min(n, (int)kMaxFftGroups)));
+  if (pl->col_sorted) G = 1;  // groups take consecutive items of the item-ordered tables
   std::vector<int> cut(G + 1, 0);
   cut[G] = n;
   if (G == n) {
@@ -752,23 +770,36 @@ sag_status configure_fft_groups(sag_plan_s* pl, int G) {
     }
     rstart[c + 1] = (int)rowperm.size();
   }
+  // Row kernel specialisation of each item (kKindGeneral for TT plans, whose
+  // rows run other kernels, and for FP64).
+  auto row_kind = [&](int item) {
+    const OrderDesc& od = pl->items[item];
+    if (!P.dwpath || pl->fmt == SAG_TT) return (int)kKindGeneral;
+    return od.pair ? kKindPair + ct_index(2 * od.M2) : od.ct2 ? kKindCt + ct_index(od.M2) : kKindRuntime;
+  };
+  if (G == 1) {
+    // one launch per kind: order the rows by kind where the heaviest-first
+    // order alternates between more kinds than launches (heaviest first
+    // within each kind)
+    std::vector<int> kinds(n), ord(n);
+    for (int j = 0; j < n; ++j) kinds[j] = row_kind(rowperm[j]);
+    if (kind_order(kinds.data(), n, ord.data())) {
+      std::vector<int> rp(n);
+      for (int j = 0; j < n; ++j) rp[j] = rowperm[ord[j]];
+      rowperm = rp;
+      for (int j = 0; j < n; ++j) rowpre[j + 1] = rowpre[j] + pl->h_nrowpair[rowperm[j]];
+    }
+  }
   cudaError_t e;
   if ((e = cudaMemcpy((void*)P.rowperm, rowperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy((void*)P.rowpre, rowpre.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice)) !=
           cudaSuccess)
     return cuda_fail(e, "row block order");
-  // Row kernel specialisation per row-table entry (kKindGeneral for TT plans,
-  // whose rows run other kernels, and for FP64).
+  // Row kernel specialisation per row-table entry.
   pl->h_rowperm = rowperm;
   pl->h_rowpre = rowpre;
   pl->h_rowkind.resize(n);
-  for (int j = 0; j < n; ++j) {
-    const OrderDesc& od = pl->items[rowperm[j]];
-    int kind = kKindGeneral;
-    if (P.dwpath && pl->fmt != SAG_TT)
-      kind = od.pair ? kKindPair + ct_index(2 * od.M2) : od.ct2 ? kKindCt + ct_index(od.M2) : kKindRuntime;
-    pl->h_rowkind[j] = kind;
-  }
+  for (int j = 0; j < n; ++j) pl->h_rowkind[j] = row_kind(rowperm[j]);
   pl->L.row = KindTable{pl->h_rowpre.data(), pl->h_rowkind.data(), n};
   pl->groups.n = 0;
   pl->fft_groups = G;
@@ -870,7 +901,7 @@ sag_status load_tuning_input(sag_plan_s* pl) {
 sag_status autotune_fft_groups(sag_plan_s* pl) {
   sag_status st = load_tuning_input(pl);
   if (st != SAG_OK) return st;
-  const int gmax = std::min(pl->P.nitems, (int)kMaxFftGroups);
+  const int gmax = pl->col_sorted ? 1 : std::min(pl->P.nitems, (int)kMaxFftGroups);
   float t[kMaxFftGroups + 1];
   for (int G = 1; G <= gmax; ++G) t[G] = 1e30f;
   for (int sweep = 0; sweep < 3; ++sweep)

@@ -58,6 +58,7 @@ struct sag_plan_s {
   sag::FftGroups groups{};
   int fft_groups = 1;                     // stream groups of the FFT stage (1: one launch per kernel)
   std::vector<int> m2_pref;               // per item: M2 of its four-step split (0: the rule)
+  bool col_sorted = false;                // column and row tables ordered by kernel kind (one FFT group)
   std::string tune_log;                   // candidates the geometry autotuner timed (JSON objects)
   std::vector<int> h_colpre, h_invpre;    // host copies of the block tables, for regrouping
   std::vector<int> h_colpre_all, h_rowpre, h_rowperm;

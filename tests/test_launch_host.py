@@ -1,7 +1,8 @@
 """Host-side check of the launch splitter that issues one kernel
 specialisation per run of equal kind (``csrc/launch.h``): merging of adjacent
 entries, cut ranges, empty entries, the fallback to the dispatching kernel
-beyond eight runs, and the compile-time length maps. No GPU."""
+beyond kMaxKindRuns runs, the kind order of mixed tables, and the compile-time
+length maps. No GPU."""
 import os
 import shutil
 import subprocess
