@@ -403,9 +403,6 @@ def run_ours(args, world, rank, local):
                    "ops_per_launch": dw["work"][k]["ops"],
                    "bytes_per_launch": dw["work"][k]["bytes"]} for k, v in dw["prof"].items()}
     kernels_per_step = sum(v[1] for v in dw["prof"].values()) / K
-    # the profiled single steps split n every step; sag_integrate (the timed
-    # region) splits it in its first step only (k_nmax, k_nsplit)
-    split_per_step = sum(dw["prof"].get(k, (0.0, 0))[1] for k in ("k_nmax", "k_nsplit")) / K
     n_bytes = 8 * s.N
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -444,7 +441,7 @@ def run_ours(args, world, rank, local):
                                     (FP64_PEAK_PER_SM_CLK if w["ops_fp64"] else FP32_PEAK_PER_SM_CLK)},
         "kernels": kernels,
         "clocks": clocks,
-        "gpu_launches": int(round(kernels_per_step * K - split_per_step * (K - 1))) + 1,
+        "gpu_launches": int(round(kernels_per_step * K)) + 1,
         "e2e": {"value": K * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n_bytes,
                 "d2h_bytes_per_step": n_bytes},
         "cpu_baseline": cpu,
