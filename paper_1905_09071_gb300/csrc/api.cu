@@ -103,14 +103,8 @@ sag_status replay(sag_plan_t pl, const sag_plan_s::GraphKey& k, cudaStream_t st,
   return SAG_OK;
 }
 
-// One RK2 step. The first stage writes n*'s double-word copy at n's scale, so
-// the second evaluation starts at its FFTs. With chain = false the step
-// starts by splitting n (k_nmax, k_nsplit: a new scale); with chain = true n's
-// copy was written by the previous step of the same sag_integrate call, at
-// the scale that call chose. Either way the second stage also writes the new
-// state's copy, so that a chained step can follow.
 sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaStream_t st,
-                        bool allow_hook, bool chain = false) {
+                        bool allow_hook) {
   EpiArgs a{};
   a.nin = n;
   a.k1buf = pl->k1buf;
@@ -118,8 +112,9 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
   a.dt = dt;
   a.mode = pl->rk == SAG_HEUN ? EPI_HEUN1 : EPI_MID1;
   a.flux = diag != nullptr;  // the outflow is only reported through diag
+  // The first stage writes n*'s double-word copy at n's scale, so the second
+  // evaluation starts at its FFTs (the scale is renewed every step).
   a.split_next = pl->P.dwpath;
-  a.presplit = chain && pl->P.dwpath;
   sag_status s = eval(pl, n, a, st, allow_hook);
   if (s != SAG_OK) return s;
   EpiArgs b{};
@@ -131,7 +126,6 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
   b.mode = pl->rk == SAG_HEUN ? EPI_HEUN2 : EPI_MID2;
   b.flux = a.flux;
   b.presplit = pl->P.dwpath;
-  b.split_next = pl->P.dwpath;
   return eval(pl, pl->nstar, b, st, allow_hook);
 }
 
@@ -373,37 +367,30 @@ sag_status sag_integrate(sag_plan_t pl, double* n, double dt, int64_t steps, dou
   }
   if ((e = enqueue_moments(pl->P, nd, dd, st)) != cudaSuccess) return cuda_fail(e, "moments");
   if (steps > 0) {
-    // Two graphs: the first step splits n at a new scale; the others chain
-    // on the copy the step before wrote (double-word path; the FP64 path's
-    // two graphs are the same step).
-    if (!pl->gexec || !pl->gexec_chain || pl->g_n != nd || pl->g_dt != dt || pl->g_diag != dd) {
-      for (cudaGraphExec_t* x : {&pl->gexec, &pl->gexec_chain})
-        if (*x) {
-          cudaGraphExecDestroy(*x);
-          *x = nullptr;
-        }
-      for (int chain = 0; chain < 2; ++chain) {
-        cudaGraph_t g = nullptr;
-        if ((e = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-          return cuda_fail(e, "begin capture");
-        sag_status s = enqueue_step(pl, nd, dt, dd, pl->cap_stream, false, chain == 1);
-        e = cudaStreamEndCapture(pl->cap_stream, &g);
-        if (s != SAG_OK) {
-          if (g) cudaGraphDestroy(g);
-          return s;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "end capture");
-        e = cudaGraphInstantiate(chain ? &pl->gexec_chain : &pl->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    if (!pl->gexec || pl->g_n != nd || pl->g_dt != dt || pl->g_diag != dd) {
+      if (pl->gexec) {
+        cudaGraphExecDestroy(pl->gexec);
+        pl->gexec = nullptr;
       }
+      cudaGraph_t g = nullptr;
+      if ((e = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "begin capture");
+      sag_status s = enqueue_step(pl, nd, dt, dd, pl->cap_stream, false);
+      e = cudaStreamEndCapture(pl->cap_stream, &g);
+      if (s != SAG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "end capture");
+      e = cudaGraphInstantiate(&pl->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
       pl->g_n = nd;
       pl->g_dt = dt;
       pl->g_diag = dd;
     }
     for (int64_t i = 0; i < steps; ++i)
-      if ((e = cudaGraphLaunch(i == 0 ? pl->gexec : pl->gexec_chain, st)) != cudaSuccess)
-        return cuda_fail(e, "graph launch");
+      if ((e = cudaGraphLaunch(pl->gexec, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
   }
   if (nh && (e = cudaMemcpyAsync(n, nd, nb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_fail(e, "copy n back");
@@ -639,11 +626,10 @@ sag_status sag_plan_set_wait_limit(sag_plan_t pl, int64_t cycles, int32_t unmet)
   // captured graphs hold the old limit in their kernel parameters
   for (auto& g : pl->gcache) cudaGraphExecDestroy(g.second);
   pl->gcache.clear();
-  for (cudaGraphExec_t* x : {&pl->gexec, &pl->gexec_chain})
-    if (*x) {
-      cudaGraphExecDestroy(*x);
-      *x = nullptr;
-    }
+  if (pl->gexec) {
+    cudaGraphExecDestroy(pl->gexec);
+    pl->gexec = nullptr;
+  }
   return SAG_OK;
 }
 

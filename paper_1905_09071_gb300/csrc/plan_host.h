@@ -79,8 +79,7 @@ struct sag_plan_s {
     int64_t i0 = 0;
   };
   std::vector<std::pair<GraphKey, cudaGraphExec_t>> gcache;
-  cudaGraphExec_t gexec = nullptr;        // sag_integrate: the first step (splits n)
-  cudaGraphExec_t gexec_chain = nullptr;  // sag_integrate: the steps after it
+  cudaGraphExec_t gexec = nullptr;
   const double* g_n = nullptr;
   double g_dt = 0.0;
   double* g_diag = nullptr;
@@ -103,7 +102,6 @@ struct sag_plan_s {
   }
   ~sag_plan_s() {
     if (gexec) cudaGraphExecDestroy(gexec);
-    if (gexec_chain) cudaGraphExecDestroy(gexec_chain);
     for (auto& g : gcache) cudaGraphExecDestroy(g.second);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (side.stream) cudaStreamDestroy(side.stream);

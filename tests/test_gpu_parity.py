@@ -269,25 +269,6 @@ def test_host_buffers_equal_device_buffers():
         assert np.array_equal(nh, n.cpu().numpy())
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_integrate_chains_steps_like_single_steps(prec):
-    # sag_integrate splits n once and chains later steps on the double-word
-    # copy the step before wrote, at that first scale; single steps split
-    # every time. While max |n| stays in one binade the two scales agree and
-    # so do the states, bitwise.
-    s = wl.random_cp(3, 700, [3, 4], seed=16)
-    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec) as pl:
-        a, b = dev(s.n0), dev(s.n0)
-        pl.integrate(a, 1e-3, 4)
-        for _ in range(4):
-            pl.rk2_step(b, 1e-3)
-        torch.cuda.synchronize()
-        assert pl.sync_status() == sag.SAG_OK
-        x, y = a.cpu().numpy(), b.cpu().numpy()
-        assert math.frexp(np.abs(x).max())[1] == math.frexp(np.abs(s.n0).max())[1]
-        assert np.array_equal(x, y)
-
-
 def test_rhs_in_place_alias():
     s = wl.random_cp(3, 300, [2, 2], seed=13)
     with sag.Plan(s.N, s.D, s.ranks, s.factors) as pl:
