@@ -441,7 +441,8 @@ def run_ours(args, world, rank, local):
                                     (FP64_PEAK_PER_SM_CLK if w["ops_fp64"] else FP32_PEAK_PER_SM_CLK)},
         "kernels": kernels,
         "clocks": clocks,
-        "gpu_launches": int(round(kernels_per_step * K)) + 1,
+        "gpu_launches": (dw["desc"]["launches_per_step"] * K if dw["desc"].get("launches_per_step", -1) > 0
+                         else int(round(kernels_per_step * K))) + 1,
         "e2e": {"value": K * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n_bytes,
                 "d2h_bytes_per_step": n_bytes},
         "cpu_baseline": cpu,

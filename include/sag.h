@@ -134,8 +134,8 @@ void sag_default_options(sag_options* opt);
  * chooses FFT lengths L_d >= d N (products of 2, 3, 5), builds twiddle tables,
  * copies the factors (FP64, plus the double-word copy for SAG_FP32_SPLIT; TT
  * core vectors that are identically zero are skipped) and allocates the
- * workspace. Every kernel of an evaluation then covers all B systems in one
- * launch. Limits: N <= 2^22, d N <= 2^24, CP ranks <= 4096, TT ranks <= 16.
+ * workspace. Every kernel of an evaluation then covers all B systems, with one
+ * launch per kernel specialisation (column or row length). Limits: N <= 2^22, d N <= 2^24, CP ranks <= 4096, TT ranks <= 16.
  * A CP rank of 0 leaves that order out (for example a purely ternary system:
  * D = 3 with R_2 = 0); every system needs one order of rank >= 1.
  * opt may be NULL (defaults). On success *out holds the plan. */
@@ -241,7 +241,11 @@ sag_status sag_kernel_work(sag_plan_t plan, int32_t id, double* ops, int32_t* op
                            double* bytes);
 
 /* JSON description of the plan's FFT geometry (per order: L, M1, M2, radix
- * schedules, block shapes), written to buf (NUL-terminated, truncated to len). */
+ * schedules, block shapes), its launch layout, the split autotuner's
+ * candidates, and launches_per_step: the kernel launches of one sag_integrate
+ * step without diagnostics (the kernel nodes of the step captured as a graph,
+ * not launched; -1 if the capture fails). Written to buf (NUL-terminated,
+ * truncated to len). */
 sag_status sag_plan_describe(sag_plan_t plan, char* buf, size_t len);
 
 /* Loss term without allocation: q = sum_d Q^(d)[n] (same definition and

@@ -782,6 +782,34 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
   return SAG_OK;
 }
 
+namespace {
+
+// Kernel launches of one sag_integrate step (no diagnostics): the kernel
+// nodes of the step captured as a graph, which is not launched. -1 if the
+// capture fails.
+int step_kernel_launches(sag_plan_t pl) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -1;
+  const sag_status s = enqueue_step(pl, pl->stage_a, 0.0, nullptr, pl->cap_stream, false);
+  const cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+  int count = -1;
+  size_t nn = 0;
+  if (s == SAG_OK && e == cudaSuccess && g && cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess) {
+      count = 0;
+      for (cudaGraphNode_t x : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(x, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++count;
+      }
+    }
+  }
+  if (g) cudaGraphDestroy(g);
+  return count;
+}
+
+}  // namespace
+
 sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
   if (!pl || !buf || len == 0) return fail(SAG_EINVAL, "NULL argument");
   const RhsParams& P = pl->P;
@@ -811,6 +839,7 @@ sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
         ", \"fft_groups\": " + std::to_string(pl->fft_groups) +
         ", \"inv_col\": " + std::to_string(pl->L.inv_blocks) + ", \"epilogue\": " +
         std::to_string(pl->L.epi_blocks) + "}, \"device_bytes\": " + std::to_string(pl->bytes) +
+        ", \"launches_per_step\": " + std::to_string(step_kernel_launches(pl)) +
         ", \"geometry_autotune\": [" + pl->tune_log + "]}";
   std::snprintf(buf, len, "%s", js.c_str());
   return SAG_OK;
