@@ -215,6 +215,53 @@ def oracle_sample(s, seconds: float, max_samples: int = 10 ** 9, warmup: int = 0
     return per_conv * convs_per_rhs, len(times), cores
 
 
+def fft_method_rhs(s, n, workers: int = -1):
+    """dn/dt of a CP system by the paper's low-rank method on the CPU with a
+    library FP64 FFT (scipy.fft): the gain term of order d is the sum over r
+    of the truncated d-fold convolution of a^(m)_r = U^(m)_r n (index = size,
+    length L >= d N, so sizes 1..N do not alias), divided by d!; the loss term
+    is the symmetrised kernel's, -n_k/(d-1)! (1/d) sum_m sum_r U^(m)_r(k)
+    prod_{m' != m} <U^(m')_r, n> (Sec. 1). A secondary CPU baseline (not the
+    oracle)."""
+    import math
+    import scipy.fft as sf
+    from paper_1905_09071_gb300 import workloads as wl
+    N, D = s.N, s.D
+    n = np.asarray(n, dtype=np.float64)
+    offs = wl.cp_layout(D, N, s.ranks)
+    rhs = np.zeros(N)
+    for d in range(2, D + 1):
+        R = s.ranks[d - 2]
+        if R == 0:
+            continue
+        U = np.asarray(s.factors[offs[d - 2]:offs[d - 1]], dtype=np.float64).reshape(d, R, N)
+        L = sf.next_fast_len(d * N + 1, real=True)
+        a = np.zeros((d, R, L))
+        a[:, :, 1:N + 1] = U * n
+        F = sf.rfft(a, axis=-1, workers=workers)
+        S = F.prod(axis=0).sum(axis=0)
+        rhs += sf.irfft(S, n=L, workers=workers)[1:N + 1] / math.factorial(d)
+        sv = U @ n  # (d, R) inner products
+        w = np.zeros(N)
+        for m in range(d):
+            w += np.prod(np.delete(sv, m, axis=0), axis=0) @ U[m]
+        rhs -= n * w / (d * math.factorial(d - 1))
+    return rhs
+
+
+def cpu_fft_baseline(s, reps: int = 3):
+    """Best of `reps` right-hand sides of fft_method_rhs on all host cores."""
+    cores = os.cpu_count() or 1
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fft_method_rhs(s, s.n0, workers=cores)
+        best = min(best, time.perf_counter() - t0)
+    return {"value": 1.0 / (2 * best), "unit": UNIT, "cores": cores,
+            "kind": "the paper's low-rank method with scipy.fft (FP64), not the oracle",
+            "sample": f"one full right-hand side of the workload, best of {reps}; 2 per RK2 step"}
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
     if rank != 0:
@@ -411,6 +458,7 @@ def run_ours(args, world, rank, local):
                "sample": f"{samples} one-convolution samples (D=2 rank-one subsystems of the "
                          f"workload's term vectors, oracle direct mode) scaled by the 96 "
                          f"convolutions of a full right-hand side and 2 right-hand sides per step"}
+    cpu_fft = cpu_fft_baseline(s) if not args.no_cpu_baseline and world == 1 else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": dw["t"] / K * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -446,6 +494,7 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": K * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n_bytes,
                 "d2h_bytes_per_step": n_bytes},
         "cpu_baseline": cpu,
+        "cpu_fft_baseline": cpu_fft,
     }
     print(json.dumps(out), flush=True)
 
@@ -542,6 +591,11 @@ def run_paper(args, world, rank, local):
     ref = rhs_at_n0[("cp", "fp64")]
     scale = np.abs(ref).max()
     tt_vs_cp = {p: float(np.abs(rhs_at_n0[("tt", p)] - ref).max() / scale) for p in ("fp32_split", "fp64")}
+    cpu_fft = None
+    if not args.no_cpu_baseline and world == 1:
+        # the CP form by the same method on the host cores with scipy.fft (FP64)
+        c = cpu_fft_baseline(wl.paper_ternary(N, "cp"), reps=2)
+        cpu_fft = dict(c, seconds_for_100_steps=K / c["value"])
     out = {"metric": "paper-shape RK2 steps/s (pure ternary Brownian kernel, N=2^19, 100 steps)",
            "value": res[("tt", "fp32_split")]["steps_per_s"], "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": W, "higher_is_better": True, "scaling": "weak", "data": "synthetic",
@@ -550,6 +604,7 @@ def run_paper(args, world, rank, local):
                                   "start or the step)"},
            "runs": {f"{f}_{p}": v for (f, p), v in res.items()},
            "tt_vs_cp_rhs_at_n0": tt_vs_cp,
+           "cpu_fft_baseline": cpu_fft,
            "context": {"paper_table1_128_cores_seconds": 12.22, "paper_table1_1_core_seconds": 257.80,
                        "note": "Table 1: the same kernel family and N on CPU cores (MKL ClusterFFT, "
                                "MPI), mu and precision not stated"}}
