@@ -38,7 +38,7 @@ def _worker(rank, world, port, out):
 
 def test_max_over_ranks_and_barrier_with_two_gloo_ranks():
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a threaded test process
         out = m.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         assert dict(out) == {0: 2.0, 1: 2.0}
