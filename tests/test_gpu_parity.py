@@ -216,6 +216,33 @@ def test_m2_reproduces_tuned_splits(throughput_case):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("fmt", ["cp", "tt"])
+def test_paper_shape_sampled_parity(fmt, prec):
+    # The paper's Sec. 3 shape at full size (pure ternary Brownian kernel,
+    # N = 2^19, FFT length 3 2^19): every gain output k <= 2048 against the
+    # oracle on the size prefix (CP form), every loss output against the
+    # oracle's inner-product route; the TT form computes the same kernel.
+    s = wl.paper_ternary(1 << 19, "cp")
+    K = 2048
+    ranks_k, f_k = _prefix(s, K)
+    p_pre, _ = oracle.rhs(s.n0[:K], s.D, ranks_k, f_k, mode=oracle.DIRECT)
+    q_ref = oracle.loss(s.n0, s.D, s.ranks, s.factors)
+    g = s if fmt == "cp" else wl.paper_ternary(1 << 19, "tt")
+    with sag.Plan(g.N, g.D, g.ranks, g.factors, fmt=sag.SAG_TT if fmt == "tt" else sag.SAG_CP,
+                  prec=prec) as pl:
+        n = dev(g.n0)
+        p, q = torch.empty_like(n), torch.empty_like(n)
+        pl.rhs_parts(n, p, q)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+        p, q = p.cpu().numpy(), q.cpu().numpy()
+    scale = np.abs(p).max() + np.abs(q_ref).max()
+    assert np.abs(p).max() <= 1.0001 * np.abs(p_pre).max() + 1e-300  # the maximum is in the prefix
+    assert nerr(p[:K], p_pre, scale) < TOL[prec]
+    assert nerr(q, q_ref, scale) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("kernel", ["constant", "product"])
 def test_full_length_fft_geometric_closed_form(kernel, prec):
     # n_k = A r^(k-1) at N = 65536, D = 4 (FFT lengths 2^17, 3 2^16, 2^18):
