@@ -1,7 +1,8 @@
 """CPU oracle for the multi-particle Smoluchowski right-hand side.
 
-TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package. The GPU library never
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()``, the
+CPU-baseline leg of ``bench.py`` (which also yields the reference outputs of
+its one-RHS error report) and its reference arm may import this package. The GPU library never
 does, and this package imports nothing from it: the two share no code.
 
 The arithmetic lives in ``sag_oracle.c`` (plain C, FP64, compensated sums);
