@@ -308,7 +308,7 @@ class Plan:
 
     def describe(self) -> dict:
         import json
-        buf = ctypes.create_string_buffer(8192)
+        buf = ctypes.create_string_buffer(1 << 16)
         _check(self._lib.sag_plan_describe(self._h, buf, len(buf)))
         return json.loads(buf.value.decode())
 
