@@ -29,6 +29,26 @@ def test_header_and_binding_agree():
     assert declared_functions() == sorted(sag.EXPORTS)
 
 
+def _struct_fields(name):
+    """(type, field) pairs of a typedef struct in include/sag.h, in order."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", text).group(1)
+    return [(" ".join(t.split()), f) for t, f in re.findall(r"([\w\s\*]+?)\s*\b(\w+)\s*;", body)]
+
+
+CTYPE = {"int32_t": ctypes.c_int32, "const int32_t*": ctypes.POINTER(ctypes.c_int32),
+         "const double*": ctypes.c_void_p}
+
+
+@pytest.mark.parametrize("name,cls", [("sag_options", sag._Options), ("sag_system", sag._System)])
+def test_structs_match_the_header(name, cls):
+    # field names, order and types of the ctypes mirrors follow include/sag.h
+    fields = _struct_fields(name)
+    assert [f for _, f in fields] == [f for f, _ in cls._fields_]
+    for (ctype, f), (g, ty) in zip(fields, cls._fields_):
+        assert ty == CTYPE[ctype.replace(" *", "*")], (f, ctype, ty)
+
+
 def test_library_exports_every_declared_function(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
