@@ -130,21 +130,32 @@ def test_m0_identity_constant_kernel_no_tail():
     assert abs((p + q).sum() - want) < 1e-14 * abs(want)
 
 
-def _scalar_heun(f, M, dt, steps):
+def _scalar_rk2(f, M, dt, steps, method):
+    """The two explicit second-order Runge-Kutta rules on a scalar ODE, written
+    out from their textbook definitions (Sec. 3 states two evaluations per step)."""
     for _ in range(steps):
         k1 = f(M)
-        k2 = f(M + dt * k1)
-        M = M + 0.5 * dt * (k1 + k2)
+        if method == oracle.HEUN:      # explicit trapezoid
+            M = M + 0.5 * dt * (k1 + f(M + dt * k1))
+        else:                          # explicit midpoint
+            M = M + dt * f(M + 0.5 * dt * k1)
     return M
 
 
-def test_m0_discrete_heun_matches_scalar_heun():
+@pytest.mark.parametrize("method", [oracle.HEUN, oracle.MIDPOINT])
+def test_m0_discrete_rk2_matches_scalar_rk2(method):
+    # For C = 1 the sizes sum to the scalar ODE dM0/dt = -M0^2/2 - M0^3/3 (D = 3,
+    # no tail at these sizes), and the full system's RK2 step summed over k is the
+    # same RK2 rule applied to that scalar ODE.
     s = wl.constant_monodisperse()  # D=3, N=64, n=e_1, dt=0.01, 100 steps
-    n, diag = oracle.integrate(s.n0, s.D, s.ranks, s.factors, s.dt, s.steps)
+    n, diag = oracle.integrate(s.n0, s.D, s.ranks, s.factors, s.dt, s.steps, method=method)
     f = lambda M: -M * M / 2.0 - M ** 3 / 3.0
-    Ms = _scalar_heun(f, 1.0, s.dt, s.steps)
+    Ms = _scalar_rk2(f, 1.0, s.dt, s.steps, method)
     assert abs(diag[-1, 0] - Ms) < 1e-14
     assert abs(n.sum() - Ms) < 1e-14
+    # the other rule's scalar recursion is far away: the method flag is honoured
+    other = _scalar_rk2(f, 1.0, s.dt, s.steps, oracle.MIDPOINT if method == oracle.HEUN else oracle.HEUN)
+    assert abs(Ms - other) > 1e-8
 
 
 def _m0_exact(t, a=0.5, b=1.0 / 3.0):
@@ -161,13 +172,14 @@ def _m0_exact(t, a=0.5, b=1.0 / 3.0):
     return 0.5 * (lo + hi)
 
 
-def test_m0_exact_solution_second_order():
+@pytest.mark.parametrize("method", [oracle.HEUN, oracle.MIDPOINT])
+def test_m0_exact_solution_second_order(method):
     exact = _m0_exact(1.0)
     assert abs(exact - 0.5724637494) < 1e-9
     errs = []
     for steps in (50, 100, 200):
         s = wl.constant_monodisperse()
-        _, diag = oracle.integrate(s.n0, s.D, s.ranks, s.factors, 1.0 / steps, steps)
+        _, diag = oracle.integrate(s.n0, s.D, s.ranks, s.factors, 1.0 / steps, steps, method=method)
         errs.append(abs(diag[-1, 0] - exact))
     assert errs[1] < 1e-5
     for e0, e1 in zip(errs, errs[1:]):
@@ -183,17 +195,22 @@ def test_m1_identity_equals_outflow(D, N, ranks):
     assert abs((k * (p + q)).sum() + o) < 1e-13 * abs(o)
 
 
-def test_m1_plus_cumulative_outflow_is_conserved():
+@pytest.mark.parametrize("method", [oracle.HEUN, oracle.MIDPOINT])
+def test_m1_plus_cumulative_outflow_is_conserved(method):
+    # Per step M1 falls by the RK2 rule's quadrature of the outflow: Heun
+    # dt/2 (O(n) + O(n*)), midpoint dt O(n*).
     s = wl.random_cp(3, 16, [2, 3], seed=4)
-    _, diag = oracle.integrate(s.n0, 3, s.ranks, s.factors, 0.05, 20)
+    _, diag = oracle.integrate(s.n0, 3, s.ranks, s.factors, 0.05, 20, method=method)
     total = diag[:, 1] + diag[:, 2]
     assert np.max(np.abs(total - total[0])) < 1e-14 * total[0]
     assert diag[-1, 2] > 0
 
 
 # ---------------------------------------------------------------- P6 binary textbook case
-def test_binary_constant_kernel_closed_form():
-    # D=2, C=1, n(0)=e_1: n_k(t) = tau^{k-1}/(1+tau)^{k+1}, tau = t/2.
+@pytest.mark.parametrize("method", [oracle.HEUN, oracle.MIDPOINT])
+def test_binary_constant_kernel_closed_form(method):
+    # D=2, C=1, n(0)=e_1: n_k(t) = tau^{k-1}/(1+tau)^{k+1}, tau = t/2; every
+    # component is pinned and the error falls 4x when dt halves (second order).
     N, T = 200, 0.6
     s = wl.constant_monodisperse(2, N)
     k = wl.sizes(N)
@@ -201,7 +218,7 @@ def test_binary_constant_kernel_closed_form():
     exact = tau ** (k - 1) / (1 + tau) ** (k + 1)
     errs = []
     for steps in (30, 60):
-        n, _ = oracle.integrate(s.n0, 2, s.ranks, s.factors, T / steps, steps, diag=False)
+        n, _ = oracle.integrate(s.n0, 2, s.ranks, s.factors, T / steps, steps, method=method, diag=False)
         errs.append(np.max(np.abs(n - exact)))
     assert errs[1] < 2e-5
     assert 3.5 < errs[0] / errs[1] < 4.5
