@@ -32,9 +32,36 @@ METRIC = "RHS evals/sec & RK2 steps/sec (N=2^16,D=4,R=16) FP32-split vs FP64 at 
 UNIT = "RK2 steps/s"
 WORKLOAD = "random_power_cp: D=4 (d=2,3,4), N=65536, CP rank 16 per order, Heun dt=1e-4"
 FP32_PEAK_PER_SM_CLK = 128      # FP32 lanes per SM per clock (FADD/FMUL/FFMA issue)
-FP64_PEAK_PER_SM_CLK = 2        # FP64 operations per SM per clock on GB300
-NUM_SMS = 152
-SM_MAX_MHZ = 2070.0
+FP64_PEAK_PER_SM_CLK = 2        # FP64 FMAs per SM per clock on GB300 (4 flops)
+SM_MAX_MHZ_DEFAULT = 2070.0
+HBM_GBS_FALLBACK = 6800.0       # the profiling recipe's copy bandwidth when no measured file exists
+# FP32 instructions per nominal flop of a double-word ("FP32-split") FFT: a
+# radix-8 butterfly with twiddles is 120 nominal flops (5 N log2 N counting,
+# 8 points x 3 stages x 5) and 656 FP32 instructions in plain double-word
+# arithmetic (26 complex adds of 16, 2 constant products of 8, 7 twiddle
+# products of 32).
+DF_OPS_PER_FLOP = 656.0 / 120.0
+
+
+def measured_peaks():
+    """HBM copy bandwidth (GB/s) and the SM clock, from the driver's measured
+    file when present (else the recipe's fallback), and the source."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        m = json.load(open(path))
+        return float(m.get("hbm_gbs", HBM_GBS_FALLBACK)), float(m.get("sm_max_mhz", SM_MAX_MHZ_DEFAULT)), \
+            "MEASURED_PEAKS.json (measured)"
+    return HBM_GBS_FALLBACK, SM_MAX_MHZ_DEFAULT, "profiling recipe fallback"
+
+
+def bench_config(world: int) -> dict:
+    """The workload every arm of this benchmark runs (identical dict in both arms)."""
+    return {"workload": WORKLOAD, "N": 65536, "D": 4, "R": 16, "dt": 1e-4, "rk": "Heun",
+            "factors": "U^(m)_r(i) = u i^a, u ~ U[0.5, 1.5], a ~ U[-0.3, 0.3], seed 1905",
+            "n0": "exp(-k/10) normalised to M0 = 1",
+            "l2": "no flush: the working set (factor copies 151 MB + FFT workspace 243 MB) is larger "
+                  "than the 129 MB L2",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def parse():
@@ -44,7 +71,6 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--prec", default="all", choices=["all", "both", "fp32_split", "fp32_split_exact", "fp64"],
                     help="paths to run (profiling runs use one)")
     ap.add_argument("--quick", action="store_true",
@@ -159,20 +185,26 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu record, or None
-    when the CUDA sources changed since that capture."""
+def csrc_sha256() -> str:
+    """Hash of the CUDA sources (file names and contents), which a DRAM traffic
+    record names so that it is only used for the kernels it was taken on."""
     import glob
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
-    rec = json.load(open(path))
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(ROOT, "paper_1905_09071_gb300", "csrc", "*"))):
         h.update(os.path.basename(p).encode())
         h.update(open(p, "rb").read())
-    if h.hexdigest() != rec.get("csrc_sha256"):
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, or None
+    when the CUDA sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    if csrc_sha256() != rec.get("csrc_sha256"):
         return None
     k = rec.get("kernels", {}).get(kernel)
     return None if k is None else float(k["dram_bytes"])
@@ -189,30 +221,41 @@ def pair_slice(s, d, r):
     return wl.cp_from_vectors(2, s.N, {2: U[:2, r:r + 1, :].copy()})
 
 
-def oracle_sample(s, seconds: float, max_samples: int = 10 ** 9, warmup: int = 0):
-    """Times the oracle (direct CP mode, all host cores) on one-convolution
-    samples of the workload, cycling over the terms (d, r). Returns
-    (seconds per full right-hand side, samples, cores)."""
+def term_slice(s, r):
+    """Rank term r of every order as a CP system of rank 1 per order. In the
+    oracle's direct mode every rank term costs the same (d - 1 truncated
+    convolutions of length N per order, and its inner products), so a full
+    right-hand side is R of these."""
+    from paper_1905_09071_gb300 import workloads as wl
+    offs = wl.cp_layout(s.D, s.N, s.ranks)
+    per = {d: s.factors[offs[d - 2]:offs[d - 1]].reshape(d, s.ranks[d - 2], s.N)[:, r:r + 1, :].copy()
+           for d in range(2, s.D + 1)}
+    return wl.cp_from_vectors(s.D, s.N, per)
+
+
+def oracle_full_rhs(s):
+    """One full right-hand side of the workload by the oracle (direct CP
+    mode, FP64) on all host cores. Returns (seconds, cores, P, Q)."""
     import oracle
-    terms = [(d, r) for d in range(2, s.D + 1) for r in range(s.ranks[d - 2])]
-    convs_per_rhs = sum((d - 1) * s.ranks[d - 2] for d in range(2, s.D + 1))
-    times = []
-    i = 0
-    t_all = time.perf_counter()
-    while True:
-        d, r = terms[i % len(terms)]
-        ranks, f = pair_slice(s, d, r)
+    cores = oracle.set_threads(0)
+    t0 = time.perf_counter()
+    p, q = oracle.rhs(s.n0, s.D, s.ranks, s.factors, mode=oracle.DIRECT)
+    return time.perf_counter() - t0, cores, p, q
+
+
+def oracle_one_core_conv(s):
+    """One truncated length-N convolution (the D = 2 rank-one subsystem of
+    term (2, 0)) by the oracle on one host core. Returns seconds."""
+    import oracle
+    prev = oracle.set_threads(0)
+    oracle.set_threads(1)
+    try:
+        ranks, f = pair_slice(s, 2, 0)
         t0 = time.perf_counter()
         oracle.rhs(s.n0, 2, ranks, f, mode=oracle.DIRECT)
-        dt = time.perf_counter() - t0
-        if i >= warmup:
-            times.append(dt)
-        i += 1
-        if len(times) >= max_samples or (time.perf_counter() - t_all >= seconds and times):
-            break
-    per_conv = sum(times) / len(times)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return per_conv * convs_per_rhs, len(times), cores
+        return time.perf_counter() - t0
+    finally:
+        oracle.set_threads(prev)
 
 
 def fft_method_rhs(s, n, workers: int = -1):
@@ -264,24 +307,59 @@ def cpu_fft_baseline(s, reps: int = 3):
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
+    """The oracle as it stands, on the host cores, on bounded samples of the
+    workload: each timed step is the oracle's right-hand side of one rank term
+    of every order (r cycling over 0..15), 1/16 of a full right-hand side;
+    when K + W such steps would take more than about 150 s, each step is one
+    truncated convolution instead (1/96 of a right-hand side). `ms_per_step`
+    is the measured time of one timed step; `value` converts it to RK2
+    steps/s of the full workload."""
     if rank != 0:
         return
+    import oracle
     from paper_1905_09071_gb300 import workloads as wl
     s = wl.random_power_cp()
-    # K samples, or as many as about 90 s of host time allows
-    sec_per_rhs, samples, cores = oracle_sample(s, seconds=90.0, max_samples=args.steps,
-                                                warmup=args.warmup)
-    value = 1.0 / (2.0 * sec_per_rhs)
-    sample = (f"{samples} timed steps; each step = the oracle's direct-mode right-hand side of a "
-              f"D=2 rank-one subsystem made of two factor vectors of one term (d, r) of the "
-              f"workload: one truncated convolution of length 65536; a full right-hand side is "
-              f"96 of them (sum_d (d-1) R_d), an RK2 step 2 right-hand sides")
+    R = s.ranks[0]
+    convs = sum((d - 1) * s.ranks[d - 2] for d in range(2, s.D + 1))
+    cores = oracle.set_threads(0)
+    K, W = args.steps, args.warmup
+
+    def term_step(i):
+        ranks, f = term_slice(s, i % R)
+        t0 = time.perf_counter()
+        oracle.rhs(s.n0, s.D, ranks, f, mode=oracle.DIRECT)
+        return time.perf_counter() - t0
+
+    def conv_step(i):
+        terms = [(d, r) for d in range(2, s.D + 1) for r in range(s.ranks[d - 2])]
+        d, r = terms[i % len(terms)]
+        ranks, f = pair_slice(s, d, r)
+        t0 = time.perf_counter()
+        oracle.rhs(s.n0, 2, ranks, f, mode=oracle.DIRECT)
+        return time.perf_counter() - t0
+
+    first = term_step(0)  # the first warm-up step, and the size check
+    if (K + W) * first <= 150.0:
+        step, per_rhs, done = term_step, R, 1
+        unit = ("the oracle's right-hand side of rank term r (r cycling over 0..15) of every order "
+                "d = 2, 3, 4: 1/16 of a full right-hand side")
+    else:
+        step, per_rhs, done = conv_step, convs, 0
+        unit = ("one truncated length-65536 convolution (a D = 2 rank-one subsystem of one term's "
+                "vectors): 1/96 of a full right-hand side")
+    for i in range(done, W):
+        step(i)
+    times = [step(W + j) for j in range(max(K, 1))]
+    t_step = sum(times) / len(times)
+    value = 1.0 / (2.0 * per_rhs * t_step)
+    sample = f"{len(times)} timed steps after {W} warm-up steps; each step = {unit}; an RK2 step is " \
+             f"2 right-hand sides = {2 * per_rhs} such steps (oracle direct CP mode, FP64, {cores} threads)"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+           "steps": len(times), "warmup": W, "ms_per_step": t_step * 1e3,
+           "timed_step": unit, "ms_per_rk2_step_extrapolated": 1e3 / value,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "N": s.N, "D": s.D, "R": 16,
-                                           "oracle_mode": "direct CP (FP64, Neumaier sums, OpenMP)"},
-           "rhs_evals_per_s": 1.0 / sec_per_rhs,
+           "data": "synthetic", "config": bench_config(world),
+           "rhs_evals_per_s": 1.0 / (per_rhs * t_step),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -316,41 +394,74 @@ def time_rhs(pl, n, out, reps):
     return e0.elapsed_time(e1) / 1e3
 
 
-def cpu_baseline_leg(s, seconds: float, K: int = 2048):
-    """The oracle leg of the run (rank 0, one GPU): the oracle timed on
-    bounded one-convolution samples of the workload (the cpu_baseline entry),
-    and its reference outputs for the one-RHS error report: the gain at sizes
-    k <= K (the oracle on the size prefix, exact for those k) and every loss
-    output (the oracle's inner-product route)."""
-    import oracle
-    from paper_1905_09071_gb300 import workloads as wl
-    sec_per_rhs, samples, cores = oracle_sample(s, seconds=seconds)
-    cpu = {"value": 1.0 / (2 * sec_per_rhs), "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{samples} one-convolution samples (D=2 rank-one subsystems of the "
-                     f"workload's term vectors, oracle direct mode) scaled by the 96 "
-                     f"convolutions of a full right-hand side and 2 right-hand sides per step"}
-    offs = wl.cp_layout(s.D, s.N, s.ranks)
-    per = {d: s.factors[offs[d - 2]:offs[d - 1]].reshape(d, s.ranks[d - 2], s.N)[:, :, :K]
-           for d in range(2, s.D + 1)}
-    rk, f = wl.cp_from_vectors(s.D, K, per)
-    p_ref, _ = oracle.rhs(s.n0[:K], s.D, rk, f, mode=oracle.DIRECT)
-    q_ref = oracle.loss(s.n0, s.D, s.ranks, s.factors)
-    return cpu, (K, p_ref, q_ref)
+def cpu_baseline_leg(s):
+    """The oracle leg of the run (rank 0, one GPU, before any GPU work): one
+    full right-hand side of the workload on all host cores, timed, whose
+    outputs are also the reference of the error report; and one truncated
+    convolution on one core (1/96 of a right-hand side)."""
+    t_all, cores, p_ref, q_ref = oracle_full_rhs(s)
+    t_conv1 = oracle_one_core_conv(s)
+    convs = sum((d - 1) * s.ranks[d - 2] for d in range(2, s.D + 1))
+    cpu = {"value": 1.0 / (2 * t_all), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"one full right-hand side of the workload (oracle direct CP mode, FP64) on {cores} "
+                     f"threads: {t_all:.2f} s; an RK2 step is 2 right-hand sides",
+           "single_core": {"value": 1.0 / (2 * convs * t_conv1), "unit": UNIT, "cores": 1,
+                           "sample": f"one truncated length-{s.N} convolution on 1 thread: {t_conv1:.2f} s; "
+                                     f"a right-hand side is {convs} of them (the inner products add "
+                                     f"under 0.1%), an RK2 step 2 right-hand sides"}}
+    return cpu, (p_ref, q_ref)
 
 
 def parity_error(pl, s, ref):
-    """Normwise error of one right-hand side at n0 against the oracle's
-    reference outputs (cpu_baseline_leg): gain outputs k <= K and every loss
-    output."""
+    """Normwise error of one right-hand side at n0 against the oracle's full
+    right-hand side (every size): max over k of |p - p_ref|, |q - q_ref| and
+    |p + q - p_ref - q_ref|, divided by max|p_ref| + max|q_ref|."""
     import torch
-    K, p_ref, q_ref = ref
+    p_ref, q_ref = ref
     n = torch.tensor(s.n0, device="cuda")
     p, q = torch.empty_like(n), torch.empty_like(n)
     pl.rhs_parts(n, p, q)
     torch.cuda.synchronize()
     p, q = p.cpu().numpy(), q.cpu().numpy()
-    scale = np.abs(p).max() + np.abs(q_ref).max()
-    return float(max(np.abs(p[:K] - p_ref).max(), np.abs(q - q_ref).max()) / scale)
+    scale = np.abs(p_ref).max() + np.abs(q_ref).max()
+    return float(max(np.abs(p - p_ref).max(), np.abs(q - q_ref).max(),
+                     np.abs(p + q - p_ref - q_ref).max()) / scale)
+
+
+def timed_regions(pl, n, dt, K, world, min_seconds=1.0, min_reps=5, max_reps=200):
+    """Times the K-step region (barrier and synchronize on both sides, CUDA
+    events, slowest rank) repeatedly, at least min_reps times and about
+    min_seconds in all; returns the median region time and every region's."""
+    first = max_over_ranks(time_integrate(pl, n, dt, K, world), world)
+    reps = int(min(max_reps, max(min_reps, np.ceil(min_seconds / max(first, 1e-9)))))
+    times = [first] + [max_over_ranks(time_integrate(pl, n, dt, K, world), world) for _ in range(reps - 1)]
+    return statistics.median(times), times
+
+
+def kernel_table(pl, prof, hbm_gbs, fp32_peak, fp64_peak):
+    """Per kernel of one right-hand side: event time per launch, the bytes it
+    must move (algorithmic) and the FFT workspace it moves besides, achieved
+    GB/s against the measured copy bandwidth, the executed-operation rate
+    against the ALU peak, and the nominal-flop time t_alu (method flops x the
+    double-word cost per flop, or FP64 flops) beside t_bytes."""
+    total = sum(v[0] for v in prof.values())
+    out = {}
+    for k, (ms, cnt) in prof.items():
+        w = pl.kernel_work(k)
+        m = pl.method_work(k)
+        t = ms / cnt / 1e3
+        fp64 = w["ops_fp64"]
+        t_bytes = w["bytes"] / (hbm_gbs * 1e9)
+        t_alu = m["flops"] / (2 * fp64_peak * 1e12) if fp64 else m["flops"] * DF_OPS_PER_FLOP / (fp32_peak * 1e12)
+        out[k] = {"ms_per_launch": ms / cnt, "launches": cnt, "share": ms / total,
+                  "ops_per_launch": w["ops"], "ops_fp64": fp64, "bytes_per_launch": w["bytes"],
+                  "workspace_bytes_per_launch": m["workspace_bytes"], "nominal_flops_per_launch": m["flops"],
+                  "achieved_gbs": w["bytes"] / t / 1e9, "hbm_frac": w["bytes"] / t / 1e9 / hbm_gbs,
+                  "achieved_gbs_with_workspace": (w["bytes"] + m["workspace_bytes"]) / t / 1e9,
+                  "alu_frac_executed": w["ops"] / t / 1e12 / (fp64_peak if fp64 else fp32_peak),
+                  "t_bytes_us": t_bytes * 1e6, "t_alu_us": t_alu * 1e6,
+                  "frac_nominal": max(t_bytes, t_alu) / t}
+    return out
 
 
 def run_ours(args, world, rank, local):
@@ -364,7 +475,7 @@ def run_ours(args, world, rank, local):
     # the oracle runs here, before any GPU work, and nowhere else in this arm
     cpu, ref = (None, None)
     if not args.no_cpu_baseline and world == 1 and not args.kernels and not args.quick:
-        cpu, ref = cpu_baseline_leg(s, seconds=args.cpu_seconds)
+        cpu, ref = cpu_baseline_leg(s)
     sampler = ClockSampler(local)
     clocks = None
     everything = (sag.SAG_FP32_SPLIT, sag.SAG_FP32_SPLIT_EXACT, sag.SAG_FP64)
@@ -409,6 +520,10 @@ def run_ours(args, world, rank, local):
         return
     if args.prec not in ("all", "both"):
         raise SystemExit("--prec other than all needs --quick")
+    hbm_gbs, sm_mhz, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = sms * FP32_PEAK_PER_SM_CLK * sm_mhz * 1e6 / 1e12   # T FP32 instructions/s
+    fp64_peak = sms * FP64_PEAK_PER_SM_CLK * sm_mhz * 1e6 / 1e12   # T FP64 FMAs/s
     for prec in precs:
         pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, autotune=tune)
         n = torch.tensor(s.n0, device="cuda")
@@ -416,10 +531,9 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         if prec == sag.SAG_FP32_SPLIT:
             sampler.start()
-        t = time_integrate(pl, n, s.dt, K, world)
+        t, regions = timed_regions(pl, n, s.dt, K, world)
         if prec == sag.SAG_FP32_SPLIT:
             clocks = sampler.stop()
-        t = max_over_ranks(t, world)
         assert pl.sync_status() == sag.SAG_OK
         out = torch.empty_like(n)
         nr = torch.tensor(s.n0, device="cuda")
@@ -432,9 +546,10 @@ def run_ours(args, world, rank, local):
             pl.rk2_step(nprof, s.dt)
         prof = pl.profile_read()
         pl.profile(False)
-        work = {name: pl.kernel_work(name) for name in prof}
+        table = kernel_table(pl, prof, hbm_gbs, fp32_peak, fp64_peak)
         err = parity_error(pl, s, ref) if (rank == 0 and ref is not None) else None
-        res[prec] = dict(t=t, t_rhs=t_rhs, prof=prof, work=work, err=err, desc=pl.describe())
+        res[prec] = dict(t=t, regions=regions, t_rhs=t_rhs, prof=prof, table=table, err=err,
+                         desc=pl.describe())
         pl.close()
 
     # end-to-end: the public call with host buffers (pinned), copies inside
@@ -456,18 +571,11 @@ def run_ours(args, world, rank, local):
     dw, dwx, f64 = res[sag.SAG_FP32_SPLIT], res[sag.SAG_FP32_SPLIT_EXACT], res[sag.SAG_FP64]
     value = K * world / dw["t"]
     # dominant kernel of the headline path and its roofline
-    name, (ms, cnt) = max(dw["prof"].items(), key=lambda kv: kv[1][0])
-    w = dw["work"][name]
-    dur = ms / cnt / 1e3
-    if w["ops_fp64"]:
-        peak = NUM_SMS * FP64_PEAK_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    else:
-        peak = NUM_SMS * FP32_PEAK_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = w["ops"] / dur / 1e12
-    total_ms = sum(v[0] for v in dw["prof"].values())
-    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / total_ms,
-                   "ops_per_launch": dw["work"][k]["ops"],
-                   "bytes_per_launch": dw["work"][k]["bytes"]} for k, v in dw["prof"].items()}
+    name = max(dw["prof"].items(), key=lambda kv: kv[1][0])[0]
+    kt = dw["table"][name]
+    dur = kt["ms_per_launch"] / 1e3
+    peak = fp64_peak if kt["ops_fp64"] else fp32_peak
+    achieved = kt["ops_per_launch"] / dur / 1e12
     kernels_per_step = sum(v[1] for v in dw["prof"].values()) / K
     n_bytes = 8 * s.N
     cpu_fft = cpu_fft_baseline(s) if not args.no_cpu_baseline and world == 1 else None
@@ -476,18 +584,21 @@ def run_ours(args, world, rank, local):
         "ms_per_step": dw["t"] / K * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32x2 (double-word FP32 FFTs; FP64 inner products, RK2, diagnostics)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": s.N, "D": s.D, "R": 16, "precision": "FP32_SPLIT",
-                   "timed": "sag_integrate: K Heun steps as CUDA-graph replays, inputs resident in HBM",
-                   "l2": "working set (factor copies 151 MB + FFT workspace 243 MB) larger than the 129 MB L2",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "fft_geometry": dw["desc"]["orders"],
-                   "fft_split_candidates": dw["desc"].get("geometry_autotune", []),
-                   "fft_stream_groups": {"fp32_split": dw["desc"]["blocks"]["fft_groups"],
-                                         "fp64": f64["desc"]["blocks"]["fft_groups"],
-                                         "chosen_by": "fixed rule" if args.no_autotune else "plan-time autotuner"}},
+        "config": bench_config(world),
+        "timed": (f"sag_integrate: K = {K} Heun steps as CUDA-graph replays, inputs resident in HBM, "
+                  f"CUDA events on the launch stream; the K-step region timed {len(dw['regions'])} times, "
+                  f"the median reported"),
+        "regions_ms": [round(t * 1e3, 4) for t in dw["regions"]],
+        "plan": {"precision": "FP32_SPLIT",
+                 "fft_geometry": dw["desc"]["orders"],
+                 "fft_split_candidates": dw["desc"].get("geometry_autotune", []),
+                 "fft_stream_groups": {"fp32_split": dw["desc"]["blocks"]["fft_groups"],
+                                       "fp64": f64["desc"]["blocks"]["fft_groups"],
+                                       "chosen_by": "fixed rule" if args.no_autotune else "plan-time autotuner"}},
         "rhs_evals_per_s": max(K, 10) / dw["t_rhs"],
         "error_vs_oracle": {"fp32_split": dw["err"], "fp32_split_exact": dwx["err"], "fp64": f64["err"],
-                            "metric": "max|x - oracle| / (max|P| + max|Q|), one RHS at n0"},
+                            "metric": "max_k |x - oracle| / (max|P_oracle| + max|Q_oracle|) over every "
+                                      "size of one right-hand side at n0 (x = gain, loss, their sum)"},
         "fp32_split_exact": {"value": K * world / dwx["t"], "unit": UNIT, "ms_per_step": dwx["t"] / K * 1e3,
                              "rhs_evals_per_s": max(K, 10) / dwx["t_rhs"],
                              "note": "every FFT butterfly in plain double-word arithmetic"},
@@ -495,11 +606,26 @@ def run_ours(args, world, rank, local):
                  "rhs_evals_per_s": max(K, 10) / f64["t_rhs"]},
         "speedup_vs_fp64": f64["t"] / dw["t"],
         "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                     "unit": "TFP64op/s" if w["ops_fp64"] else "TFP32op/s", "frac": achieved / peak,
+                     "unit": "T FP64 FMA/s" if kt["ops_fp64"] else "T FP32 instructions/s",
+                     "frac": achieved / peak,
                      "traffic": recorded_traffic(name),
-                     "peak_source": "derived: 152 SMs x %d ops/clk/SM x 2070 MHz" %
-                                    (FP64_PEAK_PER_SM_CLK if w["ops_fp64"] else FP32_PEAK_PER_SM_CLK)},
-        "kernels": kernels,
+                     "unit_of_work": "one right-hand side (the kernel's launches of one evaluation)",
+                     "peak_source": "derived: %d SMs x %d per clock x %.0f MHz (SM count from the device, "
+                                    "clock from %s)" % (sms, FP64_PEAK_PER_SM_CLK if kt["ops_fp64"]
+                                                        else FP32_PEAK_PER_SM_CLK, sm_mhz, peak_src),
+                     "views": {
+                         "executed": "achieved = the FP32 instructions the kernel's arithmetic executes "
+                                     "(counted from its radix schedules) / event time",
+                         "nominal_flops": {"flops": kt["nominal_flops_per_launch"],
+                                           "tflops": kt["nominal_flops_per_launch"] / dur / 1e12,
+                                           "df_ops_per_flop": DF_OPS_PER_FLOP,
+                                           "t_alu_us": kt["t_alu_us"], "t_bytes_us": kt["t_bytes_us"],
+                                           "t_us": dur * 1e6, "frac": kt["frac_nominal"]},
+                         "hbm": {"algorithmic_bytes": kt["bytes_per_launch"],
+                                 "workspace_bytes": kt["workspace_bytes_per_launch"],
+                                 "achieved_gbs": kt["achieved_gbs"], "peak_gbs": hbm_gbs,
+                                 "frac": kt["hbm_frac"]}}},
+        "kernels": dw["table"],
         "clocks": clocks,
         "gpu_launches": (dw["desc"]["launches_per_step"] * K if dw["desc"].get("launches_per_step", -1) > 0
                          else int(round(kernels_per_step * K))) + 1,

@@ -215,7 +215,11 @@ sag_status sag_plan_factor_count(sag_plan_t plan, int64_t* count);
 sag_status sag_plan_set_wait_limit(sag_plan_t plan, int64_t cycles, int32_t unmet);
 
 /* Waits for `stream`, then returns and clears the plan's latched device-side
- * status (SAG_OK, SAG_ENONFINITE or SAG_ETIMEOUT). */
+ * status (SAG_OK, SAG_ENONFINITE or SAG_ETIMEOUT). When a block that gave up a
+ * wait also ran out of time waiting for its own bulk copies in flight, the
+ * status is SAG_ETIMEOUT with a message saying so: copies may then still have
+ * landed in shared memory after the block ended, and the context should be
+ * treated as suspect. */
 sag_status sag_sync_status(sag_plan_t plan, void* stream);
 
 /* Kernel timing, for profiling and roofline reporting. While enabled, every
@@ -240,6 +244,18 @@ const char* sag_kernel_name(int32_t id);
 sag_status sag_kernel_work(sag_plan_t plan, int32_t id, double* ops, int32_t* ops_fp64,
                            double* bytes);
 
+/* The method's own measure of one launch of kernel id, for roofline
+ * reporting beside sag_kernel_work: *flops = nominal flops of the part of the
+ * method the launch carries out (a real FFT of length L counted as
+ * 2.5 L log2 L, split between the four-step column and row halves as
+ * 2.5 L log2 M1 and 2.5 L log2 M2; a complex product 6, an add 2; inner
+ * products 2 per factor element), whatever arithmetic carries it out; and
+ * *workspace_bytes = the bytes of intermediate FFT workspace the launch writes
+ * or reads beyond sag_kernel_work's algorithmic bytes (each transformed
+ * vector's four-step intermediate, 16 bytes per complex value; each order's
+ * spectral sum). Sec. 1 gives the method's cost as O(N D R log N). */
+sag_status sag_kernel_method_work(sag_plan_t plan, int32_t id, double* flops, double* workspace_bytes);
+
 /* JSON description of the plan's FFT geometry (per order: L, M1, M2, radix
  * schedules, block shapes), its launch layout, the split autotuner's
  * candidates, and launches_per_step: the kernel launches of one sag_integrate
@@ -256,15 +272,17 @@ sag_status sag_plan_describe(sag_plan_t plan, char* buf, size_t len);
  * that reserved its device memory up front): this call performs no cudaMalloc,
  * cudaFree or other allocation.
  *   sys: fmt = SAG_CP, factors_on_device = 1, factors a device pointer in the
- *        layout of sag_system; rank is read on the host.
+ *        layout of sag_system; rank is read on the host. As in sag_plan, a CP
+ *        rank of 0 leaves an order out, and one order needs rank >= 1.
  *   n, q: device vectors of length N (may not alias).
  * Limits: V = sum_d d R_d <= 2048 and V * ceil(N / 8192) <= 32768; larger
  * systems, host pointers or TT kernels return SAG_EINVAL / SAG_EUNSUPPORTED
- * with a message. Partial sums live in one static device array of 256 KB that
- * every device loading the library keeps until exit; all calls share it, so
- * calls that overlap on the GPU (any streams) race. The first call on each
- * device looks up that array's device address (cudaGetSymbolAddress), so make
- * it before any stream capture. Asynchronous on `stream`. */
+ * with a message. Partial sums and loss weights live in one static device
+ * array of 288 KB that every device loading the library keeps until exit; all
+ * calls share it, so calls that overlap on the GPU (any streams) race. The
+ * first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture. Asynchronous
+ * on `stream`. */
 sag_status sag_loss_noalloc(const sag_system* sys, int32_t symmetrize_q, const double* n, double* q,
                             void* stream);
 

@@ -57,6 +57,8 @@ def _load():
         lib = ctypes.CDLL(build())
         i32p = ctypes.POINTER(ctypes.c_int)
         f64p = ctypes.POINTER(ctypes.c_double)
+        lib.orc_set_threads.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_factor_count.restype = ctypes.c_long
         lib.orc_factor_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p]
         lib.orc_kernel_entry.restype = ctypes.c_double
@@ -92,6 +94,12 @@ def _f64(a):
 def _i32(a):
     a = np.ascontiguousarray(a, dtype=np.int32)
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads of the oracle's OpenMP loops for later calls from this
+    thread (n > 0 sets the count); returns the current count."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def factor_count(fmt: int, D: int, N: int, ranks) -> int:

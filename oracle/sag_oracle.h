@@ -31,6 +31,10 @@ enum { ORC_BRUTE = 0, ORC_DIRECT = 1 };   /* evaluation mode */
 enum { ORC_CP = 0, ORC_TT = 1 };          /* kernel format */
 enum { ORC_HEUN = 0, ORC_MIDPOINT = 1 };  /* explicit second-order Runge-Kutta variant */
 
+/* Threads the OpenMP loops of later calls from this host thread use (n > 0
+ * sets it; n <= 0 leaves it); returns the current count. No arithmetic. */
+int orc_set_threads(int n);
+
 /* Number of doubles the factor array holds for the given format and ranks. */
 long orc_factor_count(int fmt, int D, int N, const int* ranks);
 

@@ -643,6 +643,10 @@ sag_status sag_sync_status(sag_plan_t pl, void* stream) {
     return cuda_fail(e, "read status");
   if (status) {
     if ((e = cudaMemset(pl->P.status, 0, sizeof(unsigned))) != cudaSuccess) return cuda_fail(e, "clear status");
+    if (status & kStatusTimeoutUndrained)
+      return fail(SAG_ETIMEOUT,
+                  "a device-side wait timed out and a block exited with bulk copies still in flight: "
+                  "treat the CUDA context as suspect");
     if (status & kStatusTimeout) return fail(SAG_ETIMEOUT, "a device-side wait timed out");
     return fail(SAG_ENONFINITE, "the right-hand side produced Inf or NaN");
   }
@@ -779,6 +783,72 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
   *ops = o;
   *ops_fp64 = fp64;
   *bytes = b;
+  return SAG_OK;
+}
+
+sag_status sag_kernel_method_work(sag_plan_t pl, int32_t id, double* flops, double* workspace_bytes) {
+  if (!pl || !flops || !workspace_bytes) return fail(SAG_EINVAL, "NULL argument");
+  if (id < 0 || id >= KID_COUNT) return fail(SAG_EINVAL, "kernel id out of range");
+  // Nominal flops of the method (Sec. 1: d-fold convolutions by FFT, inner
+  // products), independent of the arithmetic that carries them out: a real
+  // FFT of length L is 2.5 L log2 L flops, split between the four-step
+  // halves as 2.5 L log2 M1 (columns) and 2.5 L log2 M2 (rows) with the
+  // four-step twiddle products (3 L: L/2 complex products of 6 flops) on the
+  // column side; a complex product 6, a complex add 2, an FMA 2.
+  // Workspace: each transformed vector's four-step intermediate, M = L/2
+  // complex values of 16 bytes (double-word or FP64), written by the forward
+  // columns and read by the rows; each order's spectral sum, written by the
+  // rows and read by the inverse columns.
+  double f = 0.0, w = 0.0;
+  double factor_elems = 0.0;
+  for (const SysDesc& s : pl->systems) factor_elems += (double)(s.vend - s.vbeg) * s.N;
+  const double Nt = (double)pl->Ntot;
+  for (const OrderDesc& od : pl->items) {
+    const double L = od.L, M = od.M, nu = od.pair ? 2.0 * od.npair : (double)od.nu;
+    const double lg1 = std::log2((double)od.M1), lg2 = std::log2((double)od.M2);
+    switch (id) {
+      case KID_FWD_COL:
+        f += nu * (od.N + 2.5 * L * lg1 + 3.0 * L);
+        w += nu * 16.0 * M;
+        break;
+      case KID_ROWS:
+        f += nu * (2.5 * L * lg2 + 5.0 * L)                       // forward rows and the real split
+             + (M + 1) * (6.0 * (od.nvec - od.R) + 2.0 * od.R)   // products over the modes, rank sum
+             + 2.5 * L * lg2 + 5.0 * L;                           // repack and inverse rows
+        w += nu * 16.0 * M + 16.0 * M;
+        break;
+      case KID_ROWS_TT:
+        f += od.nvec * (2.5 * L * lg2 + 5.0 * L);
+        w += od.nvec * 16.0 * M * 2.0;
+        break;
+      case KID_TT_CHAIN:
+        f += od.nvec * (M + 1) * 8.0;
+        w += od.nvec * 16.0 * M + 16.0 * M;
+        break;
+      case KID_ROWS_TT_INV:
+        f += 2.5 * L * lg2 + 5.0 * L;
+        w += 2.0 * 16.0 * M;
+        break;
+      case KID_INV_COL:
+        f += 2.5 * L * lg1 + 3.0 * L;
+        w += 16.0 * M;
+        break;
+      default:
+        break;
+    }
+  }
+  switch (id) {
+    case KID_NMAX: f = Nt; break;
+    case KID_NSPLIT: f = 2 * Nt; break;
+    case KID_DOT: f = 2 * factor_elems; break;
+    case KID_COEF: f = 4.0 * pl->P.Vtot; break;
+    case KID_QTERM: f = 2 * factor_elems + Nt; break;
+    case KID_EPILOGUE: f = 8 * Nt; break;
+    case KID_MOMENTS: f = 3 * Nt; break;
+    default: break;
+  }
+  *flops = f;
+  *workspace_bytes = w;
   return SAG_OK;
 }
 

@@ -72,12 +72,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // A block whose wait gave up: latch the timeout status, then let the copies
-// it has in flight on `bar` (phase `parity`) land before it exits. Called by
-// one thread; out of line, as it runs at most once.
-static __device__ __noinline__ void timeout_drain(unsigned* status, unsigned bit, uint64_t* bar,
-                                                  uint32_t parity) {
+// it has in flight on `bar` (phase `parity`) land before it exits. If that
+// second wait also runs out, the block exits with copies still in flight into
+// shared memory a later block may reuse, so `undrained_bit` is latched as
+// well and the host reports the context as suspect. Called by one thread; out
+// of line, as it runs at most once.
+static __device__ __noinline__ void timeout_drain(unsigned* status, unsigned bit, unsigned undrained_bit,
+                                                  uint64_t* bar, uint32_t parity) {
   atomicOr(status, bit);
-  mbar_wait_bounded(bar, parity, kDrainLimit);
+  if (!mbar_wait_bounded(bar, parity, kDrainLimit)) atomicOr(status, undrained_bit);
 }
 
 }  // namespace sag

@@ -441,7 +441,7 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
     if (__syncthreads_or(!ok)) {
       // Timed out: latch the status, then let this chunk's copies land (a
       // second bounded wait) before the block's shared memory is released.
-      if (threadIdx.x == 0) timeout_drain(P.status, kStatusTimeout, bar, (uint32_t)(c & 1));
+      if (threadIdx.x == 0) timeout_drain(P.status, kStatusTimeout, kStatusTimeoutUndrained, bar, (uint32_t)(c & 1));
       return;
     }
     fft_ct_first<C, P2, SLOTS, kThreads, true>(stage, P2, work, ld, tw);  // unused slots hold stale data
@@ -584,7 +584,7 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
     if (__syncthreads_or(!ok)) {
       // Timed out: latch the status, then let this chunk's copies land (a
       // second bounded wait) before the block's shared memory is released.
-      if (threadIdx.x == 0) timeout_drain(P.status, kStatusTimeout, bar, (uint32_t)(c & 1));
+      if (threadIdx.x == 0) timeout_drain(P.status, kStatusTimeout, kStatusTimeoutUndrained, bar, (uint32_t)(c & 1));
       return;
     }
     fft_ct_first<C, P2p, SLOTS, kThreads, true>(stage, P2p, work, ld, tw);  // unused slots hold stale data

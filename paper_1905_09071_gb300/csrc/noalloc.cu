@@ -25,10 +25,12 @@ constexpr int kLossMaxPartials = 32768;   // V * ceil(N / 8192) partials at most
 constexpr int kLossMaxVectors = 2048;     // V = sum_d d R_d at most (shared-memory weights)
 constexpr int kMaxDevices = 64;
 
-// Every device that loads the library holds this array until the process exits.
-// Each call overwrites every partial it later reads, so nothing in it has to
-// start at zero; concurrent calls (overlapping on any stream) race on it.
-static __device__ __align__(256) double g_loss_partials[kLossMaxPartials];
+// Every device that loads the library holds this array until the process exits:
+// kLossMaxPartials partial inner products, then kLossMaxVectors loss weights
+// coef_v (288 KB in all). Each call overwrites every entry it later reads, so
+// nothing in it has to start at zero; concurrent calls (overlapping on any
+// stream) race on it.
+static __device__ __align__(256) double g_loss_partials[kLossMaxPartials + kLossMaxVectors];
 
 std::mutex g_mu;
 double* g_partials_addr[kMaxDevices] = {};
@@ -58,15 +60,13 @@ __global__ void __launch_bounds__(256) k_loss_partials(LossDesc L, const double*
   }
 }
 
-// q_k = n_k sum_v coef_v U_v(k), coef_v = -1/(d-1)! (1/d) prod_{m' != m} s_{d,m',r}
-// (symmetrised) or -1/(d-1)! [m = d-1] prod_{m' < d-1} s_{d,m',r} (last mode).
-__global__ void __launch_bounds__(256) k_loss_assemble(LossDesc L, const double* __restrict__ U,
-                                                       const double* __restrict__ n,
-                                                       const double* __restrict__ part,
-                                                       double* __restrict__ q) {
-  extern __shared__ double sh[];
-  double* s = sh;
-  double* coef = sh + L.V;
+// One block: s_v = sum of vector v's chunk partials, then the loss weights
+// coef_v = -1/(d-1)! (1/d) prod_{m' != m} s_{d,m',r} (symmetrised) or
+// -1/(d-1)! [m = d-1] prod_{m' < d-1} s_{d,m',r} (last mode), written after
+// the partials.
+__global__ void __launch_bounds__(256) k_loss_coef(LossDesc L, const double* __restrict__ part,
+                                                   double* __restrict__ coef) {
+  extern __shared__ double s[];
   for (int v = threadIdx.x; v < L.V; v += blockDim.x) {
     double a = 0.0;
     for (int c = 0; c < L.nchunk; ++c) a += part[v * L.nchunk + c];
@@ -85,6 +85,15 @@ __global__ void __launch_bounds__(256) k_loss_assemble(LossDesc L, const double*
     const double c = L.sym ? prod / d : (m == d - 1 ? prod : 0.0);
     coef[v] = -c / f;
   }
+}
+
+// q_k = n_k sum_v coef_v U_v(k).
+__global__ void __launch_bounds__(256) k_loss_assemble(LossDesc L, const double* __restrict__ U,
+                                                       const double* __restrict__ n,
+                                                       const double* __restrict__ coef_g,
+                                                       double* __restrict__ q) {
+  extern __shared__ double coef[];
+  for (int v = threadIdx.x; v < L.V; v += blockDim.x) coef[v] = coef_g[v];
   __syncthreads();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < L.N) {
@@ -114,18 +123,22 @@ extern "C" sag_status sag_loss_noalloc(const sag_system* sys, int32_t symmetrize
   if (symmetrize_q != 0 && symmetrize_q != 1) return set_last_error(SAG_EINVAL, "symmetrize_q must be 0 or 1");
   LossDesc L{};
   L.N = sys->N;
-  L.nord = sys->D - 1;
   L.sym = symmetrize_q;
+  // As in sag_plan, a CP rank of 0 leaves an order out, and at least one order
+  // needs a rank of 1 or more.
   int64_t V = 0;
   for (int d = 2; d <= sys->D; ++d) {
     const int R = sys->rank[d - 2];
-    if (R < 1) return set_last_error(SAG_EINVAL, "CP rank must be >= 1");
-    L.d[d - 2] = d;
-    L.R[d - 2] = R;
-    L.vbase[d - 2] = (int)V;
+    if (R < 0) return set_last_error(SAG_EINVAL, "CP ranks must be >= 0");
+    if (R == 0) continue;
+    L.d[L.nord] = d;
+    L.R[L.nord] = R;
+    L.vbase[L.nord] = (int)V;
+    ++L.nord;
     V += (int64_t)d * R;
     if (V > kLossMaxVectors) break;
   }
+  if (L.nord == 0) return set_last_error(SAG_EINVAL, "every system needs one order of CP rank >= 1");
   L.nchunk = (L.N + kLossChunk - 1) / kLossChunk;
   if (V > kLossMaxVectors || V * L.nchunk > kLossMaxPartials)
     return set_last_error(SAG_EINVAL,
@@ -153,8 +166,10 @@ extern "C" sag_status sag_loss_noalloc(const sag_system* sys, int32_t symmetrize
     part = g_partials_addr[dev];
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* coef = part + kLossMaxPartials;
   k_loss_partials<<<dim3(L.nchunk, L.V), 256, 0, st>>>(L, sys->factors, n, part);
-  k_loss_assemble<<<(L.N + 255) / 256, 256, 2 * L.V * sizeof(double), st>>>(L, sys->factors, n, part, q);
+  k_loss_coef<<<1, 256, L.V * sizeof(double), st>>>(L, part, coef);
+  k_loss_assemble<<<(L.N + 255) / 256, 256, L.V * sizeof(double), st>>>(L, sys->factors, n, coef, q);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_last_error(SAG_ECUDA, cudaGetErrorString(e));
   return SAG_OK;

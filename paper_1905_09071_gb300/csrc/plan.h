@@ -97,7 +97,9 @@ struct SysScalars {
   double gflux;                  // sum_d 1/d! sum_{i in [1,N]^d} |i| C_i prod n (complete first-moment flux)
 };
 
-enum : unsigned { kStatusNonFinite = 1u, kStatusTimeout = 2u };
+// Latched device status bits. kStatusTimeoutUndrained: a block gave up a
+// wait and then also gave up waiting for its own copies in flight.
+enum : unsigned { kStatusNonFinite = 1u, kStatusTimeout = 2u, kStatusTimeoutUndrained = 4u };
 
 enum EpiMode : int {
   EPI_RHS = 0,       // dndt (and/or p, q parts)

@@ -28,6 +28,7 @@ EXPORTS = [
     "sag_last_error", "sag_version", "sag_profile_enable", "sag_profile_read", "sag_kernel_name",
     "sag_kernel_work", "sag_plan_describe", "sag_loss_noalloc", "sag_rhs_vjp", "sag_integrate_vjp",
     "sag_plan_update_factors", "sag_plan_factor_count", "sag_plan_set_wait_limit",
+    "sag_kernel_method_work",
 ]
 SAG_NUM_KERNELS = 13
 
@@ -94,6 +95,7 @@ def load(build_if_missing: bool = True):
         lib.sag_kernel_name.restype = ctypes.c_char_p
         lib.sag_kernel_work.argtypes = [vp, i32, ctypes.POINTER(f64), ctypes.POINTER(i32),
                                         ctypes.POINTER(f64)]
+        lib.sag_kernel_method_work.argtypes = [vp, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
         lib.sag_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         lib.sag_loss_noalloc.argtypes = [ctypes.POINTER(_System), i32, vp, vp, vp]
         lib.sag_rhs_vjp.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -106,7 +108,7 @@ def load(build_if_missing: bool = True):
                      "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_profile_enable",
                      "sag_profile_read", "sag_kernel_work", "sag_plan_describe", "sag_rhs_vjp",
                      "sag_integrate_vjp", "sag_plan_update_factors", "sag_plan_factor_count",
-                     "sag_plan_set_wait_limit"):
+                     "sag_plan_set_wait_limit", "sag_kernel_method_work"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -305,6 +307,16 @@ class Plan:
         _check(self._lib.sag_kernel_work(self._h, int(kid), ctypes.byref(ops), ctypes.byref(f64),
                                          ctypes.byref(b)))
         return {"ops": ops.value, "ops_fp64": bool(f64.value), "bytes": b.value}
+
+    def method_work(self, name_or_id) -> dict:
+        """Nominal method flops and FFT-workspace bytes of one launch (sag_kernel_method_work)."""
+        kid = name_or_id
+        if isinstance(name_or_id, str):
+            names = [self._lib.sag_kernel_name(i).decode() for i in range(SAG_NUM_KERNELS)]
+            kid = names.index(name_or_id)
+        fl, wb = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.sag_kernel_method_work(self._h, int(kid), ctypes.byref(fl), ctypes.byref(wb)))
+        return {"flops": fl.value, "workspace_bytes": wb.value}
 
     def describe(self) -> dict:
         import json

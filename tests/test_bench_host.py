@@ -12,13 +12,13 @@ bench = pytest.importorskip("bench")
 
 def test_traffic_record_follows_the_sources(tmp_path, monkeypatch):
     root = bench.ROOT
-    rec = json.load(open(os.path.join(root, "profiles", "traffic.json")))
     shutil.copytree(os.path.join(root, "paper_1905_09071_gb300", "csrc"),
                     tmp_path / "paper_1905_09071_gb300" / "csrc")
     (tmp_path / "profiles").mkdir()
-    shutil.copy(os.path.join(root, "profiles", "traffic.json"), tmp_path / "profiles")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.recorded_traffic("k_fwd_col") == float(rec["kernels"]["k_fwd_col"]["dram_bytes"])
+    rec = {"csrc_sha256": bench.csrc_sha256(), "kernels": {"k_fwd_col": {"dram_bytes": 123456.0}}}
+    json.dump(rec, open(tmp_path / "profiles" / "traffic.json", "w"))
+    assert bench.recorded_traffic("k_fwd_col") == 123456.0
     assert bench.recorded_traffic("no_such_kernel") is None
     with open(tmp_path / "paper_1905_09071_gb300" / "csrc" / "dw.cuh", "a") as fh:
         fh.write("\n")  # any change to the CUDA sources voids the record

@@ -50,11 +50,18 @@ def test_reference_arm_under_torchrun_prints_once():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py",
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
-           "--cpu-seconds", "1"]
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1, r.stdout
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
+    # the arm reports what it timed: one sample step, converted to RK2 steps/s
+    # of the whole workload (32 term samples per RK2 step), on the same config
+    # dict as the GPU arm
+    assert rec["steps"] == 1
+    assert abs(rec["value"] * 32 * rec["ms_per_step"] / 1e3 - 1) < 1e-9
+    sys.path.insert(0, ROOT)
+    import bench
+    assert rec["config"] == bench.bench_config(2)
