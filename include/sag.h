@@ -164,6 +164,19 @@ sag_status sag_rhs_parts(sag_plan_t plan, const double* n, double* p, double* q,
  * evaluations per step). */
 sag_status sag_rk2_step(sag_plan_t plan, double* n, double dt, void* stream);
 
+/* One stage of the plan's RK2 rule from a right-hand side k that the caller
+ * supplies, for a system whose right-hand side is assembled outside one plan
+ * (the term-parallel split: every process evaluates the CP rank terms it owns
+ * with sag_rhs and the partial right-hand sides are summed across processes;
+ * P and Q are both sums over the terms (d, r), Sec. 1). All vectors are device
+ * vectors of the plan's packed length; k may alias neither n, nstar nor k1.
+ *   stage 0: k1 = k, nstar = n + h1 k (h1 = dt for Heun, dt/2 for midpoint);
+ *            the caller then evaluates k at nstar.
+ *   stage 1: Heun n += dt/2 (k1 + k); midpoint n += dt k.
+ * A non-finite k latches SAG_ENONFINITE for sag_sync_status. Asynchronous. */
+sag_status sag_rk2_stage(sag_plan_t plan, int32_t stage, double* n, double* nstar, double* k1, const double* k,
+                         double dt, void* stream);
+
 /* `steps` RK2 steps of size dt on n, in place. The step is captured once as a
  * CUDA graph per (n, dt, diag) and replayed. diag (may be NULL; host or device)
  * receives [steps+1][B][3] doubles: M0 = sum_k n_k, M1 = sum_k k n_k and the

@@ -335,6 +335,19 @@ sag_status sag_rk2_step(sag_plan_t pl, double* n, double dt, void* stream) {
   return SAG_OK;
 }
 
+sag_status sag_rk2_stage(sag_plan_t pl, int32_t stage, double* n, double* nstar, double* k1, const double* k,
+                         double dt, void* stream) {
+  if (!pl || !n || !nstar || !k1 || !k) return fail(SAG_EINVAL, "NULL argument");
+  if (stage != 0 && stage != 1) return fail(SAG_EINVAL, "stage must be 0 or 1");
+  if (!std::isfinite(dt)) return fail(SAG_EINVAL, "dt is not finite");
+  if (!is_device_ptr(n) || !is_device_ptr(nstar) || !is_device_ptr(k1) || !is_device_ptr(k))
+    return fail(SAG_EINVAL, "sag_rk2_stage takes device vectors");
+  cudaError_t e = enqueue_rk2_stage(pl->P, stage, pl->rk == SAG_MIDPOINT ? 1 : 0, n, nstar, k1, k, dt,
+                                    static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return SAG_OK;
+}
+
 sag_status sag_integrate(sag_plan_t pl, double* n, double dt, int64_t steps, double* diag,
                          void* stream) {
   if (!pl || !n) return fail(SAG_EINVAL, "NULL argument");

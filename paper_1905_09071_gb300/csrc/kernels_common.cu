@@ -439,4 +439,34 @@ cudaError_t setup_common_kernels(const LaunchCfg& L) {
   return e;
 }
 
+// ---- one RK2 stage from a given right-hand side k (the term-parallel split,
+// where k is the sum of the ranks' partial right-hand sides): stage 0 stores
+// k1 = k and the intermediate state nstar = n + h1 k (h1 = dt for Heun, dt/2
+// for the midpoint rule); stage 1 advances n by dt/2 (k1 + k) (Heun) or
+// dt k (midpoint). A non-finite k latches the plan's status.
+__global__ void k_rk2_stage(const __grid_constant__ RhsParams P, int stage, int midpoint, double* n,
+                            double* nstar, double* k1, const double* __restrict__ k, double dt) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.Ntot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ki = k[i];
+    bad |= !isfinite(ki);
+    if (stage == 0) {
+      k1[i] = ki;
+      nstar[i] = n[i] + (midpoint ? 0.5 * dt : dt) * ki;
+    } else {
+      n[i] = midpoint ? n[i] + dt * ki : n[i] + 0.5 * dt * (k1[i] + ki);
+    }
+  }
+  if (bad) atomicOr(P.status, kStatusNonFinite);
+}
+
+cudaError_t enqueue_rk2_stage(const RhsParams& P, int stage, int midpoint, double* n, double* nstar,
+                              double* k1, const double* k, double dt, cudaStream_t st) {
+  const int64_t want = (P.Ntot + 255) / 256;
+  const int blocks = (int)(want < 4096 ? want : 4096);
+  k_rk2_stage<<<blocks, 256, 0, st>>>(P, stage, midpoint, n, nstar, k1, k, dt);
+  return cudaGetLastError();
+}
+
 }  // namespace sag

@@ -171,6 +171,9 @@ cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n,
                         double* gn, double* gU, int accumulate, cudaStream_t st);
 cudaError_t enqueue_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n,
                           cudaStream_t st);
+// One RK2 stage from a given right-hand side k (sag_rk2_stage).
+cudaError_t enqueue_rk2_stage(const RhsParams& P, int stage, int midpoint, double* n, double* nstar,
+                              double* k1, const double* k, double dt, cudaStream_t st);
 cudaError_t setup_vjp_common(const LaunchCfg& L);
 cudaError_t setup_vjp_fft_f64(const LaunchCfg& L);
 cudaError_t setup_fft_kernels_f64(const LaunchCfg& L);

@@ -28,7 +28,7 @@ EXPORTS = [
     "sag_last_error", "sag_version", "sag_profile_enable", "sag_profile_read", "sag_kernel_name",
     "sag_kernel_work", "sag_plan_describe", "sag_loss_noalloc", "sag_rhs_vjp", "sag_integrate_vjp",
     "sag_plan_update_factors", "sag_plan_factor_count", "sag_plan_set_wait_limit",
-    "sag_kernel_method_work",
+    "sag_kernel_method_work", "sag_rk2_stage",
 ]
 SAG_NUM_KERNELS = 13
 
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
         lib.sag_kernel_work.argtypes = [vp, i32, ctypes.POINTER(f64), ctypes.POINTER(i32),
                                         ctypes.POINTER(f64)]
         lib.sag_kernel_method_work.argtypes = [vp, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
+        lib.sag_rk2_stage.argtypes = [vp, i32, vp, vp, vp, vp, f64, vp]
         lib.sag_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         lib.sag_loss_noalloc.argtypes = [ctypes.POINTER(_System), i32, vp, vp, vp]
         lib.sag_rhs_vjp.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -108,7 +109,7 @@ def load(build_if_missing: bool = True):
                      "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_profile_enable",
                      "sag_profile_read", "sag_kernel_work", "sag_plan_describe", "sag_rhs_vjp",
                      "sag_integrate_vjp", "sag_plan_update_factors", "sag_plan_factor_count",
-                     "sag_plan_set_wait_limit", "sag_kernel_method_work"):
+                     "sag_plan_set_wait_limit", "sag_kernel_method_work", "sag_rk2_stage"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -236,6 +237,12 @@ class Plan:
 
     def rk2_step(self, n, dt: float, stream=None):
         _check(self._lib.sag_rk2_step(self._h, _ptr(n), float(dt), _stream(stream, n)))
+        return n
+
+    def rk2_stage(self, stage: int, n, nstar, k1, k, dt: float, stream=None):
+        """sag_rk2_stage: one stage of the plan's RK2 rule from a given right-hand side k."""
+        _check(self._lib.sag_rk2_stage(self._h, int(stage), _ptr(n), _ptr(nstar), _ptr(k1), _ptr(k),
+                                       float(dt), _stream(stream, n, nstar, k1, k)))
         return n
 
     def integrate(self, n, dt: float, steps: int, diag=None, stream=None):
