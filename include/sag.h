@@ -50,7 +50,7 @@ typedef enum {
   SAG_ENONFINITE = 6       /* the right-hand side produced Inf or NaN */
 } sag_status;
 
-typedef enum { SAG_CP = 0, SAG_TT = 1 } sag_format;
+typedef enum { SAG_CP = 0, SAG_TT = 1, SAG_CP_POWER = 2 } sag_format;
 
 /* SAG_FP64: every FFT in FP64.
  * SAG_FP32_SPLIT: FFTs in double-word FP32 (hi + lo pairs); the radix-2/3/4/8
@@ -78,6 +78,17 @@ typedef enum { SAG_HEUN = 0, SAG_MIDPOINT = 1 } sag_rk;
  *     (Eq. ch3.eq4); factors holds, for each d and each core lambda = 1..d,
  *     the array [R_{lambda-1}][R_lambda][N] (the vectors h^(lambda)_{r,r'} of
  *     Sec. 3 stored along the size axis).
+ *   fmt = SAG_CP_POWER: a CP kernel whose factors are powers of the size,
+ *     U^(m)_r(i) = u i^a (the random power-law workload's form; the
+ *     generalized Brownian kernel of Eq. ch3.eq17 is one too): rank as for
+ *     SAG_CP; factors holds, for each d in turn, the array [d][R_d][2] of
+ *     (u, a) for vector (m, r), with |a| <= 2.5. The plan expands the factors
+ *     in FP64 (u pow(i, a)) for the FP64 kernels, and with SAG_FP32_SPLIT the
+ *     double-word forward FFT generates u i^a itself (to about 1e-13
+ *     relative) instead of reading the factors (the FP64 and
+ *     SAG_FP32_SPLIT_EXACT paths read the expanded copies). No
+ *     sag_plan_update_factors; the adjoint's factor cotangent is that of the
+ *     expanded values.
  * factors_on_device = 1 if `factors` is a device pointer, 0 for host memory. */
 typedef struct {
   int32_t N;
@@ -298,6 +309,13 @@ sag_status sag_plan_describe(sag_plan_t plan, char* buf, size_t len);
  * on `stream`. */
 sag_status sag_loss_noalloc(const sag_system* sys, int32_t symmetrize_q, const double* n, double* q,
                             void* stream);
+
+/* The parametric factors' generator on its own, for checking it: out[i-1] =
+ * u i^a for i = 1..N (N <= 2^22, |a| <= 2.5), evaluated in double-word FP32
+ * exactly as the forward FFT of a SAG_CP_POWER plan does and returned as the
+ * FP64 sum of the two words. out is a device vector of N doubles. Allocates
+ * its two small tables, waits for `stream` and frees them before returning. */
+sag_status sag_power_eval(double u, double a, int32_t N, double* out, void* stream);
 
 /* Releases the plan (after the work queued on it has finished). NULL is a no-op. */
 void sag_plan_destroy(sag_plan_t plan);

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 
+#include "dw_pow.cuh"
 #include "plan_host.h"
 
 using namespace sag;
@@ -192,6 +193,47 @@ double fft_ops(int P, const radix_plan& rp, const OpCost& c) {
   return ops;
 }
 
+// SAG_CP_POWER systems as CP systems: every vector U^(m)_r(i) = u pow(i, a)
+// (FP64, host libm), in the CP layout, plus the (u, a) list in vector order
+// (orders of rank 0 contribute neither).
+sag_status expand_power(const sag_system* sys, int32_t B, std::vector<sag_system>* cp,
+                        std::vector<std::vector<double>>* store, std::vector<double>* ua) {
+  cp->assign(sys, sys + B);
+  store->resize(B);
+  ua->clear();
+  for (int b = 0; b < B; ++b) {
+    const sag_system& s = sys[b];
+    const std::string at = B > 1 ? " (system " + std::to_string(b) + ")" : "";
+    if (s.fmt != SAG_CP_POWER) return fail(SAG_EUNSUPPORTED, "all systems of a plan must share one format" + at);
+    if (!s.rank || !s.factors) return fail(SAG_EINVAL, "NULL rank or factors" + at);
+    if (s.N < 1 || s.N > (1 << 22) || s.D < 2 || s.D > kMaxD) return fail(SAG_EINVAL, "N in [1, 2^22] and D in [2, 8] required" + at);
+    int64_t npar = 0;
+    for (int d = 2; d <= s.D; ++d) {
+      if (s.rank[d - 2] < 0 || s.rank[d - 2] > 4096) return fail(SAG_EINVAL, "CP rank out of [0, 4096]" + at);
+      npar += 2LL * d * s.rank[d - 2];
+    }
+    std::vector<double> par((size_t)std::max<int64_t>(npar, 1));
+    cudaError_t e = cudaMemcpy(par.data(), s.factors, (size_t)npar * sizeof(double),
+                               s.factors_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "copy power parameters");
+    std::vector<double>& U = (*store)[b];
+    U.clear();
+    U.reserve((size_t)(npar / 2) * s.N);
+    for (int64_t v = 0; v < npar / 2; ++v) {
+      const double u = par[2 * v], a = par[2 * v + 1];
+      if (!std::isfinite(u) || !std::isfinite(a) || std::fabs(a) > 2.5)
+        return fail(SAG_EINVAL, "power factors need finite u and |a| <= 2.5" + at);
+      ua->push_back(u);
+      ua->push_back(a);
+      for (int i = 1; i <= s.N; ++i) U.push_back(u * std::pow((double)i, a));
+    }
+    (*cp)[b].fmt = SAG_CP;
+    (*cp)[b].factors = U.data();
+    (*cp)[b].factors_on_device = 0;
+  }
+  return SAG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -218,12 +260,24 @@ sag_status sag_plan(const sag_system* sys, int32_t B, const sag_options* opt, sa
   sag_options o;
   sag_default_options(&o);
   if (opt) o = *opt;
-  sag_status s = validate_systems(sys, B, o);
+  // Parametric factors: the plan is built from the expanded CP factors (FP64,
+  // u pow(i, a) on the host) and keeps (u, a) for the kernels that generate U.
+  std::vector<sag_system> cp;
+  std::vector<std::vector<double>> store;
+  std::vector<double> ua;
+  const sag_system* use = sys;
+  if (sys && B >= 1 && B <= 65535 && sys[0].fmt == SAG_CP_POWER) {
+    sag_status se = expand_power(sys, B, &cp, &store, &ua);
+    if (se != SAG_OK) return se;
+    use = cp.data();
+  }
+  sag_status s = validate_systems(use, B, o);
   if (s != SAG_OK) return s;
   sag_plan_s* pl = new (std::nothrow) sag_plan_s();
   if (!pl) return fail(SAG_ENOMEM, "host allocation");
-  s = build_plan(sys, B, o, pl);
-  if (s == SAG_OK && o.autotune) s = autotune_geometry(sys, B, o, &pl);
+  pl->pow_ua = std::move(ua);
+  s = build_plan(use, B, o, pl);
+  if (s == SAG_OK && o.autotune) s = autotune_geometry(use, B, o, &pl);
   if (s != SAG_OK) {
     delete pl;
     return s;
@@ -332,6 +386,40 @@ sag_status sag_rk2_step(sag_plan_t pl, double* n, double dt, void* stream) {
       return cuda_fail(e, "copy n back");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
   }
+  return SAG_OK;
+}
+
+sag_status sag_power_eval(double u, double a, int32_t N, double* out, void* stream) {
+  if (!out) return fail(SAG_EINVAL, "NULL argument");
+  if (N < 1 || N > (1 << 22)) return fail(SAG_EINVAL, "N must be in [1, 2^22]");
+  if (!std::isfinite(u) || !std::isfinite(a) || std::fabs(a) > 2.5)
+    return fail(SAG_EINVAL, "finite u and |a| <= 2.5 required");
+  if (!is_device_ptr(out)) return fail(SAG_EINVAL, "out must be a device pointer");
+  std::vector<float2> lt((size_t)N + 1, make_float2(0.f, 0.f));
+  for (int i = 1; i <= N; ++i) {
+    const long double l = logl((long double)i);
+    const float hi = (float)l;
+    lt[i] = make_float2(hi, (float)(l - hi));
+  }
+  std::vector<float> ek(kExpConsts);
+  make_exp_consts(ek.data());
+  const dw ud = dw_from_double(u), ad = dw_from_double(a);
+  float2* dlt = nullptr;
+  float* dek = nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMalloc(&dlt, lt.size() * sizeof(float2));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc ln table");
+  if ((e = cudaMalloc(&dek, ek.size() * sizeof(float))) != cudaSuccess) {
+    cudaFree(dlt);
+    return cuda_fail(e, "cudaMalloc exp table");
+  }
+  if ((e = cudaMemcpyAsync(dlt, lt.data(), lt.size() * sizeof(float2), cudaMemcpyHostToDevice, st)) == cudaSuccess &&
+      (e = cudaMemcpyAsync(dek, ek.data(), ek.size() * sizeof(float), cudaMemcpyHostToDevice, st)) == cudaSuccess &&
+      (e = enqueue_power_eval(make_float4(ud.hi, ud.lo, ad.hi, ad.lo), dlt, dek, N, out, st)) == cudaSuccess)
+    e = cudaStreamSynchronize(st);
+  cudaFree(dlt);
+  cudaFree(dek);
+  if (e != cudaSuccess) return cuda_fail(e, "power evaluation");
   return SAG_OK;
 }
 
@@ -727,8 +815,9 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
       b = 16 * Nt;
       fp64 = 1;
       break;
-    case KID_DOT:  // fma (u n) + running sum per size
-      o = 2 * factor_elems;
+    case KID_DOT:  // one FP64 FMA (acc += u n) per factor element; the outflow's t = <k U, n>
+                   // adds a second only when it is asked for (not counted here)
+      o = factor_elems;
       b = 8 * factor_elems + 8 * Nt;
       fp64 = 1;
       break;
@@ -911,7 +1000,8 @@ sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
     js += std::string(i ? ", " : "") + "{\"sys\": " + std::to_string(od.sys) + ", \"d\": " +
           std::to_string(od.d) + ", \"vectors\": " + std::to_string(od.nvec) +
           ", \"transformed\": " + std::to_string(od.pair ? 2 * od.npair : od.nu) +
-          ", \"pairs\": " + std::to_string(od.pair) + ", \"L\": " +
+          ", \"pairs\": " + std::to_string(od.pair) + ", \"parametric\": " + std::to_string(od.pw) +
+          ", \"L\": " +
           std::to_string(od.L) + ", \"M1\": " + std::to_string(od.M1) + ", \"M2\": " +
           std::to_string(od.M2) + ", \"radix_M1\": " + rps(od.rp1) + ", \"radix_M2\": " + rps(od.rp2) +
           ", \"W\": " + std::to_string(od.W) + ", \"G\": " + std::to_string(od.G) +

@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "async_copy.cuh"
+#include "dw_pow.cuh"
 #include "fft_ct.cuh"
 #include "plan.h"
 
@@ -41,6 +42,24 @@ __device__ __forceinline__ cdw load_a_pair(const float2* __restrict__ u, const f
   const float4 b = __ldg(reinterpret_cast<const float4*>(nn + k));
   return make_cdw(dw_mul(dw{a.x, a.y}, dw{b.x, b.y}), dw_mul(dw{a.z, a.w}, dw{b.z, b.w}));
 }
+// Parametric factors (OrderDesc::pw): a = (u i^a) o n at sizes k and k + 1,
+// the power generated in double-word (dw_pow.cuh) rather than loaded; up =
+// the vector's (u 2^-e_v, a) as double-words.
+__device__ __forceinline__ cdw gen_a_pair(const RhsParams& P, float4 up, const float2* __restrict__ nn, int N,
+                                          int k) {
+  if (k > N) return c_zero(cdw{});
+  const float4 b = __ldg(reinterpret_cast<const float4*>(nn + k));
+  const dw u{up.x, up.y}, a{up.z, up.w};
+  const float2 l0 = __ldg(P.lnt + k);
+  const dw re = dw_mul(dw_power(u, a, dw{l0.x, l0.y}, P.expk), dw{b.x, b.y});
+  dw im{0.f, 0.f};
+  if (k + 1 <= N) {
+    const float2 l1 = __ldg(P.lnt + k + 1);
+    im = dw_mul(dw_power(u, a, dw{l1.x, l1.y}, P.expk), dw{b.z, b.w});
+  }
+  return make_cdw(re, im);
+}
+
 __device__ __forceinline__ const double* vec_ptr(const RhsParams& P, int v, cd) { return P.U64 + P.voff[v]; }
 __device__ __forceinline__ const float2* vec_ptr(const RhsParams& P, int v, cdw) {
   return P.Udw + P.vdwoff[v];
@@ -110,7 +129,7 @@ __device__ __forceinline__ void col_store_ct(const C* res, int ld, const C* __re
 // Forward column pass of one block: the order's vector lv (local index) into
 // spectrum slot `slot`, column block cb. P1 > 0: compile-time length, in
 // place; P1 == 0: runtime length, ping-pong.
-template <class C, int P1>
+template <class C, int P1, bool GEN = false>
 __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc& od, int slot, int lv,
                                              int cb, const double* __restrict__ n, C* buf) {
   constexpr bool CT = P1 > 0;
@@ -127,10 +146,18 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   const auto u = vec_ptr(P, v, C{});
   const auto nn = n_ptr(P, n, od, C{});
   const int N = od.N;
+  float4 up{};
+  if constexpr (GEN) up = __ldg(P.vpow + v);
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
-    buf[c * ld + (CT ? pad8(j1) : j1)] = load_a_pair(u, nn, N, 2 * j, C{});
+    C x;
+    if constexpr (GEN) {
+      x = gen_a_pair(P, up, nn, N, 2 * j);
+    } else {
+      x = load_a_pair(u, nn, N, 2 * j, C{});
+    }
+    buf[c * ld + (CT ? pad8(j1) : j1)] = x;
   }
   __syncthreads();
   C* res;
@@ -161,7 +188,7 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
 // as the real and imaginary parts of one sequence indexed by size, j = 2 M2 j1
 // + j2, so each complex point holds one size of each vector; column block cb
 // of the M1 x 2 M2 geometry. A missing second vector (odd count) is zero.
-template <class C, int P1>
+template <class C, int P1, bool GEN = false>
 __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const OrderDesc& od, int pr, int cb,
                                                   C* buf) {
   constexpr int W = ct_cols(P1);
@@ -170,25 +197,43 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
   const int M2p = 2 * od.M2, N = od.N, d = od.d, R = od.R;
   const C* tw = static_cast<const C*>(od.twg1);  // pass tables, global layout
   const int q1 = 2 * pr, q2 = q1 + 1;
-  const float2* u1 = P.Udw + P.vdwoff[od.vbase + (q1 % d) * R + q1 / d];
-  const float2* u2 = q2 < od.nvec ? P.Udw + P.vdwoff[od.vbase + (q2 % d) * R + q2 / d] : nullptr;
   const float2* nn = P.ndw + od.ndwoff;  // indexed by size, zero at 0
   // Pass 0 straight from the factors and n: point j1 of column c is size
   // j = 2 M2 j1 + cb W + c, z = (u1 n, u2 n) there (zero beyond N).
-  ct_pass_first_from<C, P1, W, kThreads>(
-      [&](int c, int j1) -> C {
-        const int j = M2p * j1 + cb * W + c;
-        if (j > N) return c_zero(C{});
-        const float2 nb = __ldg(nn + j), a1 = __ldg(u1 + j);
-        const dw nv{nb.x, nb.y};
-        dw im{0.f, 0.f};
-        if (u2) {
-          const float2 a2 = __ldg(u2 + j);
-          im = dw_mul(dw{a2.x, a2.y}, nv);
-        }
-        return make_cdw(dw_mul(dw{a1.x, a1.y}, nv), im);
-      },
-      buf, ld);
+  if constexpr (GEN) {  // parametric factors: u i^a generated, ln j from the table
+    const int v1 = od.vbase + (q1 % d) * R + q1 / d;
+    const int v2 = q2 < od.nvec ? od.vbase + (q2 % d) * R + q2 / d : -1;
+    const float4 up1 = __ldg(P.vpow + v1);
+    const float4 up2 = v2 >= 0 ? __ldg(P.vpow + v2) : make_float4(0.f, 0.f, 0.f, 0.f);
+    ct_pass_first_from<C, P1, W, kThreads>(
+        [&](int c, int j1) -> C {
+          const int j = M2p * j1 + cb * W + c;
+          if (j > N) return c_zero(C{});
+          const float2 nb = __ldg(nn + j), lj = __ldg(P.lnt + j);
+          const dw nv{nb.x, nb.y}, l{lj.x, lj.y};
+          dw im{0.f, 0.f};
+          if (v2 >= 0) im = dw_mul(dw_power(dw{up2.x, up2.y}, dw{up2.z, up2.w}, l, P.expk), nv);
+          return make_cdw(dw_mul(dw_power(dw{up1.x, up1.y}, dw{up1.z, up1.w}, l, P.expk), nv), im);
+        },
+        buf, ld);
+  } else {
+    const float2* u1 = P.Udw + P.vdwoff[od.vbase + (q1 % d) * R + q1 / d];
+    const float2* u2 = q2 < od.nvec ? P.Udw + P.vdwoff[od.vbase + (q2 % d) * R + q2 / d] : nullptr;
+    ct_pass_first_from<C, P1, W, kThreads>(
+        [&](int c, int j1) -> C {
+          const int j = M2p * j1 + cb * W + c;
+          if (j > N) return c_zero(C{});
+          const float2 nb = __ldg(nn + j), a1 = __ldg(u1 + j);
+          const dw nv{nb.x, nb.y};
+          dw im{0.f, 0.f};
+          if (u2) {
+            const float2 a2 = __ldg(u2 + j);
+            im = dw_mul(dw{a2.x, a2.y}, nv);
+          }
+          return make_cdw(dw_mul(dw{a1.x, a1.y}, nv), im);
+        },
+        buf, ld);
+  }
   ct_passes<C, P1, W, kThreads, 1, sc.r[0], true, sc.n - 1>(buf, ld, tw);  // middle passes, in place
   // The last pass hands each output k1 of column c, times its four-step
   // twiddle, straight to the workspace (row k1, column cb W + c of the
@@ -200,7 +245,10 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
   });
 }
 
-template <class C, int KIND = kKindGeneral>
+// GEN: the double-word path's parametric factors (OrderDesc::pw), generated
+// instead of read; a separate instantiation, so the stored-factor kernels keep
+// their own register allocation.
+template <class C, int KIND = kKindGeneral, bool GEN = false>
 __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__ RhsParams P,
                                                       const double* __restrict__ n, int base, int all) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -213,26 +261,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
   const int local = bid - pre[pos];
   if constexpr (KIND >= kKindPair) {  // every block of the launch: a pair at this column length
     const int pr = local / od.ncolblk_p, cbp = local - pr * od.ncolblk_p;
-    fwd_col_pair_body<C, ct_len(KIND - kKindPair)>(P, od, pr, cbp, buf);
+    fwd_col_pair_body<C, ct_len(KIND - kKindPair), GEN>(P, od, pr, cbp, buf);
     return;
   } else if constexpr (KIND != kKindGeneral) {  // single vectors, one length form
     const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
     const int lv = (all || od.umap_off < 0) ? vloc : P.ulist[od.umap_off + vloc];
-    fwd_col_body<C, KIND == kKindRuntime ? 0 : ct_len(KIND - kKindCt)>(P, od, vloc, lv, cb, n, buf);
+    fwd_col_body<C, KIND == kKindRuntime ? 0 : ct_len(KIND - kKindCt), GEN>(P, od, vloc, lv, cb, n, buf);
     return;
   }
   if constexpr (is_dw<C>::value) {
     if (!all && od.pair) {
       const int pr = local / od.ncolblk_p, cbp = local - pr * od.ncolblk_p;
       switch (od.M1) {
-        case 64: fwd_col_pair_body<C, 64>(P, od, pr, cbp, buf); break;
-        case 96: fwd_col_pair_body<C, 96>(P, od, pr, cbp, buf); break;
-        case 128: fwd_col_pair_body<C, 128>(P, od, pr, cbp, buf); break;
-        case 192: fwd_col_pair_body<C, 192>(P, od, pr, cbp, buf); break;
-        case 256: fwd_col_pair_body<C, 256>(P, od, pr, cbp, buf); break;
-        case 384: fwd_col_pair_body<C, 384>(P, od, pr, cbp, buf); break;
-        case 512: fwd_col_pair_body<C, 512>(P, od, pr, cbp, buf); break;
-        case 768: fwd_col_pair_body<C, 768>(P, od, pr, cbp, buf); break;
+        case 64: fwd_col_pair_body<C, 64, GEN>(P, od, pr, cbp, buf); break;
+        case 96: fwd_col_pair_body<C, 96, GEN>(P, od, pr, cbp, buf); break;
+        case 128: fwd_col_pair_body<C, 128, GEN>(P, od, pr, cbp, buf); break;
+        case 192: fwd_col_pair_body<C, 192, GEN>(P, od, pr, cbp, buf); break;
+        case 256: fwd_col_pair_body<C, 256, GEN>(P, od, pr, cbp, buf); break;
+        case 384: fwd_col_pair_body<C, 384, GEN>(P, od, pr, cbp, buf); break;
+        case 512: fwd_col_pair_body<C, 512, GEN>(P, od, pr, cbp, buf); break;
+        case 768: fwd_col_pair_body<C, 768, GEN>(P, od, pr, cbp, buf); break;
         default: break;  // the plan sets pair only with a compile-time column length
       }
       return;
@@ -241,20 +289,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
   const int vloc = local / od.ncolblk, cb = local - vloc * od.ncolblk;
   const int lv = (all || od.umap_off < 0) ? vloc : P.ulist[od.umap_off + vloc];
   if constexpr (!is_dw<C>::value) {
-    fwd_col_body<C, 0>(P, od, vloc, lv, cb, n, buf);
+    fwd_col_body<C, 0, GEN>(P, od, vloc, lv, cb, n, buf);
     return;
   }
   switch (od.ct1 ? od.M1 : 0) {
-    case 64: fwd_col_body<C, 64>(P, od, vloc, lv, cb, n, buf); break;
-    case 96: fwd_col_body<C, 96>(P, od, vloc, lv, cb, n, buf); break;
-    case 128: fwd_col_body<C, 128>(P, od, vloc, lv, cb, n, buf); break;
-    case 192: fwd_col_body<C, 192>(P, od, vloc, lv, cb, n, buf); break;
-    case 256: fwd_col_body<C, 256>(P, od, vloc, lv, cb, n, buf); break;
-    case 384: fwd_col_body<C, 384>(P, od, vloc, lv, cb, n, buf); break;
-    case 512: fwd_col_body<C, 512>(P, od, vloc, lv, cb, n, buf); break;
-    case 768: fwd_col_body<C, 768>(P, od, vloc, lv, cb, n, buf); break;
-    case 1536: fwd_col_body<C, 1536>(P, od, vloc, lv, cb, n, buf); break;
-    default: fwd_col_body<C, 0>(P, od, vloc, lv, cb, n, buf); break;
+    case 64: fwd_col_body<C, 64, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    case 96: fwd_col_body<C, 96, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    case 128: fwd_col_body<C, 128, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    case 192: fwd_col_body<C, 192, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    case 256: fwd_col_body<C, 256, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    case 384: fwd_col_body<C, 384, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    case 512: fwd_col_body<C, 512, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    case 768: fwd_col_body<C, 768, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    case 1536: fwd_col_body<C, 1536, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    default: fwd_col_body<C, 0, GEN>(P, od, vloc, lv, cb, n, buf); break;
   }
 }
 

@@ -2,6 +2,7 @@
 // n, the loss-term inner products and weights, and the epilogue that
 // assembles dn/dt = P + Q and applies the Runge-Kutta stage update. Every
 // kernel covers all systems of the plan in one launch.
+#include "dw_pow.cuh"
 #include "launch.h"
 
 namespace sag {
@@ -466,6 +467,24 @@ cudaError_t enqueue_rk2_stage(const RhsParams& P, int stage, int midpoint, doubl
   const int64_t want = (P.Ntot + 255) / 256;
   const int blocks = (int)(want < 4096 ? want : 4096);
   k_rk2_stage<<<blocks, 256, 0, st>>>(P, stage, midpoint, n, nstar, k1, k, dt);
+  return cudaGetLastError();
+}
+
+// ---- the parametric factors' generator on its own: out[i - 1] = u i^a for
+// i = 1..N, evaluated exactly as the forward column kernels do (dw_pow.cuh)
+// and returned as hi + lo in FP64.
+__global__ void k_power_eval(float4 up, const float2* __restrict__ lnt, const float* __restrict__ ek, int N,
+                             double* __restrict__ out) {
+  for (int i = 1 + blockIdx.x * blockDim.x + threadIdx.x; i <= N; i += gridDim.x * blockDim.x) {
+    const float2 l = lnt[i];
+    const dw y = dw_power(dw{up.x, up.y}, dw{up.z, up.w}, dw{l.x, l.y}, ek);
+    out[i - 1] = (double)y.hi + (double)y.lo;
+  }
+}
+
+cudaError_t enqueue_power_eval(float4 up, const float2* lnt, const float* ek, int N, double* out, cudaStream_t st) {
+  const int blocks = (N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096;
+  k_power_eval<<<blocks, 256, 0, st>>>(up, lnt, ek, N, out);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,10 @@
 
 #ifndef SAG_DW_C
 #define SAG_DW_C cdw
+#define SAG_DW_GEN 1  // the generating variants exist for this element type only
+#endif
+#ifndef SAG_DW_GEN
+#define SAG_DW_GEN 0
 #endif
 
 namespace sag {
@@ -24,32 +28,43 @@ using Setup = cudaError_t (*)();
 // points, so the 1536-point columns never pair); that kind maps to kKindGeneral.
 constexpr int fwd_kind_of(int K) { return K == kKindPair + ct_index(1536) ? kKindGeneral : K; }
 
-template <int K>
+// GEN: plans of parametric factors generate u i^a in the loads (a separate
+// instantiation of every kind).
+template <int K, bool GEN>
 void fwd_kind(const RhsParams& P, const double* nin, int base, int blocks, int all, size_t smem,
               cudaStream_t st) {
-  k_fwd_col<SAG_DW_C, fwd_kind_of(K)><<<blocks, kThreads, smem, st>>>(P, nin, base, all);
+  k_fwd_col<SAG_DW_C, fwd_kind_of(K), GEN><<<blocks, kThreads, smem, st>>>(P, nin, base, all);
 }
-template <int K>
+template <int K, bool GEN>
 cudaError_t fwd_setup() {
-  return allow_max_smem(k_fwd_col<SAG_DW_C, fwd_kind_of(K)>);
+  return allow_max_smem(k_fwd_col<SAG_DW_C, fwd_kind_of(K), GEN>);
 }
-template <int... K>
+template <bool GEN, int... K>
 constexpr std::array<FwdLaunch, sizeof...(K)> fwd_launches(std::integer_sequence<int, K...>) {
-  return {{&fwd_kind<K>...}};
+  return {{&fwd_kind<K, GEN>...}};
 }
-template <int... K>
+template <bool GEN, int... K>
 constexpr std::array<Setup, sizeof...(K)> fwd_setups(std::integer_sequence<int, K...>) {
-  return {{&fwd_setup<K>...}};
+  return {{&fwd_setup<K, GEN>...}};
 }
-constexpr auto kFwd = fwd_launches(std::make_integer_sequence<int, kKindCount>{});
-constexpr auto kFwdSetup = fwd_setups(std::make_integer_sequence<int, kKindCount>{});
+constexpr auto kFwd = fwd_launches<false>(std::make_integer_sequence<int, kKindCount>{});
+constexpr auto kFwdSetup = fwd_setups<false>(std::make_integer_sequence<int, kKindCount>{});
+#if SAG_DW_GEN
+constexpr auto kFwdGen = fwd_launches<true>(std::make_integer_sequence<int, kKindCount>{});
+constexpr auto kFwdGenSetup = fwd_setups<true>(std::make_integer_sequence<int, kKindCount>{});
+#endif
 
 }  // namespace
 
 cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
                                 int base, int blocks, int all, SAG_DW_C) {
+#if SAG_DW_GEN
+  const auto& table = P.vpow ? kFwdGen : kFwd;
+#else
+  const auto& table = kFwd;  // plans of parametric factors read the stored copy on this path
+#endif
   return for_kind_runs(all ? L.col_all : L.col, base, base + blocks, [&](int kind, int b0, int b1) {
-    kFwd[kind](P, nin, b0, b1 - b0, all, L.col_smem, st);
+    table[kind](P, nin, b0, b1 - b0, all, L.col_smem, st);
     return cudaGetLastError();
   });
 }
@@ -60,6 +75,12 @@ cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L, SAG_DW_C) {
     const cudaError_t e = s();
     if (e != cudaSuccess) return e;
   }
+#if SAG_DW_GEN
+  for (Setup s : kFwdGenSetup) {
+    const cudaError_t e = s();
+    if (e != cudaSuccess) return e;
+  }
+#endif
   return cudaSuccess;
 }
 

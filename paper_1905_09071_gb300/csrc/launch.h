@@ -171,6 +171,8 @@ cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n,
                         double* gn, double* gU, int accumulate, cudaStream_t st);
 cudaError_t enqueue_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n,
                           cudaStream_t st);
+// u i^a for i = 1..N by the parametric factors' generator (sag_power_eval).
+cudaError_t enqueue_power_eval(float4 up, const float2* lnt, const float* ek, int N, double* out, cudaStream_t st);
 // One RK2 stage from a given right-hand side k (sag_rk2_stage).
 cudaError_t enqueue_rk2_stage(const RhsParams& P, int stage, int midpoint, double* n, double* nstar,
                               double* k1, const double* k, double dt, cudaStream_t st);

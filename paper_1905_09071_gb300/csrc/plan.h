@@ -67,6 +67,8 @@ struct OrderDesc {
   const void* twg2;    // pass tables of the M2-point inverse rows, global layout
   const void* twg1;    // compile-time columns: pass tables of M1, global layout
   const void* tw4c_p;  // omega_L^(j2 k1) for j2 < 2 M2 in column-block order
+  int pw;              // 1: the double-word forward columns generate U^(m)_r(i) = u i^a
+                       // (RhsParams::vpow, lnt, expk) instead of reading RhsParams::Udw
   const float* rscale; // CP, double-word path: [R] power-of-two weight of rank term r
   double pscale;       // final FP64 scale of P^(d) (1/(L d!), factors of two), before the n scale
   double gscale;       // 2^-d / (L d!): final scale of a vector's cotangent before its exponents
@@ -140,6 +142,10 @@ struct RhsParams {
   const float2* Udw;             // factors scaled by 2^-e_v, vector v at vdwoff[v]
   const int64_t* vdwoff;         // [Vtot]
   float2* ndw;                   // n scaled by 2^-e_n of its system, at SysDesc::ndwoff
+  // Parametric factors (plans of SAG_CP_POWER systems, double-word path):
+  const float4* vpow;            // [Vtot] (u 2^-e_v as hi, lo; a as hi, lo)
+  const float2* lnt;             // [max N + 1] ln i as a double-word (entry 0 is 0)
+  const float* expk;             // exp constants and table (dw_pow.cuh, kExpConsts floats)
   void* scratch;                 // forward column output, all vectors (TT: then their spectra)
   void* scratch2;                // per item: spectral sum after the inverse row step
   void* spec_nyq;                // TT: [Vtot] Nyquist value of each vector's spectrum

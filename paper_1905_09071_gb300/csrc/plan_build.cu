@@ -8,6 +8,7 @@
 #include <map>
 #include <tuple>
 
+#include "dw_pow.cuh"
 #include "plan_host.h"
 
 namespace sag {
@@ -535,6 +536,38 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     float2* Udw = nullptr;
     if ((e = pl->upload(&Udw, hdw)) != cudaSuccess) return fail(SAG_ENOMEM, "cudaMalloc dw factors");
     P.Udw = Udw;
+    if (!pl->pow_ua.empty() && !P.exact) {
+      // Parametric factors (SAG_FP32_SPLIT; the exact double-word path reads
+      // the stored copy): per vector (u 2^-e_v, a) as double-words, ln i per
+      // size (the largest N of the plan), and the exp constants.
+      if ((int64_t)pl->pow_ua.size() != 2 * (int64_t)Vtot) return fail(SAG_EINVAL, "power parameters do not match the vectors");
+      std::vector<float4> vp(Vtot);
+      for (int v = 0; v < Vtot; ++v) {
+        const dw u = dw_from_double(std::ldexp(pl->pow_ua[2 * v], -ev[v]));
+        const dw a = dw_from_double(pl->pow_ua[2 * v + 1]);
+        vp[v] = make_float4(u.hi, u.lo, a.hi, a.lo);
+      }
+      int nmax = 1;
+      for (const SysDesc& sd : S) nmax = std::max(nmax, sd.N);
+      std::vector<float2> lt((size_t)nmax + 1, make_float2(0.f, 0.f));
+      for (int i = 1; i <= nmax; ++i) {
+        const long double l = logl((long double)i);
+        const float hi = (float)l;
+        lt[i] = make_float2(hi, (float)(l - hi));
+      }
+      std::vector<float> ek(kExpConsts);
+      make_exp_consts(ek.data());
+      float4* dvp = nullptr;
+      float2* dlt = nullptr;
+      float* dek = nullptr;
+      if ((e = pl->upload(&dvp, vp)) != cudaSuccess || (e = pl->upload(&dlt, lt)) != cudaSuccess ||
+          (e = pl->upload(&dek, ek)) != cudaSuccess)
+        return fail(SAG_ENOMEM, "cudaMalloc power tables");
+      P.vpow = dvp;
+      P.lnt = dlt;
+      P.expk = dek;
+      for (OrderDesc& od : I) od.pw = 1;
+    }
     float2* ndw = nullptr;
     if ((e = pl->alloc(&ndw, (size_t)std::max<int64_t>(ndwoff, 1))) != cudaSuccess)
       return fail(SAG_ENOMEM, "cudaMalloc n");
@@ -989,6 +1022,7 @@ sag_status autotune_geometry(const sag_system* sys, int32_t B, const sag_options
     if (!cand) return fail(SAG_ENOMEM, "host allocation");
     cand->m2_pref = pref;
     cand->m2_pref[i] = alt;
+    cand->pow_ua = best->pow_ua;
     float ms = 0.0f;
     st = build_plan(sys, B, opt, cand);
     // A candidate that cannot be built (device memory) or that lost the
@@ -1031,6 +1065,8 @@ namespace sag {
 // captured graphs stay valid.
 sag_status update_factors(sag_plan_s* pl, const double* factors, int on_device) {
   if (pl->fmt != SAG_CP) return fail(SAG_EUNSUPPORTED, "factor updates need a CP plan");
+  if (!pl->pow_ua.empty())
+    return fail(SAG_EUNSUPPORTED, "a plan of parametric factors (SAG_CP_POWER) takes no factor updates");
   RhsParams& P = pl->P;
   const bool dwp = P.dwpath != 0;
   const int Vtot = P.Vtot;

@@ -66,6 +66,9 @@ struct sag_plan_s {
   std::vector<int> h_nrowpair;
   std::vector<double> h_work;             // FFT points per item, for balancing groups
   std::vector<int> h_nvec;                // vectors per item (row blocks go heaviest first)
+  // SAG_CP_POWER plans: (u, a) of every vector in vector order; the forward
+  // column kernels generate U = u i^a instead of reading it.
+  std::vector<double> pow_ua;
   bool prof = false;
   sag::EventHook hook;
   // Instantiated graphs of sag_rhs / sag_rk2_step calls, keyed by the call's

@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build
 
 SAG_OK, SAG_EINVAL, SAG_ENOMEM, SAG_ECUDA, SAG_EUNSUPPORTED, SAG_ETIMEOUT, SAG_ENONFINITE = range(7)
-SAG_CP, SAG_TT = 0, 1
+SAG_CP, SAG_TT, SAG_CP_POWER = 0, 1, 2
 SAG_FP64, SAG_FP32_SPLIT, SAG_FP32_SPLIT_EXACT = 0, 1, 2
 SAG_HEUN, SAG_MIDPOINT = 0, 1
 
@@ -28,7 +28,7 @@ EXPORTS = [
     "sag_last_error", "sag_version", "sag_profile_enable", "sag_profile_read", "sag_kernel_name",
     "sag_kernel_work", "sag_plan_describe", "sag_loss_noalloc", "sag_rhs_vjp", "sag_integrate_vjp",
     "sag_plan_update_factors", "sag_plan_factor_count", "sag_plan_set_wait_limit",
-    "sag_kernel_method_work", "sag_rk2_stage",
+    "sag_kernel_method_work", "sag_rk2_stage", "sag_power_eval",
 ]
 SAG_NUM_KERNELS = 13
 
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(f64)]
         lib.sag_kernel_method_work.argtypes = [vp, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
         lib.sag_rk2_stage.argtypes = [vp, i32, vp, vp, vp, vp, f64, vp]
+        lib.sag_power_eval.argtypes = [f64, f64, i32, vp, vp]
         lib.sag_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         lib.sag_loss_noalloc.argtypes = [ctypes.POINTER(_System), i32, vp, vp, vp]
         lib.sag_rhs_vjp.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -109,7 +110,8 @@ def load(build_if_missing: bool = True):
                      "sag_rk2_step", "sag_integrate", "sag_sync_status", "sag_profile_enable",
                      "sag_profile_read", "sag_kernel_work", "sag_plan_describe", "sag_rhs_vjp",
                      "sag_integrate_vjp", "sag_plan_update_factors", "sag_plan_factor_count",
-                     "sag_plan_set_wait_limit", "sag_kernel_method_work", "sag_rk2_stage"):
+                     "sag_plan_set_wait_limit", "sag_kernel_method_work", "sag_rk2_stage",
+                     "sag_power_eval"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -155,6 +157,13 @@ def loss_noalloc(N: int, D: int, ranks, factors, n, q, symmetrize_q: int = 1, st
     _check(lib.sag_loss_noalloc(ctypes.byref(sysd), int(symmetrize_q), _ptr(n), _ptr(q),
                                 _stream(stream, n, q)))
     return q
+
+
+def power_eval(u: float, a: float, N: int, out, stream=None):
+    """sag_power_eval: out[i-1] = u i^a (i = 1..N) by the parametric factors'
+    double-word generator, into a device FP64 tensor of N values."""
+    _check(load().sag_power_eval(float(u), float(a), int(N), _ptr(out), _stream(stream, out)))
+    return out
 
 
 def default_options() -> dict:

@@ -103,15 +103,32 @@ def random_power_cp(D: int = 4, N: int = 65536, R: int = 16, seed: int = BASE_SE
     rng = np.random.default_rng(seed)
     i = sizes(N)
     logi = np.log(i)
-    per = {}
+    per, power = {}, {}
     for d in range(2, D + 1):
         u = rng.uniform(u_range[0], u_range[1], (d, R))
         a = rng.uniform(a_range[0], a_range[1], (d, R))
         per[d] = u[:, :, None] * np.exp(a[:, :, None] * logi[None, None, :])
+        power[d] = np.stack([u, a], axis=-1)  # [d][R][2]
     ranks, f = cp_from_vectors(D, N, per)
     n0 = normalised(np.exp(-i / decay))
     return System(D, N, "cp", ranks, f, n0, dt=1e-4, steps=100, name="random_power_cp",
-                  meta={"seed": seed, "R": R})
+                  meta={"seed": seed, "R": R, "power": power})
+
+
+def power_params(D: int, power: dict) -> np.ndarray:
+    """The (u, a) pairs of a kernel whose CP factors are U^(m)_r(i) = u i^a,
+    per order d the array [d][R_d][2] flattened, orders concatenated (the
+    parametric-factor layout of the library's plan)."""
+    return np.concatenate([np.asarray(power[d], dtype=np.float64).reshape(-1) for d in range(2, D + 1)])
+
+
+def expand_power(D: int, N: int, power: dict) -> tuple[list, np.ndarray]:
+    """The same kernel's CP factors u i^a in FP64 (u * i**a), orders d = 2..D:
+    returns (ranks, flat factors)."""
+    i = sizes(N)
+    per = {d: np.asarray(power[d])[:, :, 0:1] * i[None, None, :] ** np.asarray(power[d])[:, :, 1:2]
+           for d in range(2, D + 1)}
+    return cp_from_vectors(D, N, per)
 
 
 def random_cp(D: int, N: int, ranks, seed: int, lo: float = 0.5, hi: float = 1.5) -> System:
