@@ -81,6 +81,9 @@ def parse():
                          "kernel launched once per right-hand side over every item and timed with "
                          "CUDA events (the launches the roofline figures refer to; for ncu captures); "
                          "prints the per-kernel table to stderr, no JSON line")
+    ap.add_argument("--parametric", action="store_true",
+                    help="with --kernels: the same kernel as (u, a) pairs (SAG_CP_POWER), its factors "
+                         "generated in the forward columns")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plans with the fixed launch rules instead of the plan-time autotuner")
     ap.add_argument("--m2", default=None,
@@ -484,11 +487,14 @@ def run_ours(args, world, rank, local):
     if args.kernels:
         # the timed run's plan: the same autotuned splits and stream groups,
         # or the splits given by --m2 with the rule's stream groups
+        kf = (dict(factors=wl.power_params(s.D, s.meta["power"]), fmt=sag.SAG_CP_POWER) if args.parametric
+              else dict(factors=s.factors))
         if args.m2:
-            pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT,
-                          m2=[int(x) for x in args.m2.split(",")])
+            pl = sag.Plan(s.N, s.D, s.ranks, kf["factors"], fmt=kf.get("fmt", sag.SAG_CP),
+                          prec=sag.SAG_FP32_SPLIT, m2=[int(x) for x in args.m2.split(",")])
         else:
-            pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT, autotune=tune)
+            pl = sag.Plan(s.N, s.D, s.ranks, kf["factors"], fmt=kf.get("fmt", sag.SAG_CP),
+                          prec=sag.SAG_FP32_SPLIT, autotune=tune)
         print("fft splits:", [[o["M1"], o["M2"]] for o in pl.describe()["orders"]], file=sys.stderr)
         n = torch.tensor(s.n0, device="cuda")
         pl.profile(True)
