@@ -76,6 +76,11 @@ def _load():
         lib.orc_integrate_vjp.restype = ctypes.c_int
         lib.orc_integrate_vjp.argtypes = [ctypes.c_int, ctypes.c_int, i32p, f64p, f64p, ctypes.c_double,
                                           ctypes.c_long, ctypes.c_int, ctypes.c_int, f64p, f64p, f64p]
+        lib.orc_rhs_vjp_fmt.restype = ctypes.c_int
+        lib.orc_rhs_vjp_fmt.argtypes = [ctypes.c_int] * 3 + [i32p, f64p, f64p, f64p, ctypes.c_int, f64p, f64p]
+        lib.orc_integrate_vjp_fmt.restype = ctypes.c_int
+        lib.orc_integrate_vjp_fmt.argtypes = ([ctypes.c_int] * 3 + [i32p, f64p, f64p, ctypes.c_double,
+                                              ctypes.c_long, ctypes.c_int, ctypes.c_int, f64p, f64p, f64p])
         lib.orc_brownian_entry.restype = ctypes.c_double
         lib.orc_brownian_entry.argtypes = [ctypes.c_int, f64p, i32p]
         lib.orc_brownian_tt_count.restype = ctypes.c_long
@@ -174,40 +179,40 @@ def integrate(n0, D: int, ranks, factors, dt: float, steps: int, *, fmt: int = C
     return n, dg
 
 
-def rhs_vjp(n, g, D: int, ranks, factors, *, sym: int = 1):
-    """(dF/dn)^T g and (dF/dU)^T g for a CP kernel (direct mode)."""
+def rhs_vjp(n, g, D: int, ranks, factors, *, sym: int = 1, fmt: int = CP):
+    """(dF/dn)^T g and (dF/dU)^T g (factor or core layout; direct mode)."""
     n, np_ = _f64(n)
     g, gp = _f64(g)
     N = n.shape[0]
     r, rp = _i32(ranks)
     f, fp = _f64(factors)
-    if f.size != factor_count(CP, D, N, r):
+    if f.size != factor_count(fmt, D, N, r):
         raise ValueError("factor array has the wrong length")
     gn = np.zeros(N)
     gU = np.zeros(f.size)
-    rc = _load().orc_rhs_vjp(D, N, rp, fp, np_, gp, sym,
-                             gn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                             gU.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    rc = _load().orc_rhs_vjp_fmt(fmt, D, N, rp, fp, np_, gp, sym,
+                                 gn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 gU.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if rc != 0:
         raise ValueError(f"orc_rhs_vjp failed ({rc})")
     return gn, gU
 
 
 def integrate_vjp(n0, D: int, ranks, factors, dt: float, steps: int, g_final, *, sym: int = 1,
-                  method: int = HEUN):
+                  method: int = HEUN, fmt: int = CP):
     """Discrete adjoint of `steps` RK2 steps: returns (g_n0, g_U)."""
     n0, np_ = _f64(n0)
     g, gp = _f64(g_final)
     N = n0.shape[0]
     r, rp = _i32(ranks)
     f, fp = _f64(factors)
-    if f.size != factor_count(CP, D, N, r):
+    if f.size != factor_count(fmt, D, N, r):
         raise ValueError("factor array has the wrong length")
     gn0 = np.zeros(N)
     gU = np.zeros(f.size)
-    rc = _load().orc_integrate_vjp(D, N, rp, fp, np_, float(dt), int(steps), sym, method, gp,
-                                   gn0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                   gU.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    rc = _load().orc_integrate_vjp_fmt(fmt, D, N, rp, fp, np_, float(dt), int(steps), sym, method, gp,
+                                       gn0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       gU.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if rc != 0:
         raise ValueError(f"orc_integrate_vjp failed ({rc})")
     return gn0, gU

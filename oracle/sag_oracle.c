@@ -660,30 +660,207 @@ static void vjp_cp_order(int N, int R, const double* blk, int d, const double* n
   free(a); free(c); free(t); free(s); free(z); free(gn_n);
 }
 
-int orc_rhs_vjp(int D, int N, const int* ranks, const double* factors, const double* n,
-                const double* g, int sym, double* gn, double* gU) {
-  if (!ranks_ok(ORC_CP, D, N, ranks) || !factors || !n || !g || !gn || !gU) return -1;
-  const long nf = orc_factor_count(ORC_CP, D, N, ranks);
+/* Vector-Jacobian product of a TT order (Eq. ch3.eq4), by the chain rule
+ * through the same sequence of operations the direct mode evaluates.
+ * Gain: A_l[a,b] = h^(l)_{a,b} o n; V_1[b] = A_1[0,b]; V_l[b] = sum_a
+ * V_{l-1}[a] * A_l[a,b] (truncated convolutions); p = V_d[0] / d!. Going
+ * back with G_d[0] = g / d!: the cotangent of A_l[a,b] is the correlation of
+ * G_l[b] with V_{l-1}[a] (l >= 2; G_1[b] itself for l = 1), and G_{l-1}[a] =
+ * sum_b the correlation of G_l[b] with A_l[a,b]; A = h o n passes each
+ * cotangent to h (times n) and to n (times h).
+ * Loss: q_k = c n_k w_k with c = -1/(d-1)!, w_k = sum_pos wt_pos
+ * left_{pos-1} H^(pos)(k) right_{pos+1}, left/right the products of the
+ * matrices M_l = sum_i n_i H^(l)(i) before and after position pos (as in
+ * loss_tt_order). Directly, g.q depends on n_k and H^(pos)(k); through M_l
+ * it is, for each pos, the chain e_0^T X_1 ... X_d e_0 with X_pos = z_pos =
+ * sum_k g_k n_k H^(pos)(k) and X_l = M_l elsewhere, whose derivative with
+ * respect to X_l is the outer product of the chain's prefix before l and
+ * suffix after l. */
+static void chain_prefix(int d, const int* rk, const double* X, int rmax, int upto, double* out) {
+  /* out = e_0^T X_1 ... X_upto (length rk[upto]); X_l at X + (l-1) rmax^2 */
+  double tmp[128];
+  out[0] = 1.0;
+  for (int l = 1; l <= upto; ++l) {
+    const double* Xl = X + (size_t)(l - 1) * rmax * rmax;
+    for (int b = 0; b < rk[l]; ++b) {
+      double acc = 0.0;
+      for (int a = 0; a < rk[l - 1]; ++a) acc += out[a] * Xl[(size_t)a * rmax + b];
+      tmp[b] = acc;
+    }
+    memcpy(out, tmp, sizeof(double) * rk[l]);
+  }
+  (void)d;
+}
+static void chain_suffix(int d, const int* rk, const double* X, int rmax, int from, double* out) {
+  /* out = X_from ... X_d e_0 (length rk[from - 1]) */
+  double tmp[128];
+  out[0] = 1.0;
+  for (int l = d; l >= from; --l) {
+    const double* Xl = X + (size_t)(l - 1) * rmax * rmax;
+    for (int a = 0; a < rk[l - 1]; ++a) {
+      double acc = 0.0;
+      for (int b = 0; b < rk[l]; ++b) acc += Xl[(size_t)a * rmax + b] * out[b];
+      tmp[a] = acc;
+    }
+    memcpy(out, tmp, sizeof(double) * rk[l - 1]);
+  }
+}
+
+static void vjp_tt_order(int N, const int* rk, const double* blk, int d, const double* n, const double* g,
+                         int sym, double* gn, double* gblk) {
+  const double inv_dfact = 1.0 / factorial(d);
+  const double c = -1.0 / factorial(d - 1);
+  int rmax = 1;
+  for (int l = 0; l <= d; ++l) rmax = rk[l] > rmax ? rk[l] : rmax;
+  /* ---- gain: the forward chain, every V_l kept */
+  double* V = (double*)calloc((size_t)d * rmax * N, sizeof(double)); /* V_l[b] at ((l-1) rmax + b) N */
+  double* a = (double*)malloc(sizeof(double) * N);
+  double* t = (double*)malloc(sizeof(double) * N);
+  for (int b = 0; b < rk[1]; ++b) {
+    const double* h = tt_vec(blk, rk, N, 1, 0, b);
+    for (int k = 0; k < N; ++k) V[(size_t)b * N + k] = h[k] * n[k];
+  }
+  for (int l = 2; l <= d; ++l)
+    for (int b = 0; b < rk[l]; ++b) {
+      double* vb = V + ((size_t)(l - 1) * rmax + b) * N;
+      for (int aa = 0; aa < rk[l - 1]; ++aa) {
+        const double* h = tt_vec(blk, rk, N, l, aa, b);
+        for (int k = 0; k < N; ++k) a[k] = h[k] * n[k];
+        conv_sizes(V + ((size_t)(l - 2) * rmax + aa) * N, N, a, N, t, N);
+        for (int k = 0; k < N; ++k) vb[k] += t[k];
+      }
+    }
+  /* ---- gain: back through the chain */
+  double* G = (double*)calloc((size_t)rmax * N, sizeof(double));
+  double* Gp = (double*)calloc((size_t)rmax * N, sizeof(double));
+  double* ga = (double*)malloc(sizeof(double) * N);
+  for (int k = 0; k < N; ++k) G[k] = g[k] * inv_dfact;
+  for (int l = d; l >= 1; --l) {
+    for (size_t i = 0; i < (size_t)rmax * N; ++i) Gp[i] = 0.0;
+    for (int aa = 0; aa < rk[l - 1]; ++aa)
+      for (int b = 0; b < rk[l]; ++b) {
+        const double* h = tt_vec(blk, rk, N, l, aa, b);
+        double* gh = gblk + (tt_vec(blk, rk, N, l, aa, b) - blk);
+        const double* Gb = G + (size_t)b * N;
+        if (l == 1) {
+          memcpy(ga, Gb, sizeof(double) * N);
+        } else {
+          const double* Va = V + ((size_t)(l - 2) * rmax + aa) * N;
+          /* ga[j] = sum_{i >= 1, i + j <= N} G_b[i + j] V_a[i] (sizes, 1-based) */
+#pragma omp parallel for schedule(dynamic, 64)
+          for (int j = 1; j <= N; ++j) {
+            nsum acc = {0.0, 0.0};
+            for (int i = 1; i + j <= N; ++i) ns_add(&acc, Gb[i + j - 1] * Va[i - 1]);
+            ga[j - 1] = ns_val(&acc);
+          }
+          /* G_{l-1}[a][i] += sum_{j >= 1, i + j <= N} G_b[i + j] A[j] */
+          for (int k = 0; k < N; ++k) a[k] = h[k] * n[k];
+          double* Gpa = Gp + (size_t)aa * N;
+#pragma omp parallel for schedule(dynamic, 64)
+          for (int i = 1; i <= N; ++i) {
+            nsum acc = {0.0, 0.0};
+            for (int j = 1; i + j <= N; ++j) ns_add(&acc, Gb[i + j - 1] * a[j - 1]);
+            Gpa[i - 1] += ns_val(&acc);
+          }
+        }
+        for (int k = 0; k < N; ++k) {
+          gh[k] += ga[k] * n[k];
+          gn[k] += ga[k] * h[k];
+        }
+      }
+    double* sw = G;
+    G = Gp;
+    Gp = sw;
+  }
+  /* ---- loss */
+  const size_t r2 = (size_t)rmax * rmax;
+  double* M = (double*)calloc((size_t)d * r2, sizeof(double));
+  double* X = (double*)calloc((size_t)d * r2, sizeof(double));
+  double* Gam = (double*)calloc((size_t)d * r2, sizeof(double));
+  double* gnn = (double*)malloc(sizeof(double) * N);
+  double* w = (double*)calloc(N, sizeof(double));
+  for (int k = 0; k < N; ++k) gnn[k] = g[k] * n[k];
+  for (int l = 1; l <= d; ++l)
+    for (int aa = 0; aa < rk[l - 1]; ++aa)
+      for (int b = 0; b < rk[l]; ++b)
+        M[(l - 1) * r2 + (size_t)aa * rmax + b] = dot_n(tt_vec(blk, rk, N, l, aa, b), n, N);
+  double left[128], right[128], pre[128], suf[128];
+  for (int pos = (sym ? 1 : d); pos <= d; ++pos) {
+    const double wt = sym ? 1.0 / d : 1.0;
+    chain_prefix(d, rk, M, rmax, pos - 1, left);
+    chain_suffix(d, rk, M, rmax, pos + 1, right);
+    /* direct: w_k and the cotangent of H^(pos)(k) */
+    for (int aa = 0; aa < rk[pos - 1]; ++aa)
+      for (int b = 0; b < rk[pos]; ++b) {
+        const double lr = wt * left[aa] * right[b];
+        const double* h = tt_vec(blk, rk, N, pos, aa, b);
+        double* gh = gblk + (h - blk);
+        for (int k = 0; k < N; ++k) {
+          w[k] += lr * h[k];
+          gh[k] += c * lr * gnn[k];
+        }
+      }
+    /* through M_l, l != pos: the chain with X_pos = z_pos */
+    memcpy(X, M, sizeof(double) * (size_t)d * r2);
+    for (int aa = 0; aa < rk[pos - 1]; ++aa)
+      for (int b = 0; b < rk[pos]; ++b)
+        X[(pos - 1) * r2 + (size_t)aa * rmax + b] = dot_n(tt_vec(blk, rk, N, pos, aa, b), gnn, N);
+    for (int l = 1; l <= d; ++l) {
+      if (l == pos) continue;
+      chain_prefix(d, rk, X, rmax, l - 1, pre);
+      chain_suffix(d, rk, X, rmax, l + 1, suf);
+      for (int aa = 0; aa < rk[l - 1]; ++aa)
+        for (int b = 0; b < rk[l]; ++b) Gam[(l - 1) * r2 + (size_t)aa * rmax + b] += c * wt * pre[aa] * suf[b];
+    }
+  }
+  for (int k = 0; k < N; ++k) gn[k] += c * g[k] * w[k];
+  for (int l = 1; l <= d; ++l)
+    for (int aa = 0; aa < rk[l - 1]; ++aa)
+      for (int b = 0; b < rk[l]; ++b) {
+        const double gm = Gam[(l - 1) * r2 + (size_t)aa * rmax + b];
+        if (gm == 0.0) continue;
+        const double* h = tt_vec(blk, rk, N, l, aa, b);
+        double* gh = gblk + (h - blk);
+        for (int k = 0; k < N; ++k) {
+          gn[k] += gm * h[k];
+          gh[k] += gm * n[k];
+        }
+      }
+  free(V); free(a); free(t); free(G); free(Gp); free(ga); free(M); free(X); free(Gam); free(gnn); free(w);
+}
+
+int orc_rhs_vjp_fmt(int fmt, int D, int N, const int* ranks, const double* factors, const double* n,
+                    const double* g, int sym, double* gn, double* gU) {
+  if (!ranks_ok(fmt, D, N, ranks) || !factors || !n || !g || !gn || !gU) return -1;
+  if (!tt_ranks_small(fmt, D, ranks)) return -1;
+  const long nf = orc_factor_count(fmt, D, N, ranks);
   for (int k = 0; k < N; ++k) gn[k] = 0.0;
   for (long i = 0; i < nf; ++i) gU[i] = 0.0;
   for (int d = 2; d <= D; ++d) {
     const int* rk;
-    const long off = order_offset(ORC_CP, N, ranks, d, &rk);
-    vjp_cp_order(N, rk[0], factors + off, d, n, g, sym, gn, gU + off);
+    const long off = order_offset(fmt, N, ranks, d, &rk);
+    if (fmt == ORC_CP) vjp_cp_order(N, rk[0], factors + off, d, n, g, sym, gn, gU + off);
+    else vjp_tt_order(N, rk, factors + off, d, n, g, sym, gn, gU + off);
   }
   return 0;
+}
+
+int orc_rhs_vjp(int D, int N, const int* ranks, const double* factors, const double* n,
+                const double* g, int sym, double* gn, double* gU) {
+  return orc_rhs_vjp_fmt(ORC_CP, D, N, ranks, factors, n, g, sym, gn, gU);
 }
 
 /* Reverse pass through `steps` RK2 steps from n0 (states kept in memory).
  * g_in: cotangent of the final state. Outputs g_n0 (cotangent of n0) and g_U
  * (cotangent of the factors, accumulated over all steps). */
-int orc_integrate_vjp(int D, int N, const int* ranks, const double* factors, const double* n0,
-                      double dt, long steps, int sym, int method, const double* g_in, double* g_n0,
-                      double* g_U) {
-  if (!ranks_ok(ORC_CP, D, N, ranks) || !factors || !n0 || !g_in || !g_n0 || !g_U || steps < 0)
+int orc_integrate_vjp_fmt(int fmt, int D, int N, const int* ranks, const double* factors, const double* n0,
+                          double dt, long steps, int sym, int method, const double* g_in, double* g_n0,
+                          double* g_U) {
+  if (!ranks_ok(fmt, D, N, ranks) || !factors || !n0 || !g_in || !g_n0 || !g_U || steps < 0)
     return -1;
+  if (!tt_ranks_small(fmt, D, ranks)) return -1;
   if (method != ORC_HEUN && method != ORC_MIDPOINT) return -1;
-  const long nf = orc_factor_count(ORC_CP, D, N, ranks);
+  const long nf = orc_factor_count(fmt, D, N, ranks);
   double* states = (double*)malloc(sizeof(double) * (size_t)(steps + 1) * N);
   double* p = (double*)malloc(sizeof(double) * N);
   double* q = (double*)malloc(sizeof(double) * N);
@@ -696,30 +873,36 @@ int orc_integrate_vjp(int D, int N, const int* ranks, const double* factors, con
   memcpy(states, n0, sizeof(double) * N);
   for (long s = 0; s < steps; ++s) {
     memcpy(states + (size_t)(s + 1) * N, states + (size_t)s * N, sizeof(double) * N);
-    orc_integrate(ORC_DIRECT, ORC_CP, D, N, ranks, factors, states + (size_t)(s + 1) * N, dt, 1, sym,
+    orc_integrate(ORC_DIRECT, fmt, D, N, ranks, factors, states + (size_t)(s + 1) * N, dt, 1, sym,
                   method, NULL);
   }
   memcpy(gbar, g_in, sizeof(double) * N);
   for (long i = 0; i < nf; ++i) g_U[i] = 0.0;
   for (long s = steps - 1; s >= 0; --s) {
     const double* n = states + (size_t)s * N;
-    orc_rhs(ORC_DIRECT, ORC_CP, D, N, ranks, factors, n, sym, p, q, NULL);
+    orc_rhs(ORC_DIRECT, fmt, D, N, ranks, factors, n, sym, p, q, NULL);
     const double h1 = method == ORC_HEUN ? dt : 0.5 * dt;
     for (int k = 0; k < N; ++k) ns[k] = n[k] + h1 * (p[k] + q[k]);
     /* second stage: k2 = F(n*) enters with weight dt/2 (Heun) or dt (midpoint) */
     const double w2 = method == ORC_HEUN ? 0.5 * dt : dt;
     for (int k = 0; k < N; ++k) gk[k] = w2 * gbar[k];
-    orc_rhs_vjp(D, N, ranks, factors, ns, gk, sym, gA, gUa);
+    orc_rhs_vjp_fmt(fmt, D, N, ranks, factors, ns, gk, sym, gA, gUa);
     for (long i = 0; i < nf; ++i) g_U[i] += gUa[i];
     /* first stage: k1 = F(n) enters n' with weight dt/2 (Heun, 0 for midpoint)
      * and n* with weight h1 */
     const double w1 = method == ORC_HEUN ? 0.5 * dt : 0.0;
     for (int k = 0; k < N; ++k) gk[k] = w1 * gbar[k] + h1 * gA[k];
-    orc_rhs_vjp(D, N, ranks, factors, n, gk, sym, gB, gUa);
+    orc_rhs_vjp_fmt(fmt, D, N, ranks, factors, n, gk, sym, gB, gUa);
     for (long i = 0; i < nf; ++i) g_U[i] += gUa[i];
     for (int k = 0; k < N; ++k) gbar[k] = gbar[k] + gA[k] + gB[k];
   }
   memcpy(g_n0, gbar, sizeof(double) * N);
   free(states); free(p); free(q); free(ns); free(gbar); free(gk); free(gA); free(gB); free(gUa);
   return 0;
+}
+
+int orc_integrate_vjp(int D, int N, const int* ranks, const double* factors, const double* n0,
+                      double dt, long steps, int sym, int method, const double* g_in, double* g_n0,
+                      double* g_U) {
+  return orc_integrate_vjp_fmt(ORC_CP, D, N, ranks, factors, n0, dt, steps, sym, method, g_in, g_n0, g_U);
 }

@@ -65,6 +65,14 @@ int orc_integrate(int mode, int fmt, int D, int N, const int* ranks, const doubl
 int orc_rhs_vjp(int D, int N, const int* ranks, const double* factors, const double* n,
                 const double* g, int sym, double* gn, double* gU);
 
+/* The same for either format (fmt = ORC_CP or ORC_TT; TT cotangents in the
+ * core layout). */
+int orc_rhs_vjp_fmt(int fmt, int D, int N, const int* ranks, const double* factors, const double* n,
+                    const double* g, int sym, double* gn, double* gU);
+int orc_integrate_vjp_fmt(int fmt, int D, int N, const int* ranks, const double* factors, const double* n0,
+                          double dt, long steps, int sym, int method, const double* g_in, double* g_n0,
+                          double* g_U);
+
 /* Discrete adjoint of `steps` RK2 steps from n0, CP kernels: given the
  * cotangent g_in of the final state, returns the cotangent of n0 and the
  * factors' cotangent accumulated over the steps. */

@@ -64,7 +64,7 @@ cudaError_t launch_k_fwd_col_dw(const RhsParams& P, const LaunchCfg& L, const do
   const auto& table = kFwd;  // plans of parametric factors read the stored copy on this path
 #endif
   return for_kind_runs(all ? L.col_all : L.col, base, base + blocks, [&](int kind, int b0, int b1) {
-    table[kind](P, nin, b0, b1 - b0, all, L.col_smem, st);
+    table[kind](P, nin, b0, b1 - b0, all, L.col_smem_kind[kind] ? L.col_smem_kind[kind] : L.col_smem, st);
     return cudaGetLastError();
   });
 }

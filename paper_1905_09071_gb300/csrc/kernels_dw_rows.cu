@@ -52,7 +52,7 @@ constexpr auto kRowSetup = row_setups(std::make_integer_sequence<int, kKindCount
 cudaError_t launch_k_rows_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, int base, int blocks,
                              SAG_DW_C) {
   return for_kind_runs(L.row, base, base + blocks, [&](int kind, int b0, int b1) {
-    kRows[kind](P, b0, b1 - b0, L.row_smem, st);
+    kRows[kind](P, b0, b1 - b0, L.row_smem_kind[kind] ? L.row_smem_kind[kind] : L.row_smem, st);
     return cudaGetLastError();
   });
 }

@@ -20,11 +20,15 @@ double factorial(int d) {
   return f;
 }
 
-// Smallest L = 2^a f (f in {1, 3, 5, 15}, a >= 1) with L >= need.
-int64_t choose_fft_length(int64_t need) {
+// Smallest L = 2^a f with L >= need, f in {1, 3, 5, 15}, or f in {1, 3} only
+// (the lengths whose four-step halves have compile-time and pair-form
+// kernels in the double-word path: at most 4/3 more points, 2x faster per
+// point than the run-time radix kernels a factor 5 would need).
+int64_t choose_fft_length(int64_t need, bool allow5 = true) {
   int64_t best = -1;
   const int64_t fs[4] = {1, 3, 5, 15};
   for (int64_t f : fs) {
+    if (!allow5 && f % 5 == 0) continue;
     int64_t L = 2 * f;
     while (L < need) L *= 2;
     if (best < 0 || L < best) best = L;
@@ -375,10 +379,11 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     return fail(SAG_EINVAL, "m2 needs one entry per order of the plan (" + std::to_string(I.size()) + ")");
   int64_t scr = 0, scr2 = 0, pdo = 0;
   size_t col_smem = 0, row_smem = 0, rowtt_smem = 0;
+  std::vector<size_t> item_col_smem, item_row_smem;  // per item: what its column / row blocks need
   std::vector<int> colpre(1, 0), colpre_all(1, 0), invpre(1, 0), chainpre(1, 0);
   for (OrderDesc& od : I) {
     const int d = od.d;
-    const int64_t L = choose_fft_length(std::max<int64_t>((int64_t)d * od.N, 16));
+    const int64_t L = choose_fft_length(std::max<int64_t>((int64_t)d * od.N, 16), !dwp);
     if (L > (int64_t)1 << 24) return fail(SAG_EUNSUPPORTED, "FFT length above 2^24 (d N too large)");
     od.L = (int)L;
     od.M = (int)(L / 2);
@@ -447,19 +452,20 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     chainpre.push_back(chainpre.back() + (tt ? (od.M + 1 + 255) / 256 : 0));
     // Compile-time kernels work in place (one buffer, pass tables in global
     // memory), the generic ones ping-pong and keep the natural table.
-    col_smem = std::max(col_smem, od.ct1 ? (size_t)(W * od.ld1) * csize
-                                         : (size_t)(2 * W * od.ld1 + od.M1) * csize);
+    item_col_smem.push_back(od.ct1 ? (size_t)(W * od.ld1) * csize : (size_t)(2 * W * od.ld1 + od.M1) * csize);
+    col_smem = std::max(col_smem, item_col_smem.back());
     // The compile-time row kernels stage their input (bulk copies, natural
     // order) apart from the padded work area, behind one mbarrier: 2 G
     // transforms of M2 points, or in the pair form 2 G' transforms of 2 M2
     // points. The runtime one ping-pongs.
     if (od.pair) {
       const int Gp = ct_group(2 * od.M2);
-      row_smem = std::max(row_smem, (size_t)(2 * Gp * 2 * od.M2 + 2 * Gp * od.ld2p) * csize + 16);
+      item_row_smem.push_back((size_t)(2 * Gp * 2 * od.M2 + 2 * Gp * od.ld2p) * csize + 16);
     } else {
-      row_smem = std::max(row_smem, od.ct2 ? (size_t)(2 * G * od.M2 + 2 * G * od.ld2) * csize + 16
-                                           : (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize);
+      item_row_smem.push_back(od.ct2 ? (size_t)(2 * G * od.M2 + 2 * G * od.ld2) * csize + 16
+                                     : (size_t)(2 * G * 2 * od.ld2 + od.M2) * csize);
     }
+    row_smem = std::max(row_smem, item_row_smem.back());
     rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * G * 2 * od.ld2, 6 * od.ld2) * csize +
                                           (size_t)od.M2 * csize);
     // Vector-Jacobian product kernels (CP): ping-pong column blocks; row
@@ -501,6 +507,26 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   L.col_smem = col_smem;
   L.row_smem = row_smem;
   L.inv_smem = col_smem;
+  // Each launch of one kernel specialisation gets the shared memory its own
+  // items need (the largest item of another kind would cut the occupancy of
+  // every launch); the run-time dispatching kernel keeps the plan's largest.
+  for (int k = 0; k < kKindCount; ++k) L.col_smem_kind[k] = L.row_smem_kind[k] = 0;
+  for (size_t i = 0; i < I.size(); ++i) {
+    const OrderDesc& od = I[i];
+    if (!dwp) break;
+    const int ck = od.ct1 ? kKindCt + ct_index(od.M1) : kKindRuntime;
+    L.col_smem_kind[ck] = std::max(L.col_smem_kind[ck], item_col_smem[i]);  // single vectors (adjoint too)
+    if (od.pair) {
+      const int pk = kKindPair + ct_index(od.M1);
+      L.col_smem_kind[pk] = std::max(L.col_smem_kind[pk], item_col_smem[i]);
+    }
+    if (!tt) {
+      const int rk = od.pair ? kKindPair + ct_index(2 * od.M2) : od.ct2 ? kKindCt + ct_index(od.M2) : kKindRuntime;
+      L.row_smem_kind[rk] = std::max(L.row_smem_kind[rk], item_row_smem[i]);
+    }
+  }
+  L.col_smem_kind[kKindGeneral] = col_smem;
+  L.row_smem_kind[kKindGeneral] = row_smem;
   L.rowtt_smem = rowtt_smem;
   L.epi_smem = (size_t)maxnv * sizeof(double);
   L.coef_smem = (size_t)2 * maxnv * sizeof(double);

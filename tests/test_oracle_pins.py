@@ -412,3 +412,68 @@ def test_paper_ternary_forms_agree():
                                   3: s.factors.reshape(3, 6, 40)})
     p, q = oracle.rhs(s.n0, 3, z[0], z[1], mode=oracle.DIRECT)
     assert np.abs(p - pb).max() / scale < 1e-14 and np.abs(q - qb).max() / scale < 1e-14
+
+
+# ---------------------------------------------------------------- TT adjoint
+def _F_tt(n, D, ranks, f, sym):
+    p, q = oracle.rhs(n, D, ranks, f, fmt=oracle.TT, sym=sym)
+    return p + q
+
+
+@pytest.mark.parametrize("sym", [1, 0])
+@pytest.mark.parametrize("D,N,ranks", [(2, 10, {2: [1, 3, 1]}), (3, 9, {2: [1, 2, 1], 3: [1, 2, 3, 1]}),
+                                       (4, 7, {2: [1, 1, 1], 3: [1, 2, 2, 1], 4: [1, 2, 3, 2, 1]})])
+def test_tt_rhs_vjp_matches_central_differences(D, N, ranks, sym):
+    t = wl.random_tt(D, N, ranks, seed=90 + D)
+    rng = np.random.default_rng(91)
+    g, un, uf = rng.normal(size=N), rng.normal(size=N), rng.normal(size=t.factors.size)
+    gn, gH = oracle.rhs_vjp(t.n0, g, D, t.ranks, t.factors, sym=sym, fmt=oracle.TT)
+    h = 1e-6
+    dn = (_F_tt(t.n0 + h * un, D, t.ranks, t.factors, sym) - _F_tt(t.n0 - h * un, D, t.ranks, t.factors, sym)) / (2 * h)
+    df = (_F_tt(t.n0, D, t.ranks, t.factors + h * uf, sym) - _F_tt(t.n0, D, t.ranks, t.factors - h * uf, sym)) / (2 * h)
+    assert abs(g @ dn - gn @ un) < 1e-8 * (abs(g) @ abs(dn) + 1e-30)
+    assert abs(g @ df - gH @ uf) < 1e-8 * (abs(g) @ abs(df) + 1e-30)
+
+
+@pytest.mark.parametrize("sym", [1, 0])
+def test_tt_vjp_of_diagonal_embedding_equals_cp_vjp(sym):
+    # The CP kernel and its TT diagonal embedding are the same function of n,
+    # and each CP factor value sits at one core entry: the n-cotangents agree,
+    # and so do the factor cotangents at the embedded entries.
+    s = wl.random_cp(4, 8, [2, 3, 2], seed=5)
+    t = wl.cp_to_tt_diagonal(s)
+    g = np.random.default_rng(6).normal(size=s.N)
+    gn1, gU = oracle.rhs_vjp(s.n0, g, 4, s.ranks, s.factors, sym=sym)
+    gn2, gH = oracle.rhs_vjp(t.n0, g, 4, t.ranks, t.factors, sym=sym, fmt=oracle.TT)
+    assert np.abs(gn1 - gn2).max() < 1e-14 * np.abs(gn1).max()
+    offs = wl.cp_layout(4, s.N, s.ranks)
+    toff = 0
+    for d in range(2, 5):
+        R = s.ranks[d - 2]
+        gUd = gU[offs[d - 2]:offs[d - 1]].reshape(d, R, s.N)
+        rk = [1] + [R] * (d - 1) + [1]
+        for l in range(1, d + 1):
+            blk = gH[toff:toff + rk[l - 1] * rk[l] * s.N].reshape(rk[l - 1], rk[l], s.N)
+            toff += rk[l - 1] * rk[l] * s.N
+            for r in range(R):
+                emb = blk[0, r] if l == 1 else blk[r, 0] if l == d else blk[r, r]
+                assert np.abs(emb - gUd[l - 1, r]).max() < 1e-14 * np.abs(gU).max()
+
+
+def test_tt_integrate_vjp_matches_central_differences():
+    D, N = 3, 10
+    t = wl.random_tt(D, N, {2: [1, 2, 1], 3: [1, 2, 2, 1]}, seed=95)
+    rng = np.random.default_rng(96)
+    g, un, uf = rng.normal(size=N), rng.normal(size=N), rng.normal(size=t.factors.size)
+    dt, steps = 0.05, 5
+    gn0, gH = oracle.integrate_vjp(t.n0, D, t.ranks, t.factors, dt, steps, g, fmt=oracle.TT)
+
+    def L(n0, f):
+        n, _ = oracle.integrate(n0, D, t.ranks, f, dt, steps, fmt=oracle.TT, diag=False)
+        return g @ n
+
+    h = 1e-6
+    d_n = (L(t.n0 + h * un, t.factors) - L(t.n0 - h * un, t.factors)) / (2 * h)
+    d_f = (L(t.n0, t.factors + h * uf) - L(t.n0, t.factors - h * uf)) / (2 * h)
+    assert abs(d_n - gn0 @ un) < 1e-7 * abs(d_n)
+    assert abs(d_f - gH @ uf) < 1e-7 * abs(d_f)
