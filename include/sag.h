@@ -197,16 +197,20 @@ sag_status sag_rk2_stage(sag_plan_t plan, int32_t stage, double* n, double* nsta
 sag_status sag_integrate(sag_plan_t plan, double* n, double dt, int64_t steps, double* diag,
                          void* stream);
 
-/* Adjoint (CP plans). The factors' cotangent uses the plan's vector layout:
- * the systems' CP factor arrays ([d][R_d][N] per order) concatenated in system
- * order, sag_plan_factor_count values in all.
+/* Adjoint (CP and TT plans). The factors' cotangent uses the systems' own
+ * factor layout concatenated in system order, sag_plan_factor_count values in
+ * all: CP, the arrays [d][R_d][N] per order; TT, the cores
+ * [R_{lambda-1}][R_lambda][N] per order (every core entry, also entries whose
+ * vector is zero: their cotangents are in general not zero).
  *
  * sag_rhs_vjp: vector-Jacobian product of the right-hand side at n for the
  * cotangent g (packed state layout): gn = (dF/dn)^T g, gU = (dF/dU)^T g
  * (either output may be NULL; both are overwritten). The gain term's
- * derivative is a correlation of g with the other modes' convolution,
+ * derivative is a correlation of g with the other modes' convolution (TT: with
+ * the product of the other cores, G conj(prefix[a] suffix[b]) per frequency),
  * evaluated with the same FFT lengths as the forward pass; the loss term's
- * through n, U and the inner products s = <U, n> (product rule). */
+ * through n, the factors and the inner products s = <U, n> (TT: the matrices
+ * M_lambda = sum_i n_i H^(lambda)(i)) by the product rule. */
 sag_status sag_rhs_vjp(sag_plan_t plan, const double* n, const double* g, double* gn, double* gU,
                        void* stream);
 
@@ -224,7 +228,8 @@ sag_status sag_integrate_vjp(sag_plan_t plan, const double* n0, double dt, int64
  * valid. Synchronises the device first. */
 sag_status sag_plan_update_factors(sag_plan_t plan, const double* factors, int32_t on_device);
 
-/* Number of factor values in the plan's vector layout. */
+/* Number of factor values of the plan's systems in their factor layout (the
+ * length of the adjoint's factor cotangent). */
 sag_status sag_plan_factor_count(sag_plan_t plan, int64_t* count);
 
 /* Clock-cycle limit of the plan's device-side waits (the row kernels' waits on

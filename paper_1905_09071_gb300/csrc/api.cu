@@ -509,7 +509,11 @@ namespace {
 
 // Checks that the plan can run the vector-Jacobian product.
 sag_status vjp_supported(sag_plan_t pl) {
-  if (pl->fmt != SAG_CP) return fail(SAG_EUNSUPPORTED, "the adjoint is implemented for CP kernels");
+  if (pl->fmt == SAG_TT) {
+    if ((int)pl->L.rowtt_smem > smem_limit() || (int)pl->L.vcol_smem > smem_limit())
+      return fail(SAG_EUNSUPPORTED, "adjoint blocks exceed shared memory (row or column length too large)");
+    return SAG_OK;
+  }
   if ((int)pl->L.vrow_smem > smem_limit() || (int)pl->L.vcol_smem > smem_limit())
     return fail(SAG_EUNSUPPORTED, "adjoint row blocks exceed shared memory (order or row length too large)");
   return SAG_OK;

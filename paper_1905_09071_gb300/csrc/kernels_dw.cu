@@ -52,6 +52,11 @@ cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const doub
   return P.exact ? launch_vjp_fft_dw(P, L, n, g, st, cdwx{}) : launch_vjp_fft_dw(P, L, n, g, st, cdw{});
 }
 
+cudaError_t launch_vjp_fft_tt_dw(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                                 cudaStream_t st) {
+  return P.exact ? launch_vjp_fft_tt_dw(P, L, n, g, st, cdwx{}) : launch_vjp_fft_tt_dw(P, L, n, g, st, cdw{});
+}
+
 cudaError_t setup_fft_kernels_dw(const LaunchCfg& L) {
   cudaError_t e = setup_fft_dwc<cdw>(L);
   if (e == cudaSuccess) e = setup_fft_dwc<cdwx>(L);

@@ -13,6 +13,10 @@ cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const doub
                               cudaStream_t st);
 cudaError_t launch_vjp_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
                                cudaStream_t st);
+cudaError_t launch_vjp_fft_tt_dw(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                                 cudaStream_t st);
+cudaError_t launch_vjp_fft_tt_f64(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                                  cudaStream_t st);
 
 namespace {
 
@@ -142,6 +146,132 @@ __global__ void __launch_bounds__(256) k_coef_vjp(const __grid_constant__ RhsPar
   }
 }
 
+// ---- TT: coef and sigma of every core entry, one block per order ----------
+// M_l[a][b] = <h^(l)_{a,b}, n>, Z_l[a][b] = <h^(l)_{a,b}, g o n> (0 for
+// entries without a vector). Entry (l, a, b): coef = c w_l left[a] right[b]
+// of the M chain, sigma = c sum_{pos != l} w_pos pre[a] suf[b] of the chain
+// with Z_pos in place of M_pos, c = -1/(d-1)!, w = 1/d (symmetrised) or
+// [pos = d] (last mode).
+constexpr int kTR = kMaxTTRank;
+__device__ void tt_left(const double* Mx, const double* Zx, int zpos, const int* ttr, int upto, double* out) {
+  // out = e_0^T X_1 ... X_upto, X_l = Z_l if l == zpos else M_l
+  double tmp[kTR];
+  out[0] = 1.0;
+  for (int l = 1; l <= upto; ++l) {
+    const double* X = (l == zpos ? Zx : Mx) + (l - 1) * kTR * kTR;
+    for (int b = 0; b < ttr[l]; ++b) {
+      double acc = 0.0;
+      for (int a = 0; a < ttr[l - 1]; ++a) acc = fma(out[a], X[a * kTR + b], acc);
+      tmp[b] = acc;
+    }
+    for (int b = 0; b < ttr[l]; ++b) out[b] = tmp[b];
+  }
+}
+__device__ void tt_right(const double* Mx, const double* Zx, int zpos, const int* ttr, int d, int from,
+                         double* out) {
+  // out = X_from ... X_d e_0
+  double tmp[kTR];
+  out[0] = 1.0;
+  for (int l = d; l >= from; --l) {
+    const double* X = (l == zpos ? Zx : Mx) + (l - 1) * kTR * kTR;
+    for (int a = 0; a < ttr[l - 1]; ++a) {
+      double acc = 0.0;
+      for (int b = 0; b < ttr[l]; ++b) acc = fma(X[a * kTR + b], out[b], acc);
+      tmp[a] = acc;
+    }
+    for (int a = 0; a < ttr[l - 1]; ++a) out[a] = tmp[a];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_coef_vjp_tt(const __grid_constant__ RhsParams P) {
+  __shared__ double Mx[kMaxD * kTR * kTR], Zx[kMaxD * kTR * kTR];
+  const int it = blockIdx.x;
+  const OrderDesc& od = P.ord[it];
+  const SysDesc sy = P.sys[od.sys];
+  const int d = od.d, nc = sy.ndotchunk;
+  const int* vid = P.vid + od.vid_off;
+  for (int q = threadIdx.x; q < od.nent; q += blockDim.x) {
+    int l = 1, off = 0;
+    while (q >= off + od.ttr[l - 1] * od.ttr[l]) off += od.ttr[l - 1] * od.ttr[l++];
+    const int loc = q - off, a = loc / od.ttr[l], b = loc - a * od.ttr[l];
+    const int v = vid[q];
+    double sm = 0.0, sz = 0.0;
+    if (v >= 0) {
+      const int64_t base = (int64_t)v * P.maxdotchunk;
+      for (int c = 0; c < nc; ++c) {
+        sm += P.dot_s[base + c];
+        sz += P.dot_z[base + c];
+      }
+    }
+    Mx[(l - 1) * kTR * kTR + a * kTR + b] = sm;
+    Zx[(l - 1) * kTR * kTR + a * kTR + b] = sz;
+  }
+  __syncthreads();
+  const double c = -inv_fact(d - 1);
+  for (int q = threadIdx.x; q < od.nent; q += blockDim.x) {
+    int l = 1, off = 0;
+    while (q >= off + od.ttr[l - 1] * od.ttr[l]) off += od.ttr[l - 1] * od.ttr[l++];
+    const int loc = q - off, a = loc / od.ttr[l], b = loc - a * od.ttr[l];
+    double left[kTR], right[kTR];
+    const double wl = P.sym ? 1.0 / d : (l == d ? 1.0 : 0.0);
+    double coef = 0.0;
+    if (wl != 0.0) {
+      tt_left(Mx, Zx, 0, od.ttr, l - 1, left);
+      tt_right(Mx, Zx, 0, od.ttr, d, l + 1, right);
+      coef = c * wl * left[a] * right[b];
+    }
+    double sg = 0.0;
+    for (int pos = 1; pos <= d; ++pos) {
+      if (pos == l) continue;
+      const double wp = P.sym ? 1.0 / d : (pos == d ? 1.0 : 0.0);
+      if (wp == 0.0) continue;
+      tt_left(Mx, Zx, pos, od.ttr, l - 1, left);
+      tt_right(Mx, Zx, pos, od.ttr, d, l + 1, right);
+      sg += c * wp * left[a] * right[b];
+    }
+    P.coef[od.ebase + q] = coef;
+    P.sigma[od.ebase + q] = sg;
+  }
+  if (threadIdx.x == 0 && it == sy.ibeg) {
+    P.sc[od.sys].nmax_bits = 0ull;
+    P.sc[od.sys].gmax_bits = 0ull;
+  }
+}
+
+// gn_k = g_k sum_e coef_e h_e(k) + sum_e h_e(k) (ga_e(k) + sigma_e),
+// gH_e(k) (=|+=) n_k (ga_e(k) + sigma_e) + coef_e g_k n_k, over every core
+// entry of the system (h_e = 0 for an entry without a stored vector).
+__global__ void __launch_bounds__(256) k_vjp_final_tt(const __grid_constant__ RhsParams P,
+                                                      const double* __restrict__ n,
+                                                      const double* __restrict__ g, double* gn,
+                                                      double* gH, int accumulate) {
+  const int b = find_segment(P.epipre, P.B, blockIdx.x);
+  const SysDesc sy = P.sys[b];
+  const int k = (blockIdx.x - P.epipre[b]) * blockDim.x + threadIdx.x;
+  if (k >= sy.N) return;
+  const int64_t gk = sy.noff + k;
+  const double nk = n[gk], gg = g[gk];
+  double w = 0.0, acc = 0.0;
+  for (int it = sy.ibeg; it < sy.iend; ++it) {
+    const OrderDesc& od = P.ord[it];
+    const int* vid = P.vid + od.vid_off;
+    for (int q = 0; q < od.nent; ++q) {
+      const int e = od.ebase + q, v = vid[q];
+      const double h = v >= 0 ? P.U64[P.voff[v] + k] : 0.0;
+      const int64_t o = P.eoff[e] + k;
+      const double ga = P.gaent[o] + P.sigma[e];
+      const double cf = P.coef[e];
+      w = fma(cf, h, w);
+      acc = fma(h, ga, acc);
+      if (gH) {
+        const double val = fma(nk, ga, cf * gg * nk);
+        gH[o] = accumulate ? gH[o] + val : val;
+      }
+    }
+  }
+  if (gn) gn[gk] = fma(gg, w, acc);
+}
+
 // gn_k = g_k w_k + sum_v U_v(k) (ga_v(k) + sigma_v),
 // gU_v(k) (=|+=) n_k (ga_v(k) + sigma_v) + coef_v g_k n_k.
 __global__ void __launch_bounds__(256) k_vjp_final(const __grid_constant__ RhsParams P,
@@ -195,6 +325,14 @@ cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n,
     enqueue_nsplit(P, L, n, st);
     k_gmax<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, g);
     k_gsplit<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, g);
+  }
+  if (L.has_tt) {
+    e = P.dwpath ? launch_vjp_fft_tt_dw(P, L, n, g, st) : launch_vjp_fft_tt_f64(P, L, n, g, st);
+    if (e != cudaSuccess) return e;
+    k_dot2<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, st>>>(P, n, g);
+    k_coef_vjp_tt<<<P.nitems, 256, 0, st>>>(P);
+    k_vjp_final_tt<<<L.epi_blocks, 256, 0, st>>>(P, n, g, gn, gU, accumulate);
+    return cudaGetLastError();
   }
   e = P.dwpath ? launch_vjp_fft_dw(P, L, n, g, st) : launch_vjp_fft_f64(P, L, n, g, st);
   if (e != cudaSuccess) return e;

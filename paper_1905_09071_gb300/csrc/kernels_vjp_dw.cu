@@ -2,6 +2,7 @@
 // element type SAG_DW_C (cdw here, cdwx in kernels_vjp_dwx.cu).
 #include "launch.h"
 #include "vjp_kernels.cuh"
+#include "vjp_tt.cuh"
 
 #ifndef SAG_DW_C
 #define SAG_DW_C cdw
@@ -19,11 +20,19 @@ cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const doub
   return cudaGetLastError();
 }
 
+cudaError_t launch_vjp_fft_tt_dw(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                                 cudaStream_t st, SAG_DW_C) {
+  cudaError_t e = launch_k_fwd_col_dw(P, L, n, st, 0, L.col_blocks, 0, SAG_DW_C{});
+  if (e != cudaSuccess) return e;
+  return launch_vjp_tt_after_cols<SAG_DW_C>(P, L, g, st);
+}
+
 cudaError_t setup_vjp_fft_dw(const LaunchCfg& L, SAG_DW_C) {
   (void)L;
   cudaError_t e = allow_max_smem(k_gcol<SAG_DW_C>);
   if (e == cudaSuccess) e = allow_max_smem(k_rows_vjp<SAG_DW_C>);
   if (e == cudaSuccess) e = allow_max_smem(k_inv_col_vjp<SAG_DW_C>);
+  if (e == cudaSuccess) e = setup_vjp_tt<SAG_DW_C>(L);
   return e;
 }
 

@@ -1,6 +1,7 @@
 // FFT kernels of the vector-Jacobian product, FP64 path.
 #include "launch.h"
 #include "vjp_kernels.cuh"
+#include "vjp_tt.cuh"
 
 namespace sag {
 
@@ -16,11 +17,18 @@ cudaError_t launch_vjp_fft_f64(const RhsParams& P, const LaunchCfg& L, const dou
   return cudaGetLastError();
 }
 
+cudaError_t launch_vjp_fft_tt_f64(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
+                                  cudaStream_t st) {
+  k_fwd_col<cd><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, n, 0, 0);
+  return launch_vjp_tt_after_cols<cd>(P, L, g, st);
+}
+
 cudaError_t setup_vjp_fft_f64(const LaunchCfg& L) {
   (void)L;
   cudaError_t e = allow_max_smem(k_gcol<cd>);
   if (e == cudaSuccess) e = allow_max_smem(k_rows_vjp<cd>);
   if (e == cudaSuccess) e = allow_max_smem(k_inv_col_vjp<cd>);
+  if (e == cudaSuccess) e = setup_vjp_tt<cd>(L);
   return e;
 }
 

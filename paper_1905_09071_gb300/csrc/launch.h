@@ -24,6 +24,7 @@ struct LaunchCfg {
   int col_blocks, row_blocks, inv_blocks, epi_blocks;
   int col_blocks_all;  // column blocks over every vector (the adjoint's passes)
   int chain_blocks;
+  int ent_blocks;       // TT adjoint: inverse column blocks over every core entry
   int has_tt;           // the plan's systems use TT kernels (one format per plan)
   size_t col_smem, row_smem, inv_smem, epi_smem, coef_smem, rowtt_smem;
   size_t col_smem_kind[kKindCount], row_smem_kind[kKindCount];  // per kernel specialisation
@@ -198,6 +199,8 @@ cudaError_t setup_fft_kernels_dw(const LaunchCfg& L);
   cudaError_t launch_tt_dw(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, LaunchHook* hook, C);  \
   cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,  \
                                 cudaStream_t st, C);                                                     \
+  cudaError_t launch_vjp_fft_tt_dw(const RhsParams& P, const LaunchCfg& L, const double* n,               \
+                                   const double* g, cudaStream_t st, C);                                \
   cudaError_t setup_k_fwd_col_dw(const LaunchCfg& L, C);                                                 \
   cudaError_t setup_k_rows_dw(const LaunchCfg& L, C);                                                    \
   cudaError_t setup_k_inv_col_dw(const LaunchCfg& L, C);                                                 \

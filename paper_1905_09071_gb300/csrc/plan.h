@@ -67,6 +67,8 @@ struct OrderDesc {
   const void* twg2;    // pass tables of the M2-point inverse rows, global layout
   const void* twg1;    // compile-time columns: pass tables of M1, global layout
   const void* tw4c_p;  // omega_L^(j2 k1) for j2 < 2 M2 in column-block order
+  int ebase, nent;     // TT: first global core entry, entries (sum_l R_{l-1} R_l)
+  int64_t ent_spec_off;// TT: offset (elements) of its entries' cotangent spectra
   int nfold;           // double-word path: partial inner products per transformed vector
                        // (its column blocks: ncolblk_p in the pair form, else ncolblk)
   int pw;              // 1: the double-word forward columns generate U^(m)_r(i) = u i^a
@@ -173,6 +175,13 @@ struct RhsParams {
   double* dot_z;                 // [Vtot][maxdotchunk] partial <U, g o n>
   double* sigma;                 // [Vtot] dL/ds_v through the loss weights
   const int* vexcl;              // [Vtot] sum of the other modes' exponents e_v of the rank term
+  // vector-Jacobian product workspace (TT): one cotangent per core entry
+  void* ent_spec;                // entries' cotangent spectra, per item at ent_spec_off
+  void* ent_nyq;                 // [entries] their Nyquist values
+  double* gaent;                 // cotangent of h o n per entry, at eoff
+  const int64_t* eoff;           // [entries] offset of an entry's sizes in the core layout
+  const int* eexcl;              // [entries] sum of the other cores' exponents E_l of the order
+  const int* entpre;             // [nitems + 1] inverse column blocks over the entries
   SysScalars* sc;                // [B]
   unsigned int* status;          // latched device status bits of the plan
 };

@@ -381,6 +381,9 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   size_t col_smem = 0, row_smem = 0, rowtt_smem = 0;
   std::vector<size_t> item_col_smem, item_row_smem;  // per item: what its column / row blocks need
   std::vector<int> colpre(1, 0), colpre_all(1, 0), invpre(1, 0), chainpre(1, 0);
+  std::vector<int> entpre(1, 0);  // TT adjoint: inverse column blocks over the core entries
+  int nent_tot = 0;
+  int64_t entspec = 0;
   for (OrderDesc& od : I) {
     const int d = od.d;
     const int64_t L = choose_fft_length(std::max<int64_t>((int64_t)d * od.N, 16), !dwp);
@@ -451,6 +454,14 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     colpre_all.push_back(colpre_all.back() + od.nvec * od.ncolblk);
     invpre.push_back(invpre.back() + od.ncolblk);
     chainpre.push_back(chainpre.back() + (tt ? (od.M + 1 + 255) / 256 : 0));
+    od.nent = 0;
+    if (tt)
+      for (int l = 1; l <= d; ++l) od.nent += od.ttr[l - 1] * od.ttr[l];
+    od.ebase = nent_tot;
+    nent_tot += od.nent;
+    od.ent_spec_off = entspec;
+    entspec += (int64_t)od.nent * od.M;
+    entpre.push_back(entpre.back() + od.nent * od.ncolblk);
     // Compile-time kernels work in place (one buffer, pass tables in global
     // memory), the generic ones ping-pong and keep the natural table.
     item_col_smem.push_back(od.ct1 ? (size_t)(W * od.ld1) * csize : (size_t)(2 * W * od.ld1 + od.M1) * csize);
@@ -505,6 +516,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   L.row_blocks = rowpre.back();
   L.inv_blocks = invpre.back();
   L.chain_blocks = chainpre.back();
+  L.ent_blocks = entpre.back();
   L.epi_blocks = epipre.back();
   L.has_tt = tt ? 1 : 0;
   L.col_smem = col_smem;
@@ -606,6 +618,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     P.ndw = ndw;
   }
   std::vector<float> vweight(Vtot, 1.0f);
+  std::vector<int> eexcl((size_t)std::max(nent_tot, 1), 0);  // TT: the other cores' exponents per entry
   TwiddleCache<cdw> tcw;
   TwiddleCache<cd> tcd;
   for (OrderDesc& od : I) {
@@ -623,6 +636,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       od.rscale = drs;
     } else if (dwp) {
       int off = od.vid_off;
+      std::vector<int> Els(d + 1, 0);
       for (int l = 1; l <= d; ++l) {
         const int cnt = od.ttr[l - 1] * od.ttr[l];
         int El = INT32_MIN;
@@ -631,9 +645,13 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
         if (El == INT32_MIN) El = 0;
         for (int j = 0; j < cnt; ++j)
           if (vid[off + j] >= 0) vweight[vid[off + j]] = std::ldexp(1.0f, ev[vid[off + j]] - El);
+        Els[l] = El;
         Esum += El;
         off += cnt;
       }
+      int eo = od.ebase;
+      for (int l = 1; l <= d; ++l)
+        for (int j = 0; j < od.ttr[l - 1] * od.ttr[l]; ++j) eexcl[eo++] = Esum - Els[l];
     }
     e = dwp ? item_tables<cdw>(pl, tcw, od) : item_tables<cd>(pl, tcd, od);
     if (e != cudaSuccess) return cuda_fail(e, "twiddle tables");
@@ -720,7 +738,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       pl->alloc(&P.pd, (size_t)pdo) != cudaSuccess ||
       pl->alloc(&P.dot_s, (size_t)Vtot * P.maxdotchunk) != cudaSuccess ||
       pl->alloc(&P.dot_t, (size_t)Vtot * P.maxdotchunk) != cudaSuccess ||
-      pl->alloc(&P.coef, (size_t)Vtot) != cudaSuccess ||
+      pl->alloc(&P.coef, (size_t)std::max(Vtot, nent_tot)) != cudaSuccess ||
       pl->alloc(&pl->epi_part, (size_t)L.epi_blocks * 4) != cudaSuccess ||
       pl->alloc(&P.sc, (size_t)B) != cudaSuccess || pl->alloc(&P.status, 1) != cudaSuccess ||
       pl->alloc(&pl->nstar, Nt) != cudaSuccess || pl->alloc(&pl->k1buf, Nt) != cudaSuccess ||
@@ -743,6 +761,31 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
         (dwp && pl->alloc(&P.gdw, Nt) != cudaSuccess))
       return fail(SAG_ENOMEM, "cudaMalloc adjoint workspace");
     P.vexcl = d_vexcl;
+  } else {
+    // TT adjoint: one cotangent per core entry, in the caller's core layout
+    // (eoff), so entries without a stored vector get theirs too.
+    std::vector<int64_t> eoff((size_t)std::max(nent_tot, 1), 0);
+    int64_t cur = 0;
+    for (const OrderDesc& od : I)
+      for (int q = 0; q < od.nent; ++q) {
+        eoff[od.ebase + q] = cur;
+        cur += od.N;
+      }
+    pl->nfactor = cur;
+    int *d_eexcl = nullptr, *d_entpre = nullptr;
+    int64_t* d_eoff = nullptr;
+    if (pl->upload(&d_eexcl, eexcl) != cudaSuccess || pl->upload(&d_entpre, entpre) != cudaSuccess ||
+        pl->upload(&d_eoff, eoff) != cudaSuccess ||
+        pl->alloc((unsigned char**)&P.ent_spec, (size_t)std::max<int64_t>(entspec, 1) * csize) != cudaSuccess ||
+        pl->alloc((unsigned char**)&P.ent_nyq, (size_t)std::max(nent_tot, 1) * csize) != cudaSuccess ||
+        pl->alloc(&P.gaent, (size_t)std::max<int64_t>(cur, 1)) != cudaSuccess ||
+        pl->alloc(&P.dot_z, (size_t)Vtot * P.maxdotchunk) != cudaSuccess ||
+        pl->alloc(&P.sigma, (size_t)std::max(nent_tot, 1)) != cudaSuccess ||
+        (dwp && pl->alloc(&P.gdw, Nt) != cudaSuccess))
+      return fail(SAG_ENOMEM, "cudaMalloc adjoint workspace");
+    P.eexcl = d_eexcl;
+    P.entpre = d_entpre;
+    P.eoff = d_eoff;
   }
   if ((e = cudaMemset(P.sc, 0, sizeof(SysScalars) * B)) != cudaSuccess ||
       (e = cudaMemset(P.status, 0, sizeof(unsigned))) != cudaSuccess)

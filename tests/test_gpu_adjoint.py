@@ -174,3 +174,68 @@ def test_gpu_adjoint_matches_oracle_adjoint_on_fit_problem_prefix():
         torch.cuda.synchronize()
     assert rel(gn.cpu().numpy(), gn_ref) < 1e-10
     assert rel(gU.cpu().numpy(), gU_ref) < 1e-10
+
+
+# ---------------------------------------------------------------- TT adjoint
+TT_CASES = [
+    ("random_D3_N100", lambda: wl.random_tt(3, 100, {2: [1, 2, 1], 3: [1, 2, 3, 1]}, seed=101)),
+    ("random_D4_N333", lambda: wl.random_tt(4, 333, {2: [1, 3, 1], 3: [1, 2, 2, 1], 4: [1, 2, 3, 2, 1]},
+                                            seed=102)),
+    ("theorem1_D3_N300", lambda: wl.brownian_tt(3, 300, [0.4, -0.2, 0.1])),   # zero core entries
+    ("paper_ternary_N300", lambda: wl.paper_ternary(300, "tt")),             # an all-zero order
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("sym", [1, 0])
+@pytest.mark.parametrize("name,make", TT_CASES)
+def test_tt_rhs_vjp_matches_oracle(name, make, sym, prec):
+    # Cotangents of n and of every TT core entry (the caller's core layout,
+    # also entries whose vector is zero) against the oracle's chain rule.
+    t = make()
+    g = np.random.default_rng(103).normal(size=t.N)
+    gn_ref, gH_ref = oracle.rhs_vjp(t.n0, g, t.D, t.ranks, t.factors, sym=sym, fmt=oracle.TT)
+    with sag.Plan(t.N, t.D, t.ranks, t.factors, fmt=sag.SAG_TT, prec=prec, symmetrize_q=sym) as pl:
+        assert pl.factor_count() == t.factors.size
+        gn = torch.empty(t.N, dtype=torch.float64, device="cuda")
+        gH = torch.empty(t.factors.size, dtype=torch.float64, device="cuda")
+        pl.rhs_vjp(dev(t.n0), dev(g), gn, gH)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+    assert rel(gn.cpu().numpy(), gn_ref) < TOL[prec]
+    assert rel(gH.cpu().numpy(), gH_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("rk", [sag.SAG_HEUN, sag.SAG_MIDPOINT])
+def test_tt_integrate_vjp_matches_oracle_adjoint(prec, rk):
+    t = wl.random_tt(3, 256, {2: [1, 2, 1], 3: [1, 3, 2, 1]}, seed=104)
+    steps, dt, ckpt = 9, 0.05, 4  # segments of 4, 4, 1 steps
+    g = np.random.default_rng(105).normal(size=t.N)
+    method = oracle.HEUN if rk == sag.SAG_HEUN else oracle.MIDPOINT
+    gn_ref, gH_ref = oracle.integrate_vjp(t.n0, t.D, t.ranks, t.factors, dt, steps, g, method=method,
+                                          fmt=oracle.TT)
+    with sag.Plan(t.N, t.D, t.ranks, t.factors, fmt=sag.SAG_TT, prec=prec, rk=rk) as pl:
+        gn = torch.empty(t.N, dtype=torch.float64, device="cuda")
+        gH = torch.empty(t.factors.size, dtype=torch.float64, device="cuda")
+        pl.integrate_vjp(dev(t.n0), dt, steps, dev(g), gn, gH, ckpt=ckpt)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+    assert rel(gn.cpu().numpy(), gn_ref) < 10 * TOL[prec]
+    assert rel(gH.cpu().numpy(), gH_ref) < 10 * TOL[prec]
+
+
+def test_tt_vjp_of_diagonal_embedding_equals_cp_vjp():
+    # The library's TT adjoint of the diagonal embedding of a CP kernel gives
+    # the CP adjoint's n-cotangent (FP64).
+    s = wl.random_cp(4, 500, [3, 2, 2], seed=106)
+    t = wl.cp_to_tt_diagonal(s)
+    g = dev(np.random.default_rng(107).normal(size=s.N))
+    outs = []
+    for sysm, fmt in ((s, sag.SAG_CP), (t, sag.SAG_TT)):
+        with sag.Plan(sysm.N, sysm.D, sysm.ranks, sysm.factors, fmt=fmt, prec=sag.SAG_FP64) as pl:
+            gn = torch.empty(s.N, dtype=torch.float64, device="cuda")
+            pl.rhs_vjp(dev(sysm.n0), g, gn, None)
+            torch.cuda.synchronize()
+            outs.append(gn.cpu().numpy())
+    assert rel(outs[1], outs[0]) < 1e-12
