@@ -125,36 +125,6 @@ __device__ __forceinline__ void col_store_ct(const C* res, int ld, const C* __re
   }
 }
 
-// ---- the loss term's inner products from the forward columns' loads ------
-// Block-wide sums of per-thread double-word values (warp shuffles in
-// double-word, then the warps' values in FP64), written by thread 0 to
-// dst0 (and dst1 for two values; a null destination is skipped). Every thread
-// of the block calls it.
-template <int NV>
-__device__ __forceinline__ void fold_store(dw (&f)[NV], double* dst0, double* dst1) {
-  __shared__ double red[kThreads / 32][NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i)
-    for (int o = 16; o; o >>= 1) {
-      const dw t{__shfl_xor_sync(0xffffffffu, f[i].hi, o), __shfl_xor_sync(0xffffffffu, f[i].lo, o)};
-      f[i] = dw_add(f[i], t);
-    }
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) red[threadIdx.x >> 5][i] = (double)f[i].hi + (double)f[i].lo;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      a[i] = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) a[i] += red[w][i];
-    }
-    if (dst0) *dst0 = a[0];
-    if (NV > 1 && dst1) *dst1 = a[NV - 1];
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Forward column pass of one block: the order's vector lv (local index) into
 // spectrum slot `slot`, column block cb. P1 > 0: compile-time length, in
@@ -178,7 +148,6 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
   const int N = od.N;
   float4 up{};
   if constexpr (GEN) up = __ldg(P.vpow + v);
-  dw fs[1] = {dw{0.f, 0.f}};  // double-word path: sum of the loaded U n (the loss term's <U, n>)
   for (int e = threadIdx.x; e < W * M1; e += kThreads) {
     const int c = e % W, j1 = e / W;
     const int j = M2 * j1 + cb * W + c;
@@ -188,11 +157,9 @@ __device__ __forceinline__ void fwd_col_body(const RhsParams& P, const OrderDesc
     } else {
       x = load_a_pair(u, nn, N, 2 * j, C{});
     }
-    if constexpr (is_dw<C>::value) fs[0] = dw_add(fs[0], dw_add(re_of(x), im_of(x)));
     buf[c * ld + (CT ? pad8(j1) : j1)] = x;
   }
   __syncthreads();
-  if constexpr (is_dw<C>::value) fold_store<1>(fs, P.dot_f + (int64_t)v * P.maxfold + cb, nullptr);
   C* res;
   if constexpr (CT) {
     // pass tables from global memory (no per-block fill)
@@ -233,9 +200,6 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
   const float2* nn = P.ndw + od.ndwoff;  // indexed by size, zero at 0
   // Pass 0 straight from the factors and n: point j1 of column c is size
   // j = 2 M2 j1 + cb W + c, z = (u1 n, u2 n) there (zero beyond N).
-  // fs: this thread's sums of the loaded U n of each vector (the loss term's
-  // inner products <U, n>, scaled), reduced over the block after the pass.
-  dw fs[2] = {dw{0.f, 0.f}, dw{0.f, 0.f}};
   if constexpr (GEN) {  // parametric factors: u i^a generated, ln j from the table
     const int v1 = od.vbase + (q1 % d) * R + q1 / d;
     const int v2 = q2 < od.nvec ? od.vbase + (q2 % d) * R + q2 / d : -1;
@@ -248,13 +212,8 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
           const float2 nb = __ldg(nn + j), lj = __ldg(P.lnt + j);
           const dw nv{nb.x, nb.y}, l{lj.x, lj.y};
           dw im{0.f, 0.f};
-          if (v2 >= 0) {
-            im = dw_mul(dw_power(dw{up2.x, up2.y}, dw{up2.z, up2.w}, l, P.expk), nv);
-            fs[1] = dw_add(fs[1], im);
-          }
-          const dw re = dw_mul(dw_power(dw{up1.x, up1.y}, dw{up1.z, up1.w}, l, P.expk), nv);
-          fs[0] = dw_add(fs[0], re);
-          return make_cdw(re, im);
+          if (v2 >= 0) im = dw_mul(dw_power(dw{up2.x, up2.y}, dw{up2.z, up2.w}, l, P.expk), nv);
+          return make_cdw(dw_mul(dw_power(dw{up1.x, up1.y}, dw{up1.z, up1.w}, l, P.expk), nv), im);
         },
         buf, ld);
   } else {
@@ -270,19 +229,10 @@ __device__ __forceinline__ void fwd_col_pair_body(const RhsParams& P, const Orde
           if (u2) {
             const float2 a2 = __ldg(u2 + j);
             im = dw_mul(dw{a2.x, a2.y}, nv);
-            fs[1] = dw_add(fs[1], im);
           }
-          const dw re = dw_mul(dw{a1.x, a1.y}, nv);
-          fs[0] = dw_add(fs[0], re);
-          return make_cdw(re, im);
+          return make_cdw(dw_mul(dw{a1.x, a1.y}, nv), im);
         },
         buf, ld);
-  }
-  {
-    double* base = P.dot_f + (int64_t)cb * 1;
-    const int v1 = od.vbase + (q1 % d) * R + q1 / d;
-    const int v2 = q2 < od.nvec ? od.vbase + (q2 % d) * R + q2 / d : -1;
-    fold_store<2>(fs, base + (int64_t)v1 * P.maxfold, v2 >= 0 ? base + (int64_t)v2 * P.maxfold : nullptr);
   }
   ct_passes<C, P1, W, kThreads, 1, sc.r[0], true, sc.n - 1>(buf, ld, tw);  // middle passes, in place
   // The last pass hands each output k1 of column c, times its four-step

@@ -115,11 +115,7 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ RhsParams P
 // gflux = sum_d 1/d! sum_{i in [1,N]^d} |i| C_i prod n: the same products with
 // one s replaced by the first moment t (only with flux = 1; else t = 0 and
 // gflux = 0, and the outflow derived from it is not meaningful).
-// fold = 1 (double-word path, no outflow): s comes from the forward column
-// kernels' partial sums of the scaled U n (dot_f, per column block of the
-// transformed vector; a duplicate vector takes its transformed twin's), times
-// 2^(e_v + e_n); else from k_dot's FP64 partials.
-__global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams P, int flux, int fold) {
+__global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams P, int flux) {
   extern __shared__ double csh[];  // [vectors of the system] s, then t
   __shared__ double red[32];
   const int b = blockIdx.x;
@@ -128,24 +124,11 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
   double* s = csh;
   double* t = csh + nv;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const int64_t base = (int64_t)(sy.vbeg + i) * P.maxdotchunk;
     double a = 0.0, c2 = 0.0;
-    if (fold) {
-      const int v = sy.vbeg + i;
-      int it = sy.ibeg;
-      while (it + 1 < sy.iend && v >= P.ord[it + 1].vbase) ++it;
-      const OrderDesc& od = P.ord[it];
-      int lv = v - od.vbase;
-      if (od.umap_off >= 0) lv = P.ulist[od.umap_off + P.umap[od.umap_off + lv]];
-      const int vs = od.vbase + lv;
-      const double* f = P.dot_f + (int64_t)vs * P.maxfold;
-      for (int c = 0; c < od.nfold; ++c) a += f[c];
-      a = ldexp(a, P.vexp[vs] + P.sc[b].e_n);
-    } else {
-      const int64_t base = (int64_t)(sy.vbeg + i) * P.maxdotchunk;
-      for (int c = 0; c < nc; ++c) {
-        a += P.dot_s[base + c];
-        if (flux) c2 += P.dot_t[base + c];
-      }
+    for (int c = 0; c < nc; ++c) {
+      a += P.dot_s[base + c];
+      if (flux) c2 += P.dot_t[base + c];
     }
     s[i] = a;
     t[i] = c2;
@@ -402,68 +385,35 @@ cudaError_t enqueue_eval(const RhsParams& P, const LaunchCfg& L, const double* n
   }
   // The inner products and loss weights (FP64 pipe) overlap the FFT kernels
   // (FP32 pipe) on the side stream; per-kernel timing runs everything in order.
-  // In the double-word path without the outflow the forward column kernels
-  // also form the inner products (fold): the side branch then starts after
-  // them, with the loss weights and the loss term, beside the row kernels.
-  const bool fold = P.dwpath && !A.flux;
   const bool fork = side != nullptr && hook == nullptr;
   cudaStream_t ds = fork ? side->stream : st;
-  const bool grouped = fork && groups && groups->n > 1;
   cudaError_t e;
-  auto fft = [&](cudaStream_t s, LaunchHook* h, const FftRange* r, int phase) {
-    return P.dwpath ? enqueue_fft_dw(P, L, nin, s, h, r, phase) : enqueue_fft_f64(P, L, nin, s, h, r);
-  };
-  auto side_branch = [&]() -> cudaError_t {
-    if (!fold) {
-      if (hook) hook->mark(KID_DOT, st);
-      k_dot<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, ds>>>(P, nin, A.flux);
-    }
-    if (hook) hook->mark(KID_COEF, st);
-    k_coef<<<P.B, 256, L.coef_smem, ds>>>(P, A.flux, fold ? 1 : 0);
-    if (hook) hook->mark(KID_QTERM, st);
-    k_qterm<<<L.epi_blocks, 256, L.epi_smem, ds>>>(P, nin);
-    return cudaGetLastError();
-  };
   if (fork) {
     if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess) return e;
-    if (!fold && (e = cudaStreamWaitEvent(ds, side->fork, 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ds, side->fork, 0)) != cudaSuccess) return e;
   }
-  if (!fold) {
-    if ((e = side_branch()) != cudaSuccess) return e;
-    if (fork && (e = cudaEventRecord(side->join, ds)) != cudaSuccess) return e;
-  }
-  if (grouped) {
+  if (hook) hook->mark(KID_DOT, st);
+  k_dot<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, ds>>>(P, nin, A.flux);
+  if (hook) hook->mark(KID_COEF, st);
+  k_coef<<<P.B, 256, L.coef_smem, ds>>>(P, A.flux);
+  if (hook) hook->mark(KID_QTERM, st);
+  k_qterm<<<L.epi_blocks, 256, L.epi_smem, ds>>>(P, nin);
+  if (fork && (e = cudaEventRecord(side->join, ds)) != cudaSuccess) return e;
+  if (fork && groups && groups->n > 1) {
     // one FFT chain per group, each on its own stream after the split of n
     for (int g = 0; g < groups->n; ++g) {
       cudaStream_t gs = groups->s[g].stream;
       if ((e = cudaStreamWaitEvent(gs, side->fork, 0)) != cudaSuccess) return e;
-      if (fold) {  // forward columns, then the event the side branch waits for
-        if ((e = fft(gs, nullptr, &groups->r[g], 1)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(groups->s[g].coldone, gs)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(ds, groups->s[g].coldone, 0)) != cudaSuccess) return e;
-        if ((e = fft(gs, nullptr, &groups->r[g], 2)) != cudaSuccess) return e;
-      } else if ((e = fft(gs, nullptr, &groups->r[g], 0)) != cudaSuccess) {
-        return e;
-      }
+      e = P.dwpath ? enqueue_fft_dw(P, L, nin, gs, nullptr, &groups->r[g])
+                   : enqueue_fft_f64(P, L, nin, gs, nullptr, &groups->r[g]);
+      if (e != cudaSuccess) return e;
       if ((e = cudaEventRecord(groups->s[g].join, gs)) != cudaSuccess) return e;
-    }
-    if (fold) {
-      if ((e = side_branch()) != cudaSuccess) return e;
-      if ((e = cudaEventRecord(side->join, ds)) != cudaSuccess) return e;
     }
     for (int g = 0; g < groups->n; ++g)
       if ((e = cudaStreamWaitEvent(st, groups->s[g].join, 0)) != cudaSuccess) return e;
-  } else if (fold) {
-    if ((e = fft(st, hook, nullptr, 1)) != cudaSuccess) return e;
-    if (fork) {
-      if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess) return e;
-      if ((e = cudaStreamWaitEvent(ds, side->fork, 0)) != cudaSuccess) return e;
-    }
-    if ((e = side_branch()) != cudaSuccess) return e;
-    if (fork && (e = cudaEventRecord(side->join, ds)) != cudaSuccess) return e;
-    if ((e = fft(st, hook, nullptr, 2)) != cudaSuccess) return e;
   } else {
-    if ((e = fft(st, hook, nullptr, 0)) != cudaSuccess) return e;
+    e = P.dwpath ? enqueue_fft_dw(P, L, nin, st, hook) : enqueue_fft_f64(P, L, nin, st, hook);
+    if (e != cudaSuccess) return e;
   }
   if (fork && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return e;
   if (hook) hook->mark(KID_EPILOGUE, st);

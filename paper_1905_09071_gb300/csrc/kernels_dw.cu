@@ -10,15 +10,12 @@ namespace {
 
 template <class C>
 cudaError_t enqueue_fft_dwc(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                            LaunchHook* hook, const FftRange* r, int phase) {
+                            LaunchHook* hook, const FftRange* r) {
   const FftRange all{0, L.col_blocks, 0, L.row_blocks, 0, L.inv_blocks};
   const FftRange& R = r ? *r : all;
-  cudaError_t e = cudaSuccess;
-  if (phase != 2) {
-    if (hook) hook->mark(KID_FWD_COL, st);
-    e = launch_k_fwd_col_dw(P, L, nin, st, R.col0, R.col1 - R.col0, 0, C{});
-    if (e != cudaSuccess || phase == 1) return e;
-  }
+  if (hook) hook->mark(KID_FWD_COL, st);
+  cudaError_t e = launch_k_fwd_col_dw(P, L, nin, st, R.col0, R.col1 - R.col0, 0, C{});
+  if (e != cudaSuccess) return e;
   if (L.has_tt) {
     if ((e = launch_tt_dw(P, L, st, hook, C{})) != cudaSuccess) return e;  // every item (no groups with TT)
   } else {
@@ -42,9 +39,8 @@ cudaError_t setup_fft_dwc(const LaunchCfg& L) {
 }  // namespace
 
 cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                           LaunchHook* hook, const FftRange* r, int phase) {
-  return P.exact ? enqueue_fft_dwc<cdwx>(P, L, nin, st, hook, r, phase)
-                 : enqueue_fft_dwc<cdw>(P, L, nin, st, hook, r, phase);
+                           LaunchHook* hook, const FftRange* r) {
+  return P.exact ? enqueue_fft_dwc<cdwx>(P, L, nin, st, hook, r) : enqueue_fft_dwc<cdw>(P, L, nin, st, hook, r);
 }
 
 cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,

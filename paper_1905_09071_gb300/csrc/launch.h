@@ -118,7 +118,6 @@ struct LaunchHook {
 struct SideStream {
   cudaStream_t stream;
   cudaEvent_t fork, join;
-  cudaEvent_t coldone = nullptr;  // FFT groups: after the group's forward columns
 };
 
 // Block ranges [begin, end) of the three FFT kernels' tables (colpre, rowpre in
@@ -163,9 +162,8 @@ cudaError_t enqueue_moments(const RhsParams& P, const double* n, double* diag, c
 // FFT stage over the block range r (nullptr: every item).
 cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
                             LaunchHook* hook, const FftRange* r = nullptr);
-// phase 0: the whole FFT stage; 1: the forward columns only; 2: the rest.
 cudaError_t enqueue_fft_dw(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
-                           LaunchHook* hook, const FftRange* r = nullptr, int phase = 0);
+                           LaunchHook* hook, const FftRange* r = nullptr);
 cudaError_t setup_common_kernels(const LaunchCfg& L);
 // n -> double-word with its per-system power-of-two scale (resets nothing).
 cudaError_t enqueue_nsplit(const RhsParams& P, const LaunchCfg& L, const double* n, cudaStream_t st);

@@ -69,8 +69,6 @@ struct OrderDesc {
   const void* tw4c_p;  // omega_L^(j2 k1) for j2 < 2 M2 in column-block order
   int ebase, nent;     // TT: first global core entry, entries (sum_l R_{l-1} R_l)
   int64_t ent_spec_off;// TT: offset (elements) of its entries' cotangent spectra
-  int nfold;           // double-word path: partial inner products per transformed vector
-                       // (its column blocks: ncolblk_p in the pair form, else ncolblk)
   int pw;              // 1: the double-word forward columns generate U^(m)_r(i) = u i^a
                        // (RhsParams::vpow, lnt, expk) instead of reading RhsParams::Udw
   const float* rscale; // CP, double-word path: [R] power-of-two weight of rank term r
@@ -158,13 +156,6 @@ struct RhsParams {
   const float* vweight;          // TT, double-word path: [Vtot] power-of-two weight 2^(e_v - E_lambda)
   double* pd;                    // gain per item: P^(d) of system b at pd_off
   double* dot_s;                 // [Vtot][maxdotchunk] partial <U, n>
-  // Double-word path: the forward column kernels also sum U_dw n_dw (scaled
-  // copies) per column block, [Vtot][maxfold] by transformed vector; k_coef
-  // forms s_v from them (times 2^(e_v + e_n)) unless the outflow is wanted,
-  // when k_dot forms s and the first moments t in FP64.
-  double* dot_f;
-  int maxfold;
-  const int* vexp;               // [Vtot] e_v of the double-word factor copy
   double* dot_t;                 // [Vtot][maxdotchunk] partial <k U, n>
   double* coef;                  // [Vtot] loss weights: q_k = n_k sum_v coef_v U_v(k)
   double* epi_part;              // [epilogue blocks][4] block partials

@@ -443,7 +443,6 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       od.ncolblk_p = 2 * M2 / W;
       od.ld2p = ct_ld(2 * od.M2, 2 * ct_group(2 * od.M2));
     }
-    od.nfold = od.pair ? od.ncolblk_p : od.ncolblk;
     od.scr_off = scr;
     scr += (int64_t)std::max(od.nvec, 2 * od.npair) * od.M;
     od.scr2_off = scr2;
@@ -504,8 +503,6 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     maxchunk = std::max(maxchunk, sd.ndotchunk);
   }
   P.maxdotchunk = maxchunk;
-  P.maxfold = 1;
-  for (const OrderDesc& od : I) P.maxfold = std::max(P.maxfold, od.nfold);
 
   LaunchCfg& L = pl->L;
   int maxN = 1;
@@ -744,15 +741,9 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       pl->alloc(&pl->nstar, Nt) != cudaSuccess || pl->alloc(&pl->k1buf, Nt) != cudaSuccess ||
       pl->alloc(&pl->stage_a, Nt) != cudaSuccess || pl->alloc(&pl->stage_b, Nt) != cudaSuccess ||
       pl->alloc(&pl->stage_c, Nt) != cudaSuccess || pl->alloc(&pl->dev_outflow, (size_t)B) != cudaSuccess ||
-      pl->alloc(&P.qbuf, Nt) != cudaSuccess ||
-      (dwp && pl->alloc(&P.dot_f, (size_t)Vtot * P.maxfold) != cudaSuccess))
+      pl->alloc(&P.qbuf, Nt) != cudaSuccess)
     return fail(SAG_ENOMEM, "cudaMalloc workspace");
   P.epi_part = pl->epi_part;
-  if (dwp) {
-    int* d_vexp = nullptr;
-    if (pl->upload(&d_vexp, ev) != cudaSuccess) return fail(SAG_ENOMEM, "cudaMalloc exponents");
-    P.vexp = d_vexp;
-  }
   if (!tt) {
     int* d_vexcl = nullptr;
     if (pl->upload(&d_vexcl, vexcl) != cudaSuccess || pl->alloc(&P.gabuf, hf.size()) != cudaSuccess ||
@@ -926,8 +917,7 @@ sag_status configure_fft_groups(sag_plan_s* pl, int G) {
     if (!s.stream) {
       const int prio = std::min(least, greatest + c);
       if ((e = cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio)) != cudaSuccess ||
-          (e = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming)) != cudaSuccess ||
-          (e = cudaEventCreateWithFlags(&s.coldone, cudaEventDisableTiming)) != cudaSuccess)
+          (e = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "stream");
       s.fork = nullptr;
     }
@@ -1179,8 +1169,7 @@ sag_status update_factors(sag_plan_s* pl, const double* factors, int on_device) 
         }
       }
     if ((e = cudaMemcpy((void*)P.Udw, hdw.data(), hdw.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
-        cudaSuccess ||
-        (e = cudaMemcpy((void*)P.vexp, ev.data(), sizeof(int) * Vtot, cudaMemcpyHostToDevice)) != cudaSuccess)
+        cudaSuccess)
       return cuda_fail(e, "upload dw factors");
   }
   std::vector<int> vexcl(Vtot, 0);

@@ -113,7 +113,6 @@ struct sag_plan_s {
     for (int g = 0; g < sag::kMaxFftGroups; ++g) {
       if (groups.s[g].stream) cudaStreamDestroy(groups.s[g].stream);
       if (groups.s[g].join) cudaEventDestroy(groups.s[g].join);
-      if (groups.s[g].coldone) cudaEventDestroy(groups.s[g].coldone);
     }
     for (void* q : allocs) cudaFree(q);
     if (stage_diag) cudaFree(stage_diag);

@@ -298,11 +298,10 @@ def test_host_buffers_equal_device_buffers():
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_launches_per_step(prec):
-    # One RK2 step's graph: per stage the side branch (k_dot, k_coef, k_qterm;
-    # the double-word path forms the inner products in its forward columns,
-    # so it has no k_dot) and the epilogue; per FFT group one forward-column,
-    # one row and one inverse-column launch (here each group holds one order
-    # of one kernel kind); the double-word first stage adds k_nmax and k_nsplit.
+    # One RK2 step's graph: per stage the side branch (k_dot, k_coef, k_qterm)
+    # and the epilogue; per FFT group one forward-column, one row and one
+    # inverse-column launch (here each group holds one order of one kernel
+    # kind); the double-word first stage adds k_nmax and k_nsplit.
     s = wl.random_cp(3, 500, [2, 2], seed=17)
     with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec) as pl:
         desc = pl.describe()
@@ -310,7 +309,7 @@ def test_launches_per_step(prec):
         if prec == sag.SAG_FP64:
             assert G == 1 and desc["launches_per_step"] == 14
         else:
-            assert G == 2 and desc["launches_per_step"] == 2 * (3 + 3 * G) + 2
+            assert G == 2 and desc["launches_per_step"] == 2 * (4 + 3 * G) + 2
 
 
 def test_rhs_in_place_alias():
