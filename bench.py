@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--parametric", action="store_true",
                     help="with --kernels: the same kernel as (u, a) pairs (SAG_CP_POWER), its factors "
                          "generated in the forward columns")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 256-system batch's extra key in the default run")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plans with the fixed launch rules instead of the plan-time autotuner")
     ap.add_argument("--m2", default=None,
@@ -586,6 +588,10 @@ def run_ours(args, world, rank, local):
                          "the loss-term kernels still read the FP64 factors)"}
         pp.close()
 
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = batched_measure(K=max(3, min(K, 10)), W=2, tune=tune)
+
     # end-to-end: the public call with host buffers (pinned), copies inside
     pl = sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT, autotune=tune)
     host_n = torch.tensor(s.n0).pin_memory().numpy()
@@ -613,6 +619,9 @@ def run_ours(args, world, rank, local):
     kernels_per_step = sum(v[1] for v in dw["prof"].values()) / K
     n_bytes = 8 * s.N
     cpu_fft = cpu_fft_baseline(s) if not args.no_cpu_baseline and world == 1 else None
+    if batched:
+        head_vsizes = sum(d * s.ranks[d - 2] for d in range(2, s.D + 1)) * s.N
+        batched["of_single_system_rate"] = batched["vector_sizes_per_s"] / (2 * head_vsizes * K / dw["t"])
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": dw["t"] / K * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -668,8 +677,63 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "cpu_fft_baseline": cpu_fft,
         "parametric_factors": param,
+        "batched": batched,
     }
     print(json.dumps(out), flush=True)
+
+
+def batched_measure(K: int, W: int, tune: int, world: int = 1):
+    """The 256-system batch in one plan against a loop over one plan per
+    system (both as graph-replayed RK2 steps), with the per-point rate and the
+    dominant kernel's share; returns a dict for the bench line."""
+    import torch
+    from paper_1905_09071_gb300 import sag, workloads as wl
+    systems = wl.batched_power_cp()
+    dt = systems[0].dt
+    n0 = np.concatenate([s.n0 for s in systems])
+    pl = sag.Plan.batch([(s.N, s.D, s.ranks, s.factors, sag.SAG_CP) for s in systems],
+                        prec=sag.SAG_FP32_SPLIT, autotune=tune)
+    desc = pl.describe()
+    n = torch.tensor(n0, device="cuda")
+    pl.integrate(n, dt, W)
+    t_b, regions = timed_regions(pl, n, dt, K, world, min_seconds=0.5, min_reps=3, max_reps=20)
+    assert pl.sync_status() == sag.SAG_OK
+    nb = n.cpu().numpy()
+    pl.profile(True)
+    x = torch.tensor(n0, device="cuda")
+    pl.rk2_step(x, dt)
+    prof = pl.profile_read()
+    pl.profile(False)
+    pl.close()
+    plans = [sag.Plan(s.N, s.D, s.ranks, s.factors, prec=sag.SAG_FP32_SPLIT) for s in systems]
+    ns = [torch.tensor(s.n0, device="cuda") for s in systems]
+    for p_, x in zip(plans, ns):
+        p_.integrate(x, dt, W)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for p_, x in zip(plans, ns):
+        p_.integrate(x, dt, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_loop = e0.elapsed_time(e1) / 1e3
+    nl = np.concatenate([x.cpu().numpy() for x in ns])
+    for p_ in plans:
+        p_.close()
+    vsizes = sum(sum(d * s.ranks[d - 2] for d in range(2, s.D + 1)) * s.N for s in systems)
+    total = sum(v[0] for v in prof.values())
+    return {"workload": "batched_power_cp: B=256, N in [1024, 32768] log-uniform, D in {3,4}, CP ranks in "
+                        "[4, 32], a in [-0.5, 0.5], Heun dt=1e-4, FP32-split",
+            "value": K / t_b, "unit": UNIT, "ms_per_step": t_b / K * 1e3, "steps": K,
+            "loop_over_systems": {"value": K / t_loop, "ms_per_step": t_loop / K * 1e3},
+            "speedup_vs_loop": t_loop / t_b,
+            "vector_sizes_per_s": 2 * vsizes * K / t_b,
+            "launches_per_step": desc.get("launches_per_step"),
+            "kernel_share": {k: v[0] / total for k, v in prof.items()},
+            "max_abs_diff_batched_vs_loop": float(np.max(np.abs(nb - nl))),
+            "parity": "per system against the oracle: tests/test_gpu_configs.py::"
+                      "test_batched_workload_per_system_matches_oracle"}
 
 
 def run_batched(args, world, rank, local):
