@@ -1,5 +1,5 @@
 // Compile-time Stockham FFT for the transform lengths the plan uses most
-// (powers of two and 3 * 2^k from 64 to 768): the radix schedule, spans,
+// (powers of two and 3 * 2^k from 64 to 1536): the radix schedule, spans,
 // strides and the thread-to-butterfly map are constants, so index arithmetic
 // reduces to shifts and constant multiplies, and each pass works in place in
 // one shared-memory buffer (every thread loads all of its butterflies' inputs,
@@ -172,9 +172,9 @@ SAG_CX int ct_twg(int j, int t) {
 // path). The inverse columns, about one block per SM, stay one launch.
 SAG_CX int ct_len(int i) {
   return i == 0 ? 64 : i == 1 ? 96 : i == 2 ? 128 : i == 3 ? 192 : i == 4 ? 256 : i == 5 ? 384 : i == 6 ? 512
-       : i == 7 ? 768 : 1536;
+       : i == 7 ? 768 : i == 8 ? 1024 : 1536;
 }
-constexpr int kCtLengths = 9;
+constexpr int kCtLengths = 10;
 SAG_CX int ct_index(int P) {
   for (int i = 0; i < kCtLengths; ++i)
     if (ct_len(i) == P) return i;

@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
         case 384: fwd_col_pair_body<C, 384, GEN>(P, od, pr, cbp, buf); break;
         case 512: fwd_col_pair_body<C, 512, GEN>(P, od, pr, cbp, buf); break;
         case 768: fwd_col_pair_body<C, 768, GEN>(P, od, pr, cbp, buf); break;
+        case 1024: fwd_col_pair_body<C, 1024, GEN>(P, od, pr, cbp, buf); break;
         default: break;  // the plan sets pair only with a compile-time column length
       }
       return;
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_fwd_col(const __grid_constant__
     case 384: fwd_col_body<C, 384, GEN>(P, od, vloc, lv, cb, n, buf); break;
     case 512: fwd_col_body<C, 512, GEN>(P, od, vloc, lv, cb, n, buf); break;
     case 768: fwd_col_body<C, 768, GEN>(P, od, vloc, lv, cb, n, buf); break;
+    case 1024: fwd_col_body<C, 1024, GEN>(P, od, vloc, lv, cb, n, buf); break;
     case 1536: fwd_col_body<C, 1536, GEN>(P, od, vloc, lv, cb, n, buf); break;
     default: fwd_col_body<C, 0, GEN>(P, od, vloc, lv, cb, n, buf); break;
   }
@@ -814,6 +816,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_col(const __grid_constant__
     case 384: inv_col_body<C, 384>(P, od, oi, cb, buf); break;
     case 512: inv_col_body<C, 512>(P, od, oi, cb, buf); break;
     case 768: inv_col_body<C, 768>(P, od, oi, cb, buf); break;
+    case 1024: inv_col_body<C, 1024>(P, od, oi, cb, buf); break;
     case 1536: inv_col_body<C, 1536>(P, od, oi, cb, buf); break;
     default: inv_col_body<C, 0>(P, od, oi, cb, buf); break;
   }

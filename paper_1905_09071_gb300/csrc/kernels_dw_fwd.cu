@@ -24,7 +24,7 @@ namespace {
 using FwdLaunch = void (*)(const RhsParams&, const double*, int, int, int, size_t, cudaStream_t);
 using Setup = cudaError_t (*)();
 
-// The pair form exists for column lengths up to 768 (its rows are at most 512
+// The pair form exists for column lengths up to 1024 (its rows are at most 512
 // points, so the 1536-point columns never pair); that kind maps to kKindGeneral.
 constexpr int fwd_kind_of(int K) { return K == kKindPair + ct_index(1536) ? kKindGeneral : K; }
 

@@ -430,13 +430,13 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       return fail(SAG_EUNSUPPORTED, "row length without a compile-time kernel above 128");
     od.G = G;
     // Pairs (see OrderDesc): rows of 2 M2 points with a compile-time kernel,
-    // columns of at most 768 points (the pair column kernels' lengths; the
+    // columns of at most 1024 points (the pair column kernels' lengths; the
     // rule never pairs 1536-point columns, whose rows are 2 x 512 points).
     od.pair = 0;
     od.npair = 0;
     od.ncolblk_p = 0;
     od.ld2p = 0;
-    if (od.ct1 && od.ct2 && !tt && od.umap_off < 0 && od.M1 <= 768 && 2 * od.M2 <= 512 &&
+    if (od.ct1 && od.ct2 && !tt && od.umap_off < 0 && od.M1 <= 1024 && 2 * od.M2 <= 512 &&
         ct_supported(2 * od.M2)) {
       od.pair = 1;
       od.npair = (od.nvec + 1) / 2;
@@ -1024,12 +1024,12 @@ sag_status autotune_fft_groups(sag_plan_s* pl) {
 namespace {
 
 // An alternative four-step split M = M1 M2 for the pair form: both the
-// column length M1 (at most 768) and the pair rows' 2 M2 points have
+// column length M1 (at most 1024) and the pair rows' 2 M2 points have
 // compile-time kernels, and a column block's W columns fit in M2 columns.
 bool pair_split_ok(int M, int M2) {
   if (M2 < 4 || M % (2 * M2) != 0) return false;
   const int M1 = M / M2;
-  return ct_supported(M1) && M1 <= 768 && ct_supported(M2) && ct_supported(2 * M2) && 2 * M2 <= 512 &&
+  return ct_supported(M1) && M1 <= 1024 && ct_supported(M2) && ct_supported(2 * M2) && 2 * M2 <= 512 &&
          M2 >= ct_cols(M1);
 }
 

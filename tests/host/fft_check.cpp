@@ -163,6 +163,7 @@ static long double ct_dispatch(int P, int count, bool sin, std::mt19937_64& g) {
     case 384: return ct_check<384, C>(count, sin, g);
     case 512: return ct_check<512, C>(count, sin, g);
     case 768: return ct_check<768, C>(count, sin, g);
+    case 1024: return ct_check<1024, C>(count, sin, g);
     case 1536: return ct_check<1536, C>(count, sin, g);
     default: std::printf("unsupported %d\n", P); std::exit(2);
   }

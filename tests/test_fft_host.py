@@ -54,7 +54,7 @@ def test_stockham_passes_match_direct_dft(fft_check):
         assert float(edw) < 1e-12, f"double-word length {P}: {edw}"
 
 
-CT_SIZES = [64, 96, 128, 192, 256, 384, 512, 768, 1536]
+CT_SIZES = [64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536]
 
 
 def test_compile_time_passes_padded_layout(fft_check):

@@ -136,12 +136,12 @@ def test_full_size_sampled_parity(throughput_case, prec):
     assert nerr(r[:K], p_pre + q_ref[:K], scale) < TOL[prec]
 
 
-# Four-step splits M = M1 M2 with M2 capped: pair-form columns of 512 and 768
-# points and a run-time-length 1024-point column (max_m2 = 128); 1024 and
-# 2048-point run-time columns and a compile-time 1536-point column of single
-# vectors (max_m2 = 64).
-CAPPED_SPLITS = {128: [[512, 128, 1], [768, 128, 1], [1024, 128, 0]],
-                 64: [[1024, 64, 0], [1536, 64, 0], [2048, 64, 0]]}
+# Four-step splits M = M1 M2 with M2 capped: pair-form columns of 512, 768 and
+# 1024 points (max_m2 = 128); 1024-point pair columns, a compile-time
+# 1536-point column of single vectors and a 2048-point run-time column
+# (max_m2 = 64).
+CAPPED_SPLITS = {128: [[512, 128, 1], [768, 128, 1], [1024, 128, 1]],
+                 64: [[1024, 64, 1], [1536, 64, 0], [2048, 64, 0]]}
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -163,9 +163,9 @@ def test_capped_row_length_parity(throughput_case, prec, max_m2):
 
 @pytest.mark.parametrize("prec", [sag.SAG_FP32_SPLIT, sag.SAG_FP32_SPLIT_EXACT])
 def test_geometry_autotuner(throughput_case, prec):
-    # The rule's splits are timed first, then d = 2 and d = 3 with M2 halved
-    # (d = 4 would need a 1024-point compile-time column kernel); the plan
-    # keeps the last candidate marked kept, and its results match the oracle.
+    # The rule's splits are timed first, then d = 2, 3 and 4 in turn with M2
+    # halved (d = 4: 1024-point pair columns); the plan keeps the last
+    # candidate marked kept, and its results match the oracle.
     s, K, p_pre, q_ref = throughput_case
     seen = {}
 
@@ -174,10 +174,11 @@ def test_geometry_autotuner(throughput_case, prec):
 
     p, q, _, r = gpu_parts(s, s.n0, prec, autotune=1, check=check)
     log = seen["geometry_autotune"]
-    assert len(log) == 3
+    assert len(log) == 4
     assert log[0]["splits"] == [[256, 256], [384, 256], [512, 256]] and log[0]["kept"]
     assert log[1]["splits"] == [[512, 128], [384, 256], [512, 256]]
     assert log[2]["splits"][1] == [768, 128] and log[2]["splits"][2] == [512, 256]
+    assert log[3]["splits"][2] == [1024, 128]
     assert all(e["ms_per_step"] > 0 for e in log)
     chosen = [[o["M1"], o["M2"]] for o in seen["orders"]]
     assert chosen == [e for e in log if e["kept"]][-1]["splits"]
