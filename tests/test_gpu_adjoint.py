@@ -239,3 +239,22 @@ def test_tt_vjp_of_diagonal_embedding_equals_cp_vjp():
             torch.cuda.synchronize()
             outs.append(gn.cpu().numpy())
     assert rel(outs[1], outs[0]) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [sag.SAG_FP64, sag.SAG_FP32_SPLIT])
+def test_tt_integrate_vjp_paper_shape_matches_oracle(prec):
+    # The paper's Sec. 3 kernel family (pure ternary generalized Brownian
+    # kernel, Theorem-1 cores with ranks 1, 3, 3, 1 and structural zeros, an
+    # all-zero d = 2 order) at N = 4096: 4 Heun steps, checkpoints every 2.
+    t = wl.paper_ternary(4096, "tt")
+    g = np.random.default_rng(108).normal(size=t.N) * t.n0  # a cotangent shaped like the state
+    steps, dt = 4, 1e-3
+    gn_ref, gH_ref = oracle.integrate_vjp(t.n0, t.D, t.ranks, t.factors, dt, steps, g, fmt=oracle.TT)
+    with sag.Plan(t.N, t.D, t.ranks, t.factors, fmt=sag.SAG_TT, prec=prec) as pl:
+        gn = torch.empty(t.N, dtype=torch.float64, device="cuda")
+        gH = torch.empty(t.factors.size, dtype=torch.float64, device="cuda")
+        pl.integrate_vjp(dev(t.n0), dt, steps, dev(g), gn, gH, ckpt=2)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+    assert rel(gn.cpu().numpy(), gn_ref) < 10 * TOL[prec]
+    assert rel(gH.cpu().numpy(), gH_ref) < 10 * TOL[prec]
