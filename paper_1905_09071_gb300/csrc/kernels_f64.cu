@@ -21,8 +21,13 @@ cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double
   return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st) {
-  k_fwd_col<cd><<<L.col_blocks_all, kThreads, L.col_smem, st>>>(P, nin, 0, 1);
+// Forward columns for the vector-Jacobian products: blocks of the core or
+// rank vectors (all = 0, as in the right-hand side) or of every vector
+// (all = 1). Launched from this file because the shared-memory attribute
+// belongs to this file's copy of the kernel.
+cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
+                               int blocks, int all) {
+  k_fwd_col<cd><<<blocks, kThreads, L.col_smem, st>>>(P, nin, 0, all);
   return cudaGetLastError();
 }
 

@@ -5,11 +5,12 @@
 
 namespace sag {
 
-cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st);
+cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
+                               int blocks, int all);
 
 cudaError_t launch_vjp_fft_f64(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
                               cudaStream_t st) {
-  cudaError_t e = launch_fwd_col_f64(P, L, n, st);
+  cudaError_t e = launch_fwd_col_f64(P, L, n, st, L.col_blocks_all, 1);
   if (e != cudaSuccess) return e;
   k_gcol<cd><<<L.inv_blocks, kThreads, L.vcol_smem, st>>>(P, g);
   k_rows_vjp<cd><<<L.row_blocks, kThreads, L.vrow_smem, st>>>(P);
@@ -19,7 +20,8 @@ cudaError_t launch_vjp_fft_f64(const RhsParams& P, const LaunchCfg& L, const dou
 
 cudaError_t launch_vjp_fft_tt_f64(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
                                   cudaStream_t st) {
-  k_fwd_col<cd><<<L.col_blocks, kThreads, L.col_smem, st>>>(P, n, 0, 0);
+  cudaError_t e = launch_fwd_col_f64(P, L, n, st, L.col_blocks, 0);
+  if (e != cudaSuccess) return e;
   return launch_vjp_tt_after_cols<cd>(P, L, g, st);
 }
 

@@ -148,7 +148,11 @@ inline int smem_limit() {
 
 // Lets `func` use all the dynamic shared memory its static shared memory
 // leaves free. The attribute is per function for the whole process, so a
-// per-plan value would shrink the limit of plans built earlier.
+// per-plan value would shrink the limit of plans built earlier. A template
+// kernel instantiated in several translation units is a separate function in
+// each (its host stub has internal linkage): the file that launches it must
+// set the attribute on its own copy, or launch through a function of the file
+// that does.
 template <class F>
 inline cudaError_t allow_max_smem(F* func) {
   cudaFuncAttributes a;

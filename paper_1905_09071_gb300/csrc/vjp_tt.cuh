@@ -238,7 +238,8 @@ cudaError_t launch_vjp_tt_after_cols(const RhsParams& P, const LaunchCfg& L, con
 template <class C>
 cudaError_t setup_vjp_tt(const LaunchCfg& L) {
   (void)L;
-  cudaError_t e = allow_max_smem(k_rows_tt_g<C>);
+  cudaError_t e = allow_max_smem(k_rows_tt_fwd<C>);  // this file's own copy (see allow_max_smem)
+  if (e == cudaSuccess) e = allow_max_smem(k_rows_tt_g<C>);
   if (e == cudaSuccess) e = allow_max_smem(k_rows_tt_inv_vjp<C>);
   if (e == cudaSuccess) e = allow_max_smem(k_inv_col_vjp_tt<C>);
   return e;

@@ -225,6 +225,23 @@ def test_tt_integrate_vjp_matches_oracle_adjoint(prec, rk):
     assert rel(gH.cpu().numpy(), gH_ref) < 10 * TOL[prec]
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_tt_rhs_vjp_large_blocks_matches_oracle(prec):
+    # N = 4096 with 15 distinct core vectors: the column blocks and the TT row
+    # blocks of the adjoint both need more than 48 KB of shared memory.
+    t = wl.random_tt(3, 4096, {2: [1, 4, 1], 3: [1, 3, 3, 1]}, seed=109)
+    g = np.random.default_rng(110).normal(size=t.N)
+    gn_ref, gH_ref = oracle.rhs_vjp(t.n0, g, t.D, t.ranks, t.factors, fmt=oracle.TT)
+    with sag.Plan(t.N, t.D, t.ranks, t.factors, fmt=sag.SAG_TT, prec=prec) as pl:
+        gn = torch.empty(t.N, dtype=torch.float64, device="cuda")
+        gH = torch.empty(t.factors.size, dtype=torch.float64, device="cuda")
+        pl.rhs_vjp(dev(t.n0), dev(g), gn, gH)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+    assert rel(gn.cpu().numpy(), gn_ref) < TOL[prec]
+    assert rel(gH.cpu().numpy(), gH_ref) < TOL[prec]
+
+
 def test_tt_vjp_of_diagonal_embedding_equals_cp_vjp():
     # The library's TT adjoint of the diagonal embedding of a CP kernel gives
     # the CP adjoint's n-cotangent (FP64).
