@@ -123,6 +123,35 @@ def throughput_case():
     return s, K, p_pre, q_ref
 
 
+def test_fp32_split_loss_sizewise(throughput_case):
+    # The FP32-split path keeps the inner products s_v = <U_v, n> and
+    # q = n sum_v coef_v U_v in FP64 beside its double-word FFTs: every loss
+    # output at N = 65536 against the oracle, sizewise relative error.
+    s, _, _, q_ref = throughput_case
+    _, q, _, _ = gpu_parts(s, s.n0, sag.SAG_FP32_SPLIT)
+    # The state decays to subnormal and zero values at the largest sizes; q
+    # follows it there, and a sizewise relative error means nothing for
+    # subnormal values.
+    nz = s.n0 > 1e-290
+    assert nz.sum() > 1000 and np.all(q_ref[nz] < 0)
+    assert np.all(q[s.n0 == 0] == 0.0)
+    assert float(np.max(np.abs(q[nz] - q_ref[nz]) / np.abs(q_ref[nz]))) < 1e-13
+
+
+@pytest.mark.parametrize("prec", [sag.SAG_FP32_SPLIT, sag.SAG_FP32_SPLIT_EXACT])
+@pytest.mark.parametrize("scale", [1e-40, 1e40])
+def test_loss_at_extreme_factor_scales(prec, scale):
+    # Factors near 1e+-40 (beyond FP32's range, so the double-word copies
+    # rely on their per-vector powers of two), loss weights near 1e+-80, and
+    # a state of mixed sign: the loss against the oracle.
+    t = wl.random_cp(3, 3000, [3, 2], seed=111)
+    f = t.factors * scale
+    n0 = t.n0 * np.where(np.arange(t.N) % 7 == 3, -1.0, 1.0)
+    q_ref = oracle.loss(n0, t.D, t.ranks, f)
+    _, q, _, _ = gpu_parts(wl.System(t.D, t.N, "cp", t.ranks, f, n0), n0, prec)
+    assert nerr(q, q_ref, np.abs(q_ref).max()) < 1e-13
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_full_size_sampled_parity(throughput_case, prec):
     # N = 65536: every gain output k <= 2048 against the oracle on the prefix
