@@ -637,6 +637,15 @@ __device__ __forceinline__ void rows_body_pair(const RhsParams& P, const OrderDe
       if (threadIdx.x == 0) timeout_drain(P.status, kStatusTimeout, kStatusTimeoutUndrained, bar, (uint32_t)(c & 1));
       return;
     }
+    if (od.discard) {
+      // The chunk's rows are in shared memory and no kernel reads them again
+      // (each row belongs to one block): their L2 lines go without a write-back.
+      constexpr int LPR = P2p * (int)sizeof(C) / 128;  // lines per row
+      for (int e = threadIdx.x; e < gc * nrow * LPR; e += kThreads) {
+        const int rr = e / LPR, ln = e - rr * LPR, g = rr / nrow, row = rr - g * nrow;
+        discard_l2(src + (int64_t)(p0 + g) * 2 * M + (int64_t)(row ? k1b : k1a) * P2p + ln * (128 / (int)sizeof(C)));
+      }
+    }
     fft_ct_first<C, P2p, SLOTS, kThreads, true>(stage, P2p, work, ld, tw);  // unused slots hold stale data
     fence_proxy_async_smem();
     __syncthreads();

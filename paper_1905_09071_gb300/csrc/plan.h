@@ -60,6 +60,7 @@ struct OrderDesc {
   // the real and imaginary parts of one length-L sequence, transformed as
   // M1 rows of 2 M2 points; the row pass separates their spectra.
   int pair;            // 1: the forward pass runs on pairs
+  int discard;         // pair rows: drop each workspace row's L2 lines once read (128-byte aligned)
   int npair;           // ceil(nvec / 2)
   int ncolblk_p;       // 2 M2 / W column blocks per pair
   int ld2p;            // work-area stride of the pair row transforms

@@ -433,6 +433,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     // columns of at most 1024 points (the pair column kernels' lengths; the
     // rule never pairs 1536-point columns, whose rows are 2 x 512 points).
     od.pair = 0;
+    od.discard = 0;
     od.npair = 0;
     od.ncolblk_p = 0;
     od.ld2p = 0;
@@ -445,6 +446,10 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     }
     od.scr_off = scr;
     scr += (int64_t)std::max(od.nvec, 2 * od.npair) * od.M;
+    // The pair rows drop their workspace lines from L2 once read: every row
+    // (2 M2 points, at pair p row k1: scr_off + 2 M p + 2 M2 k1 elements of
+    // 16 bytes) must start on a 128-byte line of the 256-byte aligned buffer.
+    if (od.pair && dwp && od.scr_off % 8 == 0 && (2 * od.M) % 8 == 0 && (2 * od.M2) % 8 == 0) od.discard = 1;
     od.scr2_off = scr2;
     scr2 += od.M;
     od.pd_off = pdo;
