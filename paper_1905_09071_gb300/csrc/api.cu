@@ -1009,7 +1009,7 @@ sag_status sag_plan_describe(sag_plan_t pl, char* buf, size_t len) {
           std::to_string(od.L) + ", \"M1\": " + std::to_string(od.M1) + ", \"M2\": " +
           std::to_string(od.M2) + ", \"radix_M1\": " + rps(od.rp1) + ", \"radix_M2\": " + rps(od.rp2) +
           ", \"W\": " + std::to_string(od.W) + ", \"G\": " + std::to_string(od.G) +
-          ", \"compile_time\": [" + std::to_string(od.ct1) + ", " + std::to_string(od.ct2) + "]}";
+          ", \"compile_time\": [" + std::to_string(od.ct1) + ", " + std::to_string(od.ct2 || od.ctt) + "]}";
   }
   js += "], \"orders_total\": " + std::to_string(pl->items.size()) + ", \"blocks\": {\"fwd_col\": " +
         std::to_string(pl->L.col_blocks) + ", \"rows\": " + std::to_string(pl->L.row_blocks) +

@@ -844,14 +844,66 @@ namespace sag {
 // Row pass of the TT path: row FFTs of every vector of the order at the row
 // pair {k1a, M1 - k1a}, split into real spectra 2 A[k] written back in place
 // (same rows of the workspace); the Nyquist value goes to spec_nyq.
+// The same pass with compile-time M2-point transforms (double-word, OrderDesc::
+// ctt): chunks of ct_group(M2) vectors, their two rows in the padded layout
+// (slot 2 g + row; a single-row block leaves the odd slots stale and unused),
+// transformed in place with the pass tables in global memory.
+template <class C, int P2>
+__device__ __forceinline__ void rows_tt_fwd_ct(const RhsParams& P, const OrderDesc& od, int kp, C* buf) {
+  constexpr int G = ct_group(P2), SLOTS = 2 * G, ld = ct_ld(P2, SLOTS);
+  const C* tw = static_cast<const C*>(od.twg2);
+  const int M1 = od.M1, M = od.M;
+  const int k1a = kp, k1b = M1 - kp;
+  const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
+  const int NP = nrow * P2;
+  const C* twL = static_cast<const C*>(od.twL);
+  C* spec = static_cast<C*>(P.scratch) + od.scr_off;
+  C* nyq = static_cast<C*>(P.spec_nyq) + od.vbase;
+  for (int q0 = 0; q0 < od.nvec; q0 += G) {
+    const int gc = min(G, od.nvec - q0);
+    for (int e = threadIdx.x; e < gc * NP; e += kThreads) {
+      const int g = e / NP, p = e - g * NP, row = p / P2, pos = p - row * P2;
+      buf[(2 * g + row) * ld + pad8(pos)] = spec[(int64_t)(q0 + g) * M + (int64_t)(row ? k1b : k1a) * P2 + pos];
+    }
+    __syncthreads();
+    fft_ct<C, P2, SLOTS, kThreads, true>(buf, ld, tw);
+    for (int e = threadIdx.x; e < gc * NP; e += kThreads) {
+      const int g = e / NP, p = e - g * NP, row = p / P2, pos = p - row * P2;
+      const int k1 = row ? k1b : k1a;
+      int mrow, mpos;
+      mirror_of(k1, row, pos, M1, P2, mrow, mpos);
+      const C* bg = buf + 2 * g * ld;
+      spec[(int64_t)(q0 + g) * M + (int64_t)k1 * P2 + pos] =
+          unpack2(bg[row * ld + pad8(pos)], bg[mrow * ld + pad8(mpos)], twL[k1 + M1 * pos]);
+      if (k1 == 0 && pos == 0) {
+        const C z0 = bg[0];
+        const C zc = c_conj(z0);
+        nyq[q0 + g] = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));  // 2 A[M]
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <class C>
-__global__ void __launch_bounds__(kThreads) k_rows_tt_fwd(const __grid_constant__ RhsParams P) {
+__global__ void __launch_bounds__(kThreads, 3) k_rows_tt_fwd(const __grid_constant__ RhsParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int j = find_segment(P.rowpre, P.nitems, blockIdx.x);
   const int oi = P.rowperm[j];
   const OrderDesc& od = P.ord[oi];
   const int kp = blockIdx.x - P.rowpre[j];
+  if constexpr (is_dw<C>::value) {
+    if (od.ctt) {
+      switch (od.M2) {
+        case 64: rows_tt_fwd_ct<C, 64>(P, od, kp, buf); return;
+        case 128: rows_tt_fwd_ct<C, 128>(P, od, kp, buf); return;
+        case 256: rows_tt_fwd_ct<C, 256>(P, od, kp, buf); return;
+        case 512: rows_tt_fwd_ct<C, 512>(P, od, kp, buf); return;
+        default: break;  // the plan sets ctt only for these lengths (M2 is a power of two)
+      }
+    }
+  }
   const int M1 = od.M1, M2 = od.M2, M = od.M, ld = od.ld2, G = od.G;
   const int k1a = kp, k1b = M1 - kp;
   const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
@@ -892,9 +944,10 @@ __global__ void __launch_bounds__(kThreads) k_rows_tt_fwd(const __grid_constant_
   }
 }
 
+// Power-of-two weight of core entry j (index into the plan's vid table).
 __device__ __forceinline__ cd tt_weight(cd x, const RhsParams&, int) { return x; }
-__device__ __forceinline__ cdw tt_weight(cdw x, const RhsParams& P, int v) {
-  return c_scale2(x, P.vweight[v]);
+__device__ __forceinline__ cdw tt_weight(cdw x, const RhsParams& P, int j) {
+  return c_scale2(x, P.ewt[j]);
 }
 
 // Per-frequency matrix chain of one order; thread e < M handles the spectrum
@@ -909,19 +962,17 @@ __global__ void __launch_bounds__(256) k_tt_chain(const __grid_constant__ RhsPar
   const C* spec = static_cast<const C*>(P.scratch) + od.scr_off;
   const C* nyq = static_cast<const C*>(P.spec_nyq);
   const int* vid = P.vid + od.vid_off;
-  auto load = [&](int v) -> C {
+  auto load = [&](int j) -> C {  // core entry j of the order, its vector vid[j] >= 0
+    const int v = vid[j];
     const C z = (e < M) ? spec[(int64_t)(v - od.vbase) * M + e] : nyq[v];
-    return tt_weight(z, P, v);
+    return tt_weight(z, P, od.vid_off + j);
   };
   C x[RMAX], xn[RMAX];
   const int r1 = od.ttr[1];
 #pragma unroll
   for (int b = 0; b < RMAX; ++b) {
     x[b] = c_zero(C{});
-    if (b < r1) {
-      const int v = vid[b];
-      if (v >= 0) x[b] = load(v);
-    }
+    if (b < r1 && vid[b] >= 0) x[b] = load(b);
   }
   int off = r1;
   for (int l = 2; l <= od.d; ++l) {
@@ -933,8 +984,8 @@ __global__ void __launch_bounds__(256) k_tt_chain(const __grid_constant__ RhsPar
 #pragma unroll
         for (int a = 0; a < RMAX; ++a) {
           if (a < ra) {
-            const int v = vid[off + a * rb + b];
-            if (v >= 0) xn[b] = c_add(xn[b], c_mul(x[a], load(v)));
+            const int j = off + a * rb + b;
+            if (vid[j] >= 0) xn[b] = c_add(xn[b], c_mul(x[a], load(j)));
           }
         }
       }
@@ -950,14 +1001,65 @@ __global__ void __launch_bounds__(256) k_tt_chain(const __grid_constant__ RhsPar
 // Inverse row half of the TT path: repack the spectral sum of rows
 // {k1a, M1 - k1a} (with its Nyquist value), inverse row FFTs, four-step
 // twiddle, written back in place for the inverse column kernel.
+// The same with compile-time transforms (OrderDesc::ctt): sums staged at buf,
+// the two packed rows in the padded layout after them.
+template <class C, int P2>
+__device__ __forceinline__ void rows_tt_inv_ct(const RhsParams& P, const OrderDesc& od, int oi, int kp, C* buf) {
+  constexpr int ldi = ct_ld(P2, 2);
+  const int M1 = od.M1;
+  const int k1a = kp, k1b = M1 - kp;
+  const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
+  const int NP = nrow * P2;
+  C* sS = buf;
+  C* work = buf + 2 * P2;
+  const C* twL = static_cast<const C*>(od.twL);
+  C* S = static_cast<C*>(P.scratch2) + od.scr2_off;
+  const C SM = static_cast<const C*>(P.s_nyq)[oi];
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / P2, pos = p - row * P2;
+    sS[p] = S[(int64_t)(row ? k1b : k1a) * P2 + pos];
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / P2, pos = p - row * P2;
+    const int k1 = row ? k1b : k1a;
+    const int k = k1 + M1 * pos;
+    int mrow, mpos;
+    mirror_of(k1, row, pos, M1, P2, mrow, mpos);
+    const C Sk = sS[p];
+    const C Sm = (k == 0) ? SM : C(c_conj(sS[mrow * P2 + mpos]));
+    const C zpp = c_add(c_add(Sk, Sm), c_mul_pi(c_mul(c_conj(twL[k]), c_sub(Sk, Sm))));
+    work[row * ldi + pad8(pos)] = c_conj(zpp);
+  }
+  __syncthreads();
+  fft_ct<C, P2, 2, kThreads, true>(work, ldi, static_cast<const C*>(od.twg2));
+  const C* tw4 = static_cast<const C*>(od.tw4);
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / P2, j2 = p - row * P2;
+    const int k1 = row ? k1b : k1a;
+    S[(int64_t)k1 * P2 + j2] = c_mul(work[row * ldi + pad8(j2)], tw4[j2 * k1]);
+  }
+}
+
 template <class C>
-__global__ void __launch_bounds__(kThreads) k_rows_tt_inv(const __grid_constant__ RhsParams P) {
+__global__ void __launch_bounds__(kThreads, 3) k_rows_tt_inv(const __grid_constant__ RhsParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int j = find_segment(P.rowpre, P.nitems, blockIdx.x);
   const int oi = P.rowperm[j];
   const OrderDesc& od = P.ord[oi];
   const int kp = blockIdx.x - P.rowpre[j];
+  if constexpr (is_dw<C>::value) {
+    if (od.ctt) {
+      switch (od.M2) {
+        case 64: rows_tt_inv_ct<C, 64>(P, od, oi, kp, buf); return;
+        case 128: rows_tt_inv_ct<C, 128>(P, od, oi, kp, buf); return;
+        case 256: rows_tt_inv_ct<C, 256>(P, od, oi, kp, buf); return;
+        case 512: rows_tt_inv_ct<C, 512>(P, od, oi, kp, buf); return;
+        default: break;
+      }
+    }
+  }
   const int M1 = od.M1, M2 = od.M2, ld = od.ld2;
   const int k1a = kp, k1b = M1 - kp;
   const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;

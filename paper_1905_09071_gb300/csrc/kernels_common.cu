@@ -185,8 +185,8 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
         right[l - 1][a] = acc;
       }
     }
-    // Core entries that share a vector (bitwise-identical entries of one
-    // core) add their weights; this thread owns the order's vectors.
+    // Core entries that share a vector (bitwise-identical entries of the
+    // order's cores) add their weights; this thread owns the order's vectors.
     for (int v = od.vbase; v < od.vbase + od.nvec; ++v) P.coef[v] = 0.0;
     for (int l = 1; l <= d; ++l) {
       const int ra = od.ttr[l - 1], rb = od.ttr[l];

@@ -61,6 +61,7 @@ struct OrderDesc {
   // M1 rows of 2 M2 points; the row pass separates their spectra.
   int pair;            // 1: the forward pass runs on pairs
   int discard;         // pair rows: drop each workspace row's L2 lines once read (128-byte aligned)
+  int ctt;             // TT, double-word: the row kernels run compile-time M2-point transforms
   int npair;           // ceil(nvec / 2)
   int ncolblk_p;       // 2 M2 / W column blocks per pair
   int ld2p;            // work-area stride of the pair row transforms
@@ -154,7 +155,8 @@ struct RhsParams {
   void* spec_nyq;                // TT: [Vtot] Nyquist value of each vector's spectrum
   void* s_nyq;                   // TT: [nitems] Nyquist value of each order's spectral sum
   const int* vid;                // TT: (lambda, a, b) -> vector index or -1, per item
-  const float* vweight;          // TT, double-word path: [Vtot] power-of-two weight 2^(e_v - E_lambda)
+  const float* ewt;              // TT, double-word path: per core entry (parallel to vid) the
+                                 // power-of-two weight 2^(e_v - E_lambda) of its vector v in core lambda
   double* pd;                    // gain per item: P^(d) of system b at pd_off
   double* dot_s;                 // [Vtot][maxdotchunk] partial <U, n>
   double* dot_t;                 // [Vtot][maxdotchunk] partial <k U, n>

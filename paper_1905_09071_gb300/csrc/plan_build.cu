@@ -141,7 +141,7 @@ cudaError_t item_tables(sag_plan_s* pl, TwiddleCache<C>& tc, OrderDesc& od) {
   od.tw4c_p = nullptr;
   if (e == cudaSuccess && od.ct1) e = tc.get_pass(pl, od.M1, &od.twg1);
   if (e == cudaSuccess && od.pair) e = tc.get_pass(pl, 2 * od.M2, &od.tw2p);
-  if (e == cudaSuccess && od.ct2) e = tc.get_pass(pl, od.M2, &od.twg2);
+  if (e == cudaSuccess && (od.ct2 || od.ctt)) e = tc.get_pass(pl, od.M2, &od.twg2);
   if (e == cudaSuccess && od.pair) e = tc.get_col(pl, od.M1, 2 * od.M2, od.W, &od.tw4c_p);
   return e;
 }
@@ -328,10 +328,11 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
         for (int l = 0; l <= d; ++l) od.ttr[l] = rk[l];
         od.vid_off = (int)vid.size();
         int cnt = 0;
+        // Bitwise-identical vectors of the order's cores share one id, hence one
+        // transform (the Theorem-1 cores repeat the same powers in every core);
+        // the power-of-two weight, which depends on the core, is per entry.
+        std::vector<std::pair<const double*, int>> core;
         for (int l = 1; l <= d; ++l) {
-          // within one core, bitwise-identical vectors share one id (their
-          // power-of-two weight depends on the core only)
-          std::vector<std::pair<const double*, int>> core;
           for (int a = 0; a < rk[l - 1]; ++a)
             for (int c = 0; c < rk[l]; ++c) {
               const double* x = src.data() + soff;
@@ -413,6 +414,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     // compile-time row kernel serves CP only.
     od.ct1 = (dwp && ct_supported(od.M1) && M2 >= ct_cols(od.M1)) ? 1 : 0;
     od.ct2 = (dwp && !tt && ct_supported(od.M2) && od.M2 <= 512) ? 1 : 0;
+    od.ctt = (dwp && tt && (od.M2 == 64 || od.M2 == 128 || od.M2 == 256 || od.M2 == 512)) ? 1 : 0;
     int W = 1;
     while (2 * W <= M2 && (int64_t)2 * W * od.M1 <= 2048) W *= 2;
     if (od.ct1) W = ct_cols(od.M1);
@@ -484,6 +486,9 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     row_smem = std::max(row_smem, item_row_smem.back());
     rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * G * 2 * od.ld2, 6 * od.ld2) * csize +
                                           (size_t)od.M2 * csize);
+    if (od.ctt)  // compile-time TT rows: 2 ct_group(M2) padded slots forward; sums and 2 slots inverse
+      rowtt_smem = std::max(rowtt_smem, (size_t)std::max(2 * ct_group(od.M2) * ct_ld(od.M2, 2 * ct_group(od.M2)),
+                                                          2 * od.M2 + 2 * ct_ld(od.M2, 2)) * csize);
     // Vector-Jacobian product kernels (CP): ping-pong column blocks; row
     // blocks hold the d vectors of a rank term, g's spectrum and d spectra.
     pl->L.vcol_smem = std::max(pl->L.vcol_smem, (size_t)(2 * W * od.ld1 + od.M1) * csize);
@@ -619,7 +624,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       return cuda_fail(e, "clear n");
     P.ndw = ndw;
   }
-  std::vector<float> vweight(Vtot, 1.0f);
+  std::vector<float> ewt(std::max<size_t>(vid.size(), 1), 1.0f);
   std::vector<int> eexcl((size_t)std::max(nent_tot, 1), 0);  // TT: the other cores' exponents per entry
   TwiddleCache<cdw> tcw;
   TwiddleCache<cd> tcd;
@@ -646,7 +651,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
           if (vid[off + j] >= 0) El = std::max(El, ev[vid[off + j]]);
         if (El == INT32_MIN) El = 0;
         for (int j = 0; j < cnt; ++j)
-          if (vid[off + j] >= 0) vweight[vid[off + j]] = std::ldexp(1.0f, ev[vid[off + j]] - El);
+          if (vid[off + j] >= 0) ewt[off + j] = std::ldexp(1.0f, ev[vid[off + j]] - El);
         Els[l] = El;
         Esum += El;
         off += cnt;
@@ -714,7 +719,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       pl->upload(&d_invpre, invpre) != cudaSuccess || pl->upload(&d_chainpre, chainpre) != cudaSuccess ||
       pl->upload(&d_epipre, epipre) != cudaSuccess || pl->upload(&d_vsys, vsys) != cudaSuccess ||
       pl->upload(&d_rowperm, rowperm) != cudaSuccess || pl->upload(&d_vid, vid) != cudaSuccess ||
-      pl->upload(&d_voff, voff) != cudaSuccess || pl->upload(&d_vw, vweight) != cudaSuccess ||
+      pl->upload(&d_voff, voff) != cudaSuccess || pl->upload(&d_vw, ewt) != cudaSuccess ||
       pl->upload(&d_vdwoff, vdwoff) != cudaSuccess)
     return fail(SAG_ENOMEM, "cudaMalloc tables");
   P.ord = d_ord;
@@ -733,7 +738,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   P.vid = d_vid;
   P.voff = d_voff;
   P.vdwoff = d_vdwoff;
-  P.vweight = d_vw;
+  P.ewt = d_vw;
   const size_t Nt = (size_t)pl->Ntot;
   if (pl->alloc((unsigned char**)&P.spec_nyq, (size_t)Vtot * csize) != cudaSuccess ||
       pl->alloc((unsigned char**)&P.s_nyq, (size_t)P.nitems * csize) != cudaSuccess ||

@@ -77,9 +77,10 @@ __global__ void __launch_bounds__(256) k_tt_chain_vjp(const __grid_constant__ Rh
   const C* spec = static_cast<const C*>(P.scratch) + od.scr_off;
   const C* nyq = static_cast<const C*>(P.spec_nyq);
   const int* vid = P.vid + od.vid_off;
-  auto load = [&](int v) -> C {
+  auto load = [&](int j) -> C {  // core entry j of the order, its vector vid[j] >= 0
+    const int v = vid[j];
     const C z = (e < M) ? spec[(int64_t)(v - od.vbase) * M + e] : nyq[v];
-    return tt_weight(z, P, v);
+    return tt_weight(z, P, od.vid_off + j);
   };
   const C G = (e < M) ? static_cast<const C*>(P.scratch2)[od.scr2_off + e] : static_cast<const C*>(P.s_nyq)[oi];
   C* out = static_cast<C*>(P.ent_spec) + od.ent_spec_off;
@@ -96,8 +97,8 @@ __global__ void __launch_bounds__(256) k_tt_chain_vjp(const __grid_constant__ Rh
       for (int b = 0; b < rb; ++b) {
         C acc = c_zero(C{});
         for (int a = 0; a < ra; ++a) {
-          const int v = vid[off + a * rb + b];
-          if (v >= 0) acc = c_add(acc, c_mul(pre[l - 1][a], load(v)));
+          const int j = off + a * rb + b;
+          if (vid[j] >= 0) acc = c_add(acc, c_mul(pre[l - 1][a], load(j)));
         }
         pre[l][b] = acc;
       }
@@ -120,8 +121,8 @@ __global__ void __launch_bounds__(256) k_tt_chain_vjp(const __grid_constant__ Rh
       for (int a = 0; a < ra; ++a) {
         C acc = c_zero(C{});
         for (int b = 0; b < rb; ++b) {
-          const int v = vid[offl[l] + a * rb + b];
-          if (v >= 0) acc = c_add(acc, c_mul(load(v), suf[b]));
+          const int j = offl[l] + a * rb + b;
+          if (vid[j] >= 0) acc = c_add(acc, c_mul(load(j), suf[b]));
         }
         sn[a] = acc;
       }

@@ -75,6 +75,44 @@ def test_tt_rhs_matches_oracle(name, make, sym, prec):
     assert abs(o[0] - o_ref) <= 1e3 * TOL[prec] * flux
 
 
+def _distinct_nonzero_core_vectors(s):
+    """Per order, the bitwise-distinct nonzero vectors over all of its cores."""
+    out, off, rk = [], 0, 0
+    for d in range(2, s.D + 1):
+        r = s.ranks[rk:rk + d + 1]
+        seen = set()
+        for l in range(1, d + 1):
+            for _ in range(r[l - 1] * r[l]):
+                x = s.factors[off:off + s.N]
+                off += s.N
+                if np.any(x != 0):
+                    seen.add(x.tobytes())
+        out.append(len(seen))
+        rk += d + 1
+    return out
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tt_cores_share_vectors_across_cores(prec):
+    # Theorem-1 cores repeat the powers i^mu_j in every core: an order's
+    # identical vectors are transformed once whatever core holds them. N =
+    # 12000 puts the d = 3 rows at 128 points (compile-time TT row kernels in
+    # the double-word paths).
+    s = wl.brownian_tt(3, 12000, [0.4, -0.2, 0.1])
+    want = _distinct_nonzero_core_vectors(s)
+    p_ref, q_ref = oracle.rhs(s.n0, s.D, s.ranks, s.factors, fmt=oracle.TT, mode=oracle.DIRECT)
+    scale = np.abs(p_ref).max() + np.abs(q_ref).max()
+    with plan_of(s, prec) as pl:
+        orders = pl.describe()["orders"]
+        assert [o["transformed"] for o in orders] == want
+        assert want[-1] < sum(s.ranks[3 + l] * s.ranks[4 + l] for l in range(3))  # fewer than the entries
+        if prec != sag.SAG_FP64:
+            assert orders[-1]["M2"] == 128 and orders[-1]["compile_time"][1] == 1
+        p, q, _ = run_parts(pl, s.n0)
+    assert nerr(p, p_ref, scale) < TOL[prec]
+    assert nerr(q, q_ref, scale) < TOL[prec]
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_tt_tiny_matches_brute_force(prec):
     s = wl.brownian_tt(4, 6, [0.3, -0.2, 0.15, 0.05])
