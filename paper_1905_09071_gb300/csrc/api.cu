@@ -844,9 +844,11 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
         if (od.pair)  // rows of 2 M2 points per pair; separation: 2 complex adds per pair and index
           o += (double)od.npair * od.M1 * fft_ops(2 * od.M2, ct_plan(2 * od.M2, true, make_radix_plan(2 * od.M2)), c) +
                (double)od.npair * M * 2 * c.cadd;
-        else
-          o += Vd * od.M1 * fft_ops(od.M2, ct_plan(od.M2, dwp && od.ct2, od.rp2), c)  // forward rows of every vector
-               + Vd * M * unpack;                        // real split
+        else {  // forward rows of every vector; with a slot map (repeated vectors), of each distinct one
+          const double Vr = (dwp && od.ct2 && od.umap_off >= 0) ? (double)od.nu : Vd;
+          o += Vr * od.M1 * fft_ops(od.M2, ct_plan(od.M2, dwp && od.ct2, od.rp2), c)
+               + Vr * M * unpack;                        // real split
+        }
         o += (Vd - od.R) * M * c.cmul                           // product over the modes
              + (double)od.R * M * (c.cadd + (dwp ? c.scale : 0))  // rank sum
              + M * repack + od.M1 * fft_ops(od.M2, ct_plan(od.M2, dwp && od.ct2, od.rp2), c)     // inverse rows

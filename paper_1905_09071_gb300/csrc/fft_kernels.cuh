@@ -562,6 +562,105 @@ __device__ __forceinline__ void rows_body_async(const RhsParams& P, const OrderD
   }
 }
 
+// Row pass of a CP order whose vectors repeat (a slot map, OrderDesc::
+// umap_off >= 0; compile-time P2 = M2 points): block kp transforms the rows
+// {k1a, M1 - k1a} of each distinct spectrum slot once, writing the real
+// spectra 2 A[k] back in place and the Nyquist values to spec_nyq (as the TT
+// row pass does); then it forms S = sum_r w_r prod_m A_{slot(m R + r)} at its
+// points from those rows (its own writes, read back after the barrier), and
+// ends with the inverse row half. The rank terms' d R uses of the spectra cost
+// loads instead of row transforms. Layout: 16 bytes unused (the mbarrier slot
+// of rows_body_async), then 2 G padded transforms; the inverse reuses them as
+// the staged sums (2 P2 + 1) and two padded rows.
+template <class C, int P2>
+__device__ __forceinline__ void rows_body_dup(const RhsParams& P, const OrderDesc& od, int kp,
+                                              unsigned char* smem_raw) {
+  constexpr int G = ct_group(P2), SLOTS = 2 * G, ld = ct_ld(P2, SLOTS);
+  constexpr int PPT = (2 * P2 + kThreads - 1) / kThreads;
+  static_assert(2 * P2 + 1 <= (SLOTS - 2) * ld, "staged sums fit before the inverse rows");
+  C* buf = reinterpret_cast<C*>(smem_raw + 16);
+  const C* tw = static_cast<const C*>(od.twg2);
+  const int d = od.d, R = od.R, M1 = od.M1, M = od.M;
+  const int k1a = kp, k1b = M1 - kp;
+  const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
+  const int NP = nrow * P2;
+  const C* twL = static_cast<const C*>(od.twL);
+  C* spec = static_cast<C*>(P.scratch) + od.scr_off;
+  C* nyq = static_cast<C*>(P.spec_nyq) + od.vbase;
+  for (int q0 = 0; q0 < od.nu; q0 += G) {
+    const int gc = min(G, od.nu - q0);
+    for (int e = threadIdx.x; e < gc * NP; e += kThreads) {
+      const int g = e / NP, p = e - g * NP, row = p / P2, pos = p - row * P2;
+      buf[(2 * g + row) * ld + pad8(pos)] = spec[(int64_t)(q0 + g) * M + (int64_t)(row ? k1b : k1a) * P2 + pos];
+    }
+    __syncthreads();
+    fft_ct<C, P2, SLOTS, kThreads, true>(buf, ld, tw);  // slots without data hold stale values, unused
+    for (int e = threadIdx.x; e < gc * NP; e += kThreads) {
+      const int g = e / NP, p = e - g * NP, row = p / P2, pos = p - row * P2;
+      const int k1 = row ? k1b : k1a;
+      int mrow, mpos;
+      mirror_of(k1, row, pos, M1, P2, mrow, mpos);
+      const C* bg = buf + 2 * g * ld;
+      spec[(int64_t)(q0 + g) * M + (int64_t)k1 * P2 + pos] =
+          unpack2(bg[row * ld + pad8(pos)], bg[mrow * ld + pad8(mpos)], twL[k1 + M1 * pos]);
+      if (k1 == 0 && pos == 0) {
+        const C z0 = bg[0];
+        const C zc = c_conj(z0);
+        nyq[q0 + g] = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));  // 2 A[M]
+      }
+    }
+    __syncthreads();
+  }
+  // Products and rank sum at the block's points, then staged for the inverse.
+  C* sS = buf;
+  C* work = buf + (SLOTS - 2) * ld;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = threadIdx.x + i * kThreads;
+    if (p < NP) {
+      const int row = p / P2, pos = p - row * P2;
+      const int64_t at = (int64_t)(row ? k1b : k1a) * P2 + pos;
+      C S = c_zero(C{});
+      for (int r = 0; r < R; ++r) {
+        C Pr = spec[(int64_t)cp_slot(P, od, r) * M + at];
+        for (int m = 1; m < d; ++m) Pr = c_mul(Pr, spec[(int64_t)cp_slot(P, od, m * R + r) * M + at]);
+        S = c_add(S, rank_weight(Pr, od, r));
+      }
+      sS[p] = S;
+    }
+  }
+  if (kp == 0 && threadIdx.x == 0) {
+    C S = c_zero(C{});
+    for (int r = 0; r < R; ++r) {
+      C Pr = nyq[cp_slot(P, od, r)];
+      for (int m = 1; m < d; ++m) Pr = c_mul(Pr, nyq[cp_slot(P, od, m * R + r)]);
+      S = c_add(S, rank_weight(Pr, od, r));
+    }
+    sS[NP] = S;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / P2, pos = p - row * P2;
+    const int k1 = row ? k1b : k1a;
+    const int k = k1 + M1 * pos;
+    int mrow, mpos;
+    mirror_of(k1, row, pos, M1, P2, mrow, mpos);
+    const C Sk = sS[p];
+    const C Sm = (k == 0) ? sS[NP] : c_conj(sS[mrow * P2 + mpos]);
+    const C zpp = c_add(c_add(Sk, Sm), c_mul_pi(c_mul(c_conj(twL[k]), c_sub(Sk, Sm))));
+    work[row * ld + pad8(pos)] = c_conj(zpp);
+  }
+  __syncthreads();
+  fft_ct<C, P2, 2, kThreads, true>(work, ld, tw);
+  C* dst = static_cast<C*>(P.scratch2) + od.scr2_off;
+  const C* tw4 = static_cast<const C*>(od.tw4);
+  for (int p = threadIdx.x; p < NP; p += kThreads) {
+    const int row = p / P2, j2 = p - row * P2;
+    const int k1 = row ? k1b : k1a;
+    dst[(int64_t)k1 * P2 + j2] = c_mul(work[row * ld + pad8(j2)], tw4[j2 * k1]);
+  }
+}
+
 // Row pass of the pair form (double-word, rows of P2p = 2 M2 points): block
 // kp owns rows {k1, M1 - k1} of every pair's L-geometry transform, which hold
 // every index k = k1 + M1 pos of row k1 together with its mirror L - k. The
@@ -719,7 +818,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ Rh
     rows_body_pair<C, ct_len(KIND - kKindPair)>(P, od, kp, smem_raw);
     return;
   } else if constexpr (KIND >= kKindCt) {
-    rows_body_async<C, ct_len(KIND - kKindCt)>(P, od, kp, smem_raw);
+    if (od.umap_off >= 0) rows_body_dup<C, ct_len(KIND - kKindCt)>(P, od, kp, smem_raw);
+    else rows_body_async<C, ct_len(KIND - kKindCt)>(P, od, kp, smem_raw);
     return;
   } else if constexpr (KIND == kKindRuntime) {
     rows_body<C>(P, od, kp, buf);
@@ -737,6 +837,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_rows(const __grid_constant__ Rh
       default: break;  // the plan sets pair only for these row lengths
     }
     return;
+  }
+  if (od.ct2 && od.umap_off >= 0) {
+    switch (od.M2) {
+      case 64: rows_body_dup<C, 64>(P, od, kp, smem_raw); return;
+      case 128: rows_body_dup<C, 128>(P, od, kp, smem_raw); return;
+      case 256: rows_body_dup<C, 256>(P, od, kp, smem_raw); return;
+      case 512: rows_body_dup<C, 512>(P, od, kp, smem_raw); return;
+      default: break;
+    }
   }
   switch (od.ct2 ? od.M2 : 0) {
     case 64: rows_body_async<C, 64>(P, od, kp, smem_raw); break;
