@@ -27,7 +27,7 @@ cudaError_t enqueue_fft_f64(const RhsParams& P, const LaunchCfg& L, const double
 // belongs to this file's copy of the kernel.
 cudaError_t launch_fwd_col_f64(const RhsParams& P, const LaunchCfg& L, const double* nin, cudaStream_t st,
                                int blocks, int all) {
-  k_fwd_col<cd><<<blocks, kThreads, L.col_smem, st>>>(P, nin, 0, all);
+  if (blocks > 0) k_fwd_col<cd><<<blocks, kThreads, L.col_smem, st>>>(P, nin, 0, all);
   return cudaGetLastError();
 }
 

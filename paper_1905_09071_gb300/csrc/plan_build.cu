@@ -12,6 +12,13 @@
 #include "plan_host.h"
 
 namespace sag {
+
+// A TT order whose cores hold no nonzero vector (a kernel without that
+// order's term) adds nothing to P, and the cotangents of its core entries
+// vanish (every product in the chain has a zero factor): it gets no row,
+// chain, inverse or entry blocks; its P^(d) and entry cotangents are cleared
+// once, when the plan is built.
+static bool idle_order(const OrderDesc& od) { return od.fmt == SAG_TT && od.nvec == 0; }
 namespace {
 
 double factorial(int d) {
@@ -458,8 +465,8 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     pdo += od.N;
     colpre.push_back(colpre.back() + (od.pair ? od.npair * od.ncolblk_p : od.nu * od.ncolblk));
     colpre_all.push_back(colpre_all.back() + od.nvec * od.ncolblk);
-    invpre.push_back(invpre.back() + od.ncolblk);
-    chainpre.push_back(chainpre.back() + (tt ? (od.M + 1 + 255) / 256 : 0));
+    invpre.push_back(invpre.back() + (idle_order(od) ? 0 : od.ncolblk));
+    chainpre.push_back(chainpre.back() + (tt && !idle_order(od) ? (od.M + 1 + 255) / 256 : 0));
     od.nent = 0;
     if (tt)
       for (int l = 1; l <= d; ++l) od.nent += od.ttr[l - 1] * od.ttr[l];
@@ -467,7 +474,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     nent_tot += od.nent;
     od.ent_spec_off = entspec;
     entspec += (int64_t)od.nent * od.M;
-    entpre.push_back(entpre.back() + od.nent * od.ncolblk);
+    entpre.push_back(entpre.back() + (idle_order(od) ? 0 : od.nent * od.ncolblk));
     // Compile-time kernels work in place (one buffer, pass tables in global
     // memory), the generic ones ping-pong and keep the natural table.
     item_col_smem.push_back(od.ct1 ? (size_t)(W * od.ld1) * csize : (size_t)(2 * W * od.ld1 + od.M1) * csize);
@@ -501,7 +508,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   std::stable_sort(rowperm.begin(), rowperm.end(),
                    [&](int a, int b) { return I[a].nvec > I[b].nvec; });
   std::vector<int> rowpre(1, 0);
-  for (int i : rowperm) rowpre.push_back(rowpre.back() + I[i].nrowpair);
+  for (int i : rowperm) rowpre.push_back(rowpre.back() + (idle_order(I[i]) ? 0 : I[i].nrowpair));
   // Epilogue blocks per system; largest vector count per system.
   std::vector<int> epipre(1, 0);
   int maxnv = 1, maxchunk = 1;
@@ -787,9 +794,13 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     P.eexcl = d_eexcl;
     P.entpre = d_entpre;
     P.eoff = d_eoff;
+    // entries of idle orders keep zero cotangents (no kernel writes them)
+    if ((e = cudaMemset(P.gaent, 0, sizeof(double) * (size_t)std::max<int64_t>(cur, 1))) != cudaSuccess)
+      return cuda_fail(e, "memset");
   }
   if ((e = cudaMemset(P.sc, 0, sizeof(SysScalars) * B)) != cudaSuccess ||
-      (e = cudaMemset(P.status, 0, sizeof(unsigned))) != cudaSuccess)
+      (e = cudaMemset(P.status, 0, sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMemset(P.pd, 0, sizeof(double) * (size_t)std::max<int64_t>(pdo, 1))) != cudaSuccess)  // idle orders' P^(d)
     return cuda_fail(e, "memset");
 
   e = setup_common_kernels(L);
@@ -826,7 +837,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   pl->h_nvec.resize(I.size());
   pl->h_work.resize(I.size());
   for (size_t i = 0; i < I.size(); ++i) {
-    pl->h_nrowpair[i] = I[i].nrowpair;
+    pl->h_nrowpair[i] = idle_order(I[i]) ? 0 : I[i].nrowpair;
     pl->h_nvec[i] = I[i].nvec;
     pl->h_work[i] = (double)I[i].nvec * (double)I[i].M;
   }

@@ -9,14 +9,20 @@ namespace sag {
 
 template <class C>
 cudaError_t launch_tt_stage(const RhsParams& P, const LaunchCfg& L, cudaStream_t st, LaunchHook* hook) {
+  // (a plan whose every order is idle has no blocks at all)
   if (hook) hook->mark(KID_ROWS_TT, st);
-  k_rows_tt_fwd<C><<<L.row_blocks, kThreads, L.rowtt_smem, st>>>(P);
+  if (L.row_blocks > 0) k_rows_tt_fwd<C><<<L.row_blocks, kThreads, L.rowtt_smem, st>>>(P);
   if (hook) hook->mark(KID_TT_CHAIN, st);
-  if (P.tt_rmax <= 4) k_tt_chain<C, 4><<<L.chain_blocks, 256, 0, st>>>(P);
-  else if (P.tt_rmax <= 8) k_tt_chain<C, 8><<<L.chain_blocks, 256, 0, st>>>(P);
-  else k_tt_chain<C, 16><<<L.chain_blocks, 256, 0, st>>>(P);
+  if (L.chain_blocks == 0) {
+  } else if (P.tt_rmax <= 4) {
+    k_tt_chain<C, 4><<<L.chain_blocks, 256, 0, st>>>(P);
+  } else if (P.tt_rmax <= 8) {
+    k_tt_chain<C, 8><<<L.chain_blocks, 256, 0, st>>>(P);
+  } else {
+    k_tt_chain<C, 16><<<L.chain_blocks, 256, 0, st>>>(P);
+  }
   if (hook) hook->mark(KID_ROWS_TT_INV, st);
-  k_rows_tt_inv<C><<<L.row_blocks, kThreads, L.rowtt_smem, st>>>(P);
+  if (L.row_blocks > 0) k_rows_tt_inv<C><<<L.row_blocks, kThreads, L.rowtt_smem, st>>>(P);
   return cudaGetLastError();
 }
 

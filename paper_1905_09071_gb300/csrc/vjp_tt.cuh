@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_inv_col_vjp_tt(const __grid_consta
 // and its inverse columns (into gaent).
 template <class C>
 cudaError_t launch_vjp_tt_after_cols(const RhsParams& P, const LaunchCfg& L, const double* g, cudaStream_t st) {
+  if (L.row_blocks == 0) return cudaGetLastError();  // every order idle: no cotangent spectra
   k_rows_tt_fwd<C><<<L.row_blocks, kThreads, L.rowtt_smem, st>>>(P);
   k_gcol<C><<<L.inv_blocks, kThreads, L.vcol_smem, st>>>(P, g);
   k_rows_tt_g<C><<<L.row_blocks, kThreads, L.rowtt_smem, st>>>(P);

@@ -114,6 +114,17 @@ def test_tt_cores_share_vectors_across_cores(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_tt_all_zero_cores_are_rejected(prec):
+    # An order whose cores are all zero is idle (no FFT blocks; the paper
+    # shape's d = 2 order is one); a system whose every order is zero has no
+    # right-hand side to speak of and is refused when the plan is made.
+    N, D, ranks = 3000, 3, [1, 2, 1, 1, 2, 3, 1]
+    f = np.zeros(N * (2 + 2 + 2 + 6 + 3))
+    with pytest.raises(sag.SagError, match="identically zero"):
+        sag.Plan(N, D, ranks, f, fmt=sag.SAG_TT, prec=prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_tt_tiny_matches_brute_force(prec):
     s = wl.brownian_tt(4, 6, [0.3, -0.2, 0.15, 0.05])
     p_ref, q_ref = oracle.rhs(s.n0, s.D, s.ranks, s.factors, fmt=oracle.TT, mode=oracle.BRUTE)
