@@ -274,14 +274,22 @@ __global__ void __launch_bounds__(256) k_vjp_final_tt(const __grid_constant__ Rh
 
 // gn_k = g_k w_k + sum_v U_v(k) (ga_v(k) + sigma_v),
 // gU_v(k) (=|+=) n_k (ga_v(k) + sigma_v) + coef_v g_k n_k.
+// Each 256-size epilogue block splits into kFinSplit blocks of 32 sizes x 8
+// vector groups (a warp: 32 consecutive sizes of one group, every eighth
+// vector); group 0 adds the other groups' partial sums in a fixed order.
+constexpr int kFinSizes = 32, kFinGroups = 8, kFinSplit = 256 / kFinSizes;
 __global__ void __launch_bounds__(256) k_vjp_final(const __grid_constant__ RhsParams P,
                                                    const double* __restrict__ n,
                                                    const double* __restrict__ g, double* gn,
                                                    double* gU, int accumulate) {
   extern __shared__ double fsh[];  // coef, sigma of the system's vectors
-  const int b = find_segment(P.epipre, P.B, blockIdx.x);
+  __shared__ double part[kFinGroups - 1][2][kFinSizes];
+  const int eb = blockIdx.x / kFinSplit, sub = blockIdx.x - eb * kFinSplit;
+  const int b = find_segment(P.epipre, P.B, eb);
   const SysDesc sy = P.sys[b];
   const int nv = sy.vend - sy.vbeg, N = sy.N;
+  const int kbase = (eb - P.epipre[b]) * 256 + sub * kFinSizes;
+  if (kbase >= N) return;  // the whole block
   double* coef = fsh;
   double* sig = fsh + nv;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
@@ -289,24 +297,37 @@ __global__ void __launch_bounds__(256) k_vjp_final(const __grid_constant__ RhsPa
     sig[i] = P.sigma[sy.vbeg + i];
   }
   __syncthreads();
-  const int k = (blockIdx.x - P.epipre[b]) * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  const int64_t gk = sy.noff + k;
-  const double nk = n[gk], gg = g[gk];
-  const int64_t base = P.voff[sy.vbeg] + k;  // a system's vectors are stored back to back
+  const int kl = threadIdx.x % kFinSizes, grp = threadIdx.x / kFinSizes;
+  const int k = kbase + kl;
   double w = 0.0, acc = 0.0;
-  for (int i = 0; i < nv; ++i) {
-    const int64_t o = base + (int64_t)i * N;
-    const double u = P.U64[o];
-    const double ga = P.gabuf[o] + sig[i];
-    w = fma(coef[i], u, w);
-    acc = fma(u, ga, acc);
-    if (gU) {
-      const double val = fma(nk, ga, coef[i] * gg * nk);
-      gU[o] = accumulate ? gU[o] + val : val;
+  if (k < N) {
+    const int64_t gk = sy.noff + k;
+    const double nk = n[gk], gg = g[gk];
+    const int64_t base = P.voff[sy.vbeg] + k;  // a system's vectors are stored back to back
+    for (int i = grp; i < nv; i += kFinGroups) {
+      const int64_t o = base + (int64_t)i * N;
+      const double u = P.U64[o];
+      const double ga = P.gabuf[o] + sig[i];
+      w = fma(coef[i], u, w);
+      acc = fma(u, ga, acc);
+      if (gU) {
+        const double val = fma(nk, ga, coef[i] * gg * nk);
+        gU[o] = accumulate ? gU[o] + val : val;
+      }
     }
   }
-  if (gn) gn[gk] = fma(gg, w, acc);
+  if (grp > 0) {
+    part[grp - 1][0][kl] = w;
+    part[grp - 1][1][kl] = acc;
+  }
+  __syncthreads();
+  if (grp > 0 || k >= N) return;
+  for (int q = 0; q < kFinGroups - 1; ++q) {
+    w += part[q][0][kl];
+    acc += part[q][1][kl];
+  }
+  const int64_t gk = sy.noff + k;
+  if (gn) gn[gk] = fma(g[gk], w, acc);
 }
 
 __global__ void k_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n) {
@@ -338,7 +359,7 @@ cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n,
   if (e != cudaSuccess) return e;
   k_dot2<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, st>>>(P, n, g);
   k_coef_vjp<<<P.B, 256, L.coef_smem, st>>>(P);
-  k_vjp_final<<<L.epi_blocks, 256, L.coef_smem, st>>>(P, n, g, gn, gU, accumulate);
+  k_vjp_final<<<L.epi_blocks * kFinSplit, 256, L.coef_smem, st>>>(P, n, g, gn, gU, accumulate);
   return cudaGetLastError();
 }
 

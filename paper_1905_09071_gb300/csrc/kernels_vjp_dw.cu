@@ -15,7 +15,7 @@ cudaError_t launch_vjp_fft_dw(const RhsParams& P, const LaunchCfg& L, const doub
   cudaError_t e = launch_k_fwd_col_dw(P, L, n, st, 0, L.col_blocks_all, 1, SAG_DW_C{});
   if (e != cudaSuccess) return e;
   k_gcol<SAG_DW_C><<<L.inv_blocks, kThreads, L.vcol_smem, st>>>(P, g);
-  k_rows_vjp<SAG_DW_C><<<L.row_blocks, kThreads, L.vrow_smem, st>>>(P);
+  k_rows_vjp<SAG_DW_C><<<dim3(L.row_blocks, L.vjp_rmax), kThreads, L.vrow_smem, st>>>(P);
   k_inv_col_vjp<SAG_DW_C><<<L.col_blocks_all, kThreads, L.vcol_smem, st>>>(P);
   return cudaGetLastError();
 }

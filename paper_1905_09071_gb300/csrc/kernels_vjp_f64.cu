@@ -13,7 +13,7 @@ cudaError_t launch_vjp_fft_f64(const RhsParams& P, const LaunchCfg& L, const dou
   cudaError_t e = launch_fwd_col_f64(P, L, n, st, L.col_blocks_all, 1);
   if (e != cudaSuccess) return e;
   k_gcol<cd><<<L.inv_blocks, kThreads, L.vcol_smem, st>>>(P, g);
-  k_rows_vjp<cd><<<L.row_blocks, kThreads, L.vrow_smem, st>>>(P);
+  k_rows_vjp<cd><<<dim3(L.row_blocks, L.vjp_rmax), kThreads, L.vrow_smem, st>>>(P);
   k_inv_col_vjp<cd><<<L.col_blocks_all, kThreads, L.vcol_smem, st>>>(P);
   return cudaGetLastError();
 }

@@ -26,6 +26,7 @@ struct LaunchCfg {
   int chain_blocks;
   int ent_blocks;       // TT adjoint: inverse column blocks over every core entry
   int has_tt;           // the plan's systems use TT kernels (one format per plan)
+  int vjp_rmax;         // largest CP rank of an item: the adjoint row pass's grid height
   size_t col_smem, row_smem, inv_smem, epi_smem, coef_smem, rowtt_smem;
   size_t col_smem_kind[kKindCount], row_smem_kind[kKindCount];  // per kernel specialisation
   size_t vcol_smem, vrow_smem;  // vector-Jacobian product kernels (0: not available)

@@ -530,6 +530,8 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   L.row_blocks = rowpre.back();
   L.inv_blocks = invpre.back();
   L.chain_blocks = chainpre.back();
+  L.vjp_rmax = 1;
+  for (const OrderDesc& od : I) L.vjp_rmax = std::max(L.vjp_rmax, od.R);
   L.ent_blocks = entpre.back();
   L.epi_blocks = epipre.back();
   L.has_tt = tt ? 1 : 0;

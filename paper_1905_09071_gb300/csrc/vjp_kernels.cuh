@@ -70,6 +70,10 @@ __global__ void __launch_bounds__(kThreads) k_rows_vjp(const __grid_constant__ R
   const OrderDesc& od = P.ord[P.rowperm[j]];
   const int kp = blockIdx.x - P.rowpre[j];
   const int d = od.d, R = od.R, M1 = od.M1, M2 = od.M2, M = od.M, ld = od.ld2;
+  // One block per (row pair, rank term r = blockIdx.y): the terms' vectors
+  // have slots of their own, and each block forms g's row spectrum again.
+  const int r = blockIdx.y;
+  if (r >= R) return;
   const int k1a = kp, k1b = M1 - kp;
   const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
   const int NP = nrow * M2;
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_vjp(const __grid_constant__ R
   }
   __syncthreads();
 
-  for (int r = 0; r < R; ++r) {
+  {
     // forward rows of the d vectors of rank term r
     for (int e = threadIdx.x; e < d * NP; e += kThreads) {
       const int m = e / NP, p = e - m * NP;
