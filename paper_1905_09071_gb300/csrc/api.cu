@@ -105,11 +105,14 @@ sag_status replay(sag_plan_t pl, const sag_plan_s::GraphKey& k, cudaStream_t st,
 }
 
 sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaStream_t st,
-                        bool allow_hook) {
+                        bool allow_hook, double* nstar = nullptr) {
+  // n* = the first stage's state: the plan's buffer, or the caller's (the
+  // adjoint keeps the stage states of a recomputed segment)
+  double* ns = nstar ? nstar : pl->nstar;
   EpiArgs a{};
   a.nin = n;
   a.k1buf = pl->k1buf;
-  a.out0 = pl->nstar;
+  a.out0 = ns;
   a.dt = dt;
   a.mode = pl->rk == SAG_HEUN ? EPI_HEUN1 : EPI_MID1;
   a.flux = diag != nullptr;  // the outflow is only reported through diag
@@ -119,7 +122,7 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
   sag_status s = eval(pl, n, a, st, allow_hook);
   if (s != SAG_OK) return s;
   EpiArgs b{};
-  b.nin = pl->nstar;
+  b.nin = ns;
   b.nbase = n;
   b.k1buf = pl->k1buf;
   b.diag = diag;
@@ -127,7 +130,7 @@ sag_status enqueue_step(sag_plan_t pl, double* n, double dt, double* diag, cudaS
   b.mode = pl->rk == SAG_HEUN ? EPI_HEUN2 : EPI_MID2;
   b.flux = a.flux;
   b.presplit = pl->P.dwpath;
-  return eval(pl, pl->nstar, b, st, allow_hook);
+  return eval(pl, ns, b, st, allow_hook);
 }
 
 // Operation counts of the double-word arithmetic (FP32 instructions), as
@@ -596,8 +599,9 @@ sag_status sag_integrate_vjp(sag_plan_t pl, const double* n0, double dt, int64_t
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t Nt = (size_t)pl->Ntot;
   const int64_t nck = steps > 0 ? (steps + ckpt - 1) / ckpt : 1;
-  // pool: checkpoints [nck], segment states [ckpt], x, gbar, gk, gA, gB
-  const size_t need = ((size_t)nck + (size_t)ckpt + 5) * Nt;
+  // pool: checkpoints [nck], segment states [ckpt], x, gbar, gk, gA, gB,
+  // the segment's stage states n* [ckpt]
+  const size_t need = ((size_t)nck + 2 * (size_t)ckpt + 5) * Nt;
   cudaError_t e;
   if (pl->vjp_pool_len < need) {
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
@@ -615,6 +619,7 @@ sag_status sag_integrate_vjp(sag_plan_t pl, const double* n0, double dt, int64_t
   double* gk = gbar + Nt;
   double* gA = gk + Nt;
   double* gB = gA + Nt;
+  double* stg = gB + Nt;
   const size_t nb = Nt * sizeof(double);
   const cudaMemcpyKind in_kind = is_device_ptr(n0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   double* gud;
@@ -664,7 +669,7 @@ sag_status sag_integrate_vjp(sag_plan_t pl, const double* n0, double dt, int64_t
           double* nxt = cur + Nt;
           cudaError_t r = cudaMemcpyAsync(nxt, cur, nb, cudaMemcpyDeviceToDevice, cs);
           if (r != cudaSuccess) return cuda_fail(r, "recompute");
-          sag_status q = enqueue_step(pl, nxt, dt, nullptr, cs, false);
+          sag_status q = enqueue_step(pl, nxt, dt, nullptr, cs, false, stg + (size_t)t * Nt);
           if (q != SAG_OK) return q;
         }
         return SAG_OK;
@@ -674,17 +679,23 @@ sag_status sag_integrate_vjp(sag_plan_t pl, const double* n0, double dt, int64_t
     s = phase(5, seg, len, [&](cudaStream_t cs) -> sag_status {
       for (int64_t t = len - 1; t >= 0; --t) {
         double* n = seg + (size_t)t * Nt;
-        EpiArgs a{};
-        a.nin = n;
-        a.k1buf = pl->k1buf;
-        a.out0 = pl->nstar;
-        a.dt = dt;
-        a.mode = heun ? EPI_HEUN1 : EPI_MID1;
-        sag_status q = eval(pl, n, a, cs, false);  // n* of this step
-        if (q != SAG_OK) return q;
+        // n* of this step: kept by the recomputation, except for the
+        // segment's last step, which was not recomputed
+        const double* ns = stg + (size_t)t * Nt;
+        if (t == len - 1) {
+          EpiArgs a{};
+          a.nin = n;
+          a.k1buf = pl->k1buf;
+          a.out0 = pl->nstar;
+          a.dt = dt;
+          a.mode = heun ? EPI_HEUN1 : EPI_MID1;
+          sag_status q = eval(pl, n, a, cs, false);
+          if (q != SAG_OK) return q;
+          ns = pl->nstar;
+        }
         cudaError_t r;
         if ((r = enqueue_axpby(gk, w2, gbar, 0.0, nullptr, (int64_t)Nt, cs)) != cudaSuccess ||
-            (r = enqueue_vjp(pl->P, pl->L, pl->nstar, gk, gA, gud, 1, cs)) != cudaSuccess ||
+            (r = enqueue_vjp(pl->P, pl->L, ns, gk, gA, gud, 1, cs)) != cudaSuccess ||
             (r = enqueue_axpby(gk, w1, gbar, h1, gA, (int64_t)Nt, cs)) != cudaSuccess ||
             (r = enqueue_vjp(pl->P, pl->L, n, gk, gB, gud, 1, cs)) != cudaSuccess ||
             (r = enqueue_axpby(gbar, 1.0, gbar, 1.0, gA, (int64_t)Nt, cs)) != cudaSuccess ||
