@@ -147,7 +147,7 @@ SAG_HD void stockham_bfly(const C* in, C* out, int P, int Ns, int j, const C* tw
   C x[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) x[t] = in[j + t * stride];
-  if constexpr (std::is_same<C, cdw>::value && g_radix<R>()) {
+  if constexpr (std::is_same<C, cdw>::value && g_radix<R>) {
     auto twf = [&](int t) { return tw[t * k * twstep]; };
     if (Ns > 1) g_bfly<R, true>(x, twf);
     else g_bfly<R, false>(x, twf);

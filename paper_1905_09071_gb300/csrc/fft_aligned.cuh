@@ -191,17 +191,21 @@ SAG_HD float g_maxabs(const cdw* x) {
   float m[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) m[t] = f_amax(x[t].rh, x[t].ih);
-  if constexpr (R == 3) return fmaxf(m[0], fmaxf(m[1], m[2]));
-  if constexpr (R == 6) return fmaxf(fmaxf(fmaxf(m[0], m[3]), fmaxf(m[1], m[4])), fmaxf(m[2], m[5]));
+  if constexpr (R == 3) {
+    return fmaxf(m[0], fmaxf(m[1], m[2]));
+  } else if constexpr (R == 6) {
+    return fmaxf(fmaxf(fmaxf(m[0], m[3]), fmaxf(m[1], m[4])), fmaxf(m[2], m[5]));
+  } else {
 #pragma unroll
-  for (int w = R / 2; w >= 1; w /= 2)
+    for (int w = R / 2; w >= 1; w /= 2)
 #pragma unroll
-    for (int t = 0; t < w; ++t) m[t] = fmaxf(m[t], m[t + w]);
-  return m[0];
+      for (int t = 0; t < w; ++t) m[t] = fmaxf(m[t], m[t + w]);
+    return m[0];
+  }
 }
 
 template <int R>
-constexpr bool g_radix() { return R == 2 || R == 3 || R == 4 || R == 6 || R == 8; }
+inline constexpr bool g_radix = R == 2 || R == 3 || R == 4 || R == 6 || R == 8;
 
 // Radix-R butterfly: inputs t >= 1 multiplied by tw(t) when TW, then the DFT,
 // in grid arithmetic.

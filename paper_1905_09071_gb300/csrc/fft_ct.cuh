@@ -190,7 +190,7 @@ SAG_CX bool ct_supported(int P) { return ct_index(P) >= 0; }
 // the grid-aligned arithmetic of fft_aligned.cuh, the others in dw.cuh's.
 template <int R, bool TW, class C, class TWF>
 SAG_HD void ct_bfly(C* x, TWF tw) {
-  if constexpr (std::is_same<C, cdw>::value && g_radix<R>()) {
+  if constexpr (std::is_same<C, cdw>::value && g_radix<R>) {
     g_bfly<R, TW>(x, tw);
   } else {
     if constexpr (TW)

@@ -888,21 +888,21 @@ __device__ __forceinline__ void inv_col_body(const RhsParams& P, const OrderDesc
       if (k >= 1 && k <= N) out[k - 1] = cre(w) * scale;
       if (k + 1 <= N) out[k] = -cim(w) * scale;
     });
-    return;
-  }
-  for (int e = threadIdx.x; e < W * M1; e += kThreads) {
-    const int c = e % W, k1 = e / W;
-    buf[c * ld + k1] = src[(int64_t)k1 * M2 + cb * W + c];
-  }
-  __syncthreads();
-  C* res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
-  for (int e = threadIdx.x; e < W * M1; e += kThreads) {
-    const int c = e % W, j1 = e / W;
-    const int j = M2 * j1 + cb * W + c;
-    const C w = res[c * ld + j1];
-    const int k = 2 * j;  // sizes k (real part) and k + 1 (minus the imaginary part)
-    if (k >= 1 && k <= N) out[k - 1] = cre(w) * scale;
-    if (k + 1 <= N) out[k] = -cim(w) * scale;
+  } else {
+    for (int e = threadIdx.x; e < W * M1; e += kThreads) {
+      const int c = e % W, k1 = e / W;
+      buf[c * ld + k1] = src[(int64_t)k1 * M2 + cb * W + c];
+    }
+    __syncthreads();
+    C* res = fft_batch(buf, buf1, M1, ld, W, od.rp1, tw);
+    for (int e = threadIdx.x; e < W * M1; e += kThreads) {
+      const int c = e % W, j1 = e / W;
+      const int j = M2 * j1 + cb * W + c;
+      const C w = res[c * ld + j1];
+      const int k = 2 * j;  // sizes k (real part) and k + 1 (minus the imaginary part)
+      if (k >= 1 && k <= N) out[k - 1] = cre(w) * scale;
+      if (k + 1 <= N) out[k] = -cim(w) * scale;
+    }
   }
 }
 

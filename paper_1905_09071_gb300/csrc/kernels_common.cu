@@ -42,9 +42,17 @@ __global__ void k_nmax(const __grid_constant__ RhsParams P, const double* __rest
   double m = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.N; k += gridDim.x * blockDim.x)
     m = fmax(m, fabs(x[k]));
+  // one atomic per block (warps, then the block's first warp)
+  __shared__ double wm[32];
   for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.0)
-    atomicMax(&P.sc[blockIdx.y].nmax_bits, (unsigned long long)__double_as_longlong(m));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? wm[threadIdx.x] : 0.0;
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0 && m > 0.0)
+      atomicMax(&P.sc[blockIdx.y].nmax_bits, (unsigned long long)__double_as_longlong(m));
+  }
 }
 
 __global__ void k_nsplit(const __grid_constant__ RhsParams P, const double* __restrict__ n) {

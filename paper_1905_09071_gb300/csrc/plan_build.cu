@@ -524,7 +524,16 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   LaunchCfg& L = pl->L;
   int maxN = 1;
   for (const SysDesc& sd : S) maxN = std::max(maxN, sd.N);
-  L.prep_blocks = std::max(1, std::min(64, (maxN + 255) / 256));
+  // n's max and split: a grid of (blocks, B) with a grid-stride loop; about
+  // four blocks per SM in all, at least 64 per system
+  int nsm = 152;
+  {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      nsm = v;
+  }
+  L.prep_blocks = std::max(1, std::min((maxN + 255) / 256, std::max(64, (4 * nsm + B - 1) / B)));
   L.col_blocks = colpre.back();
   L.col_blocks_all = colpre_all.back();
   L.row_blocks = rowpre.back();

@@ -273,6 +273,39 @@ def test_paper_shape_sampled_parity(fmt, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,m2", [(12000, 128), (50000, 256)])
+def test_repeated_vector_rows_sampled_parity(N, m2, prec):
+    # The Brownian CP kernel repeats its factor vectors (27 vectors, 3
+    # distinct, for d = 3): the row pass transforms each distinct spectrum
+    # once and forms the rank terms from those rows. N = 12000 and 50000 put
+    # the d = 3 rows at 128 and 256 points (the Brownian configuration and the
+    # paper shape cover 64 and 512). A slowly decaying start keeps every size
+    # in play; gain outputs k <= 2048 against the oracle on the size prefix,
+    # every loss output against its inner-product route.
+    b = wl.brownian_cp(3, N)
+    n0 = wl.normalised(np.exp(-wl.sizes(N) / (N / 8)))
+    s = wl.System(3, N, "cp", b.ranks, b.factors, n0)
+    K = 2048
+    ranks_k, f_k = _prefix(s, K)
+    p_pre, _ = oracle.rhs(n0[:K], s.D, ranks_k, f_k, mode=oracle.DIRECT)
+    q_ref = oracle.loss(n0, s.D, s.ranks, s.factors)
+    with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec) as pl:
+        o3 = pl.describe()["orders"][-1]
+        assert o3["transformed"] == 3 and o3["vectors"] == 27
+        if prec != sag.SAG_FP64:
+            assert o3["M2"] == m2 and o3["compile_time"][1] == 1
+        n = dev(n0)
+        p, q = torch.empty_like(n), torch.empty_like(n)
+        pl.rhs_parts(n, p, q)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+        p, q = p.cpu().numpy(), q.cpu().numpy()
+    scale = np.abs(p).max() + np.abs(q_ref).max()
+    assert nerr(p[:K], p_pre, scale) < TOL[prec]
+    assert nerr(q, q_ref, scale) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("kernel", ["constant", "product"])
 def test_full_length_fft_geometric_closed_form(kernel, prec):
     # n_k = A r^(k-1) at N = 65536, D = 4 (FFT lengths 2^17, 3 2^16, 2^18):
