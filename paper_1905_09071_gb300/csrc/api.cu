@@ -566,7 +566,7 @@ sag_status sag_rhs_vjp(sag_plan_t pl, const double* n, const double* g, double* 
       (s = stage(pl, gn, Nt, false, &gnd, &pl->stage_c, &lc, st)) != SAG_OK ||
       (s = stage(pl, gU, (size_t)pl->nfactor, false, &gud, &pl->stage_g, &pl->stage_g_len, st)) != SAG_OK)
     return s;
-  cudaError_t e = enqueue_vjp(pl->P, pl->L, nd, gd, gnd, gud, 0, st);
+  cudaError_t e = enqueue_vjp(pl->P, pl->L, nd, gd, gnd, gud, 0, st, &pl->side);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   bool sync = false;
   if (gn && gnd != gn) {
@@ -695,9 +695,9 @@ sag_status sag_integrate_vjp(sag_plan_t pl, const double* n0, double dt, int64_t
         }
         cudaError_t r;
         if ((r = enqueue_axpby(gk, w2, gbar, 0.0, nullptr, (int64_t)Nt, cs)) != cudaSuccess ||
-            (r = enqueue_vjp(pl->P, pl->L, ns, gk, gA, gud, 1, cs)) != cudaSuccess ||
+            (r = enqueue_vjp(pl->P, pl->L, ns, gk, gA, gud, 1, cs, &pl->side)) != cudaSuccess ||
             (r = enqueue_axpby(gk, w1, gbar, h1, gA, (int64_t)Nt, cs)) != cudaSuccess ||
-            (r = enqueue_vjp(pl->P, pl->L, n, gk, gB, gud, 1, cs)) != cudaSuccess ||
+            (r = enqueue_vjp(pl->P, pl->L, n, gk, gB, gud, 1, cs, &pl->side)) != cudaSuccess ||
             (r = enqueue_axpby(gbar, 1.0, gbar, 1.0, gA, (int64_t)Nt, cs)) != cudaSuccess ||
             (r = enqueue_axpby(gbar, 1.0, gbar, 1.0, gB, (int64_t)Nt, cs)) != cudaSuccess)
           return cuda_fail(r, "adjoint step");

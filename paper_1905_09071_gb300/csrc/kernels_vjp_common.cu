@@ -338,7 +338,7 @@ __global__ void k_axpby(double* out, double a, const double* x, double b, const 
 }  // namespace
 
 cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
-                        double* gn, double* gU, int accumulate, cudaStream_t st) {
+                        double* gn, double* gU, int accumulate, cudaStream_t st, const SideStream* side) {
   cudaError_t e;
   if (P.dwpath) {
     // n and g to double-word with their own power-of-two scales; the max
@@ -347,19 +347,24 @@ cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n,
     k_gmax<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, g);
     k_gsplit<<<dim3(L.prep_blocks, P.B), 256, 0, st>>>(P, g);
   }
-  if (L.has_tt) {
-    e = P.dwpath ? launch_vjp_fft_tt_dw(P, L, n, g, st) : launch_vjp_fft_tt_f64(P, L, n, g, st);
-    if (e != cudaSuccess) return e;
-    k_dot2<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, st>>>(P, n, g);
-    k_coef_vjp_tt<<<P.nitems, 256, 0, st>>>(P);
-    k_vjp_final_tt<<<L.epi_blocks, 256, 0, st>>>(P, n, g, gn, gU, accumulate);
-    return cudaGetLastError();
+  // The inner products and weights of the product rule need only n and g:
+  // on the side stream, beside the FFT kernels, from here on (after the
+  // splits, whose max counters k_coef_vjp clears); the final kernel joins.
+  cudaStream_t ds = side ? side->stream : st;
+  if (side) {
+    if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ds, side->fork, 0)) != cudaSuccess) return e;
   }
-  e = P.dwpath ? launch_vjp_fft_dw(P, L, n, g, st) : launch_vjp_fft_f64(P, L, n, g, st);
+  k_dot2<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, ds>>>(P, n, g);
+  if (L.has_tt) k_coef_vjp_tt<<<P.nitems, 256, 0, ds>>>(P);
+  else k_coef_vjp<<<P.B, 256, L.coef_smem, ds>>>(P);
+  if (side && (e = cudaEventRecord(side->join, ds)) != cudaSuccess) return e;
+  if (L.has_tt) e = P.dwpath ? launch_vjp_fft_tt_dw(P, L, n, g, st) : launch_vjp_fft_tt_f64(P, L, n, g, st);
+  else e = P.dwpath ? launch_vjp_fft_dw(P, L, n, g, st) : launch_vjp_fft_f64(P, L, n, g, st);
   if (e != cudaSuccess) return e;
-  k_dot2<<<dim3(P.Vtot, P.maxdotchunk), 256, 0, st>>>(P, n, g);
-  k_coef_vjp<<<P.B, 256, L.coef_smem, st>>>(P);
-  k_vjp_final<<<L.epi_blocks * kFinSplit, 256, L.coef_smem, st>>>(P, n, g, gn, gU, accumulate);
+  if (side && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return e;
+  if (L.has_tt) k_vjp_final_tt<<<L.epi_blocks, 256, 0, st>>>(P, n, g, gn, gU, accumulate);
+  else k_vjp_final<<<L.epi_blocks * kFinSplit, 256, L.coef_smem, st>>>(P, n, g, gn, gU, accumulate);
   return cudaGetLastError();
 }
 

@@ -174,8 +174,11 @@ cudaError_t setup_common_kernels(const LaunchCfg& L);
 cudaError_t enqueue_nsplit(const RhsParams& P, const LaunchCfg& L, const double* n, cudaStream_t st);
 // Vector-Jacobian product of the CP right-hand side at n for cotangent g:
 // gn = (dF/dn)^T g, gU (vector layout) = (dF/dU)^T g, added to gU if accumulate.
+// With side, the product rule's inner products run on side->stream (forked
+// and joined inside the call).
 cudaError_t enqueue_vjp(const RhsParams& P, const LaunchCfg& L, const double* n, const double* g,
-                        double* gn, double* gU, int accumulate, cudaStream_t st);
+                        double* gn, double* gU, int accumulate, cudaStream_t st,
+                        const SideStream* side = nullptr);
 cudaError_t enqueue_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n,
                           cudaStream_t st);
 // u i^a for i = 1..N by the parametric factors' generator (sag_power_eval).
