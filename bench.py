@@ -80,7 +80,8 @@ def parse():
                     help="per-kernel pass only: K non-graph RK2 steps of the FP32-split path, each "
                          "kernel launched once per right-hand side over every item and timed with "
                          "CUDA events (the launches the roofline figures refer to; for ncu captures); "
-                         "prints the per-kernel table to stderr, no JSON line")
+                         "prints the per-kernel table to stderr, no JSON line (also with --workload "
+                         "paper: both forms)")
     ap.add_argument("--parametric", action="store_true",
                     help="with --kernels: the same kernel as (u, a) pairs (SAG_CP_POWER), its factors "
                          "generated in the forward columns")
@@ -805,6 +806,30 @@ def run_paper(args, world, rank, local):
     N = 1 << 19
     K, W = 100, max(args.warmup, 1)
     tune = 0 if args.no_autotune else 1
+    if args.kernels:
+        # per-kernel pass of both forms (FP32-split): K non-graph RK2 steps each,
+        # inside the NVTX range "sag_kernels" that profilers select
+        for fmt in ("tt", "cp"):
+            s = wl.paper_ternary(N, fmt)
+            pl = sag.Plan(s.N, s.D, s.ranks, s.factors, fmt=sag.SAG_TT if fmt == "tt" else sag.SAG_CP,
+                          prec=sag.SAG_FP32_SPLIT, autotune=tune)
+            n = torch.tensor(s.n0, device="cuda")
+            pl.profile(True)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("sag_kernels")
+            for _ in range(W):
+                pl.rk2_step(n, s.dt)
+            pl.profile_read()
+            for _ in range(args.steps):
+                pl.rk2_step(n, s.dt)
+            prof = pl.profile_read()
+            torch.cuda.nvtx.range_pop()
+            assert pl.sync_status() == sag.SAG_OK
+            print(f"{fmt}: splits", [[o["M1"], o["M2"]] for o in pl.describe()["orders"]], file=sys.stderr)
+            for name, (ms, cnt) in prof.items():
+                print(f"{fmt} {name:14s} {cnt:6d} launches {1e3 * ms / cnt:9.1f} us/launch", file=sys.stderr)
+            pl.close()
+        return
     res = {}
     rhs_at_n0 = {}
     for fmt in ("tt", "cp"):
