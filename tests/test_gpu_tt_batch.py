@@ -113,6 +113,34 @@ def test_tt_cores_share_vectors_across_cores(prec):
     assert nerr(q, q_ref, scale) < TOL[prec]
 
 
+def _tt_prefix(s, K):
+    """The same TT kernel restricted to sizes 1..K (every core vector cut to its
+    first K entries): its gain term equals the full system's at every k <= K."""
+    return s.factors.reshape(-1, s.N)[:, :K].reshape(-1).copy()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tt_rows_at_256_points_sampled_parity(prec):
+    # N = 50000 puts both orders' rows at 256 points. The gain outputs
+    # k <= 2048 against the oracle on the size prefix, every loss output
+    # against the oracle's inner-product route; a slowly decaying start keeps
+    # every size in play.
+    b = wl.brownian_tt(3, 50000, [0.4, -0.2, 0.1])
+    n0 = wl.normalised(np.exp(-wl.sizes(b.N) / (b.N / 8)))
+    K = 2048
+    p_pre, _ = oracle.rhs(n0[:K], b.D, b.ranks, _tt_prefix(b, K), fmt=oracle.TT, mode=oracle.DIRECT)
+    q_ref = oracle.loss(n0, b.D, b.ranks, b.factors, fmt=oracle.TT)
+    with plan_of(b, prec) as pl:
+        orders = pl.describe()["orders"]
+        if prec != sag.SAG_FP64:
+            assert [o["M2"] for o in orders] == [256, 256]
+            assert all(o["compile_time"][1] == 1 for o in orders)
+        p, q, _ = run_parts(pl, n0)
+    scale = np.abs(p).max() + np.abs(q_ref).max()
+    assert nerr(p[:K], p_pre, scale) < TOL[prec]
+    assert nerr(q, q_ref, scale) < TOL[prec]
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_tt_all_zero_cores_are_rejected(prec):
     # An order whose cores are all zero is idle (no FFT blocks; the paper
