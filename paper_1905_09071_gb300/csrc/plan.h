@@ -120,6 +120,7 @@ struct RhsParams {
   int exact;                     // double-word path with plain double-word butterflies (cdwx)
   int64_t Ntot;                  // packed state length
   int tt_rmax;                   // largest TT rank of the plan (chain kernel variant)
+  int vjp_gmerge;                // CP adjoint rows: g's rows join the vectors' transform batch
   long long spin_limit;          // clock cycles a bounded device-side wait may take
   int wait_unmet;                // test of the timeout path: waits target a barrier nothing completes
   int dotchunk;                  // sizes per inner-product chunk

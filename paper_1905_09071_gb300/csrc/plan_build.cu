@@ -387,6 +387,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     return fail(SAG_EINVAL, "m2 needs one entry per order of the plan (" + std::to_string(I.size()) + ")");
   int64_t scr = 0, scr2 = 0, pdo = 0;
   size_t col_smem = 0, row_smem = 0, rowtt_smem = 0;
+  size_t vrow_merged = 0;  // adjoint row blocks with g's rows in the vectors' batch
   std::vector<size_t> item_col_smem, item_row_smem;  // per item: what its column / row blocks need
   std::vector<int> colpre(1, 0), colpre_all(1, 0), invpre(1, 0), chainpre(1, 0);
   std::vector<int> entpre(1, 0);  // TT adjoint: inverse column blocks over the core entries
@@ -501,6 +502,8 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
     pl->L.vcol_smem = std::max(pl->L.vcol_smem, (size_t)(2 * W * od.ld1 + od.M1) * csize);
     pl->L.vrow_smem = std::max(pl->L.vrow_smem, (size_t)(4 * d * od.ld2 + (d + 1) * (2 * od.M2 + 1) +
                                                          od.M2) * csize);
+    vrow_merged = std::max(vrow_merged, (size_t)(4 * (d + 1) * od.ld2 + (d + 1) * (2 * od.M2 + 1) +
+                                                 od.M2) * csize);  // g's rows in the vectors' batch
   }
   // Row blocks: items with the most vectors first.
   std::vector<int> rowperm(I.size());
@@ -539,6 +542,9 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   L.row_blocks = rowpre.back();
   L.inv_blocks = invpre.back();
   L.chain_blocks = chainpre.back();
+  // The adjoint rows transform g with the vectors when d + 1 slots fit.
+  P.vjp_gmerge = (!tt && vrow_merged > 0 && (int)vrow_merged <= smem_limit()) ? 1 : 0;
+  if (P.vjp_gmerge) L.vrow_smem = vrow_merged;
   L.vjp_rmax = 1;
   for (const OrderDesc& od : I) L.vjp_rmax = std::max(L.vjp_rmax, od.R);
   L.ent_blocks = entpre.back();

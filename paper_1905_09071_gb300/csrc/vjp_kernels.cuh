@@ -78,10 +78,14 @@ __global__ void __launch_bounds__(kThreads) k_rows_vjp(const __grid_constant__ R
   const int nrow = (kp == 0 || 2 * kp == M1) ? 1 : 2;
   const int NP = nrow * M2;
   const int NS = 2 * M2 + 1;  // spectrum slots per vector (positions and the Nyquist value)
+  // With RhsParams::vjp_gmerge, g's rows are transformed in the same batch as
+  // the term's d vectors (slot 0, one load and one transform phase fewer);
+  // the plan sets it when the d + 1 slots fit the shared memory.
+  const int gm = P.vjp_gmerge, nb = d + gm;
   C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + d * 2 * ld;
-  C* Gs = buf1 + d * 2 * ld;
-  C* A = Gs + NS;
+  C* buf1 = buf0 + nb * 2 * ld;
+  C* Gs = buf1 + nb * 2 * ld;
+  C* A = Gs + NS;  // Gs and the d spectra A_m, NS apart
   C* tw = A + d * NS;
   const C* tw2 = static_cast<const C*>(od.tw2);
   const C* twL = static_cast<const C*>(od.twL);
@@ -90,52 +94,56 @@ __global__ void __launch_bounds__(kThreads) k_rows_vjp(const __grid_constant__ R
   const C* gsrc = static_cast<const C*>(P.scratch2) + od.scr2_off;
   const bool nyq = kp == 0;
   for (int i = threadIdx.x; i < M2; i += kThreads) tw[i] = tw2[i];
-
-  // Spectrum of g at the block's positions.
-  for (int p = threadIdx.x; p < NP; p += kThreads) {
-    const int row = p / M2, pos = p - row * M2;
-    buf0[row * ld + pos] = gsrc[(int64_t)(row ? k1b : k1a) * M2 + pos];
-  }
-  __syncthreads();
-  C* res = fft_batch(buf0, buf1, M2, ld, nrow, od.rp2, tw);
-  for (int p = threadIdx.x; p < NP; p += kThreads) {
-    const int row = p / M2, pos = p - row * M2;
-    const int k1 = row ? k1b : k1a;
-    int mrow, mpos;
-    mirror_of(k1, row, pos, M1, M2, mrow, mpos);
-    Gs[p] = unpack2(res[row * ld + pos], res[mrow * ld + mpos], twL[k1 + M1 * pos]);
-  }
-  if (nyq && threadIdx.x == 0) {
-    const C z0 = res[0];
-    const C zc = c_conj(z0);
-    Gs[NP] = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));
-  }
-  __syncthreads();
-
-  {
-    // forward rows of the d vectors of rank term r
-    for (int e = threadIdx.x; e < d * NP; e += kThreads) {
-      const int m = e / NP, p = e - m * NP;
+  C* res;
+  if (!gm) {
+    // Spectrum of g at the block's positions.
+    for (int p = threadIdx.x; p < NP; p += kThreads) {
       const int row = p / M2, pos = p - row * M2;
-      buf0[(m * nrow + row) * ld + pos] =
-          vec[(int64_t)(m * R + r) * M + (int64_t)(row ? k1b : k1a) * M2 + pos];
+      buf0[row * ld + pos] = gsrc[(int64_t)(row ? k1b : k1a) * M2 + pos];
     }
     __syncthreads();
-    res = fft_batch(buf0, buf1, M2, ld, d * nrow, od.rp2, tw);
-    for (int e = threadIdx.x; e < d * NP; e += kThreads) {
+    res = fft_batch(buf0, buf1, M2, ld, nrow, od.rp2, tw);
+    for (int p = threadIdx.x; p < NP; p += kThreads) {
+      const int row = p / M2, pos = p - row * M2;
+      const int k1 = row ? k1b : k1a;
+      int mrow, mpos;
+      mirror_of(k1, row, pos, M1, M2, mrow, mpos);
+      Gs[p] = unpack2(res[row * ld + pos], res[mrow * ld + mpos], twL[k1 + M1 * pos]);
+    }
+    if (nyq && threadIdx.x == 0) {
+      const C z0 = res[0];
+      const C zc = c_conj(z0);
+      Gs[NP] = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));
+    }
+    __syncthreads();
+  }
+
+  {
+    // forward rows of the d vectors of rank term r (after g's, slot 0, when merged)
+    for (int e = threadIdx.x; e < nb * NP; e += kThreads) {
+      const int m = e / NP, p = e - m * NP;
+      const int row = p / M2, pos = p - row * M2;
+      const int k1 = row ? k1b : k1a;
+      buf0[(m * nrow + row) * ld + pos] =
+          (gm && m == 0) ? gsrc[(int64_t)k1 * M2 + pos] : vec[(int64_t)((m - gm) * R + r) * M + (int64_t)k1 * M2 + pos];
+    }
+    __syncthreads();
+    res = fft_batch(buf0, buf1, M2, ld, nb * nrow, od.rp2, tw);
+    C* Sp = gm ? Gs : A;  // spectrum m of the batch goes to Sp + m NS
+    for (int e = threadIdx.x; e < nb * NP; e += kThreads) {
       const int m = e / NP, p = e - m * NP;
       const int row = p / M2, pos = p - row * M2;
       const int k1 = row ? k1b : k1a;
       int mrow, mpos;
       mirror_of(k1, row, pos, M1, M2, mrow, mpos);
-      A[m * NS + p] = unpack2(res[(m * nrow + row) * ld + pos], res[(m * nrow + mrow) * ld + mpos],
-                              twL[k1 + M1 * pos]);
+      Sp[m * NS + p] = unpack2(res[(m * nrow + row) * ld + pos], res[(m * nrow + mrow) * ld + mpos],
+                               twL[k1 + M1 * pos]);
     }
-    if (nyq && threadIdx.x < d) {
+    if (nyq && threadIdx.x < nb) {
       const int m = threadIdx.x;
       const C z0 = res[(m * nrow) * ld];
       const C zc = c_conj(z0);
-      A[m * NS + NP] = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));
+      Sp[m * NS + NP] = c_add(c_add(z0, zc), c_mul_pi(c_sub(z0, zc)));
     }
     __syncthreads();
     // H_m = G conj(prod_{m' != m} A_m'), by prefix and suffix products
