@@ -135,6 +135,12 @@ typedef struct {
                             splits an autotuned plan reports, without tuning again;
                             it replaces max_m2 and the split search. */
   int32_t n_m2;          /* entries of m2: the plan's order count, else SAG_EINVAL */
+  int32_t keep_repeats;  /* 0 (default): bitwise-identical factor vectors of a CP order are
+                            transformed once (the Brownian kernel's permutations repeat
+                            vectors). Such a plan refuses a factor update
+                            (sag_plan_update_factors) that makes vectors that were
+                            identical at plan time differ. 1: every vector is treated
+                            as distinct, for plans whose factors will change (fitting). */
 } sag_options;
 
 /* Fills *opt with the defaults. */
@@ -219,13 +225,16 @@ sag_status sag_rhs_vjp(sag_plan_t plan, const double* n, const double* g, double
  * cotangent of n0 to g_n0 and the factors' cotangent, summed over the steps,
  * to g_U (either may be NULL). The forward states are recomputed from
  * checkpoints every `ckpt` steps (ckpt <= 0: about sqrt(steps)); device memory
- * for (steps/ckpt + ckpt + 5) state vectors is allocated on first use. */
+ * for (steps/ckpt + 2 ckpt + 5) state vectors (checkpoints, a segment's states
+ * and stage states, work vectors) is allocated on first use. */
 sag_status sag_integrate_vjp(sag_plan_t plan, const double* n0, double dt, int64_t steps, int64_t ckpt,
                              const double* g_final, double* g_n0, double* g_U, void* stream);
 
 /* Replaces the factors of a CP plan (same systems and ranks; vector layout as
  * above, host or device pointer) without allocating, so captured graphs stay
- * valid. Synchronises the device first. */
+ * valid. Synchronises the device first. SAG_EINVAL if the new factors make
+ * vectors differ that were bitwise identical when the plan was made (and so
+ * share one transform); build such plans with keep_repeats = 1. */
 sag_status sag_plan_update_factors(sag_plan_t plan, const double* factors, int32_t on_device);
 
 /* Number of factor values of the plan's systems in their factor layout (the

@@ -5,6 +5,9 @@ RK2 steps from n0 with the CP factors ``factors`` (a trainable tensor, any
 float dtype, in the plan's vector layout). The backward pass calls the
 library's checkpointed discrete adjoint (sag_integrate_vjp); nothing is
 differentiated by PyTorch itself. Gradients come back in the factors' dtype.
+The plan takes each call's factors by sag_plan_update_factors: build it with
+``keep_repeats=1`` when factor vectors that start out identical (the Brownian
+kernel's) will be trained apart.
 """
 from __future__ import annotations
 

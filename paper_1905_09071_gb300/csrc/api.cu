@@ -250,6 +250,7 @@ void sag_default_options(sag_options* opt) {
   opt->max_m2 = 0;
   opt->m2 = nullptr;
   opt->n_m2 = 0;
+  opt->keep_repeats = 0;
 }
 
 const char* sag_last_error(void) { return g_err.c_str(); }

@@ -179,6 +179,7 @@ sag_status validate_systems(const sag_system* sys, int32_t B, const sag_options&
   if (opt.rk != SAG_HEUN && opt.rk != SAG_MIDPOINT) return fail(SAG_EINVAL, "unknown RK2 variant");
   if (opt.symmetrize_q != 0 && opt.symmetrize_q != 1) return fail(SAG_EINVAL, "symmetrize_q must be 0 or 1");
   if (opt.autotune != 0 && opt.autotune != 1) return fail(SAG_EINVAL, "autotune must be 0 or 1");
+  if (opt.keep_repeats != 0 && opt.keep_repeats != 1) return fail(SAG_EINVAL, "keep_repeats must be 0 or 1");
   if (opt.max_m2 != 0 && (opt.max_m2 < 4 || opt.max_m2 > 512 || (opt.max_m2 & (opt.max_m2 - 1)) != 0))
     return fail(SAG_EINVAL, "max_m2 must be 0 or a power of two in [4, 512]");
   if ((opt.m2 == nullptr) != (opt.n_m2 == 0) || opt.n_m2 < 0)
@@ -308,11 +309,12 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
           const unsigned char* bytes = reinterpret_cast<const unsigned char*>(x);
           for (size_t k = 0; k < (size_t)N * sizeof(double); ++k) h = (h ^ bytes[k]) * 1099511628211ull;
           int found = -1;
-          for (int u : seen[h])
-            if (std::memcmp(x, src.data() + soff + (int64_t)ul[u] * N, (size_t)N * sizeof(double)) == 0) {
-              found = u;
-              break;
-            }
+          if (!opt.keep_repeats)  // else every vector is its own slot (its factors may change)
+            for (int u : seen[h])
+              if (std::memcmp(x, src.data() + soff + (int64_t)ul[u] * N, (size_t)N * sizeof(double)) == 0) {
+                found = u;
+                break;
+              }
           if (found < 0) {
             found = (int)ul.size();
             ul.push_back(v);
@@ -746,6 +748,8 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       pl->upload(&d_voff, voff) != cudaSuccess || pl->upload(&d_vw, ewt) != cudaSuccess ||
       pl->upload(&d_vdwoff, vdwoff) != cudaSuccess)
     return fail(SAG_ENOMEM, "cudaMalloc tables");
+  pl->h_umap = umap;  // for the checks of sag_plan_update_factors
+  pl->h_ulist = ulist;
   P.ord = d_ord;
   P.sys = d_sys;
   P.colpre = d_colpre;
@@ -1184,6 +1188,23 @@ sag_status update_factors(sag_plan_s* pl, const double* factors, int on_device) 
   if (e != cudaSuccess) return cuda_fail(e, "copy factors");
   for (double x : hf)
     if (!std::isfinite(x)) return fail(SAG_EINVAL, "factors contain Inf or NaN");
+  {
+    // Vectors that share a transform (bitwise identical at plan time) must
+    // stay identical: the forward pass transforms only the first of them.
+    std::vector<int64_t> vo(Vtot);
+    if ((e = cudaMemcpy(vo.data(), P.voff, sizeof(int64_t) * Vtot, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "read layout");
+    for (const OrderDesc& od : pl->items) {
+      if (od.umap_off < 0) continue;
+      for (int q = 0; q < od.nvec; ++q) {
+        const int rep = pl->h_ulist[od.umap_off + pl->h_umap[od.umap_off + q]];
+        if (rep != q && std::memcmp(hf.data() + vo[od.vbase + q], hf.data() + vo[od.vbase + rep],
+                                    (size_t)od.N * sizeof(double)) != 0)
+          return fail(SAG_EINVAL, "the new factors make vectors differ that were identical when the plan was "
+                                  "made (they share one transform); build the plan with keep_repeats = 1");
+      }
+    }
+  }
   if ((e = cudaMemcpy((void*)P.U64, hf.data(), nf * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "upload factors");
   std::vector<int> ev(Vtot, 0);

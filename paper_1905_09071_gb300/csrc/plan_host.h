@@ -64,6 +64,7 @@ struct sag_plan_s {
   std::vector<int> h_colpre_all, h_rowpre, h_rowperm;
   std::vector<int> h_colkind, h_colkind_all, h_rowkind;  // kernel specialisations (LaunchCfg)
   std::vector<int> h_nrowpair;
+  std::vector<int> h_umap, h_ulist;  // CP slot maps of repeated vectors (host copies)
   std::vector<double> h_work;             // FFT points per item, for balancing groups
   std::vector<int> h_nvec;                // vectors per item (row blocks go heaviest first)
   // SAG_CP_POWER plans: (u, a) of every vector in vector order; the forward

@@ -52,7 +52,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("rk", ctypes.c_int32),
                 ("symmetrize_q", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("max_m2", ctypes.c_int32), ("m2", ctypes.POINTER(ctypes.c_int32)),
-                ("n_m2", ctypes.c_int32)]
+                ("n_m2", ctypes.c_int32), ("keep_repeats", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -170,7 +170,8 @@ def default_options() -> dict:
     o = _Options()
     load().sag_default_options(ctypes.byref(o))
     return {"prec": o.prec, "rk": o.rk, "symmetrize_q": o.symmetrize_q, "autotune": o.autotune,
-            "max_m2": o.max_m2, "m2": None if not o.m2 else list(o.m2[:o.n_m2])}
+            "max_m2": o.max_m2, "m2": None if not o.m2 else list(o.m2[:o.n_m2]),
+            "keep_repeats": o.keep_repeats}
 
 
 class Plan:
@@ -181,7 +182,7 @@ class Plan:
 
     def __init__(self, N: int, D: int, ranks, factors, *, fmt: int = SAG_CP,
                  prec: int = SAG_FP32_SPLIT, rk: int = SAG_HEUN, symmetrize_q: int = 1,
-                 autotune: int = 0, max_m2: int = 0, m2=None, _systems=None):
+                 autotune: int = 0, max_m2: int = 0, m2=None, keep_repeats: int = 0, _systems=None):
         lib = load()
         systems = _systems if _systems is not None else [(N, D, ranks, factors, fmt)]
         self.B = len(systems)
@@ -203,6 +204,7 @@ class Plan:
             arr[b] = _System(int(Nb), int(Db), int(fmtb),
                              r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(fb), on_dev)
         opt = _Options(int(prec), int(rk), int(symmetrize_q), int(autotune), int(max_m2))
+        opt.keep_repeats = int(keep_repeats)
         if m2 is not None:  # M2 per order, e.g. [o["M2"] for o in plan.describe()["orders"]]
             m2a = np.ascontiguousarray(np.asarray(m2, dtype=np.int32))
             self._keep.append(m2a)
@@ -216,10 +218,11 @@ class Plan:
 
     @classmethod
     def batch(cls, systems, *, prec: int = SAG_FP32_SPLIT, rk: int = SAG_HEUN,
-              symmetrize_q: int = 1, autotune: int = 0, max_m2: int = 0, m2=None):
+              symmetrize_q: int = 1, autotune: int = 0, max_m2: int = 0, m2=None, keep_repeats: int = 0):
         """systems: list of (N, D, ranks, factors, fmt); one plan, one launch per kernel."""
         return cls(0, 0, None, None, prec=prec, rk=rk, symmetrize_q=symmetrize_q,
-                   autotune=autotune, max_m2=max_m2, m2=m2, _systems=list(systems))
+                   autotune=autotune, max_m2=max_m2, m2=m2, keep_repeats=keep_repeats,
+                   _systems=list(systems))
 
     @property
     def handle(self):

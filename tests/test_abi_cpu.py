@@ -57,7 +57,8 @@ def test_library_exports_every_declared_function(lib):
 def test_version_and_defaults(lib):
     assert b"sm_103a" in lib.sag_version()
     assert sag.default_options() == {"prec": sag.SAG_FP32_SPLIT, "rk": sag.SAG_HEUN,
-                                     "symmetrize_q": 1, "autotune": 0, "max_m2": 0, "m2": None}
+                                     "symmetrize_q": 1, "autotune": 0, "max_m2": 0, "m2": None,
+                                     "keep_repeats": 0}
 
 
 def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=True, out=True):
@@ -92,6 +93,7 @@ def _plan_status(N=8, D=3, ranks=(2, 2), fmt=sag.SAG_CP, B=1, opt=None, factors=
     (dict(opt=(1, 0, 1, 0, 1024)), sag.SAG_EINVAL),
     (dict(opt=(1, 0, 1, 0, -4)), sag.SAG_EINVAL),
     (dict(opt=(1, 0, 1, 0, 0, None, 2)), sag.SAG_EINVAL),  # n_m2 without m2
+    (dict(opt=(1, 0, 1, 0, 0, None, 0, 2)), sag.SAG_EINVAL),  # keep_repeats is 0 or 1
 ])
 def test_plan_rejects_bad_arguments(kw, status):
     st, msg = _plan_status(**kw)

@@ -273,6 +273,38 @@ def test_paper_shape_sampled_parity(fmt, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_factor_update_that_separates_repeated_vectors(prec):
+    # The Brownian CP kernel repeats vectors (the ones vector in many terms).
+    # A plan that shares their transforms refuses new factors that make them
+    # differ and keeps its old ones; a plan made with keep_repeats = 1
+    # transforms every vector and takes the update.
+    s = wl.brownian_cp(3, 500)
+    f2 = s.factors.copy()
+    f2[:s.N] *= 1.0 + 1e-3 * wl.sizes(s.N) / s.N  # order 2, mode 0, term 0: a ones vector
+    p_old, q_old = oracle.rhs(s.n0, s.D, s.ranks, s.factors, mode=oracle.DIRECT)
+    p_new, q_new = oracle.rhs(s.n0, s.D, s.ranks, f2, mode=oracle.DIRECT)
+    for keep, f_ref in ((0, (p_old, q_old)), (1, (p_new, q_new))):
+        with sag.Plan(s.N, s.D, s.ranks, s.factors, prec=prec, keep_repeats=keep) as pl:
+            o = pl.describe()["orders"]
+            assert all((x["transformed"] == x["vectors"]) == bool(keep) for x in o)
+            if keep:
+                pl.update_factors(f2)
+            else:
+                with pytest.raises(sag.SagError, match="keep_repeats"):
+                    pl.update_factors(f2)
+            n = dev(s.n0)
+            p, q = torch.empty_like(n), torch.empty_like(n)
+            pl.rhs_parts(n, p, q)
+            torch.cuda.synchronize()
+            assert pl.sync_status() == sag.SAG_OK
+        scale = np.abs(f_ref[0]).max() + np.abs(f_ref[1]).max()
+        assert nerr(p.cpu().numpy(), f_ref[0], scale) < TOL[prec]
+        assert nerr(q.cpu().numpy(), f_ref[1], scale) < TOL[prec]
+    with pytest.raises(sag.SagError):
+        sag.Plan(s.N, s.D, s.ranks, s.factors, keep_repeats=2)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("N,m2", [(12000, 128), (50000, 256)])
 def test_repeated_vector_rows_sampled_parity(N, m2, prec):
     # The Brownian CP kernel repeats its factor vectors (27 vectors, 3
