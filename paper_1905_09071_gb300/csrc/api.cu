@@ -818,8 +818,11 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
   const double load_mul = dwp ? 4.0 : 1.0;  // a = U n: dw_mul or one FP64 multiply
   double o = 0.0, b = 0.0;
   int fp64 = dwp ? 0 : 1;
-  double factor_elems = 0.0;  // sum over vectors of their length
-  for (const SysDesc& s : pl->systems) factor_elems += (double)(s.vend - s.vbeg) * s.N;
+  double factor_elems = 0.0, distinct_elems = 0.0;  // sum over vectors (distinct vectors) of their length
+  for (const SysDesc& s : pl->systems) {
+    factor_elems += (double)(s.vend - s.vbeg) * s.N;
+    distinct_elems += (double)(s.dend - s.dbeg) * s.N;
+  }
   switch (id) {
     case KID_NMAX:
       o = 2 * Nt;
@@ -833,8 +836,8 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
       break;
     case KID_DOT:  // one FP64 FMA (acc += u n) per factor element; the outflow's t = <k U, n>
                    // adds a second only when it is asked for (not counted here)
-      o = factor_elems;
-      b = 8 * factor_elems + 8 * Nt;
+      o = distinct_elems;  // repeated vectors: once per set
+      b = 8 * distinct_elems + 8 * Nt;
       fp64 = 1;
       break;
     case KID_COEF:
@@ -885,8 +888,8 @@ sag_status sag_kernel_work(sag_plan_t pl, int32_t id, double* ops, int32_t* ops_
       for (const OrderDesc& od : pl->items) b += 8.0 * od.N;  // P^(d) written
       break;
     case KID_QTERM:  // q = n (sum_v coef_v U_v(k))
-      o = factor_elems + Nt;
-      b = 8 * factor_elems + 2 * 8 * Nt;
+      o = distinct_elems + Nt;
+      b = 8 * distinct_elems + 2 * 8 * Nt;
       fp64 = 1;
       break;
     case KID_EPILOGUE:  // rhs = p + q; stage update; moments

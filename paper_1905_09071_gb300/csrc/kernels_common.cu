@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ RhsParams P
                                              const double* __restrict__ n, int flux) {
   __shared__ double sh[64];
   const int v = blockIdx.x, c = blockIdx.y;
+  if (P.vrep[v] != v) return;  // a repeated vector: the first of its set has the sums
   const SysDesc s = P.sys[P.vsys[v]];
   if (c >= s.ndotchunk) return;
   const int k0 = c * P.dotchunk, k1 = min(s.N, k0 + P.dotchunk);
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
   double* s = csh;
   double* t = csh + nv;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    const int64_t base = (int64_t)(sy.vbeg + i) * P.maxdotchunk;
+    const int64_t base = (int64_t)P.vrep[sy.vbeg + i] * P.maxdotchunk;  // repeats: the first's sums
     double a = 0.0, c2 = 0.0;
     for (int c = 0; c < nc; ++c) {
       a += P.dot_s[base + c];
@@ -221,15 +222,40 @@ __global__ void __launch_bounds__(256) k_coef(const __grid_constant__ RhsParams 
 // only the loss weights, so it runs on the side branch beside the FFT kernels.
 __global__ void __launch_bounds__(256) k_qterm(const __grid_constant__ RhsParams P,
                                                const double* __restrict__ nin) {
-  extern __shared__ double esh[];  // [vectors of the system] coef
+  extern __shared__ double esh[];  // [vectors of the system] coef, then folded weights
   const int b = find_segment(P.epipre, P.B, blockIdx.x);
   const SysDesc sy = P.sys[b];
   const int blk = blockIdx.x - P.epipre[b];
-  const int nv = sy.vend - sy.vbeg, N = sy.N;
+  const int nv = sy.vend - sy.vbeg, N = sy.N, nd = sy.dend - sy.dbeg;
   double* coef = esh;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) coef[i] = P.coef[sy.vbeg + i];
   __syncthreads();
   const int k = blk * blockDim.x + threadIdx.x;
+  if (nd < nv) {
+    // Repeated vectors: the weights of each set added (in vector order) onto
+    // its first vector, then one pass over the distinct vectors.
+    double* wsum = esh + nv;
+    for (int j = threadIdx.x; j < nd; j += blockDim.x) {
+      const int u = P.vdist[sy.dbeg + j];
+      double a = 0.0;
+      for (int i = 0; i < nv; ++i)
+        if (P.vrep[sy.vbeg + i] == u) a += coef[i];
+      wsum[j] = a;
+    }
+    __syncthreads();
+    if (k >= N) return;
+    const double* Ub = P.U64 + P.voff[sy.vbeg] + k;  // a system's vectors are back to back
+    double w0 = 0.0, w1 = 0.0;
+    int j = 0;
+    for (; j + 1 < nd; j += 2) {
+      w0 = fma(wsum[j], Ub[(int64_t)(P.vdist[sy.dbeg + j] - sy.vbeg) * N], w0);
+      w1 = fma(wsum[j + 1], Ub[(int64_t)(P.vdist[sy.dbeg + j + 1] - sy.vbeg) * N], w1);
+    }
+    if (j < nd) w0 = fma(wsum[j], Ub[(int64_t)(P.vdist[sy.dbeg + j] - sy.vbeg) * N], w0);
+    const int64_t g = sy.noff + k;
+    P.qbuf[g] = nin[g] * (w0 + w1);
+    return;
+  }
   if (k >= N) return;
   // A system's vectors are stored back to back, N sizes each.
   const double* Ub = P.U64 + P.voff[sy.vbeg] + k;

@@ -84,6 +84,7 @@ struct SysDesc {
   int64_t noff;        // packed offset of size 1
   int64_t ndwoff;      // offset of its double-word n (element index = size)
   int vbeg, vend;      // its global vectors
+  int dbeg, dend;      // its distinct vectors (the first of each repeated set) in RhsParams::vdist
   int ibeg, iend;      // its items (orders)
   int ndotchunk;       // inner-product chunks per vector
   int epi_beg, epi_blocks;  // its epilogue blocks
@@ -132,6 +133,8 @@ struct RhsParams {
   const int* colpre_all;         // [nitems + 1] column blocks over every vector (nvec per item; the adjoint)
   const int* umap;               // CP items with duplicates: spectrum slot of vector m R + r (d R entries)
   const int* ulist;              // the same items: vector (m R + r) transformed into slot u (nu entries)
+  const int* vrep;               // [Vtot] the first vector bitwise identical to v in v's order (v if unique)
+  const int* vdist;              // every system's distinct vectors (vrep[v] == v), SysDesc::dbeg..dend
   const int* rowpre;             // [nitems + 1] row kernel blocks, in rowperm order
   const int* invpre;             // [nitems + 1] inverse column kernel blocks
   const int* chainpre;           // [nitems + 1] TT chain kernel blocks

@@ -383,6 +383,19 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   P.nitems = (int)I.size();
   const int Vtot = P.Vtot;
   if (Vtot == 0) return fail(SAG_EINVAL, "every kernel is identically zero");
+  // Repeated vectors (the slot maps of CP orders): the loss term's inner
+  // products and factor passes use one vector of each repeated set.
+  std::vector<int> vrep(Vtot), vdist;
+  for (int v = 0; v < Vtot; ++v) vrep[v] = v;
+  for (const OrderDesc& od : I)
+    if (od.fmt == SAG_CP && od.umap_off >= 0)
+      for (int q = 0; q < od.nvec; ++q) vrep[od.vbase + q] = od.vbase + ulist[od.umap_off + umap[od.umap_off + q]];
+  for (SysDesc& sd : S) {
+    sd.dbeg = (int)vdist.size();
+    for (int v = sd.vbeg; v < sd.vend; ++v)
+      if (vrep[v] == v) vdist.push_back(v);
+    sd.dend = (int)vdist.size();
+  }
 
   // ---- FFT geometry of each item ------------------------------------------
   if (opt.m2 && opt.n_m2 != (int)I.size())
@@ -576,7 +589,7 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   L.col_smem_kind[kKindGeneral] = col_smem;
   L.row_smem_kind[kKindGeneral] = row_smem;
   L.rowtt_smem = rowtt_smem;
-  L.epi_smem = (size_t)maxnv * sizeof(double);
+  L.epi_smem = (size_t)2 * maxnv * sizeof(double);  // k_qterm: weights, and the folded ones of repeats
   L.coef_smem = (size_t)2 * maxnv * sizeof(double);
   if (col_smem > 227 * 1024 || row_smem > 227 * 1024 || rowtt_smem > 227 * 1024 ||
       L.coef_smem > 200 * 1024)
@@ -737,6 +750,8 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
   int64_t* d_voff = nullptr;
   int64_t* d_vdwoff = nullptr;
   float* d_vw = nullptr;
+  int* d_vrep = nullptr;
+  int* d_vdist = nullptr;
   if (pl->upload(&d_ord, I) != cudaSuccess || pl->upload(&d_sys, S) != cudaSuccess ||
       pl->upload(&d_colpre, colpre_t) != cudaSuccess || pl->upload(&d_colperm, colperm) != cudaSuccess ||
       pl->upload(&d_rowpre, rowpre) != cudaSuccess ||
@@ -746,8 +761,11 @@ sag_status build_plan(const sag_system* sys, int32_t B, const sag_options& opt, 
       pl->upload(&d_epipre, epipre) != cudaSuccess || pl->upload(&d_vsys, vsys) != cudaSuccess ||
       pl->upload(&d_rowperm, rowperm) != cudaSuccess || pl->upload(&d_vid, vid) != cudaSuccess ||
       pl->upload(&d_voff, voff) != cudaSuccess || pl->upload(&d_vw, ewt) != cudaSuccess ||
-      pl->upload(&d_vdwoff, vdwoff) != cudaSuccess)
+      pl->upload(&d_vdwoff, vdwoff) != cudaSuccess || pl->upload(&d_vrep, vrep) != cudaSuccess ||
+      pl->upload(&d_vdist, vdist) != cudaSuccess)
     return fail(SAG_ENOMEM, "cudaMalloc tables");
+  P.vrep = d_vrep;
+  P.vdist = d_vdist;
   pl->h_umap = umap;  // for the checks of sag_plan_update_factors
   pl->h_ulist = ulist;
   P.ord = d_ord;
