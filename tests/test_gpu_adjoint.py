@@ -275,3 +275,25 @@ def test_tt_integrate_vjp_paper_shape_matches_oracle(prec):
         assert pl.sync_status() == sag.SAG_OK
     assert rel(gn.cpu().numpy(), gn_ref) < 10 * TOL[prec]
     assert rel(gH.cpu().numpy(), gH_ref) < 10 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_autograd_forward_after_training_apart_repeated_vectors(prec):
+    # The fitting workload starts from the Brownian factors, whose vectors
+    # repeat; a training step makes them differ. A plan made with
+    # keep_repeats = 1 from the starting factors follows the new factors (its
+    # forward against the oracle's); a default plan refuses them.
+    from paper_1905_09071_gb300 import autograd as sag_autograd
+    p = wl.adjoint_fit_problem(N=384)
+    D, N, ranks, dt = p["D"], p["N"], p["ranks"], p["dt"]
+    steps = 20
+    f1 = p["factors0"] * (1.0 + 1e-3 * np.random.default_rng(96).normal(size=p["factors0"].size))
+    n_ref, _ = oracle.integrate(p["n0"], D, ranks, f1, dt, steps, diag=False)
+    with sag.Plan(N, D, ranks, p["factors0"], prec=prec, keep_repeats=1) as pl:
+        nT = sag_autograd.integrate(torch.tensor(f1, device="cuda"), dev(p["n0"]), pl, dt, steps, 5)
+        torch.cuda.synchronize()
+        assert pl.sync_status() == sag.SAG_OK
+    assert rel(nT.cpu().numpy(), n_ref) < TOL[prec]
+    with sag.Plan(N, D, ranks, p["factors0"], prec=prec) as pl:
+        with pytest.raises(sag.SagError, match="keep_repeats"):
+            sag_autograd.integrate(torch.tensor(f1, device="cuda"), dev(p["n0"]), pl, dt, steps, 5)
